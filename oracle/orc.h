@@ -1,0 +1,124 @@
+/*
+ * orc.h -- the CPU oracle for the compressed control-step GEMV.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is the slow, obviously-correct
+ * statement of what the library computes.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load it; the library never
+ * links, includes or calls anything here, and nothing here calls the library.
+ *
+ * Everything is plain C99 with FP64 arithmetic wherever the format does not
+ * fix a narrower precision.  OpenMP (when compiled in) is used only on the
+ * outermost row / block-row loop, so every result is independent of the
+ * thread count.
+ *
+ * What it follows (paper: "GPU Acceleration of Real-Time Control Loops"):
+ *   - Sec. 4.3: A is stored in zfp's fixed-rate mode, i.e. every block of
+ *     values costs exactly the same number of bits (rate = bits per value);
+ *     the paper sweeps rate 8 (Table 2) and names zfp as the codec.  The
+ *     paper gives no block shape, transform or coder, so the "WZ1" layout
+ *     below is this project's reading of a zfp-style fixed-rate coder:
+ *     4x4 blocks, block-floating-point with a shared exponent, a reversible
+ *     integer lifting transform, sequency ordering, negabinary, and an
+ *     embedded bit-plane coder with group tests truncated to the budget.
+ *   - Sec. 4.4, dot-product equation: r_i = sum_j A(i,j) b_j, the GEMV.
+ *   - Sec. 4.4, sequential mixed-precision listing: FP32 products summed
+ *     into an FP64 accumulator, result stored as FP32 (orc_gemv_mp).
+ *   - Sec. 2.1, thermal update T_{k+1} = A T_k + B u_k: the carried state
+ *     s <- decay*s + y is its stand-in (orc_state_update).
+ */
+#ifndef WHFF_ORACLE_H
+#define WHFF_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Blob container (shared by every format). 64-byte little-endian header:
+ *   0  char[4]  magic "WZ1\0"
+ *   4  u32      version (1)
+ *   8  u32      fmt: 1 = zfp-style fixed rate, 2 = BF16, 3 = FP16, 4 = FP8 E4M3
+ *   12 u32      rate: bits per value (fmt 1), element bits otherwise
+ *   16 i64      M (rows)
+ *   24 i64      N (columns)
+ *   32 u64      stream bytes (everything after the header)
+ *   40 u32      CRC-32 (IEEE, reflected 0xEDB88320) of the stream
+ *   44 u32      CRC-32 of header bytes 0..43
+ *   48 u8[16]   zero
+ * followed by the stream at byte 64. */
+#define ORC_HEADER_BYTES 64
+#define ORC_FMT_ZFP 1
+#define ORC_FMT_BF16 2
+#define ORC_FMT_FP16 3
+#define ORC_FMT_FP8E4M3 4
+
+/* Error codes (same meaning as the library's, separate definitions). */
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ERANGE -2
+#define ORC_ENONFINITE -3
+#define ORC_EFORMAT -5
+
+uint32_t orc_crc32(const uint8_t* p, size_t n);
+
+/* ---- WZ1 building blocks (exposed so the tests can pin each step) ---- */
+/* forward lift of one 4-vector, in place: (x0,x1,x2,x3) -> (s,d,d0,e); mod 2^32 */
+void orc_fwd_lift4(int32_t v[4]);
+/* inverse lift, in place: (s,d,d0,e) -> (x0,x1,x2,x3); mod 2^32 */
+void orc_inv_lift4(int32_t v[4]);
+/* 2-D transforms on a row-major 4x4 block (forward: rows then columns) */
+void orc_fwd_xform(int32_t b[16]);
+void orc_inv_xform(int32_t b[16]);
+uint32_t orc_int2nb(int32_t c);
+int32_t orc_nb2int(uint32_t u);
+/* perm[k] = row-major index 4*i+j of the k-th coefficient in sequency order */
+void orc_sequency(int perm[16]);
+/* embedded plane coder on 16 negabinary words; writes exactly maxbits bits
+ * starting at bit `pos` of the LSB-first word array; returns bits actually
+ * emitted (<= maxbits; the caller's buffer is pre-zeroed) */
+int orc_encode_planes(const uint32_t u[16], int maxbits, uint64_t* words, int64_t pos);
+/* inverse: reads at most maxbits bits; untransmitted bits are zero */
+int orc_decode_planes(const uint64_t* words, int64_t pos, int maxbits, uint32_t u[16]);
+
+/* One 4x4 block, float input (already FP32).  `words` must hold 16*rate bits
+ * (rate/4 words) and is fully written.  Returns ORC_OK or ORC_ERANGE/ENONFINITE. */
+int orc_wz1_encode_block(const float a[16], int rate, uint64_t* words);
+/* Decode one block: q (row-major, after the inverse transform), emax, nonzero flag. */
+void orc_wz1_decode_block(const uint64_t* words, int rate, int32_t q[16], int* emax, int* nonzero);
+/* The decoded value of one element: (double)(float)q * 2^(emax-26); 0 for a zero block. */
+double orc_wz1_value(int32_t q, int emax, int nonzero);
+
+/* ---- whole matrices ---- */
+int orc_rate_ok(int rate);
+size_t orc_blob_size(int fmt, int rate, int64_t M, int64_t N);
+/* A: FP64 row-major M x N with leading dimension lda.  blob must hold orc_blob_size bytes. */
+int orc_encode(int fmt, int rate, const double* A, int64_t M, int64_t N, int64_t lda, uint8_t* blob, size_t cap);
+/* Parse and validate a blob header (magic, version, sizes, both CRCs). */
+int orc_parse(const uint8_t* blob, size_t len, int* fmt, int* rate, int64_t* M, int64_t* N);
+/* Decode rows [row0, row0+nrows) to FP64 (row-major, ldo); row0 % 4 == 0 for fmt 1. */
+int orc_decode_rows(const uint8_t* blob, size_t len, int64_t row0, int64_t nrows, double* out, int64_t ldo);
+
+/* ---- scaled formats (precision layer) ---- */
+/* round an FP64 value to the given format, ties to even, saturating to +-fmtmax;
+ * returns the rounded value as a double and its bit pattern in *bits */
+double orc_round_fmt(int fmt, double v, uint32_t* bits);
+double orc_fmt_max(int fmt);        /* FMTMAX used to size the per-tile scale */
+double orc_fmt_decode(int fmt, uint32_t bits);
+
+/* ---- GEMV ---- */
+/* Y[:,r] = Ahat * X[:,r], FP64, sequential j order (dot-product equation). X: N x R column-major. */
+void orc_gemv64(const double* A, int64_t M, int64_t N, int64_t lda, const double* X, int R, int64_t ldx,
+                double* Y, int64_t ldy);
+/* The paper's mixed-precision rule: float product, double sum, float result. */
+void orc_gemv_mp(const double* A, int64_t M, int64_t N, int64_t lda, const double* x, float* y);
+/* Carried state: for r = 0..R-1 in order, s <- decay*s + Y[:,r]. */
+void orc_state_update(double* s, int64_t M, const double* Y, int R, int64_t ldy, double decay);
+
+int orc_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
