@@ -1,0 +1,142 @@
+/*
+ * whff.h -- C ABI of the compressed-matrix control-step library (sm_103a).
+ *
+ * The library computes the deformation / thermal control step of the paper
+ * "GPU Acceleration of Real-Time Control Loops" (Sec. 2.1, deformation
+ * equation Delta_d = C_d * S_{k+1}; Sec. 4.4, dot-product equation
+ * r_i = sum_j A(i,j) b_j) on a matrix A that stays resident in GPU memory in a
+ * compressed form (Sec. 4.3: zfp fixed-rate mode, "every value costs BPV
+ * bits"), decoded on the fly inside the GEMV kernel and never written back.
+ *
+ * Conventions for every call:
+ *   - Return value: WHFF_OK (0) or a negative WHFF_E* code; the thread-local
+ *     message of the last failure is whff_last_error().
+ *   - "stream" is a cudaStream_t passed as void* (0 = the legacy default
+ *     stream).  Device calls are asynchronous on that stream; errors found on
+ *     the device are recorded in the handle's status word and returned by
+ *     whff_sync_status().
+ *   - Device pointers are plain CUDA device addresses owned by the caller;
+ *     the library never frees them.  Host pointers are plain host memory.
+ *   - No call falls back to the CPU: without a usable sm_103a device the
+ *     device calls fail with WHFF_ECUDA.
+ *
+ * Matrix layout on input: A is FP64, row-major, M x N, leading dimension lda
+ * (>= N).  Vectors: x is FP32 N x R column-major (leading dimension ldx >= N),
+ * y is FP64 M x R column-major (ldy >= M), the state s is FP64 of length M.
+ */
+#ifndef WHFF_H
+#define WHFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Storage formats.
+ *  WHFF_FMT_ZFP: zfp-style fixed rate (Sec. 4.3; Table 2 sweeps rate 8).  The
+ *    matrix is cut into 4x4 blocks (edge blocks replicate the last valid row,
+ *    then column); each block costs exactly 16*rate bits: a nonzero flag, an
+ *    8-bit biased block exponent, and the embedded bit-plane code (group
+ *    tests, sequency order, negabinary) of the reversible integer lift of its
+ *    26-bit fixed-point values, cut at the budget.  rate: 4..64, multiple of 4.
+ *  WHFF_FMT_BF16 / FP16 / FP8E4M3: element-wise storage with one FP32 scale
+ *    per 128x128 tile, scale = amax / FMTMAX (FMTMAX 1, 32768, 448); rate is
+ *    ignored on input.
+ */
+#define WHFF_FMT_ZFP 1
+#define WHFF_FMT_BF16 2
+#define WHFF_FMT_FP16 3
+#define WHFF_FMT_FP8E4M3 4
+
+#define WHFF_OK 0
+#define WHFF_EINVAL -1     /* bad argument (null, size, leading dimension, rate) */
+#define WHFF_ERANGE -2     /* |a| >= 2^127 after rounding to FP32 */
+#define WHFF_ENONFINITE -3 /* NaN or infinity in A */
+#define WHFF_ENOMEM -4     /* device allocation failed */
+#define WHFF_EFORMAT -5    /* blob header, size or CRC mismatch */
+#define WHFF_ECUDA -6      /* a CUDA runtime call failed */
+#define WHFF_ETIMEOUT -7   /* a bounded device-side wait gave up */
+#define WHFF_EBUSY -8      /* admission refused (serving layer) */
+
+#define WHFF_BLOB_HEADER_BYTES 64
+
+typedef struct whff_handle whff_handle;
+
+/* ------------------------------------------------------------------ host side */
+
+/* Bytes of the blob (64-byte header + stream) for a format, rate and shape;
+ * 0 if the combination is invalid.  WZ1 (fmt 1): 64 + ceil(M/4)*ceil(N/4)*2*rate.
+ * Scaled formats: 64 + M*roundup(N,16)*elem_bytes + ceil(M/128)*ceil(N/128)*4. */
+size_t whff_compressed_size(int fmt, int rate, int64_t M, int64_t N);
+
+/* Compress all of A (offline encoding, Sec. 4.3: "compression can be done
+ * offline") into out[0..out_cap).  On success *out_len = the blob size.
+ * Uses all host threads (nthreads <= 0) or the given number; the result is
+ * byte-identical for every thread count.  Errors: WHFF_EINVAL, WHFF_ERANGE,
+ * WHFF_ENONFINITE. */
+int whff_compress(const double* A, int64_t M, int64_t N, int64_t lda, int fmt, int rate, void* out, size_t out_cap,
+                  size_t* out_len, int nthreads);
+
+/* Band interface for matrices too large to hold in FP64 at once.
+ * whff_blob_init writes the header fields of an empty blob; whff_compress_band
+ * encodes rows [row0, row0+nrows) given as a band (row-major, lda) -- row0 and
+ * nrows must be multiples of 4 (WZ1) or 128 (scaled formats) except for the
+ * last band; whff_blob_seal computes both CRCs once every band is in. */
+int whff_blob_init(void* blob, size_t cap, int fmt, int rate, int64_t M, int64_t N);
+int whff_compress_band(void* blob, size_t cap, const double* band, int64_t row0, int64_t nrows, int64_t lda,
+                       int nthreads);
+int whff_blob_seal(void* blob, size_t cap);
+
+/* --------------------------------------------------------------- device side */
+
+/* Make A resident: validate the blob (magic, version, sizes, CRCs), copy its
+ * stream once to device memory on the current device, allocate the split-K
+ * workspace for up to max_rhs right-hand sides (0 -> 32) and pick the launch
+ * shape.  The handle owns every device allocation it makes; the host blob may
+ * be freed afterwards.  Errors: WHFF_EFORMAT, WHFF_ENOMEM, WHFF_ECUDA. */
+int whff_create(const void* blob, size_t len, int max_rhs, void* stream, whff_handle** h);
+
+/* Shape and footprint of a resident matrix (device_bytes = all device memory held). */
+int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, int64_t* N, size_t* device_bytes);
+
+/* One control step (Sec. 2.1 / Sec. 4.4): y[:,r] = Ahat * x[:,r] for r < R,
+ * Ahat = the decoded matrix (exactly whff_decompress's output).  Products and
+ * per-lane sums in FP32 (compensated), cross-warp and cross-CTA sums and y in
+ * FP64.  If state != NULL, afterwards for r = 0..R-1 in order:
+ * state <- decay*state + y[:,r] (FP64).  x, y, state: device pointers.
+ * Deterministic for a fixed (handle, R).  Errors: WHFF_EINVAL (R > max_rhs,
+ * bad ld), WHFF_ECUDA. */
+int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
+              double decay, void* stream);
+
+/* The same step on HOST buffers: copies x (N x R, ldx) host->device, runs
+ * whff_step into handle-owned device buffers, copies y (M x R, ldy) back, all
+ * asynchronously on the stream (pinned host memory makes the copies truly
+ * asynchronous).  state is a DEVICE pointer or NULL.  The caller synchronizes
+ * the stream before reading y. */
+int whff_step_host(whff_handle* h, const float* x_host, int R, int64_t ldx, double* y_host, int64_t ldy,
+                   double* state, double decay, void* stream);
+
+/* Decode the whole matrix to FP64 row-major (ldo >= N) on the device,
+ * bit-identical to the format's definition (WZ1: (double)(float)q * 2^(emax-26);
+ * scaled: scale * q).  Sec. 5.2 measures this as decompression throughput. */
+int whff_decompress(whff_handle* h, double* out, int64_t ldo, void* stream);
+
+/* Read and clear the handle's device status word (synchronizes the stream). */
+int whff_sync_status(whff_handle* h, void* stream);
+
+/* Free every device allocation of the handle (stream-ordered on its stream). */
+void whff_destroy(whff_handle* h);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* whff_last_error(void);
+
+/* Library version string, e.g. "whff 0.1 sm_103a". */
+const char* whff_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,25 @@
+"""Compressed-matrix control step on GB300 (sm_103a).
+
+A thin binding over the C ABI of ``libwhff.so`` (declared in include/whff.h):
+every step of the path runs in the library's CUDA kernels; this package only
+marshals arguments.  PyTorch supplies device memory and streams.  If the
+library is missing it is built from ``csrc/`` with nvcc; if that is not
+possible the import fails loudly -- there is no CPU fallback.
+"""
+from .whff import (  # noqa: F401
+    FMT_BF16,
+    FMT_FP8E4M3,
+    FMT_FP16,
+    FMT_ZFP,
+    Handle,
+    WhffError,
+    compressed_size,
+    library,
+    whff_compress,
+    whff_compress_bands,
+    whff_create,
+    whff_decompress,
+    whff_destroy,
+    whff_step,
+    whff_step_host,
+)

@@ -1,0 +1,319 @@
+// gemv_kernels.cuh -- the fused decode + GEMV kernels of the control step and
+// their FP64 epilogue (Sec. 4.4: FP32 products, FP64 reduction; Sec. 2.1:
+// carried state), plus the decode-only kernels (Sec. 5.2).
+//
+// Work split: one warp owns one 4-row band of A (one WZ1 block row, or four
+// rows of a scaled format) over a column range; lanes take consecutive 4x4
+// blocks (or 16-byte chunks), so a warp streams one contiguous run of the
+// compressed stream per iteration.  Each lane keeps compensated FP32 sums
+// (TwoSum: hi + lo) per row and right-hand side; the warp folds them in FP64
+// with shuffles.  With one column range per band the warp finishes y and the
+// state itself; with several (split-K, for wide matrices whose few rows
+// cannot fill the GPU -- the cuBLAS failure mode of Sec. 5.1) the FP64
+// partials go to a workspace and a second kernel sums them in split order.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <cstdint>
+
+#include "wz1_decode.cuh"
+
+namespace whff {
+namespace dev {
+
+constexpr int kWarpsPerCta = 8;
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p) {
+  const float s = hi + p;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (p - bp);
+  hi = s;
+  lo += err;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fold a lane's (hi, lo) sums for 4 rows x R columns and write either the
+// final y (+ state) or the split-K partial.  Deterministic: fixed shuffle tree.
+template <int R>
+__device__ __forceinline__ void finish_band(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
+                                            int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
+                                            double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                                            double decay) {
+  double tot[4][R];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int r = 0; r < R; ++r) tot[i][r] = warp_sum((double)hi[i][r] + (double)lo[i][r]);
+  // lane (i*R + r) writes value (i, r)
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (lane != i * R + r) continue;
+      const int64_t row = row0 + i;
+      if (ksplit > 1) {
+        ws[((int64_t)split * R + r) * Mpad + row] = tot[i][r];
+      } else if (row < M) {
+        y[(int64_t)r * ldy + row] = tot[i][r];
+      }
+    }
+  if (ksplit == 1 && state != nullptr && lane < 4) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (lane != i) continue;
+      const int64_t row = row0 + i;
+      if (row < M) {
+        double s = state[row];
+#pragma unroll
+        for (int r = 0; r < R; ++r) s = decay * s + tot[i][r];
+        state[row] = s;
+      }
+    }
+  }
+}
+
+// x[4J .. 4J+3] of column r, zero beyond N.
+__device__ __forceinline__ float4 load_x4(const float* __restrict__ x, int64_t ldx, int r, int64_t c0, int64_t N,
+                                          bool vec_ok) {
+  const float* p = x + (int64_t)r * ldx + c0;
+  if (vec_ok && c0 + 3 < N) return __ldg(reinterpret_cast<const float4*>(p));
+  float4 v;
+  v.x = c0 < N ? __ldg(p) : 0.f;
+  v.y = c0 + 1 < N ? __ldg(p + 1) : 0.f;
+  v.z = c0 + 2 < N ? __ldg(p + 2) : 0.f;
+  v.w = c0 + 3 < N ? __ldg(p + 3) : 0.f;
+  return v;
+}
+
+// --------------------------------------------------------------- WZ1 GEMV
+template <int NW32, int R>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+    wz1_gemv_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BM, int64_t BN,
+                    const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int ksplit, int64_t jchunk,
+                    double* __restrict__ ws, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                    double decay) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t I = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+  if (I >= BM) return;  // whole warp
+  const int split = blockIdx.y;
+  const int64_t J0 = (int64_t)split * jchunk;
+  const int64_t J1 = min(BN, J0 + jchunk);
+
+  float hi[4][R], lo[4][R];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
+
+  const int64_t rowblk = I * BN;
+  for (int64_t J = J0 + lane; J < J1; J += 32) {
+    uint32_t w[NW32 + 2];
+    load_block<NW32>(stream, rowblk + J, w);
+    int32_t q[16];
+    int emax;
+    const bool nz = decode_block<NW32>(w, q, emax);
+    if (!nz) continue;
+    const float scale = __int_as_float((emax - 26 + 127) << 23);  // 2^(emax-26), a normal float
+    float a[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = __int2float_rn(q[i]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float4 xv = load_x4(x, ldx, r, 4 * J, N, x_vec_ok);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float p = a[4 * i] * xv.x;
+        p = fmaf(a[4 * i + 1], xv.y, p);
+        p = fmaf(a[4 * i + 2], xv.z, p);
+        p = fmaf(a[4 * i + 3], xv.w, p);
+        two_sum_acc(hi[i][r], lo[i][r], p * scale);
+      }
+    }
+  }
+  finish_band<R>(hi, lo, lane, 4 * I, M, split, ksplit, 4 * BM, ws, y, ldy, state, decay);
+}
+
+// ------------------------------------------------------- scaled-format GEMV
+// Element decode: FMT 2 = BF16, 3 = FP16, 4 = FP8 E4M3.  A lane reads 16
+// bytes: V = 8 (16-bit) or 16 (8-bit) consecutive elements of one row.
+template <int FMT>
+struct ScaledTraits;
+template <>
+struct ScaledTraits<2> {
+  static constexpr int V = 8;
+  __device__ static __forceinline__ void decode(uint4 raw, float (&f)[8]) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f[2 * i] = __uint_as_float(w[i] << 16);
+      f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+  }
+};
+template <>
+struct ScaledTraits<3> {
+  static constexpr int V = 8;
+  __device__ static __forceinline__ void decode(uint4 raw, float (&f)[8]) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2_raw hr;
+      hr.x = (unsigned short)(w[i] & 0xFFFF);
+      hr.y = (unsigned short)(w[i] >> 16);
+      const float2 v = __half22float2(__half2(hr));
+      f[2 * i] = v.x;
+      f[2 * i + 1] = v.y;
+    }
+  }
+};
+template <>
+struct ScaledTraits<4> {
+  static constexpr int V = 16;
+  __device__ static __forceinline__ void decode(uint4 raw, float (&f)[16]) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] & 0xFFFF), __NV_E4M3);
+      const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
+      const float2 a = __half22float2(__half2(lo));
+      const float2 b = __half22float2(__half2(hi));
+      f[4 * i] = a.x;
+      f[4 * i + 1] = a.y;
+      f[4 * i + 2] = b.x;
+      f[4 * i + 3] = b.y;
+    }
+  }
+};
+
+template <int FMT, int R>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+    scaled_gemv_kernel(const uint8_t* __restrict__ payload, const float* __restrict__ scales, int64_t M, int64_t N,
+                       int64_t ld, int64_t TN, const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int ksplit,
+                       int64_t cchunk, double* __restrict__ ws, double* __restrict__ y, int64_t ldy,
+                       double* __restrict__ state, double decay) {
+  using T = ScaledTraits<FMT>;
+  constexpr int V = T::V;
+  constexpr int EB = FMT == 4 ? 1 : 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t band = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+  const int64_t row0 = 4 * band;
+  if (row0 >= M) return;
+  const int split = blockIdx.y;
+  const int64_t c_begin = (int64_t)split * cchunk;
+  const int64_t c_end = min(ld, c_begin + cchunk);
+
+  float hi[4][R], lo[4][R];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
+
+  for (int64_t c = c_begin + (int64_t)lane * V; c < c_end; c += 32 * V) {
+    float xv[R][V];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float* xp = x + (int64_t)r * ldx + c;
+      if (x_vec_ok && c + V <= N) {
+#pragma unroll
+        for (int v = 0; v < V; v += 4) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(xp + v));
+          xv[r][v] = t.x;
+          xv[r][v + 1] = t.y;
+          xv[r][v + 2] = t.z;
+          xv[r][v + 3] = t.w;
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) xv[r][v] = c + v < N ? __ldg(xp + v) : 0.f;
+      }
+    }
+    const int64_t tcol = c / 128;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t row = row0 + i;
+      if (row >= M) break;
+      const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(payload + ((uint64_t)row * ld + c) * EB));
+      float f[V];
+      T::decode(raw, f);
+      const float s = __ldg(scales + (row / 128) * TN + tcol);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float p = f[0] * xv[r][0];
+#pragma unroll
+        for (int v = 1; v < V; ++v) p = fmaf(f[v], xv[r][v], p);
+        two_sum_acc(hi[i][r], lo[i][r], p * s);
+      }
+    }
+  }
+  finish_band<R>(hi, lo, lane, row0, M, split, ksplit, 4 * ((M + 3) / 4), ws, y, ldy, state, decay);
+}
+
+// --------------------------------------------------- split-K epilogue (FP64)
+__global__ void splitk_epilogue_kernel(const double* __restrict__ ws, int ksplit, int R, int64_t Mpad, int64_t M,
+                                       double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                                       double decay) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= M) return;
+  double s = state ? state[row] : 0.0;
+  for (int r = 0; r < R; ++r) {
+    double t = 0.0;
+    for (int k = 0; k < ksplit; ++k) t += ws[((int64_t)k * R + r) * Mpad + row];
+    y[(int64_t)r * ldy + row] = t;
+    s = decay * s + t;
+  }
+  if (state) state[row] = s;
+}
+
+// ------------------------------------------------------------- decode only
+template <int NW32>
+__global__ void wz1_decompress_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BN,
+                                      int64_t nblocks, double* __restrict__ out, int64_t ldo) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblocks) return;
+  const int64_t I = b / BN, J = b - (b / BN) * BN;
+  uint32_t w[NW32 + 2];
+  load_block<NW32>(stream, b, w);
+  int32_t q[16];
+  int emax;
+  const bool nz = decode_block<NW32>(w, q, emax);
+  const double scale = nz ? ldexp(1.0, emax - 26) : 0.0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t row = 4 * I + r;
+    if (row >= M) break;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t col = 4 * J + c;
+      if (col < N) out[row * ldo + col] = (double)__int2float_rn(q[4 * r + c]) * scale;
+    }
+  }
+}
+
+template <int FMT>
+__global__ void scaled_decompress_kernel(const uint8_t* __restrict__ payload, const float* __restrict__ scales,
+                                         int64_t M, int64_t N, int64_t ld, int64_t TN, double* __restrict__ out,
+                                         int64_t ldo) {
+  using T = ScaledTraits<FMT>;
+  constexpr int V = T::V;
+  constexpr int EB = FMT == 4 ? 1 : 2;
+  const int64_t chunks_per_row = ld / V;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * chunks_per_row) return;
+  const int64_t row = t / chunks_per_row, c = (t - row * chunks_per_row) * V;
+  const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(payload + ((uint64_t)row * ld + c) * EB));
+  float f[V];
+  T::decode(raw, f);
+  const double s = (double)__ldg(scales + (row / 128) * TN + c / 128);
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+    if (c + v < N) out[row * ldo + c + v] = s * (double)f[v];
+}
+
+}  // namespace dev
+}  // namespace whff

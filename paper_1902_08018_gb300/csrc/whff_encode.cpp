@@ -1,0 +1,489 @@
+// whff_encode.cpp -- host side of the library: blob container, CRC-32 and the
+// offline encoders (Sec. 4.3: "compression can be done offline ... the
+// encoding part is completely out of the time budget").
+//
+// WZ1 is this project's reading of zfp's fixed-rate mode (Sec. 4.3, Table 2):
+// per 4x4 block, an FP32 block-floating-point quantiser with 26 fraction bits
+// below the block exponent, a reversible integer lift (rows, then columns),
+// sequency ordering, negabinary words and an embedded bit-plane coder with
+// group tests that stops exactly at 16*rate bits.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "whff.h"
+#include "whff_blob.h"
+
+namespace whff {
+void set_error(const std::string& msg);  // whff_runtime.cu
+
+// ------------------------------------------------------------------ container
+int elem_bytes(int fmt) {
+  switch (fmt) {
+    case WHFF_FMT_BF16:
+    case WHFF_FMT_FP16:
+      return 2;
+    case WHFF_FMT_FP8E4M3:
+      return 1;
+    default:
+      return 0;
+  }
+}
+
+bool rate_valid(int rate) { return rate >= 4 && rate <= 64 && (rate & 3) == 0; }
+
+uint64_t stream_size(int fmt, int rate, int64_t M, int64_t N) {
+  if (M <= 0 || N <= 0) return 0;
+  if (fmt == WHFF_FMT_ZFP) {
+    if (!rate_valid(rate)) return 0;
+    return (uint64_t)ceil_div(M, 4) * (uint64_t)ceil_div(N, 4) * (uint64_t)(2 * rate);
+  }
+  int eb = elem_bytes(fmt);
+  if (!eb) return 0;
+  return (uint64_t)M * (uint64_t)scaled_ld(N) * (uint64_t)eb +
+         (uint64_t)ceil_div(M, kScaleTile) * (uint64_t)ceil_div(N, kScaleTile) * 4u;
+}
+
+// Slicing-by-8 CRC-32 (IEEE, reflected 0xEDB88320).
+namespace {
+struct CrcTables {
+  uint32_t t[8][256];
+  CrcTables() {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t c = i;
+      for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+      t[0][i] = c;
+    }
+    for (uint32_t i = 0; i < 256; ++i)
+      for (int s = 1; s < 8; ++s) t[s][i] = (t[s - 1][i] >> 8) ^ t[0][t[s - 1][i] & 0xFF];
+  }
+};
+const CrcTables& crc_tables() {
+  static const CrcTables tabs;
+  return tabs;
+}
+inline void st32(uint8_t* p, uint32_t v) {
+  for (int i = 0; i < 4; ++i) p[i] = uint8_t(v >> (8 * i));
+}
+inline void st64(uint8_t* p, uint64_t v) {
+  for (int i = 0; i < 8; ++i) p[i] = uint8_t(v >> (8 * i));
+}
+inline uint32_t ld32(const uint8_t* p) {
+  uint32_t v = 0;
+  for (int i = 3; i >= 0; --i) v = (v << 8) | p[i];
+  return v;
+}
+inline uint64_t ld64(const uint8_t* p) {
+  uint64_t v = 0;
+  for (int i = 7; i >= 0; --i) v = (v << 8) | p[i];
+  return v;
+}
+}  // namespace
+
+uint32_t crc32_update(uint32_t crc, const uint8_t* p, size_t n) {
+  const auto& T = crc_tables().t;
+  uint32_t c = ~crc;
+  while (n >= 8) {
+    uint32_t lo = ld32(p) ^ c, hi = ld32(p + 4);
+    c = T[7][lo & 0xFF] ^ T[6][(lo >> 8) & 0xFF] ^ T[5][(lo >> 16) & 0xFF] ^ T[4][lo >> 24] ^ T[3][hi & 0xFF] ^
+        T[2][(hi >> 8) & 0xFF] ^ T[1][(hi >> 16) & 0xFF] ^ T[0][hi >> 24];
+    p += 8;
+    n -= 8;
+  }
+  while (n--) c = (c >> 8) ^ T[0][(c ^ *p++) & 0xFF];
+  return ~c;
+}
+
+void write_header(uint8_t* blob, int fmt, int rate, int64_t M, int64_t N, uint64_t sbytes, uint32_t crc_stream) {
+  std::memset(blob, 0, kHeaderBytes);
+  std::memcpy(blob, "WZ1\0", 4);
+  st32(blob + 4, 1);
+  st32(blob + 8, (uint32_t)fmt);
+  st32(blob + 12, (uint32_t)rate);
+  st64(blob + 16, (uint64_t)M);
+  st64(blob + 24, (uint64_t)N);
+  st64(blob + 32, sbytes);
+  st32(blob + 40, crc_stream);
+  st32(blob + 44, crc32(blob, 44));
+}
+
+int read_header(const uint8_t* blob, size_t len, BlobInfo* info, bool check_stream) {
+  if (!blob || len < (size_t)kHeaderBytes) return WHFF_EFORMAT;
+  if (std::memcmp(blob, "WZ1\0", 4) != 0 || ld32(blob + 4) != 1) return WHFF_EFORMAT;
+  if (ld32(blob + 44) != crc32(blob, 44)) return WHFF_EFORMAT;
+  BlobInfo b;
+  b.fmt = (int)ld32(blob + 8);
+  b.rate = (int)ld32(blob + 12);
+  b.M = (int64_t)ld64(blob + 16);
+  b.N = (int64_t)ld64(blob + 24);
+  b.stream_bytes = ld64(blob + 32);
+  b.crc_stream = ld32(blob + 40);
+  b.crc_header = ld32(blob + 44);
+  uint64_t want = stream_size(b.fmt, b.rate, b.M, b.N);
+  if (!want || want != b.stream_bytes || len < kHeaderBytes + want) return WHFF_EFORMAT;
+  if (b.fmt != WHFF_FMT_ZFP && b.rate != 8 * elem_bytes(b.fmt)) return WHFF_EFORMAT;
+  if (check_stream && crc32(blob + kHeaderBytes, want) != b.crc_stream) return WHFF_EFORMAT;
+  *info = b;
+  return WHFF_OK;
+}
+
+// ------------------------------------------------------------------ WZ1 coder
+namespace {
+
+// Sequency order of the 16 lift coefficients: slot ranks (0, 1, 2, 2) for
+// (s, d, d0, e); sort key (rank_i + rank_j, max rank, i, j).  kSeq[k] is the
+// row-major index 4*i + j of the k-th coefficient.
+struct SeqTable {
+  int idx[16];
+  SeqTable() {
+    const int rank[4] = {0, 1, 2, 2};
+    std::vector<int> v(16);
+    for (int k = 0; k < 16; ++k) v[k] = k;
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+      int ia = a >> 2, ja = a & 3, ib = b >> 2, jb = b & 3;
+      int sa = rank[ia] + rank[ja], sb = rank[ib] + rank[jb];
+      if (sa != sb) return sa < sb;
+      int ma = std::max(rank[ia], rank[ja]), mb = std::max(rank[ib], rank[jb]);
+      if (ma != mb) return ma < mb;
+      if (ia != ib) return ia < ib;
+      return ja < jb;
+    });
+    for (int k = 0; k < 16; ++k) idx[k] = v[k];
+  }
+};
+const SeqTable& seq_table() {
+  static const SeqTable t;
+  return t;
+}
+
+// Forward reversible lift of (a, b, c, d) -> (s, dd, d0, e), two's complement mod 2^32.
+inline void lift_fwd(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
+  auto half = [](uint32_t v) { return (uint32_t)((int32_t)v >> 1); };
+  uint32_t lo_diff = b - a;
+  uint32_t lo_mean = a + half(lo_diff);
+  uint32_t hi_diff = d - c;
+  uint32_t hi_mean = c + half(hi_diff);
+  uint32_t mean_diff = hi_mean - lo_mean;
+  a = lo_mean + half(mean_diff);  // s
+  b = mean_diff;                  // d
+  d = hi_diff - lo_diff;          // e
+  c = lo_diff;                    // d0
+}
+
+// LSB-first writer into a zeroed word array, one block at a time.
+struct BitSink {
+  uint64_t* w;
+  int pos = 0;
+  void put(uint64_t v, int n) {  // the low n (<= 32) bits of v
+    if (n <= 0) return;
+    v &= (n == 64) ? ~0ull : ((1ull << n) - 1);
+    int s = pos & 63;
+    w[pos >> 6] |= v << s;
+    if (s + n > 64) w[(pos >> 6) + 1] |= v >> (64 - s);
+    pos += n;
+  }
+};
+
+// FP32 exponent e with 2^(e-1) <= |f| < 2^e (f != 0), from the bit pattern.
+inline int f32_exponent(uint32_t bits) {
+  uint32_t E = (bits >> 23) & 0xFF;
+  if (E) return (int)E - 126;
+  uint32_t m = bits & 0x7FFFFF;
+  return (32 - __builtin_clz(m)) - 149;
+}
+
+// trunc(f * 2^(26 - emax)) from the FP32 bit pattern, by shifting the significand.
+inline int32_t f32_to_fixed(uint32_t bits, int emax) {
+  uint32_t E = (bits >> 23) & 0xFF;
+  uint32_t m = bits & 0x7FFFFF;
+  int sh;  // f = sig * 2^(sh0), q = sig * 2^(sh0 + 26 - emax)
+  uint32_t sig;
+  if (E) {
+    sig = m | 0x800000u;
+    sh = (int)E - 150 + kWz1Prec - emax;
+  } else {
+    sig = m;
+    sh = -149 + kWz1Prec - emax;
+  }
+  uint32_t mag = sh >= 0 ? (sig << sh) : (sh <= -32 ? 0u : (sig >> -sh));
+  return (bits >> 31) ? -(int32_t)mag : (int32_t)mag;
+}
+
+int encode_block(const float* vals, int rate, uint64_t* out) {
+  const int nw = rate / 4;
+  std::memset(out, 0, sizeof(uint64_t) * nw);
+  uint32_t bits[16];
+  int emax = INT32_MIN;
+  for (int i = 0; i < 16; ++i) {
+    std::memcpy(&bits[i], &vals[i], 4);
+    uint32_t E = (bits[i] >> 23) & 0xFF;
+    if (E == 0xFF) return WHFF_ENONFINITE;
+    if (E >= 254) return WHFF_ERANGE;  // |f| >= 2^127
+    if (bits[i] & 0x7FFFFFFFu) emax = std::max(emax, f32_exponent(bits[i]));
+  }
+  if (emax <= kWz1Emin) return WHFF_OK;  // zero block
+  uint32_t c[16];
+  for (int i = 0; i < 16; ++i) c[i] = (uint32_t)f32_to_fixed(bits[i], emax);
+  for (int r = 0; r < 4; ++r) lift_fwd(c[4 * r], c[4 * r + 1], c[4 * r + 2], c[4 * r + 3]);
+  for (int j = 0; j < 4; ++j) lift_fwd(c[j], c[4 + j], c[8 + j], c[12 + j]);
+  const int* seq = seq_table().idx;
+  uint32_t u[16];
+  for (int k = 0; k < 16; ++k) u[k] = (c[seq[k]] + 0xAAAAAAAAu) ^ 0xAAAAAAAAu;  // negabinary
+
+  BitSink bs{out};
+  bs.put(1, 1);
+  bs.put((uint64_t)(emax + 127), 8);
+  int budget = 16 * rate - 9;
+  int n = 0;
+  for (int k = 31; k >= 0 && budget > 0; --k) {
+    uint32_t plane = 0;
+    for (int i = 0; i < 16; ++i) plane |= ((u[i] >> k) & 1u) << i;
+    int m = std::min(n, budget);
+    bs.put(plane, m);
+    budget -= m;
+    uint32_t rest = plane >> n;  // bit 0 <-> coefficient n
+    while (n < 16 && budget > 0) {
+      if (!rest) {  // group test: nothing left in this plane
+        bs.put(0, 1);
+        --budget;
+        break;
+      }
+      bs.put(1, 1);
+      --budget;
+      int z = __builtin_ctz(rest);
+      int run = 15 - n;  // positions n..14 are sent, 15 is implied
+      if (z >= run) {
+        int e = std::min(run, budget);
+        bs.put(0, e);
+        budget -= e;
+        n = 16;  // (if the budget ran out the coder stops anyway)
+        break;
+      }
+      int e = std::min(z + 1, budget);
+      bs.put(1ull << z, e);
+      budget -= e;
+      if (e < z + 1) break;
+      n += z + 1;
+      rest >>= z + 1;
+    }
+  }
+  return WHFF_OK;
+}
+
+// --------------------------------------------------------- scaled formats
+struct FmtSpec {
+  int mant, emin, bias, ebits;
+  double fmtmax;
+};
+bool fmt_spec(int fmt, FmtSpec* s) {
+  switch (fmt) {
+    case WHFF_FMT_BF16: *s = {7, -126, 127, 8, 1.0}; return true;
+    case WHFF_FMT_FP16: *s = {10, -14, 15, 5, 32768.0}; return true;
+    case WHFF_FMT_FP8E4M3: *s = {3, -6, 7, 4, 448.0}; return true;
+    default: return false;
+  }
+}
+
+// Round a finite double to the format (ties to even, saturating at fmtmax) and
+// return the bit pattern, working on the double's integer significand.
+uint32_t round_to_format(double v, const FmtSpec& f) {
+  uint64_t db;
+  std::memcpy(&db, &v, 8);
+  uint32_t sign = (uint32_t)(db >> 63);
+  uint32_t sign_bit = sign << (f.mant + f.ebits);
+  int E = (int)((db >> 52) & 0x7FF);
+  uint64_t frac = db & ((1ull << 52) - 1);
+  // saturation pattern (fmtmax is a normal value of the format)
+  int sat_e;
+  double sat_m = std::frexp(f.fmtmax, &sat_e);  // fmtmax = sat_m * 2^sat_e
+  uint32_t sat_pat = ((uint32_t)(sat_e - 1 + f.bias) << f.mant) |
+                     (uint32_t)(std::ldexp(sat_m, f.mant + 1) - std::ldexp(1.0, f.mant));
+  if (E == 0) return sign_bit;  // zero or FP64 subnormal: far below every format's quantum
+  uint64_t sig = frac | (1ull << 52);
+  int ex = std::max(E - 1023, f.emin);           // exponent of the quantum's binade
+  int sh = 52 + ex - f.mant - (E - 1023);        // sig >> sh = value / quantum
+  uint64_t q;
+  if (sh >= 64) {
+    q = 0;
+  } else {
+    q = sig >> sh;
+    uint64_t rem = sig & ((1ull << sh) - 1);
+    uint64_t half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1))) ++q;
+  }
+  if (q == 0) return sign_bit;
+  if (q >> (f.mant + 1)) {  // rounding carried into the next binade
+    q >>= 1;
+    ++ex;
+  }
+  // compare against fmtmax: value = q * 2^(ex - mant)
+  if (std::ldexp((double)q, ex - f.mant) > f.fmtmax) return sign_bit | sat_pat;
+  if (q < (1ull << f.mant)) return sign_bit | (uint32_t)q;  // subnormal of the format
+  return sign_bit | ((uint32_t)(ex + f.bias) << f.mant) | (uint32_t)(q - (1ull << f.mant));
+}
+
+// -------------------------------------------------------------- band encoder
+template <class F>
+void parallel_for(int64_t n, int nthreads, F&& fn) {
+  if (nthreads <= 0) nthreads = (int)std::max(1u, std::thread::hardware_concurrency());
+  nthreads = (int)std::min<int64_t>(nthreads, std::max<int64_t>(1, n));
+  if (nthreads == 1) {
+    for (int64_t i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::atomic<int64_t> next{0};
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t)
+    pool.emplace_back([&] {
+      for (int64_t i; (i = next.fetch_add(1)) < n;) fn(i);
+    });
+  for (auto& th : pool) th.join();
+}
+
+int encode_band_zfp(uint8_t* stream, const BlobInfo& b, const double* band, int64_t row0, int64_t nrows,
+                    int64_t lda, int nthreads) {
+  const int64_t BN = ceil_div(b.N, 4);
+  const int nw = b.rate / 4;
+  const int64_t I0 = row0 / 4, I1 = ceil_div(row0 + nrows, 4);
+  std::atomic<int> err{WHFF_OK};
+  parallel_for(I1 - I0, nthreads, [&](int64_t ii) {
+    const int64_t I = I0 + ii;
+    float vals[16];
+    uint64_t w[16];
+    for (int64_t J = 0; J < BN; ++J) {
+      for (int r = 0; r < 4; ++r) {
+        int64_t gi = std::min(4 * I + r, b.M - 1);
+        if (gi >= row0 + nrows) gi = row0 + nrows - 1;  // only the matrix's last band is ragged
+        const double* row = band + (gi - row0) * lda;
+        for (int c = 0; c < 4; ++c) vals[4 * r + c] = (float)row[std::min(4 * J + c, b.N - 1)];
+      }
+      int e = encode_block(vals, b.rate, w);
+      if (e != WHFF_OK) err.store(e);
+      uint8_t* dst = stream + (uint64_t)(I * BN + J) * (uint64_t)(8 * nw);
+      for (int k = 0; k < nw; ++k) st64(dst + 8 * k, w[k]);
+    }
+  });
+  return err.load();
+}
+
+int encode_band_scaled(uint8_t* stream, const BlobInfo& b, const double* band, int64_t row0, int64_t nrows,
+                       int64_t lda, int nthreads) {
+  FmtSpec f;
+  fmt_spec(b.fmt, &f);
+  const int eb = elem_bytes(b.fmt);
+  const int64_t ld = scaled_ld(b.N), TN = ceil_div(b.N, kScaleTile);
+  uint8_t* scales = stream + (uint64_t)b.M * (uint64_t)ld * (uint64_t)eb;
+  const int64_t T0 = row0 / kScaleTile, T1 = ceil_div(row0 + nrows, kScaleTile);
+  std::atomic<int> err{WHFF_OK};
+  parallel_for((T1 - T0) * TN, nthreads, [&](int64_t t) {
+    const int64_t ti = T0 + t / TN, tj = t % TN;
+    const int64_t i0 = ti * kScaleTile, i1 = std::min(b.M, i0 + kScaleTile);
+    const int64_t j0 = tj * kScaleTile, j1 = std::min(b.N, j0 + kScaleTile);
+    double amax = 0.0;
+    for (int64_t i = i0; i < i1; ++i)
+      for (int64_t j = j0; j < j1; ++j) {
+        double a = band[(i - row0) * lda + j];
+        if (!std::isfinite(a)) {
+          err.store(WHFF_ENONFINITE);
+          return;
+        }
+        if (std::fabs(a) >= 0x1p127) {
+          err.store(WHFF_ERANGE);
+          return;
+        }
+        amax = std::max(amax, std::fabs(a));
+      }
+    float s = amax == 0.0 ? 1.0f : (float)(amax / f.fmtmax);
+    if (s == 0.0f) s = 1.0f;
+    uint32_t sb;
+    std::memcpy(&sb, &s, 4);
+    st32(scales + 4 * (uint64_t)(ti * TN + tj), sb);
+    for (int64_t i = i0; i < i1; ++i)
+      for (int64_t j = j0; j < j1; ++j) {
+        uint32_t pat = round_to_format(band[(i - row0) * lda + j] / (double)s, f);
+        uint8_t* p = stream + ((uint64_t)i * (uint64_t)ld + (uint64_t)j) * (uint64_t)eb;
+        p[0] = uint8_t(pat);
+        if (eb == 2) p[1] = uint8_t(pat >> 8);
+      }
+  });
+  return err.load();
+}
+
+}  // namespace
+}  // namespace whff
+
+using namespace whff;
+
+extern "C" size_t whff_compressed_size(int fmt, int rate, int64_t M, int64_t N) {
+  if (fmt != WHFF_FMT_ZFP) rate = 8 * elem_bytes(fmt);
+  uint64_t s = stream_size(fmt, rate, M, N);
+  return s ? (size_t)(kHeaderBytes + s) : 0;
+}
+
+extern "C" int whff_blob_init(void* blob, size_t cap, int fmt, int rate, int64_t M, int64_t N) {
+  if (fmt != WHFF_FMT_ZFP) rate = 8 * elem_bytes(fmt);
+  uint64_t s = stream_size(fmt, rate, M, N);
+  if (!blob || !s || cap < kHeaderBytes + s) {
+    set_error("whff_blob_init: invalid format, rate, shape or capacity");
+    return WHFF_EINVAL;
+  }
+  std::memset(blob, 0, kHeaderBytes + s);
+  write_header((uint8_t*)blob, fmt, rate, M, N, s, 0);
+  return WHFF_OK;
+}
+
+static int parse_unsealed(const void* blob, size_t cap, BlobInfo* b) {
+  // header CRC is valid from init on; the stream CRC is only valid after sealing
+  return read_header((const uint8_t*)blob, cap, b, false);
+}
+
+extern "C" int whff_compress_band(void* blob, size_t cap, const double* band, int64_t row0, int64_t nrows,
+                                  int64_t lda, int nthreads) {
+  BlobInfo b;
+  if (parse_unsealed(blob, cap, &b) != WHFF_OK) {
+    set_error("whff_compress_band: blob not initialised");
+    return WHFF_EFORMAT;
+  }
+  const int align = b.fmt == WHFF_FMT_ZFP ? 4 : kScaleTile;
+  if (!band || row0 < 0 || nrows <= 0 || row0 + nrows > b.M || lda < b.N || row0 % align ||
+      (nrows % align && row0 + nrows != b.M)) {
+    set_error("whff_compress_band: band must start on a block/tile row and cover whole blocks");
+    return WHFF_EINVAL;
+  }
+  uint8_t* stream = (uint8_t*)blob + kHeaderBytes;
+  int e = b.fmt == WHFF_FMT_ZFP ? encode_band_zfp(stream, b, band, row0, nrows, lda, nthreads)
+                                : encode_band_scaled(stream, b, band, row0, nrows, lda, nthreads);
+  if (e != WHFF_OK) set_error(e == WHFF_ERANGE ? "whff_compress: |a| >= 2^127" : "whff_compress: non-finite value");
+  return e;
+}
+
+extern "C" int whff_blob_seal(void* blob, size_t cap) {
+  BlobInfo b;
+  if (parse_unsealed(blob, cap, &b) != WHFF_OK) {
+    set_error("whff_blob_seal: blob not initialised");
+    return WHFF_EFORMAT;
+  }
+  uint8_t* p = (uint8_t*)blob;
+  write_header(p, b.fmt, b.rate, b.M, b.N, b.stream_bytes, crc32(p + kHeaderBytes, b.stream_bytes));
+  return WHFF_OK;
+}
+
+extern "C" int whff_compress(const double* A, int64_t M, int64_t N, int64_t lda, int fmt, int rate, void* out,
+                             size_t out_cap, size_t* out_len, int nthreads) {
+  if (!A || lda < N) {
+    set_error("whff_compress: null matrix or lda < N");
+    return WHFF_EINVAL;
+  }
+  int e = whff_blob_init(out, out_cap, fmt, rate, M, N);
+  if (e) return e;
+  e = whff_compress_band(out, out_cap, A, 0, M, lda, nthreads);
+  if (e) return e;
+  e = whff_blob_seal(out, out_cap);
+  if (e) return e;
+  if (out_len) *out_len = whff_compressed_size(fmt, rate, M, N);
+  return WHFF_OK;
+}

@@ -1,0 +1,234 @@
+"""ctypes binding of include/whff.h (argument marshalling only).
+
+Vectors use the row-per-right-hand-side convention of PyTorch: x is a CUDA
+float32 tensor of shape (N,) or (R, N) whose rows are the R right-hand sides
+(column-major N x R with ldx = x.stride(0) in the C ABI); y is float64 (M,)
+or (R, M); the state is float64 (M,).
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+from . import build as _build
+
+FMT_ZFP = 1
+FMT_BF16 = 2
+FMT_FP16 = 3
+FMT_FP8E4M3 = 4
+
+_ERRORS = {
+    -1: "WHFF_EINVAL",
+    -2: "WHFF_ERANGE",
+    -3: "WHFF_ENONFINITE",
+    -4: "WHFF_ENOMEM",
+    -5: "WHFF_EFORMAT",
+    -6: "WHFF_ECUDA",
+    -7: "WHFF_ETIMEOUT",
+    -8: "WHFF_EBUSY",
+}
+
+
+class WhffError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """Load libwhff.so, building it first if it is missing or stale."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    so = Path(_build.OUT)
+    if not _build.up_to_date():
+        _build.build()
+    L = ctypes.CDLL(str(so))
+    P, i64, c_int, sz, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t, ctypes.c_double
+    sigs = {
+        "whff_compressed_size": (sz, [c_int, c_int, i64, i64]),
+        "whff_compress": (c_int, [P, i64, i64, i64, c_int, c_int, P, sz, ctypes.POINTER(sz), c_int]),
+        "whff_blob_init": (c_int, [P, sz, c_int, c_int, i64, i64]),
+        "whff_compress_band": (c_int, [P, sz, P, i64, i64, i64, c_int]),
+        "whff_blob_seal": (c_int, [P, sz]),
+        "whff_create": (c_int, [P, sz, c_int, P, ctypes.POINTER(P)]),
+        "whff_info": (c_int, [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(i64),
+                              ctypes.POINTER(i64), ctypes.POINTER(sz)]),
+        "whff_step": (c_int, [P, P, c_int, i64, P, i64, P, dbl, P]),
+        "whff_step_host": (c_int, [P, P, c_int, i64, P, i64, P, dbl, P]),
+        "whff_decompress": (c_int, [P, P, i64, P]),
+        "whff_sync_status": (c_int, [P, P]),
+        "whff_destroy": (None, [P]),
+        "whff_last_error": (ctypes.c_char_p, []),
+        "whff_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != 0:
+        raise WhffError(code, library().whff_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def compressed_size(fmt: int, rate: int, M: int, N: int) -> int:
+    return int(library().whff_compressed_size(fmt, rate, M, N))
+
+
+def whff_compress(A: np.ndarray, fmt: int = FMT_ZFP, rate: int = 16, nthreads: int = 0) -> np.ndarray:
+    """Offline encode of an FP64 row-major matrix -> blob (uint8 array)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    M, N = A.shape
+    n = compressed_size(fmt, rate, M, N)
+    if n == 0:
+        raise WhffError(-1, "invalid format, rate or shape")
+    out = np.empty(n, dtype=np.uint8)
+    used = ctypes.c_size_t()
+    _check(library().whff_compress(A.ctypes.data, M, N, N, fmt, rate, out.ctypes.data, n, ctypes.byref(used),
+                                   nthreads))
+    return out
+
+
+def whff_compress_bands(M: int, N: int, bands, fmt: int = FMT_ZFP, rate: int = 16, nthreads: int = 0) -> np.ndarray:
+    """Encode a matrix given as an iterable of (row0, FP64 band) without holding all of it."""
+    L = library()
+    n = compressed_size(fmt, rate, M, N)
+    if n == 0:
+        raise WhffError(-1, "invalid format, rate or shape")
+    out = np.empty(n, dtype=np.uint8)
+    _check(L.whff_blob_init(out.ctypes.data, n, fmt, rate, M, N))
+    for row0, band in bands:
+        band = np.ascontiguousarray(band, dtype=np.float64)
+        _check(L.whff_compress_band(out.ctypes.data, n, band.ctypes.data, row0, band.shape[0], band.shape[1],
+                                    nthreads))
+    _check(L.whff_blob_seal(out.ctypes.data, n))
+    return out
+
+
+def _vec_args(t, rows: int, name: str, dtype):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype:
+        raise WhffError(-1, f"{name} must be a CUDA {dtype} tensor")
+    if t.dim() == 1:
+        if t.shape[0] < rows or t.stride(0) != 1:
+            raise WhffError(-1, f"{name}: need {rows} contiguous entries")
+        return t.data_ptr(), 1, rows
+    if t.dim() != 2 or t.stride(1) != 1 or t.shape[1] < rows:
+        raise WhffError(-1, f"{name}: shape (R, {rows}) with contiguous rows expected")
+    return t.data_ptr(), t.shape[0], t.stride(0)
+
+
+class Handle:
+    """A matrix resident on the GPU (owner of the device copy and workspace)."""
+
+    def __init__(self, ptr: int):
+        self._ptr = ctypes.c_void_p(ptr)
+        f, r, m, n, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        _check(library().whff_info(self._ptr, ctypes.byref(f), ctypes.byref(r), ctypes.byref(m), ctypes.byref(n),
+                                   ctypes.byref(b)))
+        self.fmt, self.rate, self.M, self.N, self.device_bytes = f.value, r.value, m.value, n.value, b.value
+
+    @property
+    def ptr(self):
+        return self._ptr
+
+    def step(self, x, y, state=None, decay: float = 0.99, stream=None):
+        whff_step(self, x, y, state, decay, stream)
+
+    def step_host(self, x_host: np.ndarray, y_host: np.ndarray, state=None, decay: float = 0.99, stream=None):
+        whff_step_host(self, x_host, y_host, state, decay, stream)
+
+    def decompress(self, out, stream=None):
+        whff_decompress(self, out, stream)
+
+    def sync_status(self, stream=None) -> int:
+        return int(library().whff_sync_status(self._ptr, _stream_ptr(stream)))
+
+    def destroy(self):
+        if self._ptr:
+            library().whff_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def whff_create(blob, max_rhs: int = 32, stream=None) -> Handle:
+    b = np.ascontiguousarray(np.frombuffer(blob, dtype=np.uint8) if isinstance(blob, (bytes, bytearray)) else blob,
+                             dtype=np.uint8)
+    h = ctypes.c_void_p()
+    _check(library().whff_create(b.ctypes.data, b.size, max_rhs, _stream_ptr(stream), ctypes.byref(h)))
+    return Handle(h.value)
+
+
+def whff_step(h: Handle, x, y, state=None, decay: float = 0.99, stream=None):
+    import torch
+
+    xp, R, ldx = _vec_args(x, h.N, "x", torch.float32)
+    yp, Ry, ldy = _vec_args(y, h.M, "y", torch.float64)
+    if Ry != R:
+        raise WhffError(-1, "x and y disagree on the number of right-hand sides")
+    sp = 0
+    if state is not None:
+        sp, Rs, _ = _vec_args(state, h.M, "state", torch.float64)
+        if Rs != 1:
+            raise WhffError(-1, "state must be a vector")
+    _check(library().whff_step(h.ptr, xp, R, ldx, yp, ldy, sp or None, float(decay), _stream_ptr(stream)))
+
+
+def whff_step_host(h: Handle, x_host: np.ndarray, y_host: np.ndarray, state=None, decay: float = 0.99, stream=None):
+    """x_host: float32 (N,) or (R, N); y_host: float64 (M,) or (R, M); both host (ideally pinned) arrays."""
+    import torch
+
+    xh = x_host if x_host.ndim == 2 else x_host.reshape(1, -1)
+    yh = y_host if y_host.ndim == 2 else y_host.reshape(1, -1)
+    if xh.dtype != np.float32 or yh.dtype != np.float64 or xh.strides[1] != 4 or yh.strides[1] != 8:
+        raise WhffError(-1, "x_host float32 and y_host float64 with contiguous rows expected")
+    sp = 0
+    if state is not None:
+        sp, _, _ = _vec_args(state, h.M, "state", torch.float64)
+    _check(library().whff_step_host(h.ptr, xh.ctypes.data, xh.shape[0], xh.strides[0] // 4, yh.ctypes.data,
+                                    yh.strides[0] // 8, sp or None, float(decay), _stream_ptr(stream)))
+
+
+def whff_decompress(h: Handle, out, stream=None):
+    import torch
+
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.float64 or out.dim() != 2:
+        raise WhffError(-1, "out must be a 2-D CUDA float64 tensor")
+    if out.shape[0] < h.M or out.shape[1] < h.N or out.stride(1) != 1:
+        raise WhffError(-1, "out too small or not row-contiguous")
+    _check(library().whff_decompress(h.ptr, out.data_ptr(), out.stride(0), _stream_ptr(stream)))
+
+
+def whff_destroy(h: Handle):
+    h.destroy()

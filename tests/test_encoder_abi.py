@@ -1,0 +1,104 @@
+"""CPU-only checks of the library: it loads, exports every symbol include/whff.h
+declares, and its host encoder (whff_compress, the offline step of Sec. 4.3)
+produces blobs byte-identical to the oracle's, for every format, for ragged
+shapes, for band-by-band encoding and for every thread count."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def W():
+    import paper_1902_08018_gb300 as W
+
+    W.library()
+    return W
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "whff.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(whff_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(W):
+    names = _declared_functions()
+    assert len(names) >= 12
+    L = W.library()
+    for n in names:
+        assert hasattr(L, n), n
+    assert L.whff_version().startswith(b"whff")
+
+
+def test_compressed_size_formula(W):
+    for M, N, rate in [(1, 1, 4), (4096, 4096, 16), (32768, 32768, 16), (7, 9, 12)]:
+        assert W.compressed_size(W.FMT_ZFP, rate, M, N) == 64 + -(-M // 4) * -(-N // 4) * 2 * rate
+    assert W.compressed_size(W.FMT_ZFP, 6, 8, 8) == 0  # rate not a multiple of 4
+    assert W.compressed_size(W.FMT_ZFP, 16, 0, 8) == 0
+    assert W.compressed_size(W.FMT_BF16, 0, 200, 150) == 64 + 200 * 160 * 2 + 2 * 2 * 4
+
+
+@pytest.mark.parametrize("fmt,rate", [(1, 4), (1, 8), (1, 12), (1, 16), (1, 24), (1, 36), (2, 0), (3, 0), (4, 0)])
+def test_encoder_byte_identical_to_oracle(W, orc, fmt, rate):
+    import workloads
+
+    rng = np.random.default_rng(40 + fmt * 100 + rate)
+    mats = [
+        workloads.KernelMatrix(130, 12, 130, 0.2, 7).dense()[:, :97],  # smooth, ragged
+        rng.standard_normal((33, 45)) * np.exp(rng.uniform(-30, 30, size=(33, 45))),  # wild dynamic range
+        np.zeros((9, 5)),
+        np.where(rng.random((20, 20)) < 0.7, 0.0, rng.standard_normal((20, 20)) * 1e-35),  # tiny / subnormal
+    ]
+    for A in mats:
+        r = rate if fmt == 1 else 16
+        lib = W.whff_compress(A, fmt, r, nthreads=3)
+        ref = np.frombuffer(orc.encode(A, fmt, r), dtype=np.uint8)
+        assert lib.size == ref.size
+        assert (lib == ref).all()
+
+
+def test_band_encoding_and_thread_count_invariance(W, orc):
+    import workloads
+
+    km = workloads.KernelMatrix(300, 18, 300, 0.1, 9)
+    A = km.dense()
+    ref = np.frombuffer(orc.encode(A, 1, 12), dtype=np.uint8)
+    for nt in (1, 2, 7):
+        assert (W.whff_compress(A, 1, 12, nthreads=nt) == ref).all()
+    bands = ((r0, A[r0:r0 + 64]) for r0 in range(0, 300, 64))
+    assert (W.whff_compress_bands(300, 300, bands, 1, 12) == ref).all()
+    ref2 = np.frombuffer(orc.encode(A, 3), dtype=np.uint8)
+    bands = ((r0, A[r0:r0 + 128]) for r0 in range(0, 300, 128))
+    assert (W.whff_compress_bands(300, 300, bands, 3) == ref2).all()
+
+
+def test_encoder_errors(W):
+    A = np.ones((8, 8))
+    A[3, 3] = np.inf
+    with pytest.raises(W.WhffError) as e:
+        W.whff_compress(A)
+    assert e.value.code == -3
+    A[3, 3] = 3e38
+    with pytest.raises(W.WhffError) as e:
+        W.whff_compress(A)
+    assert e.value.code == -2
+    with pytest.raises(W.WhffError):
+        W.whff_compress(np.ones((8, 8)), 1, 10)
+
+
+def test_create_rejects_corrupt_blob_without_gpu(W):
+    # header checks run before any CUDA call, so they are testable on the CPU
+    blob = W.whff_compress(np.ones((8, 8)), 1, 8).copy()
+    blob[70] ^= 1  # stream byte: CRC mismatch
+    with pytest.raises(W.WhffError) as e:
+        W.whff_create(blob, stream=0)
+    assert e.value.code == -5
+    blob = W.whff_compress(np.ones((8, 8)), 1, 8).copy()
+    blob[0] = ord("X")
+    with pytest.raises(W.WhffError) as e:
+        W.whff_create(blob, stream=0)
+    assert e.value.code == -5
