@@ -201,7 +201,7 @@ def parse(blob: bytes):
 
 def decode_rows(blob: bytes, row0: int, nrows: int) -> np.ndarray:
     b = np.frombuffer(blob, dtype=np.uint8)
-    _, _, M, N = parse(blob)
+    N = int.from_bytes(b[24:32].tobytes(), "little")
     out = np.zeros((nrows, N), dtype=np.float64)
     _check(lib().orc_decode_rows(_p(b), b.size, int(row0), int(nrows), _p(out), N), "decode_rows")
     return out

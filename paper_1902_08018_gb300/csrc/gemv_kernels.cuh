@@ -244,10 +244,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       const float s = __ldg(scales + (row / 128) * TN + tcol);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float p = f[0] * xv[r][0];
+        // groups of 4 products (as in a WZ1 block row), each folded into the
+        // compensated sum together with the exact rounding error of p * s
 #pragma unroll
-        for (int v = 1; v < V; ++v) p = fmaf(f[v], xv[r][v], p);
-        two_sum_acc(hi[i][r], lo[i][r], p * s);
+        for (int g = 0; g < V; g += 4) {
+          float p = f[g] * xv[r][g];
+          p = fmaf(f[g + 1], xv[r][g + 1], p);
+          p = fmaf(f[g + 2], xv[r][g + 2], p);
+          p = fmaf(f[g + 3], xv[r][g + 3], p);
+          const float ps = p * s;
+          two_sum_acc(hi[i][r], lo[i][r], ps);
+          lo[i][r] += fmaf(p, s, -ps);
+        }
       }
     }
   }
