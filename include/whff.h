@@ -130,6 +130,22 @@ int whff_sync_status(whff_handle* h, void* stream);
 /* Free every device allocation of the handle (stream-ordered on its stream). */
 void whff_destroy(whff_handle* h);
 
+/* A step that allocates nothing (the paper has no counterpart: this serves
+ * callers that cannot call cudaMalloc -- fixed-memory real-time controllers,
+ * code inside a private memory pool, loops that must not allocate).  The
+ * caller passes the WZ1 stream (the blob minus its 64-byte header, in row-major
+ * block order, in caller-owned device memory, 16-byte aligned; 8 for rate 12),
+ * its rate (8, 12 or 16) and shape, and x, y, state as in whff_step; R must be
+ * 1, 2, 4 or 8.  Split-K partials go to a file-scope device array of
+ * WHFF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * exit; a call whose partials would not fit returns WHFF_EINVAL.  The first
+ * call on each device looks up the array's device address (make it before any
+ * stream capture).  All calls share the array: calls that overlap on the GPU
+ * race and must be serialised by the caller.  Calls no cudaMalloc/cudaFree. */
+#define WHFF_NOALLOC_SCRATCH_BYTES (4u << 20)
+int whff_step_noalloc(const void* stream_dev, int rate, int64_t M, int64_t N, const float* x, int R, int64_t ldx,
+                      double* y, int64_t ldy, double* state, double decay, void* stream);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* whff_last_error(void);
 

@@ -22,4 +22,5 @@ from .whff import (  # noqa: F401
     whff_destroy,
     whff_step,
     whff_step_host,
+    whff_step_noalloc,
 )

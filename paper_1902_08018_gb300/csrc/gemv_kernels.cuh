@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
 }
 
 // --------------------------------------------------- split-K epilogue (FP64)
-__global__ void splitk_epilogue_kernel(const double* __restrict__ ws, int ksplit, int R, int64_t Mpad, int64_t M,
+static __global__ void splitk_epilogue_kernel(const double* __restrict__ ws, int ksplit, int R, int64_t Mpad, int64_t M,
                                        double* __restrict__ y, int64_t ldy, double* __restrict__ state,
                                        double decay) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

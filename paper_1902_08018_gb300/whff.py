@@ -64,6 +64,7 @@ def library() -> ctypes.CDLL:
         "whff_decompress": (c_int, [P, P, i64, P]),
         "whff_sync_status": (c_int, [P, P]),
         "whff_destroy": (None, [P]),
+        "whff_step_noalloc": (c_int, [P, c_int, i64, i64, P, c_int, i64, P, i64, P, dbl, P]),
         "whff_last_error": (ctypes.c_char_p, []),
         "whff_version": (ctypes.c_char_p, []),
     }
@@ -232,3 +233,21 @@ def whff_decompress(h: Handle, out, stream=None):
 
 def whff_destroy(h: Handle):
     h.destroy()
+
+
+def whff_step_noalloc(stream_dev, rate: int, M: int, N: int, x, y, state=None, decay: float = 0.99, stream=None):
+    """The allocation-free step: stream_dev is a CUDA uint8 tensor holding the WZ1 stream
+    (the blob without its 64-byte header) in caller-owned memory."""
+    import torch
+
+    if not isinstance(stream_dev, torch.Tensor) or not stream_dev.is_cuda or stream_dev.dtype != torch.uint8:
+        raise WhffError(-1, "stream_dev must be a CUDA uint8 tensor")
+    xp, R, ldx = _vec_args(x, N, "x", torch.float32)
+    yp, Ry, ldy = _vec_args(y, M, "y", torch.float64)
+    if Ry != R:
+        raise WhffError(-1, "x and y disagree on the number of right-hand sides")
+    sp = 0
+    if state is not None:
+        sp, _, _ = _vec_args(state, M, "state", torch.float64)
+    _check(library().whff_step_noalloc(stream_dev.data_ptr(), rate, M, N, xp, R, ldx, yp, ldy, sp or None,
+                                       float(decay), _stream_ptr(stream)))
