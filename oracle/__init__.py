@@ -27,6 +27,8 @@ FMT_ZFP = 1
 FMT_BF16 = 2
 FMT_FP16 = 3
 FMT_FP8E4M3 = 4
+FMT_FIXED_LIFT = 5
+FMT_FIXED_BFP = 6
 HEADER_BYTES = 64
 
 
@@ -80,6 +82,9 @@ def lib():
             "orc_gemv_mp": (None, [P, c_i64, c_i64, c_i64, P, P]),
             "orc_state_update": (None, [P, c_i64, P, c_int, c_i64, ctypes.c_double]),
             "orc_num_threads": (c_int, []),
+            "orc_wz2_width": (c_int, [c_int]),
+            "orc_wz2_encode_block": (c_int, [P, c_int, c_int, P]),
+            "orc_wz2_decode_block": (None, [P, c_int, c_int, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -172,6 +177,24 @@ def decode_block(words, rate: int):
     lib().orc_wz1_decode_block(_p(w), int(rate), _p(q), ctypes.byref(emax), ctypes.byref(nz))
     vals = np.array([lib().orc_wz1_value(int(x), emax.value, nz.value) for x in q], dtype=np.float64)
     return q.reshape(4, 4), emax.value, nz.value, vals.reshape(4, 4)
+
+
+def wz2_width(rate: int) -> int:
+    return int(lib().orc_wz2_width(int(rate)))
+
+
+def wz2_encode_block(a, rate: int, lift: bool) -> np.ndarray:
+    f = np.ascontiguousarray(a, dtype=np.float32).reshape(16)
+    w = np.zeros(rate // 4, dtype=np.uint64)
+    _check(lib().orc_wz2_encode_block(_p(f), int(rate), int(bool(lift)), _p(w)), "wz2_encode_block")
+    return w
+
+
+def wz2_decode_block(words, rate: int, lift: bool) -> np.ndarray:
+    w = np.ascontiguousarray(words, dtype=np.uint64)
+    out = np.zeros(16, dtype=np.float64)
+    lib().orc_wz2_decode_block(_p(w), int(rate), int(bool(lift)), _p(out))
+    return out.reshape(4, 4)
 
 
 # ---------------------------------------------------------- whole matrices

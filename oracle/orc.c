@@ -279,6 +279,102 @@ double orc_wz1_value(int32_t q, int emax, int nonzero) {
   return ldexp((double)f, emax - WZ1_PREC);
 }
 
+/* ------------------------------------------------------ WZ2 (fixed widths) */
+#define WZ2_PREC 24
+#define WZ2_KMAX 27
+
+static const int64_t F4[4][4] = {{1, 1, 1, 1}, {-2, -2, 2, 2}, {-4, 4, 0, 0}, {4, -4, -4, 4}};
+static const int64_t G2[4][4] = {{2, -1, -1, 0}, {2, -1, 1, 0}, {2, 1, -1, -1}, {2, 1, 1, 1}};
+
+int orc_wz2_width(int rate) { return (16 * rate - 13) / 16; }
+
+static void put_bits(uint64_t* w, int64_t pos, uint64_t v, int n) {
+  for (int b = 0; b < n; b++) put_bit(w, pos + b, (unsigned)((v >> b) & 1u));
+}
+static uint64_t get_bits(const uint64_t* w, int64_t pos, int n) {
+  uint64_t v = 0;
+  for (int b = 0; b < n; b++) v |= (uint64_t)get_bit(w, pos + b) << b;
+  return v;
+}
+
+/* C = L B L^T for 4x4 integer matrices (plain triple loops). */
+static void sandwich(const int64_t L[4][4], const int64_t B[16], int64_t C[16]) {
+  int64_t T[16];
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) {
+      int64_t t = 0;
+      for (int k = 0; k < 4; k++) t += L[i][k] * B[4 * k + j];
+      T[4 * i + j] = t;
+    }
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) {
+      int64_t t = 0;
+      for (int k = 0; k < 4; k++) t += T[4 * i + k] * L[j][k];
+      C[4 * i + j] = t;
+    }
+}
+
+int orc_wz2_encode_block(const float a[16], int rate, int lift, uint64_t* words) {
+  int nwords = rate / 4;
+  for (int w = 0; w < nwords; w++) words[w] = 0;
+  int emax = WZ1_EMIN - 1000;
+  for (int i = 0; i < 16; i++) {
+    if (!isfinite(a[i])) return ORC_ENONFINITE;
+    if (fabs((double)a[i]) >= ldexp(1.0, 127)) return ORC_ERANGE;
+    if (a[i] != 0.0f) {
+      int e;
+      frexp((double)a[i], &e);
+      if (e > emax) emax = e;
+    }
+  }
+  if (emax <= WZ1_EMIN) return ORC_OK; /* zero block: all bits zero */
+  int64_t q[16], c[16], seq[16];
+  for (int i = 0; i < 16; i++) q[i] = (int64_t)trunc(ldexp((double)a[i], WZ2_PREC - emax));
+  if (lift)
+    sandwich(F4, q, c);
+  else
+    for (int i = 0; i < 16; i++) c[i] = q[i];
+  int perm[16];
+  orc_sequency(perm);
+  for (int k = 0; k < 16; k++) seq[k] = lift ? c[perm[k]] : c[k];
+  const int W = orc_wz2_width(rate);
+  const double lo = -ldexp(1.0, W - 1), hi = ldexp(1.0, W - 1) - 1.0;
+  int K = 0;
+  double v[16];
+  for (K = 0; K <= WZ2_KMAX; K++) {
+    int fits = 1;
+    for (int k = 0; k < 16; k++) {
+      v[k] = nearbyint(ldexp((double)seq[k], -K)); /* round half to even */
+      if (v[k] < lo || v[k] > hi) fits = 0;
+    }
+    if (fits) break;
+  }
+  put_bits(words, 0, (uint64_t)(emax + 127), 8);
+  put_bits(words, 8, (uint64_t)K, 5);
+  for (int k = 0; k < 16; k++) put_bits(words, 13 + (int64_t)W * k, (uint64_t)(int64_t)(v[k] - lo), W);
+  return ORC_OK;
+}
+
+void orc_wz2_decode_block(const uint64_t* words, int rate, int lift, double out[16]) {
+  int E = (int)get_bits(words, 0, 8);
+  for (int i = 0; i < 16; i++) out[i] = 0.0;
+  if (E == 0) return;
+  int emax = E - 127;
+  int K = (int)get_bits(words, 8, 5);
+  const int W = orc_wz2_width(rate);
+  int64_t v[16], V[16], T[16];
+  for (int k = 0; k < 16; k++) v[k] = (int64_t)get_bits(words, 13 + (int64_t)W * k, W) - ((int64_t)1 << (W - 1));
+  int perm[16];
+  orc_sequency(perm);
+  for (int k = 0; k < 16; k++) V[lift ? perm[k] : k] = v[k];
+  if (lift) {
+    sandwich(G2, V, T);
+    for (int i = 0; i < 16; i++) out[i] = ldexp((double)T[i], K + emax - 30);
+  } else {
+    for (int i = 0; i < 16; i++) out[i] = ldexp((double)V[i], K + emax - WZ2_PREC);
+  }
+}
+
 /* --------------------------------------------------------- scaled formats */
 /* Per 128x128 tile b: amax = max |a| (FP64); s = RN_fp32(amax / FMTMAX),
  * s = 1 when amax = 0; q = RN_fmt(a / s) with the quotient in FP64 and
@@ -359,13 +455,15 @@ double orc_fmt_decode(int fmt, uint32_t bits) {
 
 /* ------------------------------------------------------------------- blobs */
 int orc_rate_ok(int rate) { return rate >= 4 && rate <= 64 && rate % 4 == 0; }
+static int wz2_rate_ok(int rate) { return rate >= 8 && rate <= 24 && rate % 4 == 0; }
+static int is_wz2(int fmt) { return fmt == ORC_FMT_FIXED_LIFT || fmt == ORC_FMT_FIXED_BFP; }
 
 static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 static int64_t scaled_ld(int64_t N) { return cdiv(N, 16) * 16; }
 
 static size_t stream_bytes(int fmt, int rate, int64_t M, int64_t N) {
-  if (fmt == ORC_FMT_ZFP) return (size_t)(cdiv(M, 4) * cdiv(N, 4)) * (size_t)(2 * rate);
+  if (fmt == ORC_FMT_ZFP || is_wz2(fmt)) return (size_t)(cdiv(M, 4) * cdiv(N, 4)) * (size_t)(2 * rate);
   fmtdesc d;
   if (!fmt_desc(fmt, &d)) return 0;
   size_t payload = (size_t)M * (size_t)scaled_ld(N) * (size_t)d.bytes;
@@ -376,6 +474,7 @@ static size_t stream_bytes(int fmt, int rate, int64_t M, int64_t N) {
 size_t orc_blob_size(int fmt, int rate, int64_t M, int64_t N) {
   if (M <= 0 || N <= 0) return 0;
   if (fmt == ORC_FMT_ZFP && !orc_rate_ok(rate)) return 0;
+  if (is_wz2(fmt) && !wz2_rate_ok(rate)) return 0;
   size_t s = stream_bytes(fmt, rate, M, N);
   return s ? ORC_HEADER_BYTES + s : 0;
 }
@@ -413,7 +512,7 @@ static void write_header(uint8_t* blob, int fmt, int rate, int64_t M, int64_t N,
   wr32(blob + 44, orc_crc32(blob, 44));
 }
 
-static int encode_zfp(int rate, const double* A, int64_t M, int64_t N, int64_t lda, uint8_t* stream) {
+static int encode_zfp(int fmt, int rate, const double* A, int64_t M, int64_t N, int64_t lda, uint8_t* stream) {
   int64_t BM = cdiv(M, 4), BN = cdiv(N, 4);
   int nwords = rate / 4;
   int err = ORC_OK;
@@ -430,7 +529,8 @@ static int encode_zfp(int rate, const double* A, int64_t M, int64_t N, int64_t l
           if (gj > N - 1) gj = N - 1;
           a[4 * r + c] = (float)A[gi * lda + gj]; /* FP64 -> FP32, round to nearest even */
         }
-      int e = orc_wz1_encode_block(a, rate, w);
+      int e = fmt == ORC_FMT_ZFP ? orc_wz1_encode_block(a, rate, w)
+                                 : orc_wz2_encode_block(a, rate, fmt == ORC_FMT_FIXED_LIFT, w);
       if (e != ORC_OK) {
 #pragma omp critical
         err = e;
@@ -492,8 +592,8 @@ int orc_encode(int fmt, int rate, const double* A, int64_t M, int64_t N, int64_t
   uint8_t* stream = blob + ORC_HEADER_BYTES;
   memset(stream, 0, sbytes);
   int err;
-  if (fmt == ORC_FMT_ZFP)
-    err = encode_zfp(rate, A, M, N, lda, stream);
+  if (fmt == ORC_FMT_ZFP || is_wz2(fmt))
+    err = encode_zfp(fmt, rate, A, M, N, lda, stream);
   else {
     fmtdesc d;
     if (!fmt_desc(fmt, &d)) return ORC_EINVAL;
@@ -536,7 +636,7 @@ int orc_decode_rows(const uint8_t* blob, size_t len, int64_t row0, int64_t nrows
   if (e) return e;
   if (row0 < 0 || nrows < 0 || row0 + nrows > M || ldo < N) return ORC_EINVAL;
   const uint8_t* stream = blob + ORC_HEADER_BYTES;
-  if (fmt == ORC_FMT_ZFP) {
+  if (fmt == ORC_FMT_ZFP || is_wz2(fmt)) {
     if (row0 % 4) return ORC_EINVAL;
     int64_t BN = cdiv(N, 4);
     int nwords = rate / 4;
@@ -547,14 +647,20 @@ int orc_decode_rows(const uint8_t* blob, size_t len, int64_t row0, int64_t nrows
       for (int64_t J = 0; J < BN; J++) {
         const uint8_t* src = stream + (size_t)(I * BN + J) * (size_t)(8 * nwords);
         for (int k = 0; k < nwords; k++) w[k] = rd64(src + 8 * k);
-        int32_t q[16];
-        int emax, nz;
-        orc_wz1_decode_block(w, rate, q, &emax, &nz);
+        double v[16];
+        if (fmt == ORC_FMT_ZFP) {
+          int32_t q[16];
+          int emax, nz;
+          orc_wz1_decode_block(w, rate, q, &emax, &nz);
+          for (int i = 0; i < 16; i++) v[i] = orc_wz1_value(q[i], emax, nz);
+        } else {
+          orc_wz2_decode_block(w, rate, fmt == ORC_FMT_FIXED_LIFT, v);
+        }
         for (int r = 0; r < 4; r++)
           for (int c = 0; c < 4; c++) {
             int64_t gi = 4 * I + r, gj = 4 * J + c;
             if (gi >= row0 + nrows || gj >= N) continue;
-            out[(gi - row0) * ldo + gj] = orc_wz1_value(q[4 * r + c], emax, nz);
+            out[(gi - row0) * ldo + gj] = v[4 * r + c];
           }
       }
     }

@@ -53,6 +53,8 @@ extern "C" {
 #define ORC_FMT_BF16 2
 #define ORC_FMT_FP16 3
 #define ORC_FMT_FP8E4M3 4
+#define ORC_FMT_FIXED_LIFT 5 /* WZ2: fixed-width fields of the linear lift's coefficients */
+#define ORC_FMT_FIXED_BFP 6  /* WZ2 without transform: fixed-width block floating point */
 
 /* Error codes (same meaning as the library's, separate definitions). */
 #define ORC_OK 0
@@ -89,6 +91,22 @@ int orc_wz1_encode_block(const float a[16], int rate, uint64_t* words);
 void orc_wz1_decode_block(const uint64_t* words, int rate, int32_t q[16], int* emax, int* nonzero);
 /* The decoded value of one element: (double)(float)q * 2^(emax-26); 0 for a zero block. */
 double orc_wz1_value(int32_t q, int emax, int nonzero);
+
+/* ---- WZ2: fixed-allocation variant (rates 8..24, multiple of 4) ----
+ * Same 4x4 blocks, FP32 rounding and block exponent as WZ1, 24 fraction bits
+ * (q = trunc(a * 2^(24-emax))).  lift = 1: C = (4F) Q (4F)^T with the lift in
+ * exact linear form, 4F rows (1,1,1,1), (-2,-2,2,2), (-4,4,0,0), (4,-4,-4,4),
+ * coefficients in sequency order; lift = 0: C = Q in row-major order.  One
+ * shift K per block (the smallest in 0..27 with every round-half-even
+ * C/2^K inside W-bit two's complement), W = floor((16*rate - 13)/16).
+ * Header: 8 bits emax+127 (0 = zero block), 5 bits K; then 16 offset-binary
+ * fields v + 2^(W-1), W bits each, LSB-first from bit 13; the rest zero.
+ * Decoded value (exact in FP64): lift: (2G) V (2G)^T * 2^(K+emax-30) with 2G
+ * rows (2,-1,-1,0), (2,-1,1,0), (2,1,-1,-1), (2,1,1,1) = 8 (4F)^-1;
+ * no lift: V * 2^(K+emax-24). */
+int orc_wz2_width(int rate);
+int orc_wz2_encode_block(const float a[16], int rate, int lift, uint64_t* words);
+void orc_wz2_decode_block(const uint64_t* words, int rate, int lift, double out[16]);
 
 /* ---- whole matrices ---- */
 int orc_rate_ok(int rate);
