@@ -49,6 +49,16 @@ extern "C" {
 #define WHFF_FMT_BF16 2
 #define WHFF_FMT_FP16 3
 #define WHFF_FMT_FP8E4M3 4
+/*  WHFF_FMT_FIXED_LIFT / WHFF_FMT_FIXED_BFP ("WZ2"): the GPU-friendly
+ *    fixed-allocation variant that Sec. 5.2 and Sec. 6 call for.  Same 4x4
+ *    blocks, FP32 rounding and block exponent; 24 fraction bits; FIXED_LIFT
+ *    takes the lift in exact linear form (coefficients C = (4F) Q (4F)^T in
+ *    sequency order), FIXED_BFP no transform.  Each block stores emax+127
+ *    (8 bits, 0 = zero block), one shift K (5 bits, the smallest in 0..27 that
+ *    fits) and 16 offset-binary fields of W = floor((16*rate-13)/16) bits of
+ *    round-half-even(C / 2^K).  rate: 8..24, multiple of 4. */
+#define WHFF_FMT_FIXED_LIFT 5
+#define WHFF_FMT_FIXED_BFP 6
 
 #define WHFF_OK 0
 #define WHFF_EINVAL -1     /* bad argument (null, size, leading dimension, rate) */
@@ -101,6 +111,11 @@ int whff_create(const void* blob, size_t len, int max_rhs, void* stream, whff_ha
 /* Shape and footprint of a resident matrix (device_bytes = all device memory held). */
 int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, int64_t* N, size_t* device_bytes);
 
+/* Launch plan of a resident matrix: *ksplit = column splits per 4-row band
+ * (1 for matrices with enough rows to fill the GPU), *launches = kernel
+ * launches of one whff_step pass (1, or 2 with the split-K epilogue). */
+int whff_plan(const whff_handle* h, int* ksplit, int* launches);
+
 /* One control step (Sec. 2.1 / Sec. 4.4): y[:,r] = Ahat * x[:,r] for r < R,
  * Ahat = the decoded matrix (exactly whff_decompress's output).  Products and
  * per-lane sums in FP32 (compensated), cross-warp and cross-CTA sums and y in
@@ -118,6 +133,52 @@ int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, double* y, int
  * the stream before reading y. */
 int whff_step_host(whff_handle* h, const float* x_host, int R, int64_t ldx, double* y_host, int64_t ldy,
                    double* state, double decay, void* stream);
+
+/* ----------------------------------------------------- graph-captured steps */
+/* A control step captured once as a CUDA graph and replayed every period
+ * (the firm real-time loop of Sec. 1: one GEMV per millisecond, corrections
+ * within 50 ms).  whff_graph_create captures whff_step on fixed device
+ * buffers (x, y, state as in whff_step; the caller rewrites x between
+ * replays).  whff_graph_create_host captures, in order, the copy of x_host
+ * (N x R, ldx, pinned host memory) to a graph-owned device buffer, the step,
+ * and the copy of y back to y_host (M x R, ldy, pinned); state is a device
+ * pointer or NULL.  The stream is used only to capture (a temporary stream is
+ * used when it is 0); whff_graph_launch replays on any stream.  The graph owns
+ * its device buffers; the handle must outlive it.  Errors: WHFF_EINVAL,
+ * WHFF_ENOMEM, WHFF_ECUDA. */
+typedef struct whff_graph whff_graph;
+int whff_graph_create(whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
+                      double decay, void* stream, whff_graph** g);
+int whff_graph_create_host(whff_handle* h, const float* x_host, int R, int64_t ldx, double* y_host, int64_t ldy,
+                           double* state, double decay, void* stream, whff_graph** g);
+int whff_graph_launch(whff_graph* g, void* stream);
+void whff_graph_destroy(whff_graph* g);
+
+/* ------------------------------------------------------------- serving layer */
+/* A request server over resident models (Sec. 1: a firm real-time loop that
+ * tolerates a missed deadline).  Requests that arrive while a model's
+ * previous pass is on the GPU are queued and folded into its next pass as
+ * extra right-hand sides (continuous batching, batch buckets 1, 2, 4, ...,
+ * max_batch), each bucket a captured CUDA graph (H2D x, step, D2H y); the
+ * columns of a pass are applied in arrival order, so the carried state and
+ * every y are the same as for one-at-a-time service.  Different models run
+ * concurrently on nstreams streams.  Models are admitted while the sum of
+ * their device footprints (matrix, workspace, state, staging) stays within
+ * hbm_budget bytes; otherwise whff_server_add_model returns WHFF_EBUSY.  The
+ * server does not own the handles (destroy it before them). */
+typedef struct whff_server whff_server;
+int whff_server_create(size_t hbm_budget, int max_batch, int nstreams, whff_server** s);
+int whff_server_add_model(whff_server* s, whff_handle* h, double decay, int* model_id);
+int whff_server_reset_state(whff_server* s, int model_id);
+int whff_server_read_state(whff_server* s, int model_id, double* host_out);
+/* Replay a trace in real time: request i for model[i] arrives arrival_s[i]
+ * seconds after the start (non-decreasing) with x[i] (N floats, host).  On
+ * return latency_s[i] = completion - arrival as seen by the host, batch[i] =
+ * requests in its pass, and y[i] (if y and y[i] are not NULL) holds its M
+ * doubles.  WHFF_ETIMEOUT if the run exceeds max_wait_s with requests open. */
+int whff_server_run(whff_server* s, int n, const int* model, const double* arrival_s, const float* const* x,
+                    double* const* y, double* latency_s, int* batch, double max_wait_s);
+void whff_server_destroy(whff_server* s);
 
 /* Decode the whole matrix to FP64 row-major (ldo >= N) on the device,
  * bit-identical to the format's definition (WZ1: (double)(float)q * 2^(emax-26);

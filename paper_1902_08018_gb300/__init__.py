@@ -8,10 +8,14 @@ possible the import fails loudly -- there is no CPU fallback.
 """
 from .whff import (  # noqa: F401
     FMT_BF16,
+    FMT_FIXED_BFP,
+    FMT_FIXED_LIFT,
     FMT_FP8E4M3,
     FMT_FP16,
     FMT_ZFP,
+    Graph,
     Handle,
+    Server,
     WhffError,
     compressed_size,
     library,
@@ -20,6 +24,8 @@ from .whff import (  # noqa: F401
     whff_create,
     whff_decompress,
     whff_destroy,
+    whff_graph_create,
+    whff_graph_create_host,
     whff_step,
     whff_step_host,
     whff_step_noalloc,

@@ -33,7 +33,9 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t scaled_ld(int64_t N) { return ceil_div(N, 16) * 16; }
 
 int elem_bytes(int fmt);  // 2, 2, 1 for BF16, FP16, FP8; 0 otherwise
-bool rate_valid(int rate);
+bool rate_valid(int rate);       // WZ1: 4..64, multiple of 4
+bool wz2_rate_valid(int rate);   // WZ2: 8..24, multiple of 4
+bool is_blocked(int fmt);        // 4x4-block formats (WZ1, WZ2)
 uint64_t stream_size(int fmt, int rate, int64_t M, int64_t N);  // 0 if invalid
 uint32_t crc32_update(uint32_t crc, const uint8_t* p, size_t n);  // crc = 0 to start
 inline uint32_t crc32(const uint8_t* p, size_t n) { return crc32_update(0, p, n); }

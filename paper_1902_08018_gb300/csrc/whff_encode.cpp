@@ -35,11 +35,13 @@ int elem_bytes(int fmt) {
 }
 
 bool rate_valid(int rate) { return rate >= 4 && rate <= 64 && (rate & 3) == 0; }
+bool wz2_rate_valid(int rate) { return rate >= 8 && rate <= 24 && (rate & 3) == 0; }
+bool is_blocked(int fmt) { return fmt == WHFF_FMT_ZFP || fmt == WHFF_FMT_FIXED_LIFT || fmt == WHFF_FMT_FIXED_BFP; }
 
 uint64_t stream_size(int fmt, int rate, int64_t M, int64_t N) {
   if (M <= 0 || N <= 0) return 0;
-  if (fmt == WHFF_FMT_ZFP) {
-    if (!rate_valid(rate)) return 0;
+  if (is_blocked(fmt)) {
+    if (fmt == WHFF_FMT_ZFP ? !rate_valid(rate) : !wz2_rate_valid(rate)) return 0;
     return (uint64_t)ceil_div(M, 4) * (uint64_t)ceil_div(N, 4) * (uint64_t)(2 * rate);
   }
   int eb = elem_bytes(fmt);
@@ -125,7 +127,7 @@ int read_header(const uint8_t* blob, size_t len, BlobInfo* info, bool check_stre
   b.crc_header = ld32(blob + 44);
   uint64_t want = stream_size(b.fmt, b.rate, b.M, b.N);
   if (!want || want != b.stream_bytes || len < kHeaderBytes + want) return WHFF_EFORMAT;
-  if (b.fmt != WHFF_FMT_ZFP && b.rate != 8 * elem_bytes(b.fmt)) return WHFF_EFORMAT;
+  if (!is_blocked(b.fmt) && b.rate != 8 * elem_bytes(b.fmt)) return WHFF_EFORMAT;
   if (check_stream && crc32(blob + kHeaderBytes, want) != b.crc_stream) return WHFF_EFORMAT;
   *info = b;
   return WHFF_OK;
@@ -196,18 +198,18 @@ inline int f32_exponent(uint32_t bits) {
   return (32 - __builtin_clz(m)) - 149;
 }
 
-// trunc(f * 2^(26 - emax)) from the FP32 bit pattern, by shifting the significand.
-inline int32_t f32_to_fixed(uint32_t bits, int emax) {
+// trunc(f * 2^(prec - emax)) from the FP32 bit pattern, by shifting the significand.
+inline int32_t f32_to_fixed(uint32_t bits, int emax, int prec = kWz1Prec) {
   uint32_t E = (bits >> 23) & 0xFF;
   uint32_t m = bits & 0x7FFFFF;
   int sh;  // f = sig * 2^(sh0), q = sig * 2^(sh0 + 26 - emax)
   uint32_t sig;
   if (E) {
     sig = m | 0x800000u;
-    sh = (int)E - 150 + kWz1Prec - emax;
+    sh = (int)E - 150 + prec - emax;
   } else {
     sig = m;
-    sh = -149 + kWz1Prec - emax;
+    sh = -149 + prec - emax;
   }
   uint32_t mag = sh >= 0 ? (sig << sh) : (sh <= -32 ? 0u : (sig >> -sh));
   return (bits >> 31) ? -(int32_t)mag : (int32_t)mag;
@@ -271,6 +273,71 @@ int encode_block(const float* vals, int rate, uint64_t* out) {
       rest >>= z + 1;
     }
   }
+  return WHFF_OK;
+}
+
+// ------------------------------------------------ WZ2 fixed-allocation coder
+constexpr int kWz2Prec = 24;
+constexpr int kWz2Kmax = 27;
+
+inline int wz2_width(int rate) { return (16 * rate - 13) / 16; }
+
+// (4F) applied to one 4-vector: (x0+x1+x2+x3, 2(x2+x3-x0-x1), 4(x1-x0), 4((x3-x2)-(x1-x0)))
+inline void lin_fwd4(int64_t& a, int64_t& b, int64_t& c, int64_t& d) {
+  const int64_t lo = a + b, hi = c + d, dl = b - a, dh = d - c;
+  a = lo + hi;
+  b = 2 * (hi - lo);
+  c = 4 * dl;
+  d = 4 * (dh - dl);
+}
+
+// c / 2^K rounded half to even, in integers (c exact, K >= 0).
+inline int64_t shift_round_even(int64_t c, int K) {
+  if (K == 0) return c;
+  const int64_t fl = c >> K;  // floor
+  const int64_t rem = c - fl * ((int64_t)1 << K);
+  const int64_t half = (int64_t)1 << (K - 1);
+  return (rem > half || (rem == half && (fl & 1))) ? fl + 1 : fl;
+}
+
+int encode_block_wz2(const float* vals, int rate, bool lift, uint64_t* out) {
+  const int nw = rate / 4;
+  std::memset(out, 0, sizeof(uint64_t) * nw);
+  uint32_t bits[16];
+  int emax = INT32_MIN;
+  for (int i = 0; i < 16; ++i) {
+    std::memcpy(&bits[i], &vals[i], 4);
+    uint32_t E = (bits[i] >> 23) & 0xFF;
+    if (E == 0xFF) return WHFF_ENONFINITE;
+    if (E >= 254) return WHFF_ERANGE;
+    if (bits[i] & 0x7FFFFFFFu) emax = std::max(emax, f32_exponent(bits[i]));
+  }
+  if (emax <= kWz1Emin) return WHFF_OK;
+  int64_t c[16];
+  for (int i = 0; i < 16; ++i) c[i] = f32_to_fixed(bits[i], emax, kWz2Prec);
+  if (lift) {
+    for (int r = 0; r < 4; ++r) lin_fwd4(c[4 * r], c[4 * r + 1], c[4 * r + 2], c[4 * r + 3]);
+    for (int j = 0; j < 4; ++j) lin_fwd4(c[j], c[4 + j], c[8 + j], c[12 + j]);
+  }
+  const int* seq = seq_table().idx;
+  int64_t ord[16];
+  for (int k = 0; k < 16; ++k) ord[k] = lift ? c[seq[k]] : c[k];
+  const int W = wz2_width(rate);
+  const int64_t lo = -((int64_t)1 << (W - 1)), hi = ((int64_t)1 << (W - 1)) - 1;
+  int K = 0;
+  int64_t v[16];
+  for (;; ++K) {
+    bool fits = true;
+    for (int k = 0; k < 16; ++k) {
+      v[k] = shift_round_even(ord[k], K);
+      fits &= v[k] >= lo && v[k] <= hi;
+    }
+    if (fits || K == kWz2Kmax) break;
+  }
+  BitSink bs{out};
+  bs.put((uint64_t)(emax + 127), 8);
+  bs.put((uint64_t)K, 5);
+  for (int k = 0; k < 16; ++k) bs.put((uint64_t)(v[k] - lo), W);
   return WHFF_OK;
 }
 
@@ -361,7 +428,8 @@ int encode_band_zfp(uint8_t* stream, const BlobInfo& b, const double* band, int6
         const double* row = band + (gi - row0) * lda;
         for (int c = 0; c < 4; ++c) vals[4 * r + c] = (float)row[std::min(4 * J + c, b.N - 1)];
       }
-      int e = encode_block(vals, b.rate, w);
+      int e = b.fmt == WHFF_FMT_ZFP ? encode_block(vals, b.rate, w)
+                                    : encode_block_wz2(vals, b.rate, b.fmt == WHFF_FMT_FIXED_LIFT, w);
       if (e != WHFF_OK) err.store(e);
       uint8_t* dst = stream + (uint64_t)(I * BN + J) * (uint64_t)(8 * nw);
       for (int k = 0; k < nw; ++k) st64(dst + 8 * k, w[k]);
@@ -419,13 +487,13 @@ int encode_band_scaled(uint8_t* stream, const BlobInfo& b, const double* band, i
 using namespace whff;
 
 extern "C" size_t whff_compressed_size(int fmt, int rate, int64_t M, int64_t N) {
-  if (fmt != WHFF_FMT_ZFP) rate = 8 * elem_bytes(fmt);
+  if (!is_blocked(fmt)) rate = 8 * elem_bytes(fmt);
   uint64_t s = stream_size(fmt, rate, M, N);
   return s ? (size_t)(kHeaderBytes + s) : 0;
 }
 
 extern "C" int whff_blob_init(void* blob, size_t cap, int fmt, int rate, int64_t M, int64_t N) {
-  if (fmt != WHFF_FMT_ZFP) rate = 8 * elem_bytes(fmt);
+  if (!is_blocked(fmt)) rate = 8 * elem_bytes(fmt);
   uint64_t s = stream_size(fmt, rate, M, N);
   if (!blob || !s || cap < kHeaderBytes + s) {
     set_error("whff_blob_init: invalid format, rate, shape or capacity");
@@ -448,14 +516,14 @@ extern "C" int whff_compress_band(void* blob, size_t cap, const double* band, in
     set_error("whff_compress_band: blob not initialised");
     return WHFF_EFORMAT;
   }
-  const int align = b.fmt == WHFF_FMT_ZFP ? 4 : kScaleTile;
+  const int align = is_blocked(b.fmt) ? 4 : kScaleTile;
   if (!band || row0 < 0 || nrows <= 0 || row0 + nrows > b.M || lda < b.N || row0 % align ||
       (nrows % align && row0 + nrows != b.M)) {
     set_error("whff_compress_band: band must start on a block/tile row and cover whole blocks");
     return WHFF_EINVAL;
   }
   uint8_t* stream = (uint8_t*)blob + kHeaderBytes;
-  int e = b.fmt == WHFF_FMT_ZFP ? encode_band_zfp(stream, b, band, row0, nrows, lda, nthreads)
+  int e = is_blocked(b.fmt) ? encode_band_zfp(stream, b, band, row0, nrows, lda, nthreads)
                                 : encode_band_scaled(stream, b, band, row0, nrows, lda, nthreads);
   if (e != WHFF_OK) set_error(e == WHFF_ERANGE ? "whff_compress: |a| >= 2^127" : "whff_compress: non-finite value");
   return e;

@@ -1,0 +1,274 @@
+// whff_serve.cpp -- control-loop request server: resident models, admission by
+// device-memory footprint, continuous batching and CUDA-graph replay.
+//
+// The paper's controller runs one deformation GEMV per light millisecond and
+// tolerates a missed deadline at a cost in yield (Sec. 1: corrections are due
+// within 50 ms; a firm real-time system).  Here several resident models
+// receive step requests; requests that arrive while a model's previous pass
+// is on the GPU wait in its queue and are folded into the next pass as extra
+// right-hand sides (continuous batching).  Columns are applied in arrival
+// order, so the carried state s <- decay*s + y evolves exactly as if every
+// request had been served alone, and each column's y is computed by the same
+// kernel arithmetic whatever the batch (the kernels treat right-hand sides
+// independently).  Different models' passes run concurrently on a pool of
+// streams.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <vector>
+
+#include "whff.h"
+
+namespace whff {
+void set_error(const std::string& msg);
+}
+using whff::set_error;
+
+namespace {
+
+struct Model {
+  whff_handle* h = nullptr;
+  int64_t M = 0, N = 0;
+  double decay = 0.0;
+  double* d_state = nullptr;
+  float* x_pin = nullptr;    // max_batch x N, pinned
+  double* y_pin = nullptr;   // max_batch x M, pinned
+  std::vector<whff_graph*> graphs;  // bucket b -> graph for R = 1 << b
+  size_t footprint = 0;
+};
+
+int bucket_of(int n) {  // largest b with 2^b <= n
+  int b = 0;
+  while ((2 << b) <= n) ++b;
+  return b;
+}
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct whff_server {
+  size_t budget = 0, used = 0;
+  int max_batch = 8;
+  int nbuckets = 4;
+  std::vector<cudaStream_t> streams;
+  std::vector<Model> models;
+};
+
+extern "C" void whff_server_destroy(whff_server* s) {
+  if (!s) return;
+  for (auto& st : s->streams) cudaStreamSynchronize(st);
+  for (auto& m : s->models) {
+    for (auto* g : m.graphs) whff_graph_destroy(g);
+    cudaFree(m.d_state);
+    cudaFreeHost(m.x_pin);
+    cudaFreeHost(m.y_pin);
+  }
+  for (auto& st : s->streams) cudaStreamDestroy(st);
+  cudaGetLastError();
+  delete s;
+}
+
+extern "C" int whff_server_create(size_t hbm_budget, int max_batch, int nstreams, whff_server** out) {
+  if (!out || max_batch < 1 || max_batch > 8 || (max_batch & (max_batch - 1)) || nstreams < 1 || nstreams > 64) {
+    set_error("whff_server_create: max_batch must be 1, 2, 4 or 8 and nstreams in 1..64");
+    return WHFF_EINVAL;
+  }
+  *out = nullptr;
+  auto* s = new whff_server;
+  s->budget = hbm_budget;
+  s->max_batch = max_batch;
+  s->nbuckets = bucket_of(max_batch) + 1;
+  for (int i = 0; i < nstreams; ++i) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      whff_server_destroy(s);
+      set_error("whff_server_create: cudaStreamCreate failed");
+      return WHFF_ECUDA;
+    }
+    s->streams.push_back(st);
+  }
+  *out = s;
+  return WHFF_OK;
+}
+
+extern "C" int whff_server_add_model(whff_server* s, whff_handle* h, double decay, int* model_id) {
+  if (!s || !h || !model_id) {
+    set_error("whff_server_add_model: null argument");
+    return WHFF_EINVAL;
+  }
+  Model m;
+  int fmt, rate;
+  size_t dev_bytes = 0;
+  if (whff_info(h, &fmt, &rate, &m.M, &m.N, &dev_bytes)) return WHFF_EINVAL;
+  // resident matrix + state + one staging pair per batch bucket
+  size_t staging = 0;
+  for (int b = 0; b < s->nbuckets; ++b) staging += (size_t)(1 << b) * (size_t)(m.N * 4 + m.M * 8);
+  m.footprint = dev_bytes + (size_t)m.M * 8 + staging;
+  if (s->used + m.footprint > s->budget) {
+    set_error("whff_server_add_model: device-memory budget exceeded (" + std::to_string(s->used + m.footprint) +
+              " > " + std::to_string(s->budget) + " bytes)");
+    return WHFF_EBUSY;
+  }
+  m.h = h;
+  m.decay = decay;
+  auto fail = [&](int code, const char* what) {
+    for (auto* g : m.graphs) whff_graph_destroy(g);
+    cudaFree(m.d_state);
+    cudaFreeHost(m.x_pin);
+    cudaFreeHost(m.y_pin);
+    cudaGetLastError();
+    set_error(std::string("whff_server_add_model: ") + what);
+    return code;
+  };
+  if (cudaMalloc(&m.d_state, (size_t)m.M * 8) != cudaSuccess || cudaMemset(m.d_state, 0, (size_t)m.M * 8) != cudaSuccess)
+    return fail(WHFF_ENOMEM, "state allocation failed");
+  if (cudaMallocHost(&m.x_pin, (size_t)s->max_batch * m.N * 4) != cudaSuccess ||
+      cudaMallocHost(&m.y_pin, (size_t)s->max_batch * m.M * 8) != cudaSuccess)
+    return fail(WHFF_ENOMEM, "pinned staging allocation failed");
+  for (int b = 0; b < s->nbuckets; ++b) {
+    whff_graph* g = nullptr;
+    int e = whff_graph_create_host(h, m.x_pin, 1 << b, m.N, m.y_pin, m.M, m.d_state, decay, s->streams[0], &g);
+    if (e) return fail(e, "graph capture failed");
+    m.graphs.push_back(g);
+  }
+  s->used += m.footprint;
+  *model_id = (int)s->models.size();
+  s->models.push_back(m);
+  return WHFF_OK;
+}
+
+extern "C" int whff_server_reset_state(whff_server* s, int model_id) {
+  if (!s || model_id < 0 || model_id >= (int)s->models.size()) {
+    set_error("whff_server_reset_state: bad model");
+    return WHFF_EINVAL;
+  }
+  Model& m = s->models[model_id];
+  if (cudaMemset(m.d_state, 0, (size_t)m.M * 8) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    set_error("whff_server_reset_state: CUDA error");
+    return WHFF_ECUDA;
+  }
+  return WHFF_OK;
+}
+
+extern "C" int whff_server_read_state(whff_server* s, int model_id, double* host_out) {
+  if (!s || !host_out || model_id < 0 || model_id >= (int)s->models.size()) {
+    set_error("whff_server_read_state: bad argument");
+    return WHFF_EINVAL;
+  }
+  Model& m = s->models[model_id];
+  if (cudaMemcpy(host_out, m.d_state, (size_t)m.M * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    set_error("whff_server_read_state: CUDA error");
+    return WHFF_ECUDA;
+  }
+  return WHFF_OK;
+}
+
+// Replay a request trace in real time.  Request i is for model[i], arrives at
+// arrival_s[i] seconds after the start (non-decreasing) and carries the N
+// floats at x[i].  On return latency_s[i] = completion - arrival (completion =
+// the moment the host observes the pass's copy of y back), batch[i] = the
+// number of requests in its pass, and, if y[i] is not NULL, the M doubles of
+// its result are stored there.  max_wait_s bounds the whole run (a watchdog:
+// WHFF_ETIMEOUT if it expires with requests still open).
+extern "C" int whff_server_run(whff_server* s, int n, const int* model, const double* arrival_s,
+                               const float* const* x, double* const* y, double* latency_s, int* batch,
+                               double max_wait_s) {
+  if (!s || n < 0 || (n && (!model || !arrival_s || !x || !latency_s || !batch))) {
+    set_error("whff_server_run: bad argument");
+    return WHFF_EINVAL;
+  }
+  const int nm = (int)s->models.size();
+  for (int i = 0; i < n; ++i)
+    if (model[i] < 0 || model[i] >= nm || !x[i] || (i && arrival_s[i] < arrival_s[i - 1])) {
+      set_error("whff_server_run: bad request " + std::to_string(i));
+      return WHFF_EINVAL;
+    }
+  struct Pass {
+    std::vector<int> reqs;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+  };
+  std::vector<std::deque<int>> queue(nm);
+  std::vector<Pass> inflight(nm);
+  for (auto& p : inflight)
+    if (cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming) != cudaSuccess) {
+      set_error("whff_server_run: cudaEventCreate failed");
+      return WHFF_ECUDA;
+    }
+  const int nst = (int)s->streams.size();
+  int next_stream = 0, next_arrival = 0, done = 0, rr = 0;
+  int err = WHFF_OK;
+  const double t0 = now_s();
+  while (done < n) {
+    const double t = now_s() - t0;
+    if (t > max_wait_s) {
+      err = WHFF_ETIMEOUT;
+      set_error("whff_server_run: watchdog expired with requests open");
+      break;
+    }
+    while (next_arrival < n && arrival_s[next_arrival] <= t) {
+      queue[model[next_arrival]].push_back(next_arrival);
+      ++next_arrival;
+    }
+    for (int m = 0; m < nm; ++m) {  // completions
+      Pass& p = inflight[m];
+      if (!p.busy) continue;
+      cudaError_t q = cudaEventQuery(p.ev);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) {
+        err = WHFF_ECUDA;
+        set_error(std::string("whff_server_run: pass failed: ") + cudaGetErrorString(q));
+        break;
+      }
+      const double tc = now_s() - t0;
+      const Model& md = s->models[m];
+      for (size_t k = 0; k < p.reqs.size(); ++k) {
+        const int r = p.reqs[k];
+        latency_s[r] = tc - arrival_s[r];
+        batch[r] = (int)p.reqs.size();
+        if (y && y[r]) std::memcpy(y[r], md.y_pin + k * md.M, (size_t)md.M * 8);
+      }
+      done += (int)p.reqs.size();
+      p.reqs.clear();
+      p.busy = false;
+    }
+    if (err) break;
+    for (int k = 0; k < nm; ++k) {  // dispatch, round robin over models
+      const int m = (rr + k) % nm;
+      Pass& p = inflight[m];
+      if (p.busy || queue[m].empty()) continue;
+      const int take = 1 << bucket_of(std::min<int>((int)queue[m].size(), s->max_batch));
+      Model& md = s->models[m];
+      for (int c = 0; c < take; ++c) {
+        const int r = queue[m].front();
+        queue[m].pop_front();
+        std::memcpy(md.x_pin + (size_t)c * md.N, x[r], (size_t)md.N * 4);
+        p.reqs.push_back(r);
+      }
+      cudaStream_t st = s->streams[next_stream];
+      next_stream = (next_stream + 1) % nst;
+      int e = whff_graph_launch(md.graphs[bucket_of(take)], st);
+      if (e == WHFF_OK && cudaEventRecord(p.ev, st) != cudaSuccess) e = WHFF_ECUDA;
+      if (e) {
+        err = e;
+        break;
+      }
+      p.busy = true;
+    }
+    rr = (rr + 1) % std::max(nm, 1);
+    if (err) break;
+  }
+  if (err) cudaDeviceSynchronize();
+  for (auto& p : inflight) cudaEventDestroy(p.ev);
+  cudaGetLastError();
+  return err;
+}

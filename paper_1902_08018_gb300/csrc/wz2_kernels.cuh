@@ -1,0 +1,338 @@
+// wz2_kernels.cuh -- the fixed-allocation variant ("WZ2") of the zfp-style
+// fixed-rate format: decode-only and fused decode + GEMV kernels.
+//
+// Sec. 5.2 finds the zfp decoder sequential (52 % of the run time) and Sec. 6
+// asks for GPU-friendly decompression.  WZ2 keeps the 4x4 block and its
+// exponent but stores every coefficient in a field of fixed width W at a fixed
+// bit offset, so a block decodes with a handful of shifts and masks whose
+// positions are compile-time constants.  With the lift taken in its exact
+// linear form A_blk = (2G) V (2G)^T * 2^(K+emax-30), the product needs no
+// inverse transform per block: y_I = (2G) sum_J s_J V_J ((2G)^T x_J) * 2^-3,
+// s_J = 2^(K_J+emax_J-27), so a lane multiplies the stored coefficients with
+// the transformed x chunk and the (2G) mixing happens once per 4-row band in
+// the FP64 epilogue.
+#pragma once
+#include <cstdint>
+
+#include "gemv_kernels.cuh"
+
+namespace whff {
+namespace dev {
+
+template <int RATE>
+struct Wz2Layout {
+  static constexpr int kWords = RATE / 2;               // 32-bit words per block
+  static constexpr int kW = (16 * RATE - 13) / 16;      // field width
+  static constexpr uint32_t kMask = (1u << kW) - 1u;
+  static constexpr float kBias = 8388608.0f + (float)(1u << (kW - 1));  // 2^23 + 2^(W-1)
+  static_assert(kW >= 7 && kW <= 23, "WZ2 rates 8..24");
+};
+
+// Field k (offset-binary) -> float value v, exactly: the field is OR-ed into
+// the mantissa of 2^23, then 2^23 + 2^(W-1) is subtracted (exact, |v| < 2^22).
+template <int RATE, int K>
+__device__ __forceinline__ float wz2_field(const uint32_t (&w)[Wz2Layout<RATE>::kWords]) {
+  using L = Wz2Layout<RATE>;
+  constexpr int off = 13 + L::kW * K;
+  constexpr int wi = off / 32, sh = off % 32;
+  uint32_t u;
+  if constexpr (sh + L::kW <= 32) {
+    u = (w[wi] >> sh) & L::kMask;
+  } else {
+    u = __funnelshift_r(w[wi], w[wi + 1], sh) & L::kMask;
+  }
+  return __uint_as_float(u | 0x4B000000u) - L::kBias;
+}
+
+template <int RATE>
+__device__ __forceinline__ void wz2_fields(const uint32_t (&w)[Wz2Layout<RATE>::kWords], float (&f)[16]) {
+  f[0] = wz2_field<RATE, 0>(w);
+  f[1] = wz2_field<RATE, 1>(w);
+  f[2] = wz2_field<RATE, 2>(w);
+  f[3] = wz2_field<RATE, 3>(w);
+  f[4] = wz2_field<RATE, 4>(w);
+  f[5] = wz2_field<RATE, 5>(w);
+  f[6] = wz2_field<RATE, 6>(w);
+  f[7] = wz2_field<RATE, 7>(w);
+  f[8] = wz2_field<RATE, 8>(w);
+  f[9] = wz2_field<RATE, 9>(w);
+  f[10] = wz2_field<RATE, 10>(w);
+  f[11] = wz2_field<RATE, 11>(w);
+  f[12] = wz2_field<RATE, 12>(w);
+  f[13] = wz2_field<RATE, 13>(w);
+  f[14] = wz2_field<RATE, 14>(w);
+  f[15] = wz2_field<RATE, 15>(w);
+}
+
+template <int RATE>
+__device__ __forceinline__ void wz2_load(const uint8_t* __restrict__ base, int64_t blk,
+                                         uint32_t (&w)[Wz2Layout<RATE>::kWords]) {
+  constexpr int NW = Wz2Layout<RATE>::kWords;
+  const uint8_t* p = base + (uint64_t)blk * (uint64_t)(4 * NW);
+  if constexpr (NW % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NW / 4; ++i) {
+      const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p) + i);
+      w[4 * i] = v.x;
+      w[4 * i + 1] = v.y;
+      w[4 * i + 2] = v.z;
+      w[4 * i + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NW / 2; ++i) {
+      const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p) + i);
+      w[2 * i] = v.x;
+      w[2 * i + 1] = v.y;
+    }
+  }
+}
+
+// Coefficient matrix V (row-major 4x4, index 4a+b) from the fields: sequency
+// order with the lift, row-major without.
+template <bool LIFT>
+__device__ __forceinline__ void wz2_unpermute(const float (&f)[16], float (&V)[16]) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) V[LIFT ? seq_index(k) : k] = f[k];
+}
+
+// Fold a band's FP64 sums and (with the lift) mix them with 2G, scaled.
+template <bool LIFT, int R>
+__device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
+                                           int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
+                                           double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                                           double decay) {
+  double z[4][R];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int r = 0; r < R; ++r) z[i][r] = warp_sum((double)hi[i][r] + (double)lo[i][r]);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    double t[4];
+    if (LIFT) {  // y = (2G) z * 2^-3, 2G rows (2,-1,-1,0), (2,-1,1,0), (2,1,-1,-1), (2,1,1,1)
+      const double a = 2.0 * z[0][r];
+      t[0] = (a - z[1][r] - z[2][r]) * 0.125;
+      t[1] = (a - z[1][r] + z[2][r]) * 0.125;
+      t[2] = (a + z[1][r] - z[2][r] - z[3][r]) * 0.125;
+      t[3] = (a + z[1][r] + z[2][r] + z[3][r]) * 0.125;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[i] = z[i][r] * 8.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) z[i][r] = t[i];
+  }
+  // lane (i*R + r) writes value (i, r)
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (lane != i * R + r) continue;
+      const int64_t row = row0 + i;
+      if (ksplit == 2) {  // segment partial: ws[row0 + r*4 + i] (row0 = 4*(band*maxseg+seg)*R)
+        ws[row0 + r * 4 + i] = z[i][r];
+      } else if (ksplit > 1) {
+        ws[((int64_t)split * R + r) * Mpad + row] = z[i][r];
+      } else if (row < M) {
+        y[(int64_t)r * ldy + row] = z[i][r];
+      }
+    }
+  if (ksplit == 1 && state != nullptr && lane < 4) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (lane != i) continue;
+      const int64_t row = row0 + i;
+      if (row < M) {
+        double s = state[row];
+#pragma unroll
+        for (int r = 0; r < R; ++r) s = decay * s + z[i][r];
+        state[row] = s;
+      }
+    }
+  }
+}
+
+// One block's contribution, scaled: p[i][r] = s * sum_b V[i][b] xt_r[b].
+template <int RATE, bool LIFT, int R>
+__device__ __forceinline__ void wz2_block_partial(const uint32_t (&w)[Wz2Layout<RATE>::kWords],
+                                                  const float* __restrict__ x, int64_t ldx, int64_t c0, int64_t N,
+                                                  bool x_fast, bool x_vec_ok, float (&p)[4][R]) {
+  const uint32_t E = w[0] & 0xFFu;
+  const uint32_t K = (w[0] >> 8) & 31u;
+  // 2^(emax+K-27) is always a normal float; a zero block (E = 0) scales by 0
+  const float s = E ? __uint_as_float((E + K - 27u) << 23) : 0.f;
+  float f[16], V[16];
+  wz2_fields<RATE>(w, f);
+  wz2_unpermute<LIFT>(f, V);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const float4 xv = x_fast ? __ldg(reinterpret_cast<const float4*>(x + (int64_t)r * ldx + c0))
+                             : load_x4(x, ldx, r, c0, N, x_vec_ok);
+    float xt[4];
+    if (LIFT) {  // (2G)^T x
+      const float a = xv.x + xv.y, b = xv.z + xv.w, c = xv.x + xv.z, d = xv.y + xv.w;
+      xt[0] = 2.f * (a + b);
+      xt[1] = b - a;
+      xt[2] = d - c;
+      xt[3] = xv.w - xv.z;
+    } else {
+      xt[0] = xv.x;
+      xt[1] = xv.y;
+      xt[2] = xv.z;
+      xt[3] = xv.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float q = V[4 * i] * xt[0];
+      q = fmaf(V[4 * i + 1], xt[1], q);
+      q = fmaf(V[4 * i + 2], xt[2], q);
+      q = fmaf(V[4 * i + 3], xt[3], q);
+      p[i][r] = q * s;
+    }
+  }
+}
+
+// Persistent kernel with exact balance: the G resident warps split the
+// band-major sequence of all BM*BN blocks into G contiguous ranges of L
+// blocks.  A range covers pieces of one to a few 4-row bands; for every piece
+// the warp folds its lanes' sums and either writes y (and the state) directly,
+// when the band lies inside one range, or stores the piece's partial in
+// ws[band][segment] for wz2_segment_epilogue, which adds a band's segments in
+// order.  Each lane keeps two blocks in flight (both loads issued before
+// either is decoded) and feeds its TwoSum accumulators once per pair.
+template <int RATE, bool LIFT, int R>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+    wz2_gemv_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BM, int64_t BN,
+                    const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int64_t L, int maxseg,
+                    double* __restrict__ ws, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                    double decay) {
+  constexpr int NW = Wz2Layout<RATE>::kWords;
+  constexpr int64_t kBlockBytes = 4 * NW;
+  const int lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  const int64_t total = BM * BN;
+  const bool x_fast = x_vec_ok && (N % 4 == 0);
+  int64_t b0 = g * L;
+  const int64_t b1 = min(total, b0 + L);
+  while (b0 < b1) {
+    const int64_t I = b0 / BN;
+    const int64_t piece_end = min(b1, (I + 1) * BN);
+    const int64_t J0 = b0 - I * BN, J1 = piece_end - I * BN;
+    const int64_t g_lo = (I * BN) / L, g_hi = ((I + 1) * BN - 1) / L;
+
+    float hi[4][R], lo[4][R];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
+
+    const uint8_t* base = stream + (uint64_t)(I * BN) * kBlockBytes;
+    int64_t J = J0 + lane;
+    for (; J + 32 < J1; J += 64) {
+      uint32_t w0[NW], w1[NW];
+      wz2_load<RATE>(base, J, w0);
+      wz2_load<RATE>(base, J + 32, w1);
+      float p0[4][R], p1[4][R];
+      wz2_block_partial<RATE, LIFT, R>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
+      wz2_block_partial<RATE, LIFT, R>(w1, x, ldx, 4 * (J + 32), N, x_fast, x_vec_ok, p1);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r] + p1[i][r]);
+    }
+    if (J < J1) {
+      uint32_t w0[NW];
+      wz2_load<RATE>(base, J, w0);
+      float p0[4][R];
+      wz2_block_partial<RATE, LIFT, R>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r]);
+    }
+    if (g_lo == g_hi) {  // the whole band is in this range: finish it here
+      wz2_finish<LIFT, R>(hi, lo, lane, 4 * I, M, 0, 1, 4 * BM, ws, y, ldy, state, decay);
+    } else {  // one segment of a shared band: ws[(band * maxseg + seg) * R + r][i]
+      wz2_finish<LIFT, R>(hi, lo, lane, 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, 2, 0, ws, y, ldy, state,
+                          decay);
+    }
+    b0 = piece_end;
+  }
+}
+
+// Sum the segments of bands shared by several warp ranges, in segment order,
+// then the state update (bands inside one range were finished by the kernel).
+__global__ void wz2_segment_epilogue(const double* __restrict__ ws, int64_t M, int64_t BN, int64_t L, int maxseg,
+                                     int R, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                                     double decay) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= M) return;
+  const int64_t I = row / 4;
+  const int i = (int)(row % 4);
+  const int64_t g_lo = (I * BN) / L, g_hi = ((I + 1) * BN - 1) / L;
+  if (g_lo == g_hi) return;
+  double s = state ? state[row] : 0.0;
+  for (int r = 0; r < R; ++r) {
+    double t = 0.0;
+    for (int64_t seg = 0; seg <= g_hi - g_lo; ++seg) t += ws[((I * maxseg + seg) * R + r) * 4 + i];
+    y[(int64_t)r * ldy + row] = t;
+    s = decay * s + t;
+  }
+  if (state) state[row] = s;
+}
+
+template <int RATE, bool LIFT>
+__global__ void wz2_decompress_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BN,
+                                      int64_t nblocks, double* __restrict__ out, int64_t ldo) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblocks) return;
+  const int64_t I = b / BN, J = b - (b / BN) * BN;
+  uint32_t w[Wz2Layout<RATE>::kWords];
+  wz2_load<RATE>(stream, b, w);
+  const int E = (int)(w[0] & 0xFFu);
+  const int K = (int)((w[0] >> 8) & 31u);
+  float f[16], Vf[16];
+  wz2_fields<RATE>(w, f);
+  wz2_unpermute<LIFT>(f, Vf);
+  int32_t T[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) T[i] = (int32_t)Vf[i];  // exact: |v| < 2^22
+  double scale;
+  if (LIFT) {
+    // T = (2G) V (2G)^T, integers below 2^27: columns, then rows
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int s0 = pass ? 1 : 4, s1 = pass ? 4 : 1;  // pass 0: along a (stride 4); pass 1: along b
+        int32_t& v0 = T[j * s1];
+        int32_t& v1 = T[j * s1 + s0];
+        int32_t& v2 = T[j * s1 + 2 * s0];
+        int32_t& v3 = T[j * s1 + 3 * s0];
+        const int32_t a = 2 * v0;
+        const int32_t r0 = a - v1 - v2, r1 = a - v1 + v2, r2 = a + v1 - v2 - v3, r3 = a + v1 + v2 + v3;
+        v0 = r0;
+        v1 = r1;
+        v2 = r2;
+        v3 = r3;
+      }
+    }
+    scale = ldexp(1.0, K + (E - 127) - 30);
+  } else {
+    scale = ldexp(1.0, K + (E - 127) - 24);
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t row = 4 * I + r;
+    if (row >= M) break;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t col = 4 * J + c;
+      if (col < N) out[row * ldo + col] = E ? (double)T[4 * r + c] * scale : 0.0;
+    }
+  }
+}
+
+}  // namespace dev
+}  // namespace whff

@@ -18,6 +18,8 @@ FMT_ZFP = 1
 FMT_BF16 = 2
 FMT_FP16 = 3
 FMT_FP8E4M3 = 4
+FMT_FIXED_LIFT = 5
+FMT_FIXED_BFP = 6
 
 _ERRORS = {
     -1: "WHFF_EINVAL",
@@ -59,12 +61,23 @@ def library() -> ctypes.CDLL:
         "whff_create": (c_int, [P, sz, c_int, P, ctypes.POINTER(P)]),
         "whff_info": (c_int, [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(i64),
                               ctypes.POINTER(i64), ctypes.POINTER(sz)]),
+        "whff_plan": (c_int, [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
         "whff_step": (c_int, [P, P, c_int, i64, P, i64, P, dbl, P]),
         "whff_step_host": (c_int, [P, P, c_int, i64, P, i64, P, dbl, P]),
         "whff_decompress": (c_int, [P, P, i64, P]),
         "whff_sync_status": (c_int, [P, P]),
         "whff_destroy": (None, [P]),
         "whff_step_noalloc": (c_int, [P, c_int, i64, i64, P, c_int, i64, P, i64, P, dbl, P]),
+        "whff_graph_create": (c_int, [P, P, c_int, i64, P, i64, P, dbl, P, ctypes.POINTER(P)]),
+        "whff_graph_create_host": (c_int, [P, P, c_int, i64, P, i64, P, dbl, P, ctypes.POINTER(P)]),
+        "whff_graph_launch": (c_int, [P, P]),
+        "whff_graph_destroy": (None, [P]),
+        "whff_server_create": (c_int, [sz, c_int, c_int, ctypes.POINTER(P)]),
+        "whff_server_add_model": (c_int, [P, P, dbl, ctypes.POINTER(c_int)]),
+        "whff_server_reset_state": (c_int, [P, c_int]),
+        "whff_server_read_state": (c_int, [P, c_int, P]),
+        "whff_server_run": (c_int, [P, c_int, P, P, P, P, P, P, dbl]),
+        "whff_server_destroy": (None, [P]),
         "whff_last_error": (ctypes.c_char_p, []),
         "whff_version": (ctypes.c_char_p, []),
     }
@@ -152,6 +165,12 @@ class Handle:
     @property
     def ptr(self):
         return self._ptr
+
+    def plan(self):
+        """(ksplit, kernel launches per pass of up to 8 right-hand sides)."""
+        k, n = ctypes.c_int(), ctypes.c_int()
+        _check(library().whff_plan(self._ptr, ctypes.byref(k), ctypes.byref(n)))
+        return k.value, n.value
 
     def step(self, x, y, state=None, decay: float = 0.99, stream=None):
         whff_step(self, x, y, state, decay, stream)
@@ -251,3 +270,116 @@ def whff_step_noalloc(stream_dev, rate: int, M: int, N: int, x, y, state=None, d
         sp, _, _ = _vec_args(state, M, "state", torch.float64)
     _check(library().whff_step_noalloc(stream_dev.data_ptr(), rate, M, N, xp, R, ldx, yp, ldy, sp or None,
                                        float(decay), _stream_ptr(stream)))
+
+
+class Graph:
+    """A captured control step (whff_graph_create / whff_graph_create_host)."""
+
+    def __init__(self, ptr: int, keep=()):
+        self._ptr = ctypes.c_void_p(ptr)
+        self._keep = keep  # buffers the graph reads or writes
+
+    def launch(self, stream=None):
+        _check(library().whff_graph_launch(self._ptr, _stream_ptr(stream)))
+
+    def destroy(self):
+        if self._ptr:
+            library().whff_graph_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def whff_graph_create(h: Handle, x, y, state=None, decay: float = 0.99, stream=None) -> Graph:
+    import torch
+
+    xp, R, ldx = _vec_args(x, h.N, "x", torch.float32)
+    yp, Ry, ldy = _vec_args(y, h.M, "y", torch.float64)
+    if Ry != R:
+        raise WhffError(-1, "x and y disagree on the number of right-hand sides")
+    sp = _vec_args(state, h.M, "state", torch.float64)[0] if state is not None else 0
+    g = ctypes.c_void_p()
+    _check(library().whff_graph_create(h.ptr, xp, R, ldx, yp, ldy, sp or None, float(decay), _stream_ptr(stream),
+                                       ctypes.byref(g)))
+    return Graph(g.value, (x, y, state))
+
+
+def whff_graph_create_host(h: Handle, x_host: np.ndarray, y_host: np.ndarray, state=None, decay: float = 0.99,
+                           stream=None) -> Graph:
+    """x_host float32 (R, N) and y_host float64 (R, M): pinned host arrays the graph copies from / to."""
+    import torch
+
+    xh = x_host if x_host.ndim == 2 else x_host.reshape(1, -1)
+    yh = y_host if y_host.ndim == 2 else y_host.reshape(1, -1)
+    if xh.dtype != np.float32 or yh.dtype != np.float64 or xh.strides[1] != 4 or yh.strides[1] != 8:
+        raise WhffError(-1, "x_host float32 and y_host float64 with contiguous rows expected")
+    sp = _vec_args(state, h.M, "state", torch.float64)[0] if state is not None else 0
+    g = ctypes.c_void_p()
+    _check(library().whff_graph_create_host(h.ptr, xh.ctypes.data, xh.shape[0], xh.strides[0] // 4, yh.ctypes.data,
+                                            yh.strides[0] // 8, sp or None, float(decay), _stream_ptr(stream),
+                                            ctypes.byref(g)))
+    return Graph(g.value, (x_host, y_host, state))
+
+
+class Server:
+    """Request server over resident models (continuous batching, graph replay)."""
+
+    def __init__(self, hbm_budget: int, max_batch: int = 8, nstreams: int = 4):
+        p = ctypes.c_void_p()
+        _check(library().whff_server_create(int(hbm_budget), max_batch, nstreams, ctypes.byref(p)))
+        self._ptr = p
+        self.models = []
+
+    def add_model(self, h: Handle, decay: float = 0.99) -> int:
+        mid = ctypes.c_int()
+        _check(library().whff_server_add_model(self._ptr, h.ptr, float(decay), ctypes.byref(mid)))
+        self.models.append(h)
+        return mid.value
+
+    def reset_state(self, model_id: int):
+        _check(library().whff_server_reset_state(self._ptr, model_id))
+
+    def read_state(self, model_id: int) -> np.ndarray:
+        out = np.empty(self.models[model_id].M, dtype=np.float64)
+        _check(library().whff_server_read_state(self._ptr, model_id, out.ctypes.data))
+        return out
+
+    def run(self, model, arrival_s, xs, want_y: bool = False, max_wait_s: float = 600.0):
+        """model: int array, arrival_s: float array (non-decreasing), xs: list of float32 host
+        vectors.  Returns (latency_s, batch, ys or None)."""
+        n = len(model)
+        model = np.ascontiguousarray(model, dtype=np.int32)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        xs = [np.ascontiguousarray(v, dtype=np.float32) for v in xs]
+        xptr = (ctypes.c_void_p * n)(*[v.ctypes.data for v in xs])
+        ys = None
+        yptr = None
+        if want_y:
+            ys = [np.empty(self.models[m].M, dtype=np.float64) for m in model]
+            yptr = (ctypes.c_void_p * n)(*[v.ctypes.data for v in ys])
+        lat = np.empty(n, dtype=np.float64)
+        bat = np.empty(n, dtype=np.int32)
+        _check(library().whff_server_run(self._ptr, n, model.ctypes.data, arr.ctypes.data, xptr, yptr,
+                                         lat.ctypes.data, bat.ctypes.data, float(max_wait_s)))
+        return lat, bat, ys
+
+    def destroy(self):
+        if self._ptr:
+            library().whff_server_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.destroy()

@@ -61,6 +61,11 @@ CASES = [
     (3, 0, 257, 500),
     (4, 0, 129, 1000),
     (4, 0, 24, 9000),     # wide scaled: split-K
+    (5, 16, 257, 513),
+    (5, 8, 130, 97),
+    (5, 24, 16, 20000),   # wide WZ2: split-K
+    (6, 12, 301, 300),
+    (6, 20, 3001, 40),
 ]
 
 
@@ -79,12 +84,12 @@ def test_decompress_bit_exact(env, orc, fmt, rate, M, N):
     assert np.isnan(got[:, N:]).all()  # nothing written past N
 
 
-@pytest.mark.parametrize("rate", [4, 20, 36, 64])
-def test_decompress_other_rates(env, orc, rate):
+@pytest.mark.parametrize("fmt,rate", [(1, 4), (1, 20), (1, 36), (1, 64), (5, 12), (5, 20), (6, 8), (6, 24)])
+def test_decompress_other_rates(env, orc, fmt, rate):
     W, torch = env
     rng = np.random.default_rng(rate)
     A = rng.standard_normal((37, 41)) * np.exp(rng.uniform(-8, 8, size=(37, 41)))
-    blob = W.whff_compress(A, 1, rate)
+    blob = W.whff_compress(A, fmt, rate)
     ref = orc.decode(blob.tobytes())
     with W.whff_create(blob) as h:
         out = torch.empty((37, 41), dtype=torch.float64, device="cuda")

@@ -1,0 +1,128 @@
+"""Graph-captured steps and the request server, through the C ABI.
+
+  * a captured step replays to exactly the result of whff_step;
+  * served requests get exactly the y they would get alone, in any batch;
+  * the carried state after a bursty trace equals the oracle's recursion
+    s <- decay*s + y over the requests in arrival order;
+  * models beyond the device-memory budget are refused (WHFF_EBUSY).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    import paper_1902_08018_gb300 as W
+
+    W.library()
+    return W, torch
+
+
+def _matrix(n, seed):
+    import workloads
+
+    g = int(np.ceil(np.sqrt(n)))
+    return workloads.KernelMatrix(n, g, n, 0.1, seed).dense()
+
+
+def _step_alone(W, torch, h, x):
+    xt = torch.from_numpy(x.astype(np.float32)).cuda()
+    y = torch.zeros(h.M, dtype=torch.float64, device="cuda")
+    h.step(xt, y, None, 0.99)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+@pytest.mark.parametrize("fmt,rate", [(1, 16), (5, 16), (6, 12)])
+def test_graph_replay_equals_step(env, fmt, rate):
+    W, torch = env
+    A = _matrix(600, 21)
+    blob = W.whff_compress(A, fmt, rate)
+    rng = np.random.default_rng(3)
+    with W.whff_create(blob) as h:
+        x = torch.zeros((2, 600), dtype=torch.float32, device="cuda")
+        y = torch.zeros((2, 600), dtype=torch.float64, device="cuda")
+        s = torch.zeros(600, dtype=torch.float64, device="cuda")
+        s_ref = torch.zeros(600, dtype=torch.float64, device="cuda")
+        y_ref = torch.zeros((2, 600), dtype=torch.float64, device="cuda")
+        with W.whff_graph_create(h, x, y, s, 0.9) as g:
+            for it in range(4):
+                xv = torch.from_numpy(rng.standard_normal((2, 600)).astype(np.float32)).cuda()
+                x.copy_(xv)
+                g.launch()
+                h.step(xv, y_ref, s_ref, 0.9)
+                torch.cuda.synchronize()
+                assert torch.equal(y, y_ref)
+                assert torch.equal(s, s_ref)
+
+
+def test_host_graph_replay(env):
+    W, torch = env
+    A = _matrix(500, 22)
+    blob = W.whff_compress(A, 5, 16)
+    rng = np.random.default_rng(4)
+    with W.whff_create(blob) as h:
+        xh = torch.zeros((4, 500), dtype=torch.float32).pin_memory()
+        yh = torch.zeros((4, 500), dtype=torch.float64).pin_memory()
+        with W.whff_graph_create_host(h, xh.numpy(), yh.numpy()) as g:
+            for it in range(3):
+                X = rng.standard_normal((4, 500)).astype(np.float32)
+                xh.numpy()[:] = X
+                g.launch()
+                torch.cuda.synchronize()
+                for r in range(4):
+                    assert (yh.numpy()[r] == _step_alone(W, torch, h, X[r])).all()
+
+
+def test_server_batches_give_the_results_of_single_service(env, orc):
+    W, torch = env
+    sizes = [(256, 1, 16), (777, 5, 16), (1024, 6, 8)]
+    handles, blobs = [], []
+    for n, fmt, rate in sizes:
+        blob = W.whff_compress(_matrix(n, n), fmt, rate)
+        blobs.append(blob)
+        handles.append(W.whff_create(blob, max_rhs=8))
+    rng = np.random.default_rng(5)
+    # bursts: many requests arrive at once, so passes are batched 1..8 wide
+    n_req = 120
+    model = rng.integers(0, len(sizes), size=n_req)
+    arrival = np.sort(np.repeat(np.arange(n_req // 10) * 2e-3, 10))
+    xs = [rng.standard_normal(sizes[m][0]).astype(np.float32) for m in model]
+    with W.Server(hbm_budget=8 << 30, max_batch=8, nstreams=3) as srv:
+        ids = [srv.add_model(h, decay=0.95) for h in handles]
+        lat, bat, ys = srv.run(model, arrival, xs, want_y=True)
+        states = [srv.read_state(i) for i in ids]
+    assert bat.max() > 1  # some passes were batched
+    assert (lat > 0).all()
+    for i in range(n_req):
+        alone = _step_alone(W, torch, handles[model[i]], xs[i])
+        assert (ys[i] == alone).all(), i
+    for m, (n, fmt, rate) in enumerate(sizes):
+        Ahat = orc.decode(blobs[m].tobytes())
+        s = np.zeros(n)
+        for i in np.nonzero(model == m)[0]:  # arrival order
+            s = orc.state_update(s, orc.gemv64(Ahat, xs[i].astype(np.float64)).reshape(n, 1), 0.95)
+        assert np.linalg.norm(states[m] - s) <= 1e-6 * np.linalg.norm(s)
+    for h in handles:
+        h.destroy()
+
+
+def test_server_admission_by_footprint(env):
+    W, torch = env
+    blob = W.whff_compress(_matrix(512, 1), 5, 16)
+    h1 = W.whff_create(blob, max_rhs=8)
+    h2 = W.whff_create(blob, max_rhs=8)
+    # room for one model (its matrix, workspace and staging) but not for two
+    with W.Server(hbm_budget=int(h1.device_bytes * 1.6), max_batch=8, nstreams=1) as srv:
+        srv.add_model(h1)
+        with pytest.raises(W.WhffError) as e:
+            srv.add_model(h2)
+        assert e.value.code == -8  # WHFF_EBUSY
+    h1.destroy()
+    h2.destroy()
