@@ -63,6 +63,13 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-baseline", action="store_true")
     p.add_argument("--json-out", default=None)
+    p.add_argument("--serve", action="store_true", help="run the serving workload instead of the control loop")
+    p.add_argument("--serve-fmt", default="wz2-lift:8")
+    p.add_argument("--serve-orders", default="8192,16384,32768,49152,65536,65536,32768,16384")
+    p.add_argument("--serve-seconds", type=float, default=2.0)
+    p.add_argument("--serve-hz", type=float, default=2000.0)
+    p.add_argument("--deadline-us", type=float, default=500.0)
+    p.add_argument("--firm", type=int, default=1, help="1: drop requests past their deadline (firm real time)")
     return p.parse_args()
 
 
@@ -75,13 +82,16 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+KERNEL_SOURCES = ("gemv_kernels.cuh", "wz1_decode.cuh", "wz2_kernels.cuh")
+
+
 def kernel_source_hash():
+    """Hash of the device-kernel sources the ncu counters in profiles/ were taken on."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1902_08018_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -411,6 +421,103 @@ def run_whff(args, rank, world, local_rank):
     return res
 
 
+# ------------------------------------------------------------ serving arm
+def run_serve(args, rank, world, local_rank):
+    """Resident control models served through the C++ request server: Poisson
+    arrivals per model, continuous batching into graph-replayed passes,
+    admission by device-memory footprint; latency = host-observed completion
+    of the pass that carried a request minus its arrival."""
+    import torch
+
+    import paper_1902_08018_gb300 as W
+    import workloads
+
+    torch.cuda.set_device(local_rank)
+    fmt_name, rate = args.serve_fmt.split(":")
+    fmt, rate = FMT_CODES[fmt_name], int(rate)
+    orders = [int(v) for v in args.serve_orders.split(",")]
+    free, _ = torch.cuda.mem_get_info()
+    t0 = time.perf_counter()
+    handles, blobs_bytes = [], []
+    for k, n in enumerate(orders):
+        g = int(np.ceil(np.sqrt(n)))
+        km = workloads.KernelMatrix(n, g, n, 0.05, workloads.SEED_BASE + 5 + 1000 * k)
+        blob = W.whff_compress_bands(n, n, km.bands(2048), fmt, rate)
+        handles.append(W.whff_create(blob, max_rhs=8))
+        blobs_bytes.append(blob.size - 64)
+        del blob
+    setup_s = time.perf_counter() - t0
+    budget = int(free * 0.9)
+    rng = np.random.default_rng(workloads.SEED_BASE + 5)
+    events = []
+    for k, n in enumerate(orders):
+        arr = workloads.poisson_arrivals(args.serve_hz, args.serve_seconds, workloads.SEED_BASE + 50 + k)
+        events += [(t, k) for t in arr]
+    events.sort()
+    model = np.array([m for _, m in events], dtype=np.int32)
+    arrival = np.array([t for t, _ in events], dtype=np.float64)
+    pools = []  # per model: 64 heat-load-like vectors
+    for k, n in enumerate(orders):
+        pools.append([rng.standard_normal(n).astype(np.float32) for _ in range(64)])
+    xs = [pools[m][i % 64] for i, m in enumerate(model)]
+    admitted, refused = [], []
+    with ClockSampler(local_rank) as clk, W.Server(budget, max_batch=8, nstreams=8) as srv:
+        ids = {}
+        for k, h in enumerate(handles):
+            try:
+                ids[k] = srv.add_model(h, DECAY)
+                admitted.append(k)
+            except W.WhffError:
+                refused.append(k)
+        keep = np.isin(model, admitted)
+        remap = np.array([ids.get(k, -1) for k in range(len(orders))])
+        m_ids = remap[model[keep]]
+        xs_k = [x for x, kp in zip(xs, keep) if kp]
+        # short warm-up trace (first 200 requests' pattern), then the measured trace
+        drop = args.deadline_us * 1e-6 if args.firm else 0.0
+        srv.run(m_ids[:200], arrival[keep][:200] - arrival[keep][0], xs_k[:200], drop_after_s=drop)
+        lat, bat, _, status = srv.run(m_ids, arrival[keep], xs_k, max_wait_s=args.serve_seconds * 60 + 60,
+                                      drop_after_s=drop, return_status=True)
+    clocks = clk.summary()
+    lat_us = lat * 1e6
+    served = status != 2
+    miss = (status != 0) | (lat_us > args.deadline_us)
+
+    def pct(v, q):
+        return float(np.percentile(v, q)) if v.size else None
+
+    per = {}
+    for k in admitted:
+        sel = model[keep] == k
+        l = lat_us[sel & served]
+        per[f"N={orders[k]}#{k}"] = {"requests": int(sel.sum()), "served": int((sel & served).sum()),
+                                   "p50_us": pct(l, 50), "p99_us": pct(l, 99), "p999_us": pct(l, 99.9),
+                                   "miss_rate": float(miss[sel].mean()),
+                                   "mean_batch": float(bat[sel & served].mean()) if l.size else 0.0,
+                                   "pass_bytes": blobs_bytes[k]}
+    passes = sum(1.0 / b for b in bat[served])  # each pass counted once over its requests
+    streamed = sum(blobs_bytes[model[keep][i]] / bat[i] for i in np.nonzero(served)[0])
+    wall = float(np.max(arrival[keep] + lat)) if len(arrival) else 0.0
+    lat_us = lat_us[served]
+    for h in handles:
+        h.destroy()
+    return {
+        "mode": "serve", "metric": "serving: p50/p99/p99.9 control-step latency and deadline misses",
+        "value": float(np.percentile(lat_us, 99)), "unit": "us (p99, all requests)", "higher_is_better": False,
+        "n_gpus": world, "config": {"workload": f"serving-{len(orders)}-models-{fmt_name}-{rate}", "orders": orders,
+                                    "arrival_hz_per_model": args.serve_hz, "seconds": args.serve_seconds,
+                                    "deadline_us": args.deadline_us, "max_batch": 8, "streams": 8,
+                                    "hbm_budget_bytes": budget},
+        "admitted": admitted, "refused": refused, "requests": int(keep.sum()),
+        "p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
+        "p999_us": float(np.percentile(lat_us, 99.9)), "miss_rate": float(miss.mean()),
+        "dropped": int((status == 2).sum()), "firm": bool(args.firm),
+        "passes": round(passes), "mean_batch": float(np.mean(bat[served])),
+        "streamed_GB_s": round(streamed / max(wall, 1e-9) / 1e9, 1), "per_model": per, "clocks": clocks,
+        "setup_s": round(setup_s, 1),
+    }
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
     """The CPU oracle as it stands, on the host cores, on the same workload and metric:
@@ -461,6 +568,8 @@ def main():
         if rank != 0:
             return
         res = run_reference(args, rank, world)
+    elif args.serve:
+        res = run_serve(args, rank, world, local_rank)
     else:
         if world > 1:
             import torch

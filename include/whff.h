@@ -172,12 +172,18 @@ int whff_server_add_model(whff_server* s, whff_handle* h, double decay, int* mod
 int whff_server_reset_state(whff_server* s, int model_id);
 int whff_server_read_state(whff_server* s, int model_id, double* host_out);
 /* Replay a trace in real time: request i for model[i] arrives arrival_s[i]
- * seconds after the start (non-decreasing) with x[i] (N floats, host).  On
- * return latency_s[i] = completion - arrival as seen by the host, batch[i] =
- * requests in its pass, and y[i] (if y and y[i] are not NULL) holds its M
- * doubles.  WHFF_ETIMEOUT if the run exceeds max_wait_s with requests open. */
+ * seconds after the start (non-decreasing) with x[i] (N floats, host).
+ * Dispatch is earliest-deadline-first; each model runs on its own stream,
+ * smaller models at higher stream priority.  With drop_after_s > 0 the server
+ * is firm real-time (Sec. 1: a late correction is useless): a request still
+ * queued drop_after_s after arrival is discarded.  On return latency_s[i] =
+ * completion - arrival as seen by the host (for a dropped request its age
+ * when discarded), batch[i] = requests in its pass (0 if dropped), status[i]
+ * (optional) = 0 in time, 1 late, 2 dropped, and y[i] (if y and y[i] are not
+ * NULL) holds its M doubles.  WHFF_ETIMEOUT if the run exceeds max_wait_s. */
 int whff_server_run(whff_server* s, int n, const int* model, const double* arrival_s, const float* const* x,
-                    double* const* y, double* latency_s, int* batch, double max_wait_s);
+                    double* const* y, double* latency_s, int* batch, int* status, double drop_after_s,
+                    double max_wait_s);
 void whff_server_destroy(whff_server* s);
 
 /* Decode the whole matrix to FP64 row-major (ldo >= N) on the device,

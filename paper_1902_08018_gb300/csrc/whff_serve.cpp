@@ -58,13 +58,43 @@ struct whff_server {
   size_t budget = 0, used = 0;
   int max_batch = 8;
   int nbuckets = 4;
-  std::vector<cudaStream_t> streams;
+  std::vector<cudaStream_t> streams;        // capture pool
+  std::vector<cudaStream_t> model_streams;  // one per model, priority by footprint
   std::vector<Model> models;
 };
+
+namespace {
+
+// One stream per model; smaller footprints (shorter passes) get higher priority,
+// so that a cheap model's pass is not stuck behind a long one.
+int make_model_streams(whff_server* s) {
+  for (auto st : s->model_streams) cudaStreamDestroy(st);
+  s->model_streams.clear();
+  int lo = 0, hi = 0;  // CUDA: numerically lower = higher priority
+  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return WHFF_ECUDA;
+  const int nm = (int)s->models.size();
+  std::vector<int> order(nm);
+  for (int i = 0; i < nm; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return s->models[a].footprint < s->models[b].footprint; });
+  std::vector<int> prio(nm, lo);
+  const int levels = lo - hi + 1;
+  for (int rank = 0; rank < nm; ++rank)
+    prio[order[rank]] = hi + (nm > 1 ? (rank * (levels - 1)) / (nm - 1) : 0);
+  for (int i = 0; i < nm; ++i) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio[i]) != cudaSuccess) return WHFF_ECUDA;
+    s->model_streams.push_back(st);
+  }
+  return WHFF_OK;
+}
+
+}  // namespace
 
 extern "C" void whff_server_destroy(whff_server* s) {
   if (!s) return;
   for (auto& st : s->streams) cudaStreamSynchronize(st);
+  for (auto& st : s->model_streams) cudaStreamSynchronize(st);
   for (auto& m : s->models) {
     for (auto* g : m.graphs) whff_graph_destroy(g);
     cudaFree(m.d_state);
@@ -72,6 +102,7 @@ extern "C" void whff_server_destroy(whff_server* s) {
     cudaFreeHost(m.y_pin);
   }
   for (auto& st : s->streams) cudaStreamDestroy(st);
+  for (auto& st : s->model_streams) cudaStreamDestroy(st);
   cudaGetLastError();
   delete s;
 }
@@ -174,14 +205,18 @@ extern "C" int whff_server_read_state(whff_server* s, int model_id, double* host
 
 // Replay a request trace in real time.  Request i is for model[i], arrives at
 // arrival_s[i] seconds after the start (non-decreasing) and carries the N
-// floats at x[i].  On return latency_s[i] = completion - arrival (completion =
-// the moment the host observes the pass's copy of y back), batch[i] = the
-// number of requests in its pass, and, if y[i] is not NULL, the M doubles of
-// its result are stored there.  max_wait_s bounds the whole run (a watchdog:
-// WHFF_ETIMEOUT if it expires with requests still open).
+// floats at x[i].  Dispatch is earliest-deadline-first over the idle models
+// with queued requests; each model's pass runs on its own stream.  With
+// drop_after_s > 0 the server is firm real-time: a request still queued
+// drop_after_s after its arrival is discarded (status 2) instead of served
+// late.  On return latency_s[i] = completion - arrival as seen by the host
+// (for a dropped request: the age at which it was discarded), batch[i] =
+// requests in its pass (0 if dropped), status[i] (if not NULL) = 0 served in
+// time, 1 served late, 2 dropped, and y[i] (if y and y[i] are not NULL) its M
+// doubles.  max_wait_s bounds the whole run (WHFF_ETIMEOUT if it expires).
 extern "C" int whff_server_run(whff_server* s, int n, const int* model, const double* arrival_s,
                                const float* const* x, double* const* y, double* latency_s, int* batch,
-                               double max_wait_s) {
+                               int* status, double drop_after_s, double max_wait_s) {
   if (!s || n < 0 || (n && (!model || !arrival_s || !x || !latency_s || !batch))) {
     set_error("whff_server_run: bad argument");
     return WHFF_EINVAL;
@@ -192,6 +227,10 @@ extern "C" int whff_server_run(whff_server* s, int n, const int* model, const do
       set_error("whff_server_run: bad request " + std::to_string(i));
       return WHFF_EINVAL;
     }
+  if ((int)s->model_streams.size() != nm && make_model_streams(s) != WHFF_OK) {
+    set_error("whff_server_run: cannot create model streams");
+    return WHFF_ECUDA;
+  }
   struct Pass {
     std::vector<int> reqs;
     cudaEvent_t ev = nullptr;
@@ -204,8 +243,8 @@ extern "C" int whff_server_run(whff_server* s, int n, const int* model, const do
       set_error("whff_server_run: cudaEventCreate failed");
       return WHFF_ECUDA;
     }
-  const int nst = (int)s->streams.size();
-  int next_stream = 0, next_arrival = 0, done = 0, rr = 0;
+  const bool firm = drop_after_s > 0.0;
+  int next_arrival = 0, done = 0;
   int err = WHFF_OK;
   const double t0 = now_s();
   while (done < n) {
@@ -235,6 +274,7 @@ extern "C" int whff_server_run(whff_server* s, int n, const int* model, const do
         const int r = p.reqs[k];
         latency_s[r] = tc - arrival_s[r];
         batch[r] = (int)p.reqs.size();
+        if (status) status[r] = (firm && latency_s[r] > drop_after_s) ? 1 : 0;
         if (y && y[r]) std::memcpy(y[r], md.y_pin + k * md.M, (size_t)md.M * 8);
       }
       done += (int)p.reqs.size();
@@ -242,10 +282,27 @@ extern "C" int whff_server_run(whff_server* s, int n, const int* model, const do
       p.busy = false;
     }
     if (err) break;
-    for (int k = 0; k < nm; ++k) {  // dispatch, round robin over models
-      const int m = (rr + k) % nm;
+    if (firm) {  // discard requests whose deadline has already passed
+      const double tn = now_s() - t0;
+      for (int m = 0; m < nm; ++m)
+        while (!queue[m].empty() && tn - arrival_s[queue[m].front()] > drop_after_s) {
+          const int r = queue[m].front();
+          queue[m].pop_front();
+          latency_s[r] = tn - arrival_s[r];
+          batch[r] = 0;
+          if (status) status[r] = 2;
+          ++done;
+        }
+    }
+    for (;;) {  // dispatch: earliest deadline (oldest queued request) first
+      int best = -1;
+      for (int m = 0; m < nm; ++m)
+        if (!inflight[m].busy && !queue[m].empty() &&
+            (best < 0 || arrival_s[queue[m].front()] < arrival_s[queue[best].front()]))
+          best = m;
+      if (best < 0) break;
+      const int m = best;
       Pass& p = inflight[m];
-      if (p.busy || queue[m].empty()) continue;
       const int take = 1 << bucket_of(std::min<int>((int)queue[m].size(), s->max_batch));
       Model& md = s->models[m];
       for (int c = 0; c < take; ++c) {
@@ -254,8 +311,7 @@ extern "C" int whff_server_run(whff_server* s, int n, const int* model, const do
         std::memcpy(md.x_pin + (size_t)c * md.N, x[r], (size_t)md.N * 4);
         p.reqs.push_back(r);
       }
-      cudaStream_t st = s->streams[next_stream];
-      next_stream = (next_stream + 1) % nst;
+      cudaStream_t st = s->model_streams[m];
       int e = whff_graph_launch(md.graphs[bucket_of(take)], st);
       if (e == WHFF_OK && cudaEventRecord(p.ev, st) != cudaSuccess) e = WHFF_ECUDA;
       if (e) {
@@ -264,7 +320,6 @@ extern "C" int whff_server_run(whff_server* s, int n, const int* model, const do
       }
       p.busy = true;
     }
-    rr = (rr + 1) % std::max(nm, 1);
     if (err) break;
   }
   if (err) cudaDeviceSynchronize();

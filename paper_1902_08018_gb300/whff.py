@@ -76,7 +76,7 @@ def library() -> ctypes.CDLL:
         "whff_server_add_model": (c_int, [P, P, dbl, ctypes.POINTER(c_int)]),
         "whff_server_reset_state": (c_int, [P, c_int]),
         "whff_server_read_state": (c_int, [P, c_int, P]),
-        "whff_server_run": (c_int, [P, c_int, P, P, P, P, P, P, dbl]),
+        "whff_server_run": (c_int, [P, c_int, P, P, P, P, P, P, P, dbl, dbl]),
         "whff_server_destroy": (None, [P]),
         "whff_last_error": (ctypes.c_char_p, []),
         "whff_version": (ctypes.c_char_p, []),
@@ -354,9 +354,10 @@ class Server:
         _check(library().whff_server_read_state(self._ptr, model_id, out.ctypes.data))
         return out
 
-    def run(self, model, arrival_s, xs, want_y: bool = False, max_wait_s: float = 600.0):
+    def run(self, model, arrival_s, xs, want_y: bool = False, max_wait_s: float = 600.0,
+            drop_after_s: float = 0.0, return_status: bool = False):
         """model: int array, arrival_s: float array (non-decreasing), xs: list of float32 host
-        vectors.  Returns (latency_s, batch, ys or None)."""
+        vectors.  Returns (latency_s, batch, ys or None[, status])."""
         n = len(model)
         model = np.ascontiguousarray(model, dtype=np.int32)
         arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
@@ -369,9 +370,11 @@ class Server:
             yptr = (ctypes.c_void_p * n)(*[v.ctypes.data for v in ys])
         lat = np.empty(n, dtype=np.float64)
         bat = np.empty(n, dtype=np.int32)
+        st = np.empty(n, dtype=np.int32)
         _check(library().whff_server_run(self._ptr, n, model.ctypes.data, arr.ctypes.data, xptr, yptr,
-                                         lat.ctypes.data, bat.ctypes.data, float(max_wait_s)))
-        return lat, bat, ys
+                                         lat.ctypes.data, bat.ctypes.data, st.ctypes.data, float(drop_after_s),
+                                         float(max_wait_s)))
+        return (lat, bat, ys, st) if return_status else (lat, bat, ys)
 
     def destroy(self):
         if self._ptr:

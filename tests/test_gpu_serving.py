@@ -126,3 +126,31 @@ def test_server_admission_by_footprint(env):
         assert e.value.code == -8  # WHFF_EBUSY
     h1.destroy()
     h2.destroy()
+
+
+def test_firm_mode_drops_expired_requests(env, orc):
+    # firm real time: a request whose deadline passed while queued is discarded; the
+    # state then follows only the served requests, still in arrival order
+    W, torch = env
+    n = 2048
+    blob = W.whff_compress(_matrix(n, 9), 5, 16)
+    h = W.whff_create(blob, max_rhs=8)
+    rng = np.random.default_rng(6)
+    n_req = 200
+    arrival = np.zeros(n_req)  # everything at once: most requests expire in the queue
+    xs = [rng.standard_normal(n).astype(np.float32) for _ in range(n_req)]
+    with W.Server(hbm_budget=8 << 30, max_batch=8, nstreams=1) as srv:
+        mid = srv.add_model(h, decay=0.9)
+        lat, bat, ys, status = srv.run(np.zeros(n_req, dtype=np.int32), arrival, xs, want_y=True,
+                                       drop_after_s=20e-6, return_status=True)
+        state = srv.read_state(mid)
+    assert set(np.unique(status)) <= {0, 1, 2}
+    assert (status == 2).any() and (status != 2).any()
+    assert (bat[status == 2] == 0).all() and (bat[status != 2] > 0).all()
+    Ahat = orc.decode(blob.tobytes())
+    s = np.zeros(n)
+    for i in np.nonzero(status != 2)[0]:
+        assert (ys[i] == _step_alone(W, torch, h, xs[i])).all()
+        s = orc.state_update(s, orc.gemv64(Ahat, xs[i].astype(np.float64)).reshape(n, 1), 0.9)
+    assert np.linalg.norm(state - s) <= 1e-6 * np.linalg.norm(s)
+    h.destroy()
