@@ -154,6 +154,35 @@ int whff_graph_create_host(whff_handle* h, const float* x_host, int R, int64_t l
 int whff_graph_launch(whff_graph* g, void* stream);
 void whff_graph_destroy(whff_graph* g);
 
+/* ------------------------------------------------------- tuning and batches */
+/* Launch shape of the fixed-allocation (WZ2) kernels: blocks kept in flight
+ * per lane (2 or 4) and resident CTAs per SM of the persistent grid (the
+ * arithmetic, and so every result, is the same for every shape).
+ * whff_tune times every candidate on the resident matrix (iters steps each,
+ * R = 1, CUDA events on the stream) and keeps the fastest; *best_ms (optional)
+ * receives its step time.  whff_get_config / whff_set_config read and apply a
+ * shape (e.g. from a cache keyed by format, rate, shape and SM count).  WZ2
+ * handles only (WHFF_EINVAL otherwise). */
+int whff_tune(whff_handle* h, int iters, void* stream, double* best_ms);
+int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_sm);
+int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm);
+
+/* Many resident matrices in one step (uneven sizes, R[i] right-hand sides
+ * each): one persistent launch per right-hand-side class (8, 4, 2, 1) whose
+ * warps split the concatenated block order of all matrices into equal
+ * ranges; R[i] is taken in column groups of 8, then one group of 4, 2, 1.
+ * All matrices must be WZ2 of one format and rate.  whff_batch_step: x[i]
+ * (N_i x R[i], ldx[i]), y[i] (M_i x R[i], ldy[i]), state[i] (M_i, may be NULL,
+ * or state itself NULL) are device pointers; each state is updated for
+ * r = 0..R[i]-1 in order after all of its matrix's columns are computed.
+ * The device work tables of a batch are rewritten by every step: issue the
+ * steps of one batch on one stream (they are ordered there). */
+typedef struct whff_batch whff_batch;
+int whff_batch_create(whff_handle* const* hs, const int* R, int count, whff_batch** b);
+int whff_batch_step(whff_batch* b, const float* const* x, const int64_t* ldx, double* const* y, const int64_t* ldy,
+                    double* const* state, double decay, void* stream);
+void whff_batch_destroy(whff_batch* b);
+
 /* ------------------------------------------------------------- serving layer */
 /* A request server over resident models (Sec. 1: a firm real-time loop that
  * tolerates a missed deadline).  Requests that arrive while a model's

@@ -7,6 +7,7 @@ library is missing it is built from ``csrc/`` with nvcc; if that is not
 possible the import fails loudly -- there is no CPU fallback.
 """
 from .whff import (  # noqa: F401
+    Batch,
     FMT_BF16,
     FMT_FIXED_BFP,
     FMT_FIXED_LIFT,

@@ -18,7 +18,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-Xcompiler", "-fPIC", f"-I{ROOT / 'include'}", f"-I{CSRC}"]
 
-CUDA_SOURCES = ["whff_runtime.cu", "whff_noalloc.cu"]
+CUDA_SOURCES = ["whff_runtime.cu", "whff_noalloc.cu", "wz2_r8.cu", "wz2_r12.cu", "wz2_r16.cu", "wz2_r20.cu",
+                "wz2_r24.cu"]
 HOST_SOURCES = ["whff_encode.cpp", "whff_serve.cpp"]
 
 

@@ -6,9 +6,10 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "gemv_kernels.cuh"
-#include "wz2_kernels.cuh"
+#include "wz2_dispatch.h"
 #include "whff.h"
 #include "whff_blob.h"
 
@@ -44,9 +45,11 @@ struct whff_handle {
   int ksplit = 1;
   int64_t chunk = 0;            // J blocks (WZ1) or columns (scaled) per split
   int ctas_per_sm = 4;          // resident CTAs per SM of the persistent kernels
+  int unroll = 2;               // WZ2: blocks in flight per lane (R = 1 kernel)
   int64_t range_ctas = 0;       // WZ2: CTAs of the range-partitioned persistent grid
   int64_t range_len = 0;        // WZ2: blocks per warp range
   int maxseg = 1;               // WZ2: most ranges sharing one band (1 = none shared)
+  int ws_rhs = 8;               // right-hand sides the workspace is sized for
   cudaStream_t create_stream = nullptr;
 };
 
@@ -143,53 +146,34 @@ int launch_wz1(const whff_handle* h, const float* x, int R, int64_t ldx, bool ve
   }
 }
 
-template <int RATE, bool LIFT>
-int launch_wz2_rate(const whff_handle* h, const float* x, int R, int64_t ldx, bool vec, double* y, int64_t ldy,
-                    double* state, double decay, cudaStream_t st) {
-  // persistent: one wave of CTAs; warp g owns blocks [g*L, (g+1)*L) of the band-major order
-  dim3 grid((unsigned)h->range_ctas);
-  dim3 block(dev::kWarpsPerCta * 32);
-  const uint8_t* s = h->d_stream;
-  const auto& b = h->info;
-#define WZ2_CASE(RR)                                                                                      \
-  case RR:                                                                                                \
-    dev::wz2_gemv_kernel<RATE, LIFT, RR><<<grid, block, 0, st>>>(s, b.M, b.N, h->BM, h->BN, x, ldx, vec, \
-                                                                 h->range_len, h->maxseg, h->d_ws, y,     \
-                                                                 ldy, state, decay);                      \
-    break;
-  switch (R) {
-    WZ2_CASE(1)
-    WZ2_CASE(2)
-    WZ2_CASE(4)
-    WZ2_CASE(8)
-    default:
-      return WHFF_EINVAL;
+int launch_wz2(const whff_handle* h, const float* x, int R, int64_t ldx, bool vec, double* y, int64_t ldy,
+               double* state, double decay, cudaStream_t st) {
+  Wz2Step a{h->d_stream, h->info.M, h->info.N, h->BM, h->BN, x, ldx, vec, h->range_len, h->maxseg, h->d_ws,
+            y, ldy, state, decay, h->range_ctas, R == 1 ? h->unroll : 2, h->info.fmt == WHFF_FMT_FIXED_LIFT, R};
+  int e;
+  switch (h->info.rate) {
+    case 8: e = wz2_launch<8>(a, st); break;
+    case 12: e = wz2_launch<12>(a, st); break;
+    case 16: e = wz2_launch<16>(a, st); break;
+    case 20: e = wz2_launch<20>(a, st); break;
+    case 24: e = wz2_launch<24>(a, st); break;
+    default: e = -1;
   }
-#undef WZ2_CASE
-  if (h->maxseg > 1) {
-    dev::wz2_segment_epilogue<<<(unsigned)((b.M + 255) / 256), 256, 0, st>>>(h->d_ws, b.M, h->BN, h->range_len,
-                                                                            h->maxseg, R, y, ldy, state, decay);
+  if (e) {
+    set_error("whff_step: WZ2 rates are 8..24 in steps of 4 and R 1, 2, 4 or 8 per pass");
+    return WHFF_EINVAL;
   }
   return WHFF_OK;
 }
 
-template <bool LIFT>
-int launch_wz2(const whff_handle* h, const float* x, int R, int64_t ldx, bool vec, double* y, int64_t ldy,
-               double* state, double decay, cudaStream_t st) {
-  switch (h->info.rate) {
-    case 8:
-      return launch_wz2_rate<8, LIFT>(h, x, R, ldx, vec, y, ldy, state, decay, st);
-    case 12:
-      return launch_wz2_rate<12, LIFT>(h, x, R, ldx, vec, y, ldy, state, decay, st);
-    case 16:
-      return launch_wz2_rate<16, LIFT>(h, x, R, ldx, vec, y, ldy, state, decay, st);
-    case 20:
-      return launch_wz2_rate<20, LIFT>(h, x, R, ldx, vec, y, ldy, state, decay, st);
-    case 24:
-      return launch_wz2_rate<24, LIFT>(h, x, R, ldx, vec, y, ldy, state, decay, st);
-    default:
-      set_error("whff_step: WZ2 rates are 8..24 in steps of 4");
-      return WHFF_EINVAL;
+int wz2_occ(int rate, bool lift, int unroll) {
+  switch (rate) {
+    case 8: return wz2_occupancy<8>(lift, unroll);
+    case 12: return wz2_occupancy<12>(lift, unroll);
+    case 16: return wz2_occupancy<16>(lift, unroll);
+    case 20: return wz2_occupancy<20>(lift, unroll);
+    case 24: return wz2_occupancy<24>(lift, unroll);
+    default: return 0;
   }
 }
 
@@ -231,10 +215,8 @@ int launch_pass(const whff_handle* h, const float* x, int R, int64_t ldx, double
       e = launch_wz1(h, x, R, ldx, vec, y, ldy, state, decay, st);
       break;
     case WHFF_FMT_FIXED_LIFT:
-      e = launch_wz2<true>(h, x, R, ldx, vec, y, ldy, state, decay, st);
-      break;
     case WHFF_FMT_FIXED_BFP:
-      e = launch_wz2<false>(h, x, R, ldx, vec, y, ldy, state, decay, st);
+      e = launch_wz2(h, x, R, ldx, vec, y, ldy, state, decay, st);
       break;
     case WHFF_FMT_BF16:
       e = launch_scaled_fmt<2>(h, x, R, ldx, vec, y, ldy, state, decay, st);
@@ -299,27 +281,8 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
   }
   h->Mpad = 4 * ceil_div(info.M, 4);
   if (info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) {
-    // resident CTAs per SM of the persistent kernel (same for every R <= 8 within 1)
-    int occ = 0;
-    const bool lift = info.fmt == WHFF_FMT_FIXED_LIFT;
-    cudaError_t oe = cudaErrorInvalidValue;
-#define OCC(RT)                                                                                              \
-  case RT:                                                                                                   \
-    oe = lift ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RT, true, 1>,     \
-                                                              dev::kWarpsPerCta * 32, 0)                    \
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RT, false, 1>,    \
-                                                              dev::kWarpsPerCta * 32, 0);                   \
-    break;
-    switch (info.rate) {
-      OCC(8) OCC(12) OCC(16) OCC(20) OCC(24)
-      default: break;
-    }
-#undef OCC
-    if (oe != cudaSuccess || occ <= 0) {
-      cudaGetLastError();
-      occ = 4;
-    }
-    h->ctas_per_sm = occ;
+    const int occ = wz2_occ(info.rate, info.fmt == WHFF_FMT_FIXED_LIFT, h->unroll);
+    h->ctas_per_sm = occ > 0 ? occ : 4;
   }
   if (is_blocked(info.fmt)) {
     h->BM = ceil_div(info.M, 4);
@@ -335,6 +298,7 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
   h->ws_bytes = h->ksplit > 1 ? (size_t)h->ksplit * (size_t)std::min(max_rhs, kMaxRhsKernel) * (size_t)h->Mpad * 8 : 0;
   if (h->maxseg > 1)
     h->ws_bytes = (size_t)h->BM * (size_t)h->maxseg * (size_t)std::min(max_rhs, kMaxRhsKernel) * 4 * 8;
+  h->ws_rhs = std::min(max_rhs, kMaxRhsKernel);
   if ((h->ws_bytes && cudaMalloc(&h->d_ws, h->ws_bytes) != cudaSuccess) ||
       cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->d_x, (size_t)info.N * (size_t)max_rhs * sizeof(float)) != cudaSuccess ||
@@ -563,22 +527,20 @@ extern "C" int whff_decompress(whff_handle* h, double* out, int64_t ldo, void* s
 #undef DZ
   } else if (is_blocked(b.fmt)) {
     const int64_t nb = h->BM * h->BN;
-    const unsigned grid = (unsigned)((nb + threads - 1) / threads);
     const bool lift = b.fmt == WHFF_FMT_FIXED_LIFT;
-#define D2(R_)                                                                                                  \
-  case R_:                                                                                                      \
-    if (lift)                                                                                                   \
-      dev::wz2_decompress_kernel<R_, true><<<grid, threads, 0, st>>>(h->d_stream, b.M, b.N, h->BN, nb, out, ldo); \
-    else                                                                                                        \
-      dev::wz2_decompress_kernel<R_, false><<<grid, threads, 0, st>>>(h->d_stream, b.M, b.N, h->BN, nb, out, ldo); \
-    break;
+    int e;
     switch (b.rate) {
-      D2(8) D2(12) D2(16) D2(20) D2(24)
-      default:
-        set_error("whff_decompress: unsupported WZ2 rate");
-        return WHFF_EINVAL;
+      case 8: e = wz2_decompress<8>(h->d_stream, b.M, b.N, h->BN, nb, out, ldo, lift, st); break;
+      case 12: e = wz2_decompress<12>(h->d_stream, b.M, b.N, h->BN, nb, out, ldo, lift, st); break;
+      case 16: e = wz2_decompress<16>(h->d_stream, b.M, b.N, h->BN, nb, out, ldo, lift, st); break;
+      case 20: e = wz2_decompress<20>(h->d_stream, b.M, b.N, h->BN, nb, out, ldo, lift, st); break;
+      case 24: e = wz2_decompress<24>(h->d_stream, b.M, b.N, h->BN, nb, out, ldo, lift, st); break;
+      default: e = -1;
     }
-#undef D2
+    if (e) {
+      set_error("whff_decompress: unsupported WZ2 rate");
+      return WHFF_EINVAL;
+    }
   } else {
     const int64_t ld = scaled_ld(b.N), TN = ceil_div(b.N, kScaleTile);
     const float* scales =
@@ -622,4 +584,328 @@ extern "C" void whff_destroy(whff_handle* h) {
   cudaFree(h->d_y);
   cudaGetLastError();
   delete h;
+}
+
+// ------------------------------------------------------------------ tuning
+namespace {
+
+int apply_config(whff_handle* h, int unroll, int ctas_per_sm) {
+  h->unroll = unroll;
+  h->ctas_per_sm = ctas_per_sm;
+  choose_ranges(h);
+  const size_t need = h->maxseg > 1 ? (size_t)h->BM * (size_t)h->maxseg * (size_t)h->ws_rhs * 4 * 8 : 0;
+  if (need > h->ws_bytes) {
+    cudaFree(h->d_ws);
+    h->d_ws = nullptr;
+    if (cudaMalloc(&h->d_ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      h->ws_bytes = 0;
+      set_error("whff_set_config: workspace allocation failed");
+      return WHFF_ENOMEM;
+    }
+    h->ws_bytes = need;
+  }
+  return WHFF_OK;
+}
+
+bool is_wz2(const whff_handle* h) {
+  return h->info.fmt == WHFF_FMT_FIXED_LIFT || h->info.fmt == WHFF_FMT_FIXED_BFP;
+}
+
+}  // namespace
+
+extern "C" int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_sm) {
+  if (!h) {
+    set_error("whff_get_config: null handle");
+    return WHFF_EINVAL;
+  }
+  if (unroll) *unroll = h->unroll;
+  if (ctas_per_sm) *ctas_per_sm = h->ctas_per_sm;
+  return WHFF_OK;
+}
+
+extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm) {
+  if (!h || !is_wz2(h) || (unroll != 2 && unroll != 4) || ctas_per_sm < 1) {
+    set_error("whff_set_config: WZ2 handles only; unroll 2 or 4; ctas_per_sm >= 1");
+    return WHFF_EINVAL;
+  }
+  const int occ = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, unroll);
+  if (occ <= 0 || ctas_per_sm > occ) {
+    set_error("whff_set_config: more CTAs per SM than can be resident");
+    return WHFF_EINVAL;
+  }
+  return apply_config(h, unroll, ctas_per_sm);
+}
+
+// Time every (unroll, CTAs per SM) candidate on this matrix with R = 1 and
+// keep the fastest.  Uses the handle's own staging buffers (x = 0).
+extern "C" int whff_tune(whff_handle* h, int iters, void* stream, double* best_ms) {
+  if (!h || !is_wz2(h) || iters < 1) {
+    set_error("whff_tune: WZ2 handles only, iters >= 1");
+    return WHFF_EINVAL;
+  }
+  const cudaStream_t st = as_stream(stream);
+  WHFF_CUDA_TRY(cudaMemsetAsync(h->d_x, 0, (size_t)h->info.N * 4, st));
+  cudaEvent_t e0, e1;
+  WHFF_CUDA_TRY(cudaEventCreate(&e0));
+  WHFF_CUDA_TRY(cudaEventCreate(&e1));
+  const int orig_u = h->unroll, orig_c = h->ctas_per_sm;
+  double best = 1e30;
+  int bu = orig_u, bc = orig_c;
+  int err = WHFF_OK;
+  for (int u : {2, 4}) {
+    const int occ = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, u);
+    for (int c = occ; c >= 1 && c >= occ - 2; --c) {
+      if ((err = apply_config(h, u, c)) != WHFF_OK) break;
+      if ((err = whff_step(h, h->d_x, 1, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream)) != WHFF_OK) break;
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < iters && err == WHFF_OK; ++k)
+        err = whff_step(h, h->d_x, 1, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) err = WHFF_ECUDA;
+      if (err) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / iters < best) {
+        best = ms / iters;
+        bu = u;
+        bc = c;
+      }
+    }
+    if (err) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err) {
+    apply_config(h, orig_u, orig_c);
+    return err;
+  }
+  if (best_ms) *best_ms = best;
+  return apply_config(h, bu, bc);
+}
+
+// ------------------------------------------------------------------ batches
+struct whff_batch {
+  struct Group {
+    int R = 1;
+    std::vector<int> members;          // (handle index, column offset) pairs flattened below
+    std::vector<int> col0;
+    std::vector<dev::BatchEntry> host;  // filled per step
+    dev::BatchEntry* d_entries = nullptr;
+    int64_t* d_row_begin = nullptr;
+    std::vector<double*> ws;
+    int64_t total_blocks = 0, total_rows = 0, L = 1, ctas = 1;
+    bool any_shared = false;
+  };
+  std::vector<whff_handle*> hs;
+  int rate = 0;
+  bool lift = true;
+  std::vector<Group> groups;
+  dev::BatchEntry* pinned = nullptr;   // staging for the table uploads
+  size_t pinned_entries = 0;
+  dev::BatchState* state_pinned = nullptr;
+  dev::BatchState* d_state = nullptr;
+  int64_t* d_state_rows = nullptr;
+  int64_t state_rows = 0;
+  std::vector<int> R;
+  cudaEvent_t copied = nullptr;        // the last step's table copies have been read
+};
+
+extern "C" void whff_batch_destroy(whff_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  for (auto& g : b->groups) {
+    cudaFree(g.d_entries);
+    cudaFree(g.d_row_begin);
+    for (double* w : g.ws) cudaFree(w);
+  }
+  if (b->copied) cudaEventDestroy(b->copied);
+  cudaFreeHost(b->pinned);
+  cudaFreeHost(b->state_pinned);
+  cudaFree(b->d_state);
+  cudaFree(b->d_state_rows);
+  cudaGetLastError();
+  delete b;
+}
+
+// Plan one persistent launch per right-hand-side class (1, 2, 4, 8) over
+// count resident matrices of one WZ2 format and rate; R[i] may be any
+// positive count, taken in column groups of 8, 4, 2, 1 (a matrix with 32
+// right-hand sides enters the R = 8 launch four times).
+extern "C" int whff_batch_create(whff_handle* const* hs, const int* R, int count, whff_batch** out) {
+  if (!hs || !R || !out || count < 1) {
+    set_error("whff_batch_create: bad argument");
+    return WHFF_EINVAL;
+  }
+  *out = nullptr;
+  auto* b = new whff_batch;
+  b->hs.assign(hs, hs + count);
+  b->rate = hs[0]->info.rate;
+  b->lift = hs[0]->info.fmt == WHFF_FMT_FIXED_LIFT;
+  for (int i = 0; i < count; ++i)
+    if (!hs[i] || !is_wz2(hs[i]) || hs[i]->info.rate != b->rate || is_wz2(hs[i]) != is_wz2(hs[0]) ||
+        (hs[i]->info.fmt == WHFF_FMT_FIXED_LIFT) != b->lift || R[i] < 1) {
+      whff_batch_destroy(b);
+      set_error("whff_batch_create: all matrices must be resident WZ2 of one format and rate, R >= 1");
+      return WHFF_EINVAL;
+    }
+  const int classes[4] = {8, 4, 2, 1};
+  for (int cls : classes) {
+    whff_batch::Group g;
+    g.R = cls;
+    for (int i = 0; i < count; ++i) {
+      int c = 0, left = R[i];
+      for (int k : classes) {  // decompose R[i] into 8s, then one 4, 2, 1
+        while (left >= k && (k == 8 || left < 2 * k)) {
+          if (k == cls) {
+            g.members.push_back(i);
+            g.col0.push_back(c);
+          }
+          c += k;
+          left -= k;
+        }
+      }
+    }
+    if (!g.members.empty()) b->groups.push_back(g);
+  }
+  const whff_handle* h0 = hs[0];
+  for (auto& g : b->groups) {
+    const int n = (int)g.members.size();
+    g.host.resize(n);
+    int64_t blocks = 0, rows = 0;
+    std::vector<int64_t> row_begin(n);
+    for (int k = 0; k < n; ++k) {
+      const whff_handle* h = hs[g.members[k]];
+      g.host[k].block_begin = blocks;
+      row_begin[k] = rows;
+      blocks += h->BM * h->BN;
+      rows += h->info.M;
+    }
+    g.total_blocks = blocks;
+    g.total_rows = rows;
+    const int occ = wz2_occ(b->rate, b->lift, g.R == 1 ? 2 : 1);
+    const int64_t warps_cap = (int64_t)h0->sm_count * std::max(occ, 1) * dev::kWarpsPerCta;
+    int64_t warps = std::min<int64_t>(warps_cap, std::max<int64_t>(1, (blocks + 63) / 64));
+    warps = (warps + dev::kWarpsPerCta - 1) / dev::kWarpsPerCta * dev::kWarpsPerCta;
+    g.ctas = warps / dev::kWarpsPerCta;
+    g.L = (blocks + warps - 1) / warps;
+    for (int k = 0; k < n; ++k) {
+      const whff_handle* h = hs[g.members[k]];
+      int maxseg = 1;
+      for (int64_t I = 0; I < h->BM; ++I) {
+        const int64_t first = g.host[k].block_begin + I * h->BN;
+        maxseg = (int)std::max<int64_t>(maxseg, (first + h->BN - 1) / g.L - first / g.L + 1);
+      }
+      g.host[k].maxseg = maxseg;
+      double* w = nullptr;
+      if (maxseg > 1) {
+        g.any_shared = true;
+        if (cudaMalloc(&w, (size_t)h->BM * maxseg * g.R * 4 * 8) != cudaSuccess) {
+          cudaGetLastError();
+          whff_batch_destroy(b);
+          set_error("whff_batch_create: workspace allocation failed");
+          return WHFF_ENOMEM;
+        }
+      }
+      g.ws.push_back(w);
+    }
+    if (cudaMalloc(&g.d_entries, sizeof(dev::BatchEntry) * n) != cudaSuccess ||
+        cudaMalloc(&g.d_row_begin, sizeof(int64_t) * n) != cudaSuccess ||
+        cudaMemcpy(g.d_row_begin, row_begin.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      whff_batch_destroy(b);
+      set_error("whff_batch_create: table allocation failed");
+      return WHFF_ENOMEM;
+    }
+    b->pinned_entries += n;
+  }
+  b->R.assign(R, R + count);
+  std::vector<int64_t> srows(count);
+  for (int i = 0; i < count; ++i) {
+    srows[i] = b->state_rows;
+    b->state_rows += hs[i]->info.M;
+  }
+  if (cudaMallocHost(&b->state_pinned, sizeof(dev::BatchState) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_state, sizeof(dev::BatchState) * count) != cudaSuccess ||
+      cudaMalloc(&b->d_state_rows, sizeof(int64_t) * count) != cudaSuccess ||
+      cudaMemcpy(b->d_state_rows, srows.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    whff_batch_destroy(b);
+    set_error("whff_batch_create: state table allocation failed");
+    return WHFF_ENOMEM;
+  }
+  if (cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&b->pinned, sizeof(dev::BatchEntry) * b->pinned_entries) != cudaSuccess) {
+    cudaGetLastError();
+    whff_batch_destroy(b);
+    set_error("whff_batch_create: pinned staging allocation failed");
+    return WHFF_ENOMEM;
+  }
+  *out = b;
+  return WHFF_OK;
+}
+
+// One step of every matrix of the batch: x[i] (N_i x R_i, ldx[i]), y[i]
+// (M_i x R_i, ldy[i]) and state[i] (M_i or NULL) are device pointers; the
+// state update keeps the column order r = 0..R_i-1 (the column groups of a
+// matrix run in order: R = 8 launches first, then 4, 2, 1).
+extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64_t* ldx, double* const* y,
+                               const int64_t* ldy, double* const* state, double decay, void* stream) {
+  if (!b || !x || !ldx || !y || !ldy) {
+    set_error("whff_batch_step: bad argument");
+    return WHFF_EINVAL;
+  }
+  const cudaStream_t st = as_stream(stream);
+  // the pinned tables are reused: wait until the previous step's copies ran
+  WHFF_CUDA_TRY(cudaEventSynchronize(b->copied));
+  size_t off = 0;
+  for (auto& g : b->groups) {
+    const int n = (int)g.members.size();
+    for (int k = 0; k < n; ++k) {
+      const int i = g.members[k];
+      const whff_handle* h = b->hs[i];
+      dev::BatchEntry& e = g.host[k];
+      e.stream = h->d_stream;
+      e.x = x[i] + (int64_t)g.col0[k] * ldx[i];
+      e.y = y[i] + (int64_t)g.col0[k] * ldy[i];
+      e.state = nullptr;  // the state is applied once per matrix after all groups
+      e.ws = g.ws[k];
+      e.M = h->info.M;
+      e.N = h->info.N;
+      e.BM = h->BM;
+      e.BN = h->BN;
+      e.ldx = ldx[i];
+      e.ldy = ldy[i];
+      e.decay = decay;
+      b->pinned[off + k] = e;
+    }
+    WHFF_CUDA_TRY(cudaMemcpyAsync(g.d_entries, b->pinned + off, sizeof(dev::BatchEntry) * n,
+                                  cudaMemcpyHostToDevice, st));
+    Wz2Batch a{g.d_entries, g.d_row_begin, n, g.total_blocks, g.total_rows, g.L, g.ctas, g.any_shared, b->lift, g.R};
+    int e;
+    switch (b->rate) {
+      case 8: e = wz2_batched_launch<8>(a, st); break;
+      case 12: e = wz2_batched_launch<12>(a, st); break;
+      case 16: e = wz2_batched_launch<16>(a, st); break;
+      case 20: e = wz2_batched_launch<20>(a, st); break;
+      case 24: e = wz2_batched_launch<24>(a, st); break;
+      default: e = -1;
+    }
+    if (e) {
+      set_error("whff_batch_step: launch failed");
+      return WHFF_EINVAL;
+    }
+    off += n;
+  }
+  if (state) {
+    const int count = (int)b->hs.size();
+    for (int i = 0; i < count; ++i)
+      b->state_pinned[i] = dev::BatchState{state[i], y[i], ldy[i], b->hs[i]->info.M, b->R[i], decay};
+    WHFF_CUDA_TRY(cudaMemcpyAsync(b->d_state, b->state_pinned, sizeof(dev::BatchState) * count,
+                                  cudaMemcpyHostToDevice, st));
+    wz2_batched_state_launch(b->d_state, b->d_state_rows, count, b->state_rows, st);
+  }
+  WHFF_CUDA_TRY(cudaEventRecord(b->copied, st));
+  WHFF_CUDA_TRY(cudaGetLastError());
+  return WHFF_OK;
 }

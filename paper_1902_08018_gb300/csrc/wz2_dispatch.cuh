@@ -1,0 +1,96 @@
+// wz2_dispatch.cuh -- definitions behind wz2_dispatch.h; included once per
+// rate by wz2_r<rate>.cu, which instantiates them for that rate.
+#pragma once
+#include "wz2_dispatch.h"
+#include "wz2_kernels.cuh"
+
+namespace whff {
+
+template <int RATE, bool LIFT, int R, int U>
+static void wz2_launch_one(const Wz2Step& a, cudaStream_t st) {
+  dev::wz2_gemv_kernel<RATE, LIFT, R, U><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
+      a.stream, a.M, a.N, a.BM, a.BN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg, a.ws, a.y, a.ldy, a.state, a.decay);
+}
+
+template <int RATE, bool LIFT>
+static int wz2_launch_lift(const Wz2Step& a, cudaStream_t st) {
+  switch (a.R) {
+    case 1:
+      if (a.unroll == 4) wz2_launch_one<RATE, LIFT, 1, 4>(a, st);
+      else wz2_launch_one<RATE, LIFT, 1, 2>(a, st);
+      break;
+    case 2: wz2_launch_one<RATE, LIFT, 2, 2>(a, st); break;
+    case 4: wz2_launch_one<RATE, LIFT, 4, 2>(a, st); break;
+    case 8: wz2_launch_one<RATE, LIFT, 8, 2>(a, st); break;
+    default: return -1;
+  }
+  if (a.maxseg > 1)
+    dev::wz2_segment_epilogue<<<(unsigned)((a.M + 255) / 256), 256, 0, st>>>(a.ws, a.M, a.BN, a.L, a.maxseg, a.R,
+                                                                            a.y, a.ldy, a.state, a.decay);
+  return 0;
+}
+
+template <int RATE>
+int wz2_launch(const Wz2Step& a, cudaStream_t st) {
+  return a.lift ? wz2_launch_lift<RATE, true>(a, st) : wz2_launch_lift<RATE, false>(a, st);
+}
+
+template <int RATE, bool LIFT, int R>
+static void wz2_batched_one(const Wz2Batch& b, cudaStream_t st) {
+  constexpr int U = 2;
+  dev::wz2_batched_kernel<RATE, LIFT, R, U><<<(unsigned)b.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
+      b.entries, b.nentries, b.total_blocks, b.L);
+}
+
+template <int RATE>
+int wz2_batched_launch(const Wz2Batch& b, cudaStream_t st) {
+#define WZ2B(LF, RR) \
+  if (b.lift == LF && b.R == RR) wz2_batched_one<RATE, LF, RR>(b, st);
+  WZ2B(true, 1) WZ2B(true, 2) WZ2B(true, 4) WZ2B(true, 8)
+  WZ2B(false, 1) WZ2B(false, 2) WZ2B(false, 4) WZ2B(false, 8)
+#undef WZ2B
+  if (b.R != 1 && b.R != 2 && b.R != 4 && b.R != 8) return -1;
+  if (b.any_shared)
+    dev::wz2_batched_epilogue<<<(unsigned)((b.total_rows + 255) / 256), 256, 0, st>>>(b.entries, b.row_begin,
+                                                                                     b.nentries, b.total_rows, b.L,
+                                                                                     b.R);
+  return 0;
+}
+
+template <int RATE>
+int wz2_decompress(const uint8_t* stream, int64_t M, int64_t N, int64_t BN, int64_t nblocks, double* out,
+                   int64_t ldo, bool lift, cudaStream_t st) {
+  const unsigned grid = (unsigned)((nblocks + 255) / 256);
+  if (lift)
+    dev::wz2_decompress_kernel<RATE, true><<<grid, 256, 0, st>>>(stream, M, N, BN, nblocks, out, ldo);
+  else
+    dev::wz2_decompress_kernel<RATE, false><<<grid, 256, 0, st>>>(stream, M, N, BN, nblocks, out, ldo);
+  return 0;
+}
+
+template <int RATE>
+int wz2_occupancy(bool lift, int unroll) {
+  int occ = 0;
+  cudaError_t e;
+  const int threads = dev::kWarpsPerCta * 32;
+  if (lift)
+    e = unroll == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, true, 1, 4>, threads, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, true, 1, 2>, threads, 0);
+  else
+    e = unroll == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, false, 1, 4>, threads, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, false, 1, 2>, threads, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ;
+}
+
+}  // namespace whff
+
+#define WHFF_INSTANTIATE_WZ2(RATE)                                                                            \
+  template int whff::wz2_launch<RATE>(const whff::Wz2Step&, cudaStream_t);                                    \
+  template int whff::wz2_batched_launch<RATE>(const whff::Wz2Batch&, cudaStream_t);                           \
+  template int whff::wz2_decompress<RATE>(const uint8_t*, int64_t, int64_t, int64_t, int64_t, double*, int64_t, \
+                                          bool, cudaStream_t);                                                \
+  template int whff::wz2_occupancy<RATE>(bool, int);

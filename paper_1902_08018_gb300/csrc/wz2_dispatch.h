@@ -1,0 +1,58 @@
+// wz2_dispatch.h -- host-side entry points of the WZ2 kernels, one translation
+// unit per rate (wz2_r<rate>.cu) so that the instantiations build in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "wz2_batch.h"
+
+namespace whff {
+
+struct Wz2Step {
+  const uint8_t* stream;
+  int64_t M, N, BM, BN;
+  const float* x;
+  int64_t ldx;
+  bool x_vec_ok;
+  int64_t L;       // blocks per warp range
+  int maxseg;      // most ranges sharing one band
+  double* ws;
+  double* y;
+  int64_t ldy;
+  double* state;
+  double decay;
+  int64_t ctas;    // grid size (persistent)
+  int unroll;      // blocks in flight per lane: 2 or 4 (R = 1), 2 otherwise
+  bool lift;
+  int R;           // 1, 2, 4 or 8
+};
+
+
+struct Wz2Batch {
+  const dev::BatchEntry* entries;  // device table
+  const int64_t* row_begin;        // device prefix of rows
+  int nentries;
+  int64_t total_blocks, total_rows, L;
+  int64_t ctas;
+  bool any_shared;                 // some band is split between warp ranges
+  bool lift;
+  int R;
+};
+
+// state step of a batch (rate independent; defined in the rate-16 unit)
+int wz2_batched_state_launch(const dev::BatchState* table, const int64_t* row_begin, int n, int64_t total_rows,
+                             cudaStream_t st);
+
+template <int RATE>
+int wz2_launch(const Wz2Step& a, cudaStream_t st);
+template <int RATE>
+int wz2_batched_launch(const Wz2Batch& b, cudaStream_t st);
+template <int RATE>
+int wz2_decompress(const uint8_t* stream, int64_t M, int64_t N, int64_t BN, int64_t nblocks, double* out,
+                   int64_t ldo, bool lift, cudaStream_t st);
+// resident CTAs per SM of the R = 1 kernel for the given unroll (0 on error)
+template <int RATE>
+int wz2_occupancy(bool lift, int unroll);
+
+}  // namespace whff

@@ -15,6 +15,7 @@
 #include <cstdint>
 
 #include "gemv_kernels.cuh"
+#include "wz2_batch.h"
 
 namespace whff {
 namespace dev {
@@ -193,22 +194,73 @@ __device__ __forceinline__ void wz2_block_partial(const uint32_t (&w)[Wz2Layout<
   }
 }
 
-// Persistent kernel with exact balance: the G resident warps split the
+// Accumulate the blocks [J0, J1) of one 4-row band (lane l takes J0+l,
+// J0+l+32, ...) into the lane's TwoSum sums.  The arithmetic is fixed: the
+// lane's blocks are taken in pairs (its 1st and 2nd, 3rd and 4th, ...), each
+// pair's two scaled partials are added and the sum enters the TwoSum; an odd
+// last block enters alone.  So every right-hand side gets the same rounding
+// whatever R, UNROLL or the batch it is in.  UNROLL (2 or 4) blocks per lane
+// are kept in flight: their loads are issued before any is decoded.
+template <int RATE, bool LIFT, int R, int UNROLL>
+__device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int64_t J0, int64_t J1, int lane,
+                                          const float* __restrict__ x, int64_t ldx, int64_t N, bool x_fast,
+                                          bool x_vec_ok, float (&hi)[4][R], float (&lo)[4][R]) {
+  static_assert(UNROLL == 2 || UNROLL == 4, "blocks are consumed in pairs");
+  constexpr int NW = Wz2Layout<RATE>::kWords;
+  int64_t J = J0 + lane;
+  for (; J + 32 * (UNROLL - 1) < J1; J += 32 * UNROLL) {
+    uint32_t w[UNROLL][NW];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) wz2_load<RATE>(base, J + 32 * u, w[u]);
+#pragma unroll
+    for (int u = 0; u < UNROLL; u += 2) {
+      float p0[4][R], p1[4][R];
+      wz2_block_partial<RATE, LIFT, R>(w[u], x, ldx, 4 * (J + 32 * u), N, x_fast, x_vec_ok, p0);
+      wz2_block_partial<RATE, LIFT, R>(w[u + 1], x, ldx, 4 * (J + 32 * (u + 1)), N, x_fast, x_vec_ok, p1);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r] + p1[i][r]);
+    }
+  }
+  for (; J + 32 < J1; J += 64) {  // remaining whole pairs
+    uint32_t w0[NW], w1[NW];
+    wz2_load<RATE>(base, J, w0);
+    wz2_load<RATE>(base, J + 32, w1);
+    float p0[4][R], p1[4][R];
+    wz2_block_partial<RATE, LIFT, R>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
+    wz2_block_partial<RATE, LIFT, R>(w1, x, ldx, 4 * (J + 32), N, x_fast, x_vec_ok, p1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r] + p1[i][r]);
+  }
+  if (J < J1) {  // odd last block
+    uint32_t w0[NW];
+    wz2_load<RATE>(base, J, w0);
+    float p0[4][R];
+    wz2_block_partial<RATE, LIFT, R>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r]);
+  }
+}
+
+// Persistent kernel with exact balance: the G warps of the grid split the
 // band-major sequence of all BM*BN blocks into G contiguous ranges of L
 // blocks.  A range covers pieces of one to a few 4-row bands; for every piece
 // the warp folds its lanes' sums and either writes y (and the state) directly,
 // when the band lies inside one range, or stores the piece's partial in
 // ws[band][segment] for wz2_segment_epilogue, which adds a band's segments in
-// order.  Each lane keeps two blocks in flight (both loads issued before
-// either is decoded) and feeds its TwoSum accumulators once per pair.
-template <int RATE, bool LIFT, int R>
+// order.
+template <int RATE, bool LIFT, int R, int UNROLL>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
     wz2_gemv_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BM, int64_t BN,
                     const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int64_t L, int maxseg,
                     double* __restrict__ ws, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
                     double decay) {
-  constexpr int NW = Wz2Layout<RATE>::kWords;
-  constexpr int64_t kBlockBytes = 4 * NW;
+  constexpr int64_t kBlockBytes = 4 * Wz2Layout<RATE>::kWords;
   const int lane = threadIdx.x & 31;
   const int64_t g = (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   const int64_t total = BM * BN;
@@ -218,39 +270,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   while (b0 < b1) {
     const int64_t I = b0 / BN;
     const int64_t piece_end = min(b1, (I + 1) * BN);
-    const int64_t J0 = b0 - I * BN, J1 = piece_end - I * BN;
     const int64_t g_lo = (I * BN) / L, g_hi = ((I + 1) * BN - 1) / L;
-
     float hi[4][R], lo[4][R];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
-
-    const uint8_t* base = stream + (uint64_t)(I * BN) * kBlockBytes;
-    int64_t J = J0 + lane;
-    for (; J + 32 < J1; J += 64) {
-      uint32_t w0[NW], w1[NW];
-      wz2_load<RATE>(base, J, w0);
-      wz2_load<RATE>(base, J + 32, w1);
-      float p0[4][R], p1[4][R];
-      wz2_block_partial<RATE, LIFT, R>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
-      wz2_block_partial<RATE, LIFT, R>(w1, x, ldx, 4 * (J + 32), N, x_fast, x_vec_ok, p1);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r] + p1[i][r]);
-    }
-    if (J < J1) {
-      uint32_t w0[NW];
-      wz2_load<RATE>(base, J, w0);
-      float p0[4][R];
-      wz2_block_partial<RATE, LIFT, R>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r]);
-    }
+    wz2_piece<RATE, LIFT, R, UNROLL>(stream + (uint64_t)(I * BN) * kBlockBytes, b0 - I * BN, piece_end - I * BN,
+                                     lane, x, ldx, N, x_fast, x_vec_ok, hi, lo);
     if (g_lo == g_hi) {  // the whole band is in this range: finish it here
       wz2_finish<LIFT, R>(hi, lo, lane, 4 * I, M, 0, 1, 4 * BM, ws, y, ldy, state, decay);
     } else {  // one segment of a shared band: ws[(band * maxseg + seg) * R + r][i]
@@ -263,9 +290,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
 
 // Sum the segments of bands shared by several warp ranges, in segment order,
 // then the state update (bands inside one range were finished by the kernel).
-__global__ void wz2_segment_epilogue(const double* __restrict__ ws, int64_t M, int64_t BN, int64_t L, int maxseg,
-                                     int R, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
-                                     double decay) {
+static __global__ void wz2_segment_epilogue(const double* __restrict__ ws, int64_t M, int64_t BN, int64_t L,
+                                            int maxseg, int R, double* __restrict__ y, int64_t ldy,
+                                            double* __restrict__ state, double decay) {
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= M) return;
   const int64_t I = row / 4;
@@ -280,6 +307,103 @@ __global__ void wz2_segment_epilogue(const double* __restrict__ ws, int64_t M, i
     s = decay * s + t;
   }
   if (state) state[row] = s;
+}
+
+// ------------------------------------------------------------- batched launch
+// First global block of band I of entry e, and its warp-range span.
+__device__ __forceinline__ void batch_band_span(const BatchEntry& e, int64_t I, int64_t L, int64_t& g_lo,
+                                                int64_t& g_hi) {
+  const int64_t first = e.block_begin + I * e.BN;
+  g_lo = first / L;
+  g_hi = (first + e.BN - 1) / L;
+}
+
+// One persistent launch over all matrices of a batch that share a format,
+// rate and right-hand-side count: the global block order is the entries'
+// band-major orders one after another, split into contiguous warp ranges
+// exactly as for a single matrix.
+template <int RATE, bool LIFT, int R, int UNROLL>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+    wz2_batched_kernel(const BatchEntry* __restrict__ entries, int nentries, int64_t total, int64_t L) {
+  constexpr int64_t kBlockBytes = 4 * Wz2Layout<RATE>::kWords;
+  const int lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  int64_t b0 = g * L;
+  const int64_t b1 = min(total, b0 + L);
+  int ei = 0;
+  while (b0 < b1) {
+    while (ei + 1 < nentries && entries[ei + 1].block_begin <= b0) ++ei;  // warp-uniform
+    const BatchEntry& e = entries[ei];
+    const int64_t local = b0 - e.block_begin;
+    const int64_t I = local / e.BN;
+    const int64_t piece_end = min(b1, e.block_begin + (I + 1) * e.BN);
+    int64_t g_lo, g_hi;
+    batch_band_span(e, I, L, g_lo, g_hi);
+    const bool x_vec_ok = (reinterpret_cast<uintptr_t>(e.x) % 16 == 0) && (e.ldx % 4 == 0);
+    const bool x_fast = x_vec_ok && (e.N % 4 == 0);
+    float hi[4][R], lo[4][R];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
+    wz2_piece<RATE, LIFT, R, UNROLL>(e.stream + (uint64_t)(I * e.BN) * kBlockBytes, local - I * e.BN,
+                                     piece_end - e.block_begin - I * e.BN, lane, e.x, e.ldx, e.N, x_fast, x_vec_ok,
+                                     hi, lo);
+    if (g_lo == g_hi) {
+      wz2_finish<LIFT, R>(hi, lo, lane, 4 * I, e.M, 0, 1, 4 * e.BM, e.ws, e.y, e.ldy, e.state, e.decay);
+    } else {
+      wz2_finish<LIFT, R>(hi, lo, lane, 4 * ((I * e.maxseg + (g - g_lo)) * R), e.M, 0, 2, 0, e.ws, e.y, e.ldy,
+                          e.state, e.decay);
+    }
+    b0 = piece_end;
+  }
+}
+
+// State update of a batch, after every column group has written y: thread per
+// (matrix, row), rows of matrix k are global rows [row_begin[k], +M_k).
+static __global__ void wz2_batched_state(const BatchState* __restrict__ st, const int64_t* __restrict__ row_begin,
+                                         int n, int64_t total_rows) {
+  const int64_t grow = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (grow >= total_rows) return;
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (row_begin[mid] <= grow) lo = mid; else hi = mid - 1;
+  }
+  const BatchState& b = st[lo];
+  if (!b.state) return;
+  const int64_t row = grow - row_begin[lo];
+  double s = b.state[row];
+  for (int r = 0; r < b.R; ++r) s = b.decay * s + b.y[(int64_t)r * b.ldy + row];
+  b.state[row] = s;
+}
+
+// Segment epilogue of a batch: thread per (entry, row); rows of entry e are
+// global rows [row_begin[e], row_begin[e] + M_e).
+static __global__ void wz2_batched_epilogue(const BatchEntry* __restrict__ entries, const int64_t* __restrict__ row_begin,
+                                            int nentries, int64_t total_rows, int64_t L, int R) {
+  const int64_t grow = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (grow >= total_rows) return;
+  int lo = 0, hi = nentries - 1;  // last entry with row_begin <= grow
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (row_begin[mid] <= grow) lo = mid; else hi = mid - 1;
+  }
+  const BatchEntry& e = entries[lo];
+  const int64_t row = grow - row_begin[lo];
+  const int64_t I = row / 4;
+  const int i = (int)(row % 4);
+  int64_t g_lo, g_hi;
+  batch_band_span(e, I, L, g_lo, g_hi);
+  if (g_lo == g_hi) return;
+  double s = e.state ? e.state[row] : 0.0;
+  for (int r = 0; r < R; ++r) {
+    double t = 0.0;
+    for (int64_t seg = 0; seg <= g_hi - g_lo; ++seg) t += e.ws[((I * e.maxseg + seg) * R + r) * 4 + i];
+    e.y[(int64_t)r * e.ldy + row] = t;
+    s = e.decay * s + t;
+  }
+  if (e.state) e.state[row] = s;
 }
 
 template <int RATE, bool LIFT>

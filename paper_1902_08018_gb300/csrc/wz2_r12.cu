@@ -1,0 +1,3 @@
+// WZ2 kernels at rate 12 (bits per value): instantiation unit.
+#include "wz2_dispatch.cuh"
+WHFF_INSTANTIATE_WZ2(12)

@@ -78,6 +78,12 @@ def library() -> ctypes.CDLL:
         "whff_server_read_state": (c_int, [P, c_int, P]),
         "whff_server_run": (c_int, [P, c_int, P, P, P, P, P, P, P, dbl, dbl]),
         "whff_server_destroy": (None, [P]),
+        "whff_tune": (c_int, [P, c_int, P, ctypes.POINTER(dbl)]),
+        "whff_get_config": (c_int, [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "whff_set_config": (c_int, [P, c_int, c_int]),
+        "whff_batch_create": (c_int, [P, P, c_int, ctypes.POINTER(P)]),
+        "whff_batch_step": (c_int, [P, P, P, P, P, P, dbl, P]),
+        "whff_batch_destroy": (None, [P]),
         "whff_last_error": (ctypes.c_char_p, []),
         "whff_version": (ctypes.c_char_p, []),
     }
@@ -165,6 +171,42 @@ class Handle:
     @property
     def ptr(self):
         return self._ptr
+
+    def tune(self, iters: int = 20, stream=None, cache: str | None = None) -> dict:
+        """Pick the fastest launch shape (WZ2); with `cache` (a JSON path) reuse / store the
+        result keyed by format, rate, shape and SM count."""
+        import json
+        import os
+
+        import torch
+
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        key = f"fmt{self.fmt}-rate{self.rate}-{self.M}x{self.N}-sm{sms}"
+        db = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                db = json.load(f)
+        if key in db:
+            self.set_config(db[key]["unroll"], db[key]["ctas_per_sm"])
+            return dict(db[key], cached=True)
+        ms = ctypes.c_double()
+        _check(library().whff_tune(self._ptr, iters, _stream_ptr(stream), ctypes.byref(ms)))
+        u, c = self.config()
+        rec = {"unroll": u, "ctas_per_sm": c, "ms": ms.value}
+        if cache:
+            db[key] = rec
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            with open(cache, "w") as f:
+                json.dump(db, f, indent=1)
+        return dict(rec, cached=False)
+
+    def config(self):
+        u, c = ctypes.c_int(), ctypes.c_int()
+        _check(library().whff_get_config(self._ptr, ctypes.byref(u), ctypes.byref(c)))
+        return u.value, c.value
+
+    def set_config(self, unroll: int, ctas_per_sm: int):
+        _check(library().whff_set_config(self._ptr, unroll, ctas_per_sm))
 
     def plan(self):
         """(ksplit, kernel launches per pass of up to 8 right-hand sides)."""
@@ -379,6 +421,49 @@ class Server:
     def destroy(self):
         if self._ptr:
             library().whff_server_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.destroy()
+
+
+class Batch:
+    """Many resident WZ2 matrices stepped together (whff_batch_create / whff_batch_step)."""
+
+    def __init__(self, handles, R):
+        self.handles = list(handles)
+        self.R = [int(r) for r in R]
+        arr = (ctypes.c_void_p * len(self.handles))(*[h.ptr.value for h in self.handles])
+        rs = (ctypes.c_int * len(self.R))(*self.R)
+        p = ctypes.c_void_p()
+        _check(library().whff_batch_create(arr, rs, len(self.handles), ctypes.byref(p)))
+        self._ptr = p
+
+    def step(self, xs, ys, states=None, decay: float = 0.99, stream=None):
+        """xs[i]: CUDA float32 (R_i, N_i); ys[i]: float64 (R_i, M_i); states[i]: float64 (M_i,) or None."""
+        import torch
+
+        n = len(self.handles)
+        xp, lx, yp, ly = [], [], [], []
+        for i, h in enumerate(self.handles):
+            p, R, ld = _vec_args(xs[i], h.N, "x", torch.float32)
+            q, Ry, ldy = _vec_args(ys[i], h.M, "y", torch.float64)
+            if R != self.R[i] or Ry != self.R[i]:
+                raise WhffError(-1, f"matrix {i}: expected {self.R[i]} right-hand sides")
+            xp.append(p), lx.append(ld), yp.append(q), ly.append(ldy)
+        sp = None
+        if states is not None:
+            sp = (ctypes.c_void_p * n)(*[(s.data_ptr() if s is not None else None) for s in states])
+        _check(library().whff_batch_step(self._ptr, (ctypes.c_void_p * n)(*xp), (ctypes.c_int64 * n)(*lx),
+                                         (ctypes.c_void_p * n)(*yp), (ctypes.c_int64 * n)(*ly), sp, float(decay),
+                                         _stream_ptr(stream)))
+
+    def destroy(self):
+        if self._ptr:
+            library().whff_batch_destroy(self._ptr)
             self._ptr = ctypes.c_void_p()
 
     def __enter__(self):
