@@ -2,10 +2,11 @@
 // their FP64 epilogue (Sec. 4.4: FP32 products, FP64 reduction; Sec. 2.1:
 // carried state), plus the decode-only kernels (Sec. 5.2).
 //
-// Work split: one warp owns one 4-row band of A (one WZ1 block row, or four
-// rows of a scaled format) over a column range; lanes take consecutive 4x4
-// blocks (or 16-byte chunks), so a warp streams one contiguous run of the
-// compressed stream per iteration.  Each lane keeps compensated FP32 sums
+// Work split (WZ1): one warp owns one 4-row band of A (one block row) over a
+// column range; lanes take consecutive 4x4 blocks, so a warp streams one
+// contiguous run of the compressed stream per iteration.  (The fixed-
+// allocation and scaled formats use the persistent range schedule of
+// wz2_kernels.cuh / scaled_kernels.cuh.)  Each lane keeps compensated FP32 sums
 // (TwoSum: hi + lo) per row and right-hand side; the warp folds them in FP64
 // with shuffles.  With one column range per band the warp finishes y and the
 // state itself; with several (split-K, for wide matrices whose few rows
@@ -190,77 +191,6 @@ struct ScaledTraits<4> {
     }
   }
 };
-
-template <int FMT, int R>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
-    scaled_gemv_kernel(const uint8_t* __restrict__ payload, const float* __restrict__ scales, int64_t M, int64_t N,
-                       int64_t ld, int64_t TN, const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int ksplit,
-                       int64_t cchunk, double* __restrict__ ws, double* __restrict__ y, int64_t ldy,
-                       double* __restrict__ state, double decay) {
-  using T = ScaledTraits<FMT>;
-  constexpr int V = T::V;
-  constexpr int EB = FMT == 4 ? 1 : 2;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t band = (int64_t)blockIdx.x * kWarpsPerCta + warp;
-  const int64_t row0 = 4 * band;
-  if (row0 >= M) return;
-  const int split = blockIdx.y;
-  const int64_t c_begin = (int64_t)split * cchunk;
-  const int64_t c_end = min(ld, c_begin + cchunk);
-
-  float hi[4][R], lo[4][R];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
-
-  for (int64_t c = c_begin + (int64_t)lane * V; c < c_end; c += 32 * V) {
-    float xv[R][V];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const float* xp = x + (int64_t)r * ldx + c;
-      if (x_vec_ok && c + V <= N) {
-#pragma unroll
-        for (int v = 0; v < V; v += 4) {
-          const float4 t = __ldg(reinterpret_cast<const float4*>(xp + v));
-          xv[r][v] = t.x;
-          xv[r][v + 1] = t.y;
-          xv[r][v + 2] = t.z;
-          xv[r][v + 3] = t.w;
-        }
-      } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) xv[r][v] = c + v < N ? __ldg(xp + v) : 0.f;
-      }
-    }
-    const int64_t tcol = c / 128;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t row = row0 + i;
-      if (row >= M) break;
-      const uint4 raw = __ldcs(reinterpret_cast<const uint4*>(payload + ((uint64_t)row * ld + c) * EB));
-      float f[V];
-      T::decode(raw, f);
-      const float s = __ldg(scales + (row / 128) * TN + tcol);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        // groups of 4 products (as in a WZ1 block row), each folded into the
-        // compensated sum together with the exact rounding error of p * s
-#pragma unroll
-        for (int g = 0; g < V; g += 4) {
-          float p = f[g] * xv[r][g];
-          p = fmaf(f[g + 1], xv[r][g + 1], p);
-          p = fmaf(f[g + 2], xv[r][g + 2], p);
-          p = fmaf(f[g + 3], xv[r][g + 3], p);
-          const float ps = p * s;
-          two_sum_acc(hi[i][r], lo[i][r], ps);
-          lo[i][r] += fmaf(p, s, -ps);
-        }
-      }
-    }
-  }
-  finish_band<R>(hi, lo, lane, row0, M, split, ksplit, 4 * ((M + 3) / 4), ws, y, ldy, state, decay);
-}
 
 // --------------------------------------------------- split-K epilogue (FP64)
 static __global__ void splitk_epilogue_kernel(const double* __restrict__ ws, int ksplit, int R, int64_t Mpad, int64_t M,

@@ -1,0 +1,57 @@
+// Scaled-format GEMV launches (BF16, FP16, FP8 E4M3): instantiation unit.
+#include "scaled_kernels.cuh"
+#include "wz2_dispatch.h"
+
+namespace whff {
+
+template <int FMT, int R>
+static void scaled_one(const ScaledStep& a, cudaStream_t st) {
+  dev::scaled_range_kernel<FMT, R><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
+      a.payload, a.scales, a.M, a.N, a.ld, a.TN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg, a.ws, a.y, a.ldy, a.state,
+      a.decay);
+}
+
+template <int FMT>
+static int scaled_fmt(const ScaledStep& a, cudaStream_t st) {
+  switch (a.R) {
+    case 1: scaled_one<FMT, 1>(a, st); break;
+    case 2: scaled_one<FMT, 2>(a, st); break;
+    case 4: scaled_one<FMT, 4>(a, st); break;
+    case 8: scaled_one<FMT, 8>(a, st); break;
+    default: return -1;
+  }
+  return 0;
+}
+
+int scaled_launch(const ScaledStep& a, cudaStream_t st) {
+  int e;
+  switch (a.fmt) {
+    case 2: e = scaled_fmt<2>(a, st); break;
+    case 3: e = scaled_fmt<3>(a, st); break;
+    case 4: e = scaled_fmt<4>(a, st); break;
+    default: return -1;
+  }
+  if (e) return e;
+  if (a.maxseg > 1) {  // shared bands: the chunks of a band are the "blocks" of the segment epilogue
+    const int V = a.fmt == 4 ? 16 : 8;
+    dev::wz2_segment_epilogue<<<(unsigned)((a.M + 255) / 256), 256, 0, st>>>(a.ws, a.M, a.ld / V, a.L, a.maxseg,
+                                                                            a.R, a.y, a.ldy, a.state, a.decay);
+  }
+  return 0;
+}
+
+int scaled_occupancy(int fmt) {
+  int occ = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  const int threads = dev::kWarpsPerCta * 32;
+  if (fmt == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<2, 1>, threads, 0);
+  if (fmt == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<3, 1>, threads, 0);
+  if (fmt == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<4, 1>, threads, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ;
+}
+
+}  // namespace whff

@@ -50,6 +50,11 @@ struct whff_handle {
   int64_t range_len = 0;        // WZ2: blocks per warp range
   int maxseg = 1;               // WZ2: most ranges sharing one band (1 = none shared)
   int ws_rhs = 8;               // right-hand sides the workspace is sized for
+  double* d_ws_mma = nullptr;   // WZ2 tensor-core passes: ksplit x 32 x Mpad partials
+  size_t ws_mma_bytes = 0;
+  int mma_ksplit = 1;
+  int64_t mma_jchunk = 0;
+  int mma_min_rhs = 9;          // passes of at least this many columns use tcgen05
   cudaStream_t create_stream = nullptr;
 };
 
@@ -65,6 +70,10 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 // WZ2: split the band-major block order into one contiguous range per
 // resident warp (exact balance); bands that straddle ranges get segments.
 void choose_ranges(whff_handle* h) {
+  if (!is_blocked(h->info.fmt)) {  // scaled formats: units are 16-byte column chunks of a 4-row band
+    h->BM = ceil_div(h->info.M, 4);
+    h->BN = scaled_ld(h->info.N) / (h->info.fmt == WHFF_FMT_FP8E4M3 ? 16 : 8);
+  }
   const int64_t total = h->BM * h->BN;
   const int64_t warps_cap = (int64_t)h->sm_count * h->ctas_per_sm * dev::kWarpsPerCta;
   int64_t warps = std::min<int64_t>(warps_cap, std::max<int64_t>(1, (total + 63) / 64));  // >= 64 blocks each
@@ -82,7 +91,7 @@ void choose_ranges(whff_handle* h) {
 }
 
 void choose_split(whff_handle* h) {
-  if (h->info.fmt == WHFF_FMT_FIXED_LIFT || h->info.fmt == WHFF_FMT_FIXED_BFP) {
+  if (h->info.fmt != WHFF_FMT_ZFP) {  // WZ2 and scaled formats: persistent warp ranges
     choose_ranges(h);
     return;
   }
@@ -177,32 +186,18 @@ int wz2_occ(int rate, bool lift, int unroll) {
   }
 }
 
-template <int FMT>
-int launch_scaled_fmt(const whff_handle* h, const float* x, int R, int64_t ldx, bool vec, double* y, int64_t ldy,
-                      double* state, double decay, cudaStream_t st) {
+int launch_scaled(const whff_handle* h, const float* x, int R, int64_t ldx, bool vec, double* y, int64_t ldy,
+                  double* state, double decay, cudaStream_t st) {
   const auto& b = h->info;
   const int64_t ld = scaled_ld(b.N);
-  const int64_t TN = ceil_div(b.N, kScaleTile);
-  const uint8_t* payload = h->d_stream;
-  const float* scales =
-      reinterpret_cast<const float*>(h->d_stream + (uint64_t)b.M * (uint64_t)ld * (uint64_t)elem_bytes(FMT));
-  dim3 grid((unsigned)((h->Mpad / 4 + dev::kWarpsPerCta - 1) / dev::kWarpsPerCta), (unsigned)h->ksplit);
-  dim3 block(dev::kWarpsPerCta * 32);
-#define SC_CASE(RR)                                                                                         \
-  case RR:                                                                                                  \
-    dev::scaled_gemv_kernel<FMT, RR><<<grid, block, 0, st>>>(payload, scales, b.M, b.N, ld, TN, x, ldx, vec, \
-                                                             h->ksplit, h->chunk, h->d_ws, y, ldy, state,    \
-                                                             decay);                                        \
-    break;
-  switch (R) {
-    SC_CASE(1)
-    SC_CASE(2)
-    SC_CASE(4)
-    SC_CASE(8)
-    default:
-      return WHFF_EINVAL;
+  ScaledStep a{b.fmt, h->d_stream,
+               reinterpret_cast<const float*>(h->d_stream + (uint64_t)b.M * (uint64_t)ld * (uint64_t)elem_bytes(b.fmt)),
+               b.M, b.N, ld, ceil_div(b.N, kScaleTile), x, ldx, vec, h->range_len, h->maxseg, h->d_ws, y, ldy, state,
+               decay, h->range_ctas, R};
+  if (scaled_launch(a, st)) {
+    set_error("whff_step: scaled formats take R 1, 2, 4 or 8 per pass");
+    return WHFF_EINVAL;
   }
-#undef SC_CASE
   return WHFF_OK;
 }
 
@@ -219,19 +214,15 @@ int launch_pass(const whff_handle* h, const float* x, int R, int64_t ldx, double
       e = launch_wz2(h, x, R, ldx, vec, y, ldy, state, decay, st);
       break;
     case WHFF_FMT_BF16:
-      e = launch_scaled_fmt<2>(h, x, R, ldx, vec, y, ldy, state, decay, st);
-      break;
     case WHFF_FMT_FP16:
-      e = launch_scaled_fmt<3>(h, x, R, ldx, vec, y, ldy, state, decay, st);
-      break;
     case WHFF_FMT_FP8E4M3:
-      e = launch_scaled_fmt<4>(h, x, R, ldx, vec, y, ldy, state, decay, st);
+      e = launch_scaled(h, x, R, ldx, vec, y, ldy, state, decay, st);
       break;
     default:
       e = WHFF_EINVAL;
   }
   if (e) return e;
-  if (h->ksplit > 1 && h->info.fmt != WHFF_FMT_FIXED_LIFT && h->info.fmt != WHFF_FMT_FIXED_BFP) {
+  if (h->ksplit > 1 && h->info.fmt == WHFF_FMT_ZFP) {
     const int threads = 256;
     dev::splitk_epilogue_kernel<<<(unsigned)((h->info.M + threads - 1) / threads), threads, 0, st>>>(
         h->d_ws, h->ksplit, R, h->Mpad, h->info.M, y, ldy, state, decay);
@@ -283,6 +274,9 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
   if (info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) {
     const int occ = wz2_occ(info.rate, info.fmt == WHFF_FMT_FIXED_LIFT, h->unroll);
     h->ctas_per_sm = occ > 0 ? occ : 4;
+  } else if (!is_blocked(info.fmt)) {
+    const int occ = scaled_occupancy(info.fmt);
+    h->ctas_per_sm = occ > 0 ? occ : 4;
   }
   if (is_blocked(info.fmt)) {
     h->BM = ceil_div(info.M, 4);
@@ -299,6 +293,21 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
   if (h->maxseg > 1)
     h->ws_bytes = (size_t)h->BM * (size_t)h->maxseg * (size_t)std::min(max_rhs, kMaxRhsKernel) * 4 * 8;
   h->ws_rhs = std::min(max_rhs, kMaxRhsKernel);
+  if ((info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) && max_rhs >= h->mma_min_rhs) {
+    // tensor-core passes: tiles of 32 bands; split the columns so that about two waves of
+    // CTAs (3 resident per SM) are in flight, chunks a multiple of the 16-block stage
+    const int64_t tiles = ceil_div(h->BM, 32);
+    int64_t ks = std::max<int64_t>(1, ceil_div((int64_t)h->sm_count * 3 * 2, tiles));
+    ks = std::min<int64_t>(ks, std::max<int64_t>(1, h->BN / 64));
+    h->mma_jchunk = ceil_div(ceil_div(h->BN, ks), 16) * 16;
+    h->mma_ksplit = (int)ceil_div(h->BN, h->mma_jchunk);
+    h->ws_mma_bytes = (size_t)h->mma_ksplit * (size_t)std::min(max_rhs, 32) * (size_t)h->Mpad * 8;
+    if (cudaMalloc(&h->d_ws_mma, h->ws_mma_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("whff_create: cudaMalloc of the tensor-core workspace failed");
+      return fail(WHFF_ENOMEM);
+    }
+  }
   if ((h->ws_bytes && cudaMalloc(&h->d_ws, h->ws_bytes) != cudaSuccess) ||
       cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->d_x, (size_t)info.N * (size_t)max_rhs * sizeof(float)) != cudaSuccess ||
@@ -328,10 +337,26 @@ extern "C" int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, 
   if (M) *M = h->info.M;
   if (N) *N = h->info.N;
   if (device_bytes)
-    *device_bytes = h->info.stream_bytes + h->ws_bytes + sizeof(int) + (size_t)h->info.N * h->max_rhs * 4 +
+    *device_bytes = h->info.stream_bytes + h->ws_bytes + h->ws_mma_bytes + sizeof(int) + (size_t)h->info.N * h->max_rhs * 4 +
                     (size_t)h->info.M * h->max_rhs * 8;
   return WHFF_OK;
 }
+
+namespace whff {
+namespace {
+int launch_mma(const whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
+               double decay, cudaStream_t st) {
+  MmaStep a{h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, h->d_stream, h->info.M, h->info.N, h->BM, h->BN,
+            h->Mpad, x, ldx, R, h->mma_ksplit, h->mma_jchunk, h->d_ws_mma, y, ldy, state, decay, h->d_status};
+  if (mma_launch(a, st)) {
+    set_error("whff_step: tensor-core pass failed to launch");
+    return WHFF_ECUDA;
+  }
+  WHFF_CUDA_TRY(cudaGetLastError());
+  return WHFF_OK;
+}
+}  // namespace
+}  // namespace whff
 
 extern "C" int whff_plan(const whff_handle* h, int* ksplit, int* launches) {
   if (!h) {
@@ -355,10 +380,17 @@ extern "C" int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, dou
   int r0 = 0;
   while (r0 < R) {
     const int left = R - r0;
-    const int pass = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-    int e = launch_pass(h, x + (int64_t)r0 * ldx, pass, ldx, y + (int64_t)r0 * ldy, ldy, state, decay, st);
+    int e;
+    if (h->d_ws_mma && left >= h->mma_min_rhs) {  // dense contraction: tcgen05, up to 32 columns per pass
+      const int pass = left < 32 ? left : 32;
+      e = launch_mma(h, x + (int64_t)r0 * ldx, pass, ldx, y + (int64_t)r0 * ldy, ldy, state, decay, st);
+      r0 += pass;
+    } else {
+      const int pass = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+      e = launch_pass(h, x + (int64_t)r0 * ldx, pass, ldx, y + (int64_t)r0 * ldy, ldy, state, decay, st);
+      r0 += pass;
+    }
     if (e) return e;
-    r0 += pass;
   }
   return WHFF_OK;
 }
@@ -579,6 +611,7 @@ extern "C" void whff_destroy(whff_handle* h) {
   if (h->create_stream) cudaStreamSynchronize(h->create_stream);
   cudaFree(h->d_stream);
   cudaFree(h->d_ws);
+  cudaFree(h->d_ws_mma);
   cudaFree(h->d_status);
   cudaFree(h->d_x);
   cudaFree(h->d_y);

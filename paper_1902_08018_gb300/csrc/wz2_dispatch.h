@@ -44,6 +44,47 @@ struct Wz2Batch {
 int wz2_batched_state_launch(const dev::BatchState* table, const int64_t* row_begin, int n, int64_t total_rows,
                              cudaStream_t st);
 
+struct ScaledStep {
+  int fmt;  // 2 BF16, 3 FP16, 4 FP8 E4M3
+  const uint8_t* payload;
+  const float* scales;
+  int64_t M, N, ld, TN;
+  const float* x;
+  int64_t ldx;
+  bool x_vec_ok;
+  int64_t L;
+  int maxseg;
+  double* ws;
+  double* y;
+  int64_t ldy;
+  double* state;
+  double decay;
+  int64_t ctas;
+  int R;
+};
+int scaled_launch(const ScaledStep& a, cudaStream_t st);  // scaled.cu
+
+// Tensor-core pass of up to 32 right-hand sides over a WZ2 matrix (mma.cu).
+struct MmaStep {
+  int rate;
+  bool lift;
+  const uint8_t* stream;
+  int64_t M, N, BM, BN, Mpad;
+  const float* x;
+  int64_t ldx;
+  int R;           // 1..32 (padded to 16 or 32 inside)
+  int ksplit;
+  int64_t jchunk;  // blocks per column split (a multiple of 16)
+  double* ws;      // ksplit x R x Mpad
+  double* y;
+  int64_t ldy;
+  double* state;
+  double decay;
+  int* status;
+};
+int mma_launch(const MmaStep& a, cudaStream_t st);
+int scaled_occupancy(int fmt);
+
 template <int RATE>
 int wz2_launch(const Wz2Step& a, cudaStream_t st);
 template <int RATE>

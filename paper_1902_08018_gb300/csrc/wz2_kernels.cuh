@@ -97,12 +97,20 @@ __device__ __forceinline__ void wz2_unpermute(const float (&f)[16], float (&V)[1
   for (int k = 0; k < 16; ++k) V[LIFT ? seq_index(k) : k] = f[k];
 }
 
-// Fold a band's FP64 sums and (with the lift) mix them with 2G, scaled.
+// Fold a band's FP64 sums and map them to y: MIX 1 = the lift's 2G mixing
+// and 2^-3, MIX 2 = 2^3 (no transform), MIX 0 = identity (scaled formats).
 template <bool LIFT, int R>
 __device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
                                            int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
                                            double* __restrict__ y, int64_t ldy, double* __restrict__ state,
-                                           double decay) {
+                                           double decay);
+
+template <int MIX, int R>
+__device__ __forceinline__ void band_finish(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
+                                            int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
+                                            double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                                            double decay) {
+  constexpr bool LIFT = MIX == 1;
   double z[4][R];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -119,7 +127,7 @@ __device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float 
       t[3] = (a + z[1][r] + z[2][r] + z[3][r]) * 0.125;
     } else {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) t[i] = z[i][r] * 8.0;
+      for (int i = 0; i < 4; ++i) t[i] = MIX == 2 ? z[i][r] * 8.0 : z[i][r];
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) z[i][r] = t[i];
@@ -155,6 +163,14 @@ __device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float 
 }
 
 // One block's contribution, scaled: p[i][r] = s * sum_b V[i][b] xt_r[b].
+template <bool LIFT, int R>
+__device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
+                                           int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
+                                           double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                                           double decay) {
+  band_finish<LIFT ? 1 : 2, R>(hi, lo, lane, row0, M, split, ksplit, Mpad, ws, y, ldy, state, decay);
+}
+
 template <int RATE, bool LIFT, int R>
 __device__ __forceinline__ void wz2_block_partial(const uint32_t (&w)[Wz2Layout<RATE>::kWords],
                                                   const float* __restrict__ x, int64_t ldx, int64_t c0, int64_t N,
