@@ -787,6 +787,7 @@ extern "C" int whff_batch_create(whff_handle* const* hs, const int* R, int count
     whff_batch::Group g;
     g.R = cls;
     for (int i = 0; i < count; ++i) {
+      if (R[i] >= hs[i]->mma_min_rhs && hs[i]->d_ws_mma) continue;  // tensor-core passes instead
       int c = 0, left = R[i];
       for (int k : classes) {  // decompose R[i] into 8s, then one 4, 2, 1
         while (left >= k && (k == 8 || left < 2 * k)) {
@@ -891,6 +892,14 @@ extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64
   const cudaStream_t st = as_stream(stream);
   // the pinned tables are reused: wait until the previous step's copies ran
   WHFF_CUDA_TRY(cudaEventSynchronize(b->copied));
+  // matrices with many right-hand sides: tensor-core passes of their own (state included)
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    whff_handle* h = b->hs[i];
+    if (b->R[i] >= h->mma_min_rhs && h->d_ws_mma) {
+      int e = whff_step(h, x[i], b->R[i], ldx[i], y[i], ldy[i], state ? state[i] : nullptr, decay, stream);
+      if (e) return e;
+    }
+  }
   size_t off = 0;
   for (auto& g : b->groups) {
     const int n = (int)g.members.size();
@@ -932,8 +941,10 @@ extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64
   }
   if (state) {
     const int count = (int)b->hs.size();
-    for (int i = 0; i < count; ++i)
-      b->state_pinned[i] = dev::BatchState{state[i], y[i], ldy[i], b->hs[i]->info.M, b->R[i], decay};
+    for (int i = 0; i < count; ++i) {
+      const bool own = b->R[i] >= b->hs[i]->mma_min_rhs && b->hs[i]->d_ws_mma;  // state already applied
+      b->state_pinned[i] = dev::BatchState{own ? nullptr : state[i], y[i], ldy[i], b->hs[i]->info.M, b->R[i], decay};
+    }
     WHFF_CUDA_TRY(cudaMemcpyAsync(b->d_state, b->state_pinned, sizeof(dev::BatchState) * count,
                                   cudaMemcpyHostToDevice, st));
     wz2_batched_state_launch(b->d_state, b->d_state_rows, count, b->state_rows, st);

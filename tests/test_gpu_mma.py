@@ -1,0 +1,64 @@
+"""Tensor-core (tcgen05) passes for many right-hand sides on WZ2 matrices,
+through the C ABI: every column within relative L2 1e-6 of the FP64 oracle
+GEMV on the decoded matrix, for ragged shapes, split columns and R that mixes
+tensor-core (>= 9 columns) and CUDA-core passes; the carried state follows
+the oracle recursion in column order."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    import paper_1902_08018_gb300 as W
+
+    W.library()
+    return W, torch
+
+
+def _matrix(M, N, seed, length=0.1):
+    import workloads
+
+    n = max(M, N)
+    g = int(np.ceil(np.sqrt(n)))
+    return workloads.KernelMatrix(n, g, n, length, seed).dense()[:M, :N]
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("fmt,rate,M,N,R", [
+    (5, 16, 128, 64, 16),      # one tile, one stage
+    (5, 16, 260, 1000, 32),    # ragged rows and columns, several stages
+    (6, 12, 300, 3001, 17),
+    (5, 8, 1500, 1200, 9),
+    (5, 24, 64, 20000, 32),    # wide: split columns
+    (6, 20, 2050, 700, 40),    # 32 on tensor cores + 8 on CUDA cores
+])
+def test_tensor_core_passes_match_oracle(env, orc, fmt, rate, M, N, R):
+    W, torch = env
+    A = _matrix(M, N, M + N)
+    blob = W.whff_compress(A, fmt, rate)
+    Ahat = orc.decode(blob.tobytes())
+    rng = np.random.default_rng(R)
+    X = rng.standard_normal((R, N)).astype(np.float32)
+    ref = orc.gemv64(Ahat, X.T.astype(np.float64))
+    with W.whff_create(blob, max_rhs=64) as h:
+        x = torch.from_numpy(X).cuda()
+        y = torch.zeros((R, M), dtype=torch.float64, device="cuda")
+        s = torch.full((M,), 1.0, dtype=torch.float64, device="cuda")
+        h.step(x, y, s, 0.95)
+        torch.cuda.synchronize()
+        assert h.sync_status() == 0
+        Y = y.cpu().numpy()
+    for r in range(R):
+        assert _rel(Y[r], ref[:, r]) <= TOL, (r, _rel(Y[r], ref[:, r]))
+    s_ref = orc.state_update(np.ones(M), ref, 0.95)
+    assert _rel(s.cpu().numpy(), s_ref) <= TOL
