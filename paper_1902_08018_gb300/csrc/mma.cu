@@ -9,8 +9,12 @@ static int mma_one(const MmaStep& a, cudaStream_t st) {
   using S = dev::MmaSmem<NR>;
   auto kern = dev::wz2_mma_kernel<RATE, LIFT, NR>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes) != cudaSuccess) return -1;
+  const int64_t nstages = (a.BN + dev::kMmaStageBlocks - 1) / dev::kMmaStageBlocks;
+  const int64_t bthreads = nstages * dev::kMmaStageBlocks * NR;
+  dev::wz2_mma_btiles<LIFT, NR><<<(unsigned)((bthreads + 255) / 256), 256, 0, st>>>(a.x, a.ldx, a.N, a.R, nstages,
+                                                                                   a.btiles);
   dim3 grid((unsigned)((a.BM + dev::kMmaBands - 1) / dev::kMmaBands), (unsigned)a.ksplit);
-  kern<<<grid, dev::kMmaThreads, S::kBytes, st>>>(a.stream, a.N, a.BM, a.BN, a.x, a.ldx, a.R, a.jchunk, a.ws, a.Mpad,
+  kern<<<grid, dev::kMmaThreads, S::kBytes, st>>>(a.stream, a.BM, a.BN, a.btiles, a.R, a.jchunk, a.ws, a.Mpad,
                                                  a.status);
   dev::wz2_mma_finish<LIFT><<<(unsigned)((a.BM + 127) / 128), 128, 0, st>>>(a.ws, a.ksplit, a.R, a.Mpad, a.M, a.y,
                                                                            a.ldy, a.state, a.decay);

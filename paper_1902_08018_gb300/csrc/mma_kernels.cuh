@@ -14,14 +14,16 @@
 // covers one stage (16 blocks = 64 columns of K) and is drained into TwoSum
 // FP32 registers after every stage, so FP32 rounding never sees long sums.
 //
-// CTA = 4 warps = 128 threads; tile = 32 bands (128 coefficient rows) x NR
+// CTA = 8 warps = 256 threads; tile = 32 bands (128 coefficient rows) x NR
 // right-hand sides x a column range of the matrix.  Per stage every thread
-// decodes 4 blocks into the A tile and transforms 4 x-chunks into the B tile
-// (shared memory, canonical no-swizzle K-major layout: 8x16-byte core
-// matrices, 128 B apart along K and 256 B apart along M/N); one thread issues
-// the 24 MMAs and commits them to an mbarrier; all threads wait (bounded),
-// drain their TMEM lane, and go on.  Partials go to a workspace per column
-// split; mma_finish sums splits, mixes with 2G and applies the state.
+// decodes 2 blocks into the A tile (shared memory, canonical no-swizzle
+// K-major layout: 8x16-byte core matrices, 128 B apart along K and 256 B
+// apart along M/N) and copies its part of the B tile, which a small kernel
+// builds once per step for all stages; one thread issues the 24 MMAs and
+// commits them to an mbarrier; the next stage's blocks are loaded meanwhile;
+// all threads wait (bounded) and drain TMEM (warps w and w+4 share the lanes
+// 32(w%4).. and take half the columns each).  Partials go to a workspace per
+// column split; mma_finish sums splits, mixes with 2G and applies the state.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -33,7 +35,7 @@
 namespace whff {
 namespace dev {
 
-constexpr int kMmaThreads = 128;
+constexpr int kMmaThreads = 256;       // 8 warps; warps w and w+4 share TMEM lanes 32(w%4)..
 constexpr int kMmaBands = 32;         // 128 coefficient rows per tile
 constexpr int kMmaStageBlocks = 16;   // K = 64 per stage
 constexpr int kMmaKSteps = 4;         // K = 16 per instruction
@@ -122,6 +124,17 @@ __device__ __forceinline__ void tmem_load_row<32>(uint32_t taddr, float (&v)[32]
 }
 
 template <>
+__device__ __forceinline__ void tmem_load_row<8>(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
 __device__ __forceinline__ void tmem_load_row<16>(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
@@ -135,15 +148,59 @@ __device__ __forceinline__ void tmem_load_row<16>(uint32_t taddr, float (&v)[16]
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Grid: (ceil(BM/32), ksplit).  ws[(split * R + r) * Mpad4 + coefficient row]
+// The B operand of every stage, built once per step: for column block J and
+// right-hand side r, (2G)^T x_J (or x_J without the lift) in three BF16
+// pieces, already in the shared-memory tile layout of its 16-block stage:
+// out[stage][piece][kstep] = NR x 16 BF16 tile.  Thread per (stage, J, r).
+template <bool LIFT, int NR>
+__global__ void wz2_mma_btiles(const float* __restrict__ x, int64_t ldx, int64_t N, int R, int64_t nstages,
+                               uint8_t* __restrict__ out) {
+  using S = MmaSmem<NR>;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nstages * kMmaStageBlocks * NR) return;
+  const int r = (int)(q % NR);
+  const int jl = (int)((q / NR) % kMmaStageBlocks);
+  const int64_t stage = q / ((int64_t)NR * kMmaStageBlocks);
+  const int64_t J = stage * kMmaStageBlocks + jl;
+  float xt[4] = {0.f, 0.f, 0.f, 0.f};
+  if (r < R) {
+    float xv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) xv[c] = 4 * J + c < N ? __ldg(x + (int64_t)r * ldx + 4 * J + c) : 0.f;
+    if (LIFT) {
+      const float aa = xv[0] + xv[1], bb = xv[2] + xv[3], cc = xv[0] + xv[2], dd = xv[1] + xv[3];
+      xt[0] = 2.f * (aa + bb);
+      xt[1] = bb - aa;
+      xt[2] = dd - cc;
+      xt[3] = xv[3] - xv[2];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) xt[c] = xv[c];
+    }
+  }
+  __nv_bfloat16 p[3][4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) split3(xt[b], p[0][b], p[1][b], p[2][b]);
+  const int kstep = jl >> 2, kk = (jl & 3) * 4;
+  uint8_t* base = out + stage * (int64_t)S::kB;
+#pragma unroll
+  for (int pc = 0; pc < 3; ++pc)
+    *reinterpret_cast<uint2*>(base + (pc * kMmaKSteps + kstep) * S::kBTile + tile_off(r, kk)) =
+        make_uint2(pack2(p[pc][0], p[pc][1]), pack2(p[pc][2], p[pc][3]));
+}
+
+// Grid: (ceil(BM/32), ksplit).  ws[(split * R + r) * Mpad + coefficient row]
 // receives the split's FP64 partial of Z (coefficient rows, not yet mixed).
+// Thread t decodes blocks (t & 7) and (t & 7) + 8 of band t >> 3 in every
+// stage; the next stage's compressed words are loaded while the MMAs of the
+// current one run.
 template <int RATE, bool LIFT, int NR>
-__global__ void __launch_bounds__(kMmaThreads)
-    wz2_mma_kernel(const uint8_t* __restrict__ stream, int64_t N, int64_t BM, int64_t BN, const float* __restrict__ x,
-                   int64_t ldx, int R, int64_t jchunk, double* __restrict__ ws, int64_t Mpad,
-                   int* __restrict__ status) {
+__global__ void __launch_bounds__(kMmaThreads, 2)
+    wz2_mma_kernel(const uint8_t* __restrict__ stream, int64_t BM, int64_t BN, const uint8_t* __restrict__ btiles,
+                   int R, int64_t jchunk, double* __restrict__ ws, int64_t Mpad, int* __restrict__ status) {
   using S = MmaSmem<NR>;
   constexpr int NW = Wz2Layout<RATE>::kWords;
+  constexpr int HALF = NR / 2;  // TMEM columns drained by each of the two warps on a lane quarter
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* As = smem;
   uint8_t* Bs = smem + S::kA;
@@ -153,7 +210,7 @@ __global__ void __launch_bounds__(kMmaThreads)
   const int t = threadIdx.x, warp = t >> 5;
   const int64_t band0 = (int64_t)blockIdx.x * kMmaBands;
   const int split = blockIdx.y;
-  const int64_t J0 = (int64_t)split * jchunk;
+  const int64_t J0 = (int64_t)split * jchunk;  // a multiple of the 16-block stage
   const int64_t J1 = min(BN, J0 + jchunk);
   const uint32_t bar_a = smem_addr(bar);
 
@@ -171,37 +228,61 @@ __global__ void __launch_bounds__(kMmaThreads)
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  float hi[NR], lo[NR];
+  float hi[HALF], lo[HALF];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) hi[r] = lo[r] = 0.f;
+  for (int r = 0; r < HALF; ++r) hi[r] = lo[r] = 0.f;
 
-  const int my_band = t >> 2;     // decode: thread -> band (32 bands x 4 threads)
-  const int my_sub = t & 3;       // its blocks in a stage: my_sub + 4u, u = 0..3
+  const int my_band = t >> 3;
+  const int my_sub = t & 7;
   const int64_t band = band0 + my_band;
-  bool ok = true;
-  uint32_t phase = 0;
-  for (int64_t Js = J0; Js < J1 && ok; Js += kMmaStageBlocks) {
-    // ---- A tile: this thread's 4 blocks of its band
+  constexpr int kBVec = S::kB / 16;                              // uint4 in a B tile
+  constexpr int BV = (kBVec + kMmaThreads - 1) / kMmaThreads;    // per thread (the last one guarded)
+  // two stages of compressed words in flight (ring of 2), one B tile ahead
+  uint32_t w[2][2][NW];
+  uint4 bnext[BV];
+  auto fetch = [&](int slot, int64_t Js) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int jl = my_sub + 4 * u;  // block within the stage, 0..15
-      const int64_t J = Js + jl;
-      float V[16];
-      float s = 0.f;
+    for (int u = 0; u < 2; ++u) {
+      const int64_t J = Js + my_sub + 8 * u;
       if (band < BM && J < J1) {
-        uint32_t w[NW];
-        wz2_load<RATE>(stream, band * BN + J, w);
-        const uint32_t E = w[0] & 0xFFu, K = (w[0] >> 8) & 31u;
-        s = E ? __uint_as_float((E + K - 27u) << 23) : 0.f;
-        float f[16];
-        wz2_fields<RATE>(w, f);
-        wz2_unpermute<LIFT>(f, V);
+        wz2_load<RATE>(stream, band * BN + J, w[slot][u]);
       } else {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) V[i] = 0.f;
+        for (int i = 0; i < NW; ++i) w[slot][u][i] = 0u;  // a zero block: E = 0, scale 0
       }
-      const int kstep = jl >> 2;          // 4 blocks (16 K) per MMA step
-      const int kk = (jl & 3) * 4;        // K offset inside the step
+    }
+  };
+  auto fetch_b = [&](int64_t Js) {
+    const uint4* src = reinterpret_cast<const uint4*>(btiles + (Js / kMmaStageBlocks) * (int64_t)S::kB);
+#pragma unroll
+    for (int i = 0; i < BV; ++i)
+      if (t + i * kMmaThreads < kBVec) bnext[i] = __ldg(src + t + i * kMmaThreads);
+  };
+  // The descriptors of a stage never change: base descriptors of the A and B
+  // tiles plus a compile-time offset in 16-byte units in the start-address
+  // field (shared addresses stay below 256 KB, so the field cannot carry).
+  const uint64_t a_base = smem_desc(smem_addr(As), 128, 256);
+  const uint64_t b_base = smem_desc(smem_addr(Bs), 128, 256);
+  if (J0 < J1) {
+    fetch(0, J0);
+    fetch_b(J0);
+  }
+  if (J0 + kMmaStageBlocks < J1) fetch(1, J0 + kMmaStageBlocks);
+  bool ok = true;
+  uint32_t phase = 0;
+  // one stage; `slot` is a literal at every call, so the ring stays in registers
+  auto stage = [&](const int slot, const int64_t Js) -> bool {
+    // ---- A tile: this thread's 2 blocks of its band
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int jl = my_sub + 8 * u;
+      uint32_t (&wu)[NW] = w[slot][u];
+      const uint32_t E = wu[0] & 0xFFu, K = (wu[0] >> 8) & 31u;
+      const float s = E ? __uint_as_float((E + K - 27u) << 23) : 0.f;
+      float f[16], V[16];
+      wz2_fields<RATE>(wu, f);
+      wz2_unpermute<LIFT>(f, V);
+      const int kstep = jl >> 2, kk = (jl & 3) * 4;
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const int row = 4 * my_band + a;
@@ -209,43 +290,17 @@ __global__ void __launch_bounds__(kMmaThreads)
 #pragma unroll
         for (int b = 0; b < 4; ++b) split3(V[4 * a + b] * s, p[0][b], p[1][b], p[2][b]);
 #pragma unroll
-        for (int pc = 0; pc < 3; ++pc) {
-          uint8_t* dst = As + (pc * kMmaKSteps + kstep) * S::kATile + tile_off(row, kk);
-          *reinterpret_cast<uint2*>(dst) = make_uint2(pack2(p[pc][0], p[pc][1]), pack2(p[pc][2], p[pc][3]));
-        }
+        for (int pc = 0; pc < 3; ++pc)
+          *reinterpret_cast<uint2*>(As + (pc * kMmaKSteps + kstep) * S::kATile + tile_off(row, kk)) =
+              make_uint2(pack2(p[pc][0], p[pc][1]), pack2(p[pc][2], p[pc][3]));
       }
     }
-    // ---- B tile: (2G)^T x for 16 column blocks x NR right-hand sides
-    for (int q = t; q < kMmaStageBlocks * NR; q += kMmaThreads) {
-      const int jl = q % kMmaStageBlocks, r = q / kMmaStageBlocks;
-      const int64_t J = Js + jl;
-      float xt[4] = {0.f, 0.f, 0.f, 0.f};
-      if (r < R && J < J1) {
-        float xv[4];
+    // ---- B tile: this stage's prebuilt pieces (fetched one stage ahead)
+    {
+      uint4* dst = reinterpret_cast<uint4*>(Bs);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) xv[c] = 4 * J + c < N ? __ldg(x + (int64_t)r * ldx + 4 * J + c) : 0.f;
-        if (LIFT) {
-          const float aa = xv[0] + xv[1], bb = xv[2] + xv[3], cc = xv[0] + xv[2], dd = xv[1] + xv[3];
-          xt[0] = 2.f * (aa + bb);
-          xt[1] = bb - aa;
-          xt[2] = dd - cc;
-          xt[3] = xv[3] - xv[2];
-        } else {
-          xt[0] = xv[0];
-          xt[1] = xv[1];
-          xt[2] = xv[2];
-          xt[3] = xv[3];
-        }
-      }
-      __nv_bfloat16 p[3][4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) split3(xt[b], p[0][b], p[1][b], p[2][b]);
-      const int kstep = jl >> 2, kk = (jl & 3) * 4;
-#pragma unroll
-      for (int pc = 0; pc < 3; ++pc) {
-        uint8_t* dst = Bs + (pc * kMmaKSteps + kstep) * S::kBTile + tile_off(r, kk);
-        *reinterpret_cast<uint2*>(dst) = make_uint2(pack2(p[pc][0], p[pc][1]), pack2(p[pc][2], p[pc][3]));
-      }
+      for (int i = 0; i < BV; ++i)
+        if (t + i * kMmaThreads < kBVec) dst[t + i * kMmaThreads] = bnext[i];
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor-core reads
     __syncthreads();
@@ -260,8 +315,8 @@ __global__ void __launch_bounds__(kMmaThreads)
           // products A_p B_q with p + q <= 2: (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
           const int pa = m == 2 || m == 4 ? 1 : m == 5 ? 2 : 0;
           const int pb = m == 1 || m == 4 ? 1 : m == 3 ? 2 : 0;
-          const uint64_t ad = smem_desc(smem_addr(As + (pa * kMmaKSteps + ks) * S::kATile), 128, 256);
-          const uint64_t bd = smem_desc(smem_addr(Bs + (pb * kMmaKSteps + ks) * S::kBTile), 128, 256);
+          const uint64_t ad = a_base + (uint64_t)(((pa * kMmaKSteps + ks) * S::kATile) >> 4);
+          const uint64_t bd = b_base + (uint64_t)(((pb * kMmaKSteps + ks) * S::kBTile) >> 4);
           asm volatile(
               "{\n\t.reg .pred p;\n\t"
               "setp.ne.b32 p, %4, 0;\n\t"
@@ -273,29 +328,40 @@ __global__ void __launch_bounds__(kMmaThreads)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_a)
                    : "memory");
     }
+    // loads in flight while the tensor cores work: the B tile of the next stage
+    // and the compressed blocks of the stage after it (this slot is now free)
+    if (Js + kMmaStageBlocks < J1) fetch_b(Js + kMmaStageBlocks);
+    if (Js + 2 * kMmaStageBlocks < J1) fetch(slot, Js + 2 * kMmaStageBlocks);
     // every thread waits (bounded) for the commit; the CTA then agrees on the
     // outcome, so a timeout is a uniform exit and never a barrier deadlock
     if (!__syncthreads_and(mbar_wait(bar_a, phase) ? 1 : 0)) {
       ok = false;
       if (t == 0) atomicExch(status, WHFF_ETIMEOUT);
       (void)mbar_wait(bar_a, phase);  // give the MMAs in flight a second bounded chance
-      break;
+      return false;
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    float v[NR];
-    tmem_load_row<NR>(tmem + ((uint32_t)(32 * warp) << 16), v);  // lane = row t of the tile
+    float v[HALF];
+    // lane quarter (warp % 4), column half (warp / 4)
+    tmem_load_row<HALF>(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(HALF * (warp >> 2)), v);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) two_sum_acc(hi[r], lo[r], v[r]);
+    for (int r = 0; r < HALF; ++r) two_sum_acc(hi[r], lo[r], v[r]);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();  // the next stage overwrites the tiles and the accumulator
+    return true;
+  };
+  for (int64_t Js = J0; Js < J1 && ok; Js += 2 * kMmaStageBlocks) {
+    ok = stage(0, Js);
+    if (ok && Js + kMmaStageBlocks < J1) ok = stage(1, Js + kMmaStageBlocks);
   }
   if (ok) {
-    const int64_t row = 4 * band0 + t;  // coefficient row of the tile
+    const int64_t row = 4 * band0 + 32 * (warp & 3) + (t & 31);  // coefficient row of the tile
+    const int c0 = HALF * (warp >> 2);
     if (row < Mpad) {
 #pragma unroll
-      for (int r = 0; r < NR; ++r)
-        if (r < R) ws[((int64_t)split * R + r) * Mpad + row] = (double)hi[r] + (double)lo[r];
+      for (int r = 0; r < HALF; ++r)
+        if (c0 + r < R) ws[((int64_t)split * R + c0 + r) * Mpad + row] = (double)hi[r] + (double)lo[r];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");

@@ -51,6 +51,7 @@ struct whff_handle {
   int maxseg = 1;               // WZ2: most ranges sharing one band (1 = none shared)
   int ws_rhs = 8;               // right-hand sides the workspace is sized for
   double* d_ws_mma = nullptr;   // WZ2 tensor-core passes: ksplit x 32 x Mpad partials
+  uint8_t* d_btiles = nullptr;  // WZ2 tensor-core passes: B operand pieces per stage
   size_t ws_mma_bytes = 0;
   int mma_ksplit = 1;
   int64_t mma_jchunk = 0;
@@ -302,7 +303,10 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
     h->mma_jchunk = ceil_div(ceil_div(h->BN, ks), 16) * 16;
     h->mma_ksplit = (int)ceil_div(h->BN, h->mma_jchunk);
     h->ws_mma_bytes = (size_t)h->mma_ksplit * (size_t)std::min(max_rhs, 32) * (size_t)h->Mpad * 8;
-    if (cudaMalloc(&h->d_ws_mma, h->ws_mma_bytes) != cudaSuccess) {
+    const size_t btile_bytes = (size_t)ceil_div(h->BN, 16) * 3 * 4 * 32 * 16 * 2;  // stages x pieces x ksteps x NR<=32 tile
+    h->ws_mma_bytes += btile_bytes;
+    if (cudaMalloc(&h->d_ws_mma, h->ws_mma_bytes - btile_bytes) != cudaSuccess ||
+        cudaMalloc(&h->d_btiles, btile_bytes) != cudaSuccess) {
       cudaGetLastError();
       set_error("whff_create: cudaMalloc of the tensor-core workspace failed");
       return fail(WHFF_ENOMEM);
@@ -347,7 +351,8 @@ namespace {
 int launch_mma(const whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
                double decay, cudaStream_t st) {
   MmaStep a{h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, h->d_stream, h->info.M, h->info.N, h->BM, h->BN,
-            h->Mpad, x, ldx, R, h->mma_ksplit, h->mma_jchunk, h->d_ws_mma, y, ldy, state, decay, h->d_status};
+            h->Mpad, x, ldx, R, h->mma_ksplit, h->mma_jchunk, h->d_ws_mma, h->d_btiles, y, ldy, state, decay,
+            h->d_status};
   if (mma_launch(a, st)) {
     set_error("whff_step: tensor-core pass failed to launch");
     return WHFF_ECUDA;
@@ -612,6 +617,7 @@ extern "C" void whff_destroy(whff_handle* h) {
   cudaFree(h->d_stream);
   cudaFree(h->d_ws);
   cudaFree(h->d_ws_mma);
+  cudaFree(h->d_btiles);
   cudaFree(h->d_status);
   cudaFree(h->d_x);
   cudaFree(h->d_y);

@@ -76,6 +76,7 @@ struct MmaStep {
   int ksplit;
   int64_t jchunk;  // blocks per column split (a multiple of 16)
   double* ws;      // ksplit x R x Mpad
+  uint8_t* btiles; // B operand pieces of every 16-block stage (built per pass)
   double* y;
   int64_t ldy;
   double* state;
