@@ -347,27 +347,33 @@ def run_whff(args, rank, world, local_rank):
                          "bytes": int(sb), "ms_per_step": round(ms, 5), "p99_us": float(np.percentile(per * 1e3, 99)),
                          "rel_err": err}
         hh.destroy()
-    # ---------------- many right-hand sides on the headline matrix (R >= 9: tensor cores)
+    # ---------------- many right-hand sides on the headline matrix, on both engines
     multi = {}
+    sb = blobs[head].size - 64
     for Rm in [int(v) for v in filter(None, args.rhs_sweep.split(","))]:
         hh = W.whff_create(blobs[head], max_rhs=Rm)
+        default_min = hh.crossover
         Xr = torch.from_numpy(np.random.default_rng(Rm).standard_normal((Rm, order)).astype(np.float32)).to(dev)
         Yr = torch.zeros((Rm, order), dtype=torch.float64, device=dev)
-        for _ in range(3):
-            hh.step(Xr, Yr, None, DECAY, stream)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = max(5, min(50, args.sweep_steps // 8))
-        f0.record(stream)
-        for _ in range(reps):
-            hh.step(Xr, Yr, None, DECAY, stream)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms = f0.elapsed_time(f1) / reps
-        sb = blobs[head].size - 64
-        multi[str(Rm)] = {"ms_per_step": round(ms, 4), "engine": "tcgen05" if Rm >= 9 else "cuda-core",
-                          "GB_s": round(sb / (ms * 1e-3) / 1e9, 1), "pct_hbm": round(100 * sb / (ms * 1e-3) / 1e9 / peak, 2),
+        entry = {"default_engine": "tcgen05" if Rm >= default_min else "cuda-core"}
+        engines = [("cuda-core", 33)] + ([("tcgen05", 2)] if Rm >= 2 and default_min <= 32 else [])
+        for eng, cross in engines:
+            hh.crossover = cross
+            for _ in range(3):
+                hh.step(Xr, Yr, None, DECAY, stream)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(5, min(50, args.sweep_steps // 8))
+            f0.record(stream)
+            for _ in range(reps):
+                hh.step(Xr, Yr, None, DECAY, stream)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            ms = f0.elapsed_time(f1) / reps
+            entry[eng] = {"ms_per_step": round(ms, 4), "GB_s": round(sb / (ms * 1e-3) / 1e9, 1),
+                          "pct_hbm": round(100 * sb / (ms * 1e-3) / 1e9 / peak, 2),
                           "effective_tflops": round(Rm * order * (2 * order - 1) / (ms * 1e-3) / 1e12, 2)}
+        multi[str(Rm)] = entry
         hh.destroy()
 
     ok = [(v["bytes"], k) for k, v in formats.items() if v["rel_err"] <= ERR_TARGET]

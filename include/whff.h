@@ -117,11 +117,13 @@ int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, int64_t* N,
 int whff_plan(const whff_handle* h, int* ksplit, int* launches);
 
 /* One control step (Sec. 2.1 / Sec. 4.4): y[:,r] = Ahat * x[:,r] for r < R,
- * taken in passes: with a WZ2 matrix whose handle allows max_rhs >= 9, passes
- * of 9..32 columns run on the tensor cores (tcgen05: the stored coefficients
- * and the transformed x split exactly into three BF16 pieces each, six MMAs
- * per step into FP32 TMEM, drained every 64 columns of K into compensated
- * sums); otherwise passes of 8, 4, 2, 1 columns run on the CUDA cores.
+ * taken in passes: with a WZ2 matrix whose handle allows max_rhs >= 2, passes
+ * of crossover..32 columns (default crossover 9, see whff_set_crossover) run
+ * on the tensor cores (tcgen05: the stored coefficients split exactly into
+ * 1-3 BF16 pieces by field width and the transformed x into three, the
+ * piece products above 2^-24 accumulate in FP32 TMEM, drained every 64
+ * columns of K into compensated sums); otherwise passes of 8, 4, 2, 1
+ * columns run on the CUDA cores.
  * Ahat = the decoded matrix (exactly whff_decompress's output).  Products and
  * per-lane sums in FP32 (compensated), cross-warp and cross-CTA sums and y in
  * FP64.  If state != NULL, afterwards for r = 0..R-1 in order:
@@ -172,12 +174,22 @@ int whff_tune(whff_handle* h, int iters, void* stream, double* best_ms);
 int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_sm);
 int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm);
 
+/* Crossover of the two engines (Sec. 4.4's GEMV with many right-hand sides is
+ * a GEMM): passes of at least min_rhs columns run on the tensor cores, smaller
+ * ones on the CUDA cores.  Default 9; 33 = CUDA cores only.  Tensor-core
+ * passes need a WZ2 handle created with max_rhs >= 2 (WHFF_EINVAL otherwise,
+ * unless min_rhs = 33); whff_get_crossover reports 33 for handles without
+ * them.  Both engines meet the same accuracy bar; their roundings differ. */
+int whff_get_crossover(const whff_handle* h, int* min_rhs);
+int whff_set_crossover(whff_handle* h, int min_rhs);
+
 /* Many resident matrices in one step (uneven sizes, R[i] right-hand sides
  * each): one persistent launch per right-hand-side class (8, 4, 2, 1) whose
  * warps split the concatenated block order of all matrices into equal
  * ranges; R[i] is taken in column groups of 8, then one group of 4, 2, 1;
- * a matrix with R[i] >= 9 whose handle was created with max_rhs >= 9 is
- * instead stepped by its own tensor-core passes (see whff_step).
+ * a matrix with R[i] at or above its handle's crossover (tensor-core passes
+ * available, see whff_set_crossover) is instead stepped by its own
+ * tensor-core passes (see whff_step).
  * All matrices must be WZ2 of one format and rate.  whff_batch_step: x[i]
  * (N_i x R[i], ldx[i]), y[i] (M_i x R[i], ldy[i]), state[i] (M_i, may be NULL,
  * or state itself NULL) are device pointers; each state is updated for

@@ -1,29 +1,36 @@
 // mma_kernels.cuh -- many right-hand sides on the 5th-generation tensor cores.
 //
 // With R right-hand sides the step Y = A X is a dense contraction (Sec. 4.4's
-// GEMV becomes a GEMM), so for R >= 16 the fixed-allocation (WZ2) kernels run
+// GEMV becomes a GEMM), so for R >= 9 the fixed-allocation (WZ2) kernels run
 // it on tcgen05.  In the transform domain the contraction is
 //     Z_band = sum_J (s_J V_J) ((2G)^T X_J),   Y_band = (2G) Z_band * 2^-3,
-// a GEMM whose A operand is the stored integer coefficients (|v| < 2^22)
-// times a power-of-two block scale, and whose B operand is the transformed x.
+// a GEMM whose A operand is the stored integer coefficients times a
+// power-of-two block scale, and whose B operand is the transformed x.
 //
-// Precision (the 1e-6 bar): A splits EXACTLY into three BF16 pieces (8+8+6
-// bits); B (FP32) into three BF16 pieces (8+8+8 bits, exact).  Six products
-// A_p B_q with p+q <= 2 are issued (kind::f16, BF16 in, FP32 accumulate in
-// TMEM); the dropped ones are below 2^-24 of |a||x|.  The TMEM accumulator
-// covers one stage (16 blocks = 64 columns of K) and is drained into TwoSum
-// FP32 registers after every stage, so FP32 rounding never sees long sums.
+// Precision (the 1e-6 bar): a coefficient of a W-bit field has at most W-1
+// significant bits, so A splits EXACTLY into PA = ceil((W-1)/8) BF16 pieces
+// (1 at rate 8, 2 at rates 12 and 16, 3 at 20 and 24); B (FP32) into three
+// BF16 pieces (8+8+8 bits, exact).  The products A_p B_q with p+q <= 2 are
+// issued (kind::f16, BF16 in, FP32 accumulate in TMEM); the dropped ones are
+// below 2^-24 of |a||x|.  The tensor cores' FP32 accumulate is not a
+// round-to-nearest sum, so A_0 B_0 goes to its own accumulator and the cross
+// products, about 2^-8 smaller, to a second one: only a few additions happen
+// at full magnitude.  Both cover at most kMmaDrainStages stages of one tile
+// (16 blocks = 64 columns of K each) and are then added and drained into
+// TwoSum FP32 registers, so FP32 rounding never sees long sums.
 //
-// CTA = 8 warps = 256 threads; tile = 32 bands (128 coefficient rows) x NR
-// right-hand sides x a column range of the matrix.  Per stage every thread
-// decodes 2 blocks into the A tile (shared memory, canonical no-swizzle
-// K-major layout: 8x16-byte core matrices, 128 B apart along K and 256 B
-// apart along M/N) and copies its part of the B tile, which a small kernel
-// builds once per step for all stages; one thread issues the 24 MMAs and
-// commits them to an mbarrier; the next stage's blocks are loaded meanwhile;
-// all threads wait (bounded) and drain TMEM (warps w and w+4 share the lanes
-// 32(w%4).. and take half the columns each).  Partials go to a workspace per
-// column split; mma_finish sums splits, mixes with 2G and applies the state.
+// CTA = 8 warps = 256 threads, persistent: the grid splits the sequence of
+// (tile, stage) items -- tile = 32 bands = 128 coefficient rows, stage = 16
+// blocks of K -- into equal contiguous ranges.  Two stages are in flight:
+// while the tensor cores multiply stage k (A and B tiles of buffer k % 2),
+// the threads decode stage k+1 into the other A tile and drain the other TMEM
+// accumulator when stage k-1 closed its group; the words of stage k+2 are already
+// being loaded, and one thread brings the prebuilt B tile of stage k+1 in with
+// a bulk copy (cp.async.bulk) tracked by an mbarrier.  A tile row m holds
+// coefficient row a of band b as m = 32a + b, which makes every warp's tile
+// stores bank-conflict free.  At the end of a tile piece the FP32 sums go to
+// the workspace as one FP64 segment partial; wz2_mma_finish adds a band's
+// segments in order, mixes with 2G and applies the state.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -39,6 +46,7 @@ constexpr int kMmaThreads = 256;       // 8 warps; warps w and w+4 share TMEM la
 constexpr int kMmaBands = 32;         // 128 coefficient rows per tile
 constexpr int kMmaStageBlocks = 16;   // K = 64 per stage
 constexpr int kMmaKSteps = 4;         // K = 16 per instruction
+constexpr int kMmaDrainStages = 1;    // stages of one tile accumulated in TMEM between drains
 constexpr uint32_t kMmaSpinLimit = 1u << 22;  // try_wait polls: bounded to seconds
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -76,13 +84,29 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
+// BF16 pieces of one A coefficient: its field has at most W-1 significant bits.
+template <int RATE>
+struct MmaPieces {
+  static constexpr int kBits = Wz2Layout<RATE>::kW - 1;
+  static constexpr int kA = kBits <= 8 ? 1 : kBits <= 16 ? 2 : 3;
+  static constexpr int kProducts = kA == 1 ? 3 : kA == 2 ? 5 : 6;  // A_p B_q, p + q <= 2
+};
+
+// B operand of one stage: 3 pieces x 4 K steps of NR x 16 BF16.
 template <int NR>
+struct MmaBTile {
+  static constexpr int kBTile = NR * 16 * 2;
+  static constexpr int kB = 3 * kMmaKSteps * kBTile;
+};
+
+// Shared memory: A and B tiles of two stages, then 4 mbarriers and the TMEM slot.
+template <int RATE, int NR>
 struct MmaSmem {
   static constexpr int kATile = 128 * 16 * 2;  // one piece, one K step
-  static constexpr int kBTile = NR * 16 * 2;
-  static constexpr int kA = 3 * kMmaKSteps * kATile;
-  static constexpr int kB = 3 * kMmaKSteps * kBTile;
-  static constexpr int kBytes = kA + kB + 64;  // + mbarrier and TMEM slot
+  static constexpr int kA = MmaPieces<RATE>::kA * kMmaKSteps * kATile;
+  static constexpr int kB = MmaBTile<NR>::kB;
+  static constexpr int kBars = 2 * (kA + kB);
+  static constexpr int kBytes = kBars + 64;
 };
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
@@ -134,6 +158,25 @@ __device__ __forceinline__ void tmem_load_row<8>(uint32_t taddr, float (&v)[8]) 
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Eight columns from each of two accumulators, summed: one wait for both
+// loads, tied to their registers so no use can move above it.
+__device__ __forceinline__ void tmem_load_sum8(uint32_t ta, uint32_t tb, float (&v)[8]) {
+  uint32_t a[8], b[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7])
+               : "r"(ta));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7])
+               : "r"(tb));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                 "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7])
+               :
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(a[i]) + __uint_as_float(b[i]);
+}
+
 template <>
 __device__ __forceinline__ void tmem_load_row<16>(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -155,7 +198,7 @@ __device__ __forceinline__ void tmem_load_row<16>(uint32_t taddr, float (&v)[16]
 template <bool LIFT, int NR>
 __global__ void wz2_mma_btiles(const float* __restrict__ x, int64_t ldx, int64_t N, int R, int64_t nstages,
                                uint8_t* __restrict__ out) {
-  using S = MmaSmem<NR>;
+  using S = MmaBTile<NR>;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nstages * kMmaStageBlocks * NR) return;
   const int r = (int)(q % NR);
@@ -189,38 +232,92 @@ __global__ void wz2_mma_btiles(const float* __restrict__ x, int64_t ldx, int64_t
         make_uint2(pack2(p[pc][0], p[pc][1]), pack2(p[pc][2], p[pc][3]));
 }
 
-// Grid: (ceil(BM/32), ksplit).  ws[(split * R + r) * Mpad + coefficient row]
-// receives the split's FP64 partial of Z (coefficient rows, not yet mixed).
-// Thread t decodes blocks (t & 7) and (t & 7) + 8 of band t >> 3 in every
-// stage; the next stage's compressed words are loaded while the MMAs of the
-// current one run.
+
+// cvt.rn.bf16x2.f32: the packed pair (lo in bits 0-15, hi in bits 16-31).
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;\n" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
+
+// Four values of one tile row, split exactly into PA BF16 pieces; piece p of
+// the pair (v0, v1) is d[p][0], of (v2, v3) d[p][1].
+template <int PA>
+__device__ __forceinline__ void split_row(const float (&v)[4], uint32_t (&d)[PA][2]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float a = v[2 * h], b = v[2 * h + 1];
+#pragma unroll
+    for (int p = 0; p < PA; ++p) {
+      d[p][h] = bf16x2_rn(a, b);
+      if (p + 1 < PA) {
+        a -= bf16_lo(d[p][h]);
+        b -= bf16_hi(d[p][h]);
+      }
+    }
+  }
+}
+
+// Products (p, q): m = 0 is (0,0), which goes to the "big" accumulator; the
+// others (0,1) (1,0) (0,2) (1,1) (2,0) -- the first kProducts-1 of them with
+// p < PA -- to the "small" one.
+__device__ __forceinline__ constexpr int mma_prod_a(int PA, int m) {
+  return PA == 1 ? 0 : (m == 2 || m == 4) ? 1 : m == 5 ? 2 : 0;
+}
+__device__ __forceinline__ constexpr int mma_prod_b(int PA, int m) {
+  return PA == 1 ? m : (m == 1 || m == 4) ? 1 : m == 3 ? 2 : 0;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+
+// One thread: expect `bytes` on `bar` and start the bulk copy global -> shared.
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Persistent grid over the item sequence (tile, stage), item = tile * S + stage,
+// CTA g taking items [g L, g L + L).  ws[((tile * maxseg + seg) * R + r) * 128 + m]
+// receives the FP64 partial of tile row m (= 32a + band) for the CTA's segment
+// seg = g - (tile S) / L of the tile.
 template <int RATE, bool LIFT, int NR>
-__global__ void __launch_bounds__(kMmaThreads, 2)
+__global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)  // 3 A pieces: 120 KB of tiles
     wz2_mma_kernel(const uint8_t* __restrict__ stream, int64_t BM, int64_t BN, const uint8_t* __restrict__ btiles,
-                   int R, int64_t jchunk, double* __restrict__ ws, int64_t Mpad, int* __restrict__ status) {
-  using S = MmaSmem<NR>;
+                   int R, int64_t S, int64_t total, int64_t L, int maxseg, double* __restrict__ ws,
+                   int* __restrict__ status) {
+  using SM = MmaSmem<RATE, NR>;
+  constexpr int PA = MmaPieces<RATE>::kA;
+  constexpr int NP = MmaPieces<RATE>::kProducts;
   constexpr int NW = Wz2Layout<RATE>::kWords;
   constexpr int HALF = NR / 2;  // TMEM columns drained by each of the two warps on a lane quarter
+  constexpr uint32_t kCols = 4 * NR;  // accumulator pairs (big, small) of two groups: 64 or 128 columns
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* As = smem;
-  uint8_t* Bs = smem + S::kA;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::kA + S::kB);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::kA + S::kB + 16);
+  const uint32_t s_base = smem_addr(smem);
+  const uint32_t mma_bar = s_base + SM::kBars;  // two mbarriers: MMAs of buffer 0, 1 done
+  const uint32_t b_bar = mma_bar + 16;          // two mbarriers: B tile of buffer 0, 1 landed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SM::kBars + 32);
 
-  const int t = threadIdx.x, warp = t >> 5;
-  const int64_t band0 = (int64_t)blockIdx.x * kMmaBands;
-  const int split = blockIdx.y;
-  const int64_t J0 = (int64_t)split * jchunk;  // a multiple of the 16-block stage
-  const int64_t J1 = min(BN, J0 + jchunk);
-  const uint32_t bar_a = smem_addr(bar);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int64_t it0 = (int64_t)blockIdx.x * L;
+  const int64_t n = max((int64_t)0, min(total, it0 + L) - it0);
 
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a));
+    mbar_init(mma_bar, 1);
+    mbar_init(mma_bar + 8, 1);
+    mbar_init(b_bar, 1);
+    mbar_init(b_bar + 8, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 0) {  // TMEM: NR fp32 columns (at least 32)
+  if (warp == 0) {  // TMEM: four accumulators of NR fp32 columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tslot)),
-                 "r"(NR < 32 ? 32 : NR));
+                 "r"(kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -228,55 +325,96 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  float hi[HALF], lo[HALF];
-#pragma unroll
-  for (int r = 0; r < HALF; ++r) hi[r] = lo[r] = 0.f;
+  // decode assignment: band 8(warp%4) + lane%8 of the tile, blocks jl and jl+4
+  // of the stage, jl = 8(warp/4) + lane/8
+  const int band_l = 8 * (warp & 3) + (lane & 7);
+  const int jl0 = 8 * (warp >> 2) + (lane >> 3);
+  // drain assignment: tile row 32(warp%4) + lane, accumulator columns HALF(warp/4)..
+  const int m_row = 32 * (warp & 3) + lane;
+  const int c0 = HALF * (warp >> 2);
 
-  const int my_band = t >> 3;
-  const int my_sub = t & 7;
-  const int64_t band = band0 + my_band;
-  constexpr int kBVec = S::kB / 16;                              // uint4 in a B tile
-  constexpr int BV = (kBVec + kMmaThreads - 1) / kMmaThreads;    // per thread (the last one guarded)
-  // two stages of compressed words in flight (ring of 2), one B tile ahead
-  uint32_t w[2][2][NW];
-  uint4 bnext[BV];
-  auto fetch = [&](int slot, int64_t Js) {
+  // Cursors (tile, stage) of the next item to fetch, to copy B for and to
+  // issue; they advance in item order, so the loop has no divisions.
+  const int tile0 = (int)(it0 / S), st0 = (int)(it0 - (int64_t)tile0 * S);
+  int f_tile = tile0, f_st = st0, b_st = st0, m_tile = tile0, m_st = st0;
+
+  uint32_t w[2][2][NW];  // compressed words of two stages (ring), 2 blocks each
+  auto fetch = [&](int slot) {
+    const int64_t band = 32 * (int64_t)f_tile + band_l;
+    const int64_t J = 16 * (int64_t)f_st + jl0;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const int64_t J = Js + my_sub + 8 * u;
-      if (band < BM && J < J1) {
-        wz2_load<RATE>(stream, band * BN + J, w[slot][u]);
+      if (band < BM && J + 4 * u < BN) {
+        wz2_load<RATE>(stream, band * BN + J + 4 * u, w[slot][u]);
       } else {
 #pragma unroll
         for (int i = 0; i < NW; ++i) w[slot][u][i] = 0u;  // a zero block: E = 0, scale 0
       }
     }
+    if (++f_st == S) f_st = 0, ++f_tile;
   };
-  auto fetch_b = [&](int64_t Js) {
-    const uint4* src = reinterpret_cast<const uint4*>(btiles + (Js / kMmaStageBlocks) * (int64_t)S::kB);
+  int64_t copied = -1;  // thread 0: last stage whose B tile copy was started
+  auto b_copy = [&](int64_t k) {  // thread 0 only: B tile of stage k into buffer k % 2
+    const int buf = (int)(k & 1);
+    bulk_copy_g2s(s_base + 2 * SM::kA + buf * SM::kB, btiles + (int64_t)b_st * SM::kB, (uint32_t)SM::kB,
+                  b_bar + 8 * buf);
+    if (++b_st == S) b_st = 0;
+    copied = k;
+  };
+
+  float hi[HALF], lo[HALF];
 #pragma unroll
-    for (int i = 0; i < BV; ++i)
-      if (t + i * kMmaThreads < kBVec) bnext[i] = __ldg(src + t + i * kMmaThreads);
+  for (int r = 0; r < HALF; ++r) hi[r] = lo[r] = 0.f;
+  int cur_tile = tile0;  // tile of the sums in hi/lo
+  auto flush = [&]() {
+    const int64_t seg = (int64_t)blockIdx.x - ((int64_t)cur_tile * S) / L;
+    double* dst = ws + (((int64_t)cur_tile * maxseg + seg) * R) * 128 + m_row;
+#pragma unroll
+    for (int r = 0; r < HALF; ++r) {
+      if (c0 + r < R) dst[(int64_t)(c0 + r) * 128] = (double)hi[r] + (double)lo[r];
+      hi[r] = lo[r] = 0.f;
+    }
   };
-  // The descriptors of a stage never change: base descriptors of the A and B
-  // tiles plus a compile-time offset in 16-byte units in the start-address
-  // field (shared addresses stay below 256 KB, so the field cannot carry).
-  const uint64_t a_base = smem_desc(smem_addr(As), 128, 256);
-  const uint64_t b_base = smem_desc(smem_addr(Bs), 128, 256);
-  if (J0 < J1) {
-    fetch(0, J0);
-    fetch_b(J0);
+  // drain accumulator pair `acc` (big + small), which holds a group of stages of tile `tile`
+  auto drain = [&](int acc, int tile) {
+    if (tile != cur_tile) {
+      flush();
+      cur_tile = tile;
+    }
+    const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(2 * acc * NR + c0);
+#pragma unroll
+    for (int h = 0; h < HALF; h += 8) {
+      float v[8];
+      tmem_load_sum8(ta + h, ta + NR + h, v);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) two_sum_acc(hi[h + r], lo[h + r], v[r]);
+    }
+  };
+
+  const uint64_t a_desc0 = smem_desc(s_base, 128, 256);
+  const uint64_t b_desc0 = smem_desc(s_base + 2 * SM::kA, 128, 256);
+  bool ok = true;          // this thread's waits all ended in time
+  int64_t committed = -1;  // thread 0: last stage whose MMAs were committed
+  // accumulator groups: up to kMmaDrainStages consecutive stages of one tile
+  // share a TMEM accumulator (alternating 0, 1); a group is drained after its
+  // last stage's MMAs complete
+  int gpos = 0, gacc = 0;
+  bool p_ends = false;  // stage k-1 closed its group ...
+  int p_acc = 0, p_tile = tile0;  // ... in accumulator p_acc, of tile p_tile
+  if (n > 0) {
+    fetch(0);
+    if (t == 0) b_copy(0);
   }
-  if (J0 + kMmaStageBlocks < J1) fetch(1, J0 + kMmaStageBlocks);
-  bool ok = true;
-  uint32_t phase = 0;
-  // one stage; `slot` is a literal at every call, so the ring stays in registers
-  auto stage = [&](const int slot, const int64_t Js) -> bool {
-    // ---- A tile: this thread's 2 blocks of its band
+  if (n > 1) fetch(1);
+
+  // one stage; `buf` is a literal at every call, so the ring stays in registers
+  auto stage = [&](const int buf, const int64_t k) -> bool {
+    uint8_t* As = smem + buf * SM::kA;
+    // ---- A tile: this thread's 2 blocks
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const int jl = my_sub + 8 * u;
-      uint32_t (&wu)[NW] = w[slot][u];
+      const int jl = jl0 + 4 * u;
+      uint32_t (&wu)[NW] = w[buf][u];
       const uint32_t E = wu[0] & 0xFFu, K = (wu[0] >> 8) & 31u;
       const float s = E ? __uint_as_float((E + K - 27u) << 23) : 0.f;
       float f[16], V[16];
@@ -285,111 +423,130 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
       const int kstep = jl >> 2, kk = (jl & 3) * 4;
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const int row = 4 * my_band + a;
-        __nv_bfloat16 p[3][4];
+        const float v[4] = {V[4 * a] * s, V[4 * a + 1] * s, V[4 * a + 2] * s, V[4 * a + 3] * s};
+        uint32_t d[PA][2];
+        split_row<PA>(v, d);
+        const uint32_t off = tile_off(32 * a + band_l, kk);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) split3(V[4 * a + b] * s, p[0][b], p[1][b], p[2][b]);
-#pragma unroll
-        for (int pc = 0; pc < 3; ++pc)
-          *reinterpret_cast<uint2*>(As + (pc * kMmaKSteps + kstep) * S::kATile + tile_off(row, kk)) =
-              make_uint2(pack2(p[pc][0], p[pc][1]), pack2(p[pc][2], p[pc][3]));
+        for (int p = 0; p < PA; ++p)
+          *reinterpret_cast<uint2*>(As + (p * kMmaKSteps + kstep) * SM::kATile + off) = make_uint2(d[p][0], d[p][1]);
       }
-    }
-    // ---- B tile: this stage's prebuilt pieces (fetched one stage ahead)
-    {
-      uint4* dst = reinterpret_cast<uint4*>(Bs);
-#pragma unroll
-      for (int i = 0; i < BV; ++i)
-        if (t + i * kMmaThreads < kBVec) dst[t + i * kMmaThreads] = bnext[i];
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor-core reads
-    __syncthreads();
+    if (!__syncthreads_and(ok ? 1 : 0)) return false;
+    // group bookkeeping of stage k (the same in every thread)
+    const bool init = gpos == 0;
+    const int acc = gacc;
+    const int tile_k = m_tile;
+    const bool ends = ++gpos == kMmaDrainStages || m_st == S - 1 || k == n - 1;
+    if (ends) gpos = 0, gacc ^= 1;
+    if (++m_st == S) m_st = 0, ++m_tile;
     if (t == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      constexpr uint32_t idesc = mma_idesc<NR>();
-      uint32_t acc = 0;
+      if (!mbar_wait(b_bar + 8 * buf, (uint32_t)((k >> 1) & 1))) {
+        ok = false;
+        atomicExch(status, WHFF_ETIMEOUT);
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        constexpr uint32_t idesc = mma_idesc<NR>();
+        const uint64_t ad0 = a_desc0 + (uint64_t)((buf * SM::kA) >> 4);
+        const uint64_t bd0 = b_desc0 + (uint64_t)((buf * SM::kB) >> 4);
+        const uint32_t d_big = tmem + (uint32_t)(2 * acc * NR), d_small = d_big + NR;
+        // the cross products first (small accumulator), then A_0 B_0 (big one):
+        // a truncating accumulate then loses little
 #pragma unroll
-      for (int ks = 0; ks < kMmaKSteps; ++ks) {
+        for (int mm = 1; mm <= NP; ++mm) {
+          const int m = mm % NP;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-          // products A_p B_q with p + q <= 2: (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
-          const int pa = m == 2 || m == 4 ? 1 : m == 5 ? 2 : 0;
-          const int pb = m == 1 || m == 4 ? 1 : m == 3 ? 2 : 0;
-          const uint64_t ad = a_base + (uint64_t)(((pa * kMmaKSteps + ks) * S::kATile) >> 4);
-          const uint64_t bd = b_base + (uint64_t)(((pb * kMmaKSteps + ks) * S::kBTile) >> 4);
-          asm volatile(
-              "{\n\t.reg .pred p;\n\t"
-              "setp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-          acc = 1;
+          for (int ks = 0; ks < kMmaKSteps; ++ks) {
+            const int pa = mma_prod_a(PA, m), pb = mma_prod_b(PA, m);
+            const uint64_t ad = ad0 + (uint64_t)(((pa * kMmaKSteps + ks) * SM::kATile) >> 4);
+            const uint64_t bd = bd0 + (uint64_t)(((pb * kMmaKSteps + ks) * MmaBTile<NR>::kBTile) >> 4);
+            const uint32_t accumulate = (init && ks == 0 && (m == 0 || m == 1)) ? 0u : 1u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(m ? d_small : d_big),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+          }
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         mma_bar + 8 * buf)
+                     : "memory");
+        committed = k;
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_a)
-                   : "memory");
     }
-    // loads in flight while the tensor cores work: the B tile of the next stage
-    // and the compressed blocks of the stage after it (this slot is now free)
-    if (Js + kMmaStageBlocks < J1) fetch_b(Js + kMmaStageBlocks);
-    if (Js + 2 * kMmaStageBlocks < J1) fetch(slot, Js + 2 * kMmaStageBlocks);
-    // every thread waits (bounded) for the commit; the CTA then agrees on the
-    // outcome, so a timeout is a uniform exit and never a barrier deadlock
-    if (!__syncthreads_and(mbar_wait(bar_a, phase) ? 1 : 0)) {
-      ok = false;
-      if (t == 0) atomicExch(status, WHFF_ETIMEOUT);
-      (void)mbar_wait(bar_a, phase);  // give the MMAs in flight a second bounded chance
-      return false;
+    // this ring slot is free: the words of stage k+2 are loaded while the MMAs run
+    if (k + 2 < n) fetch(buf);
+    if (k >= 1) {  // stage k-1 (other buffer): wait for its MMAs; drain its group if it closed one
+      const bool done = __all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * (buf ^ 1), (uint32_t)(((k - 1) >> 1) & 1)));
+      if (!done) {
+        if (ok && lane == 0) atomicExch(status, WHFF_ETIMEOUT);
+        ok = false;
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (t == 0 && ok && k + 1 < n) b_copy(k + 1);  // its B tile buffer is free now
+        if (p_ends) drain(p_acc, p_tile);
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      }
+    } else if (t == 0 && ok && k + 1 < n) {
+      b_copy(k + 1);
     }
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    float v[HALF];
-    // lane quarter (warp % 4), column half (warp / 4)
-    tmem_load_row<HALF>(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(HALF * (warp >> 2)), v);
-#pragma unroll
-    for (int r = 0; r < HALF; ++r) two_sum_acc(hi[r], lo[r], v[r]);
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();  // the next stage overwrites the tiles and the accumulator
+    p_ends = ends;
+    p_acc = acc;
+    p_tile = tile_k;
     return true;
   };
-  for (int64_t Js = J0; Js < J1 && ok; Js += 2 * kMmaStageBlocks) {
-    ok = stage(0, Js);
-    if (ok && Js + kMmaStageBlocks < J1) ok = stage(1, Js + kMmaStageBlocks);
+
+  bool alive = true;
+  for (int64_t k = 0; k < n && alive; k += 2) {
+    alive = stage(0, k);
+    if (alive && k + 1 < n) alive = stage(1, k + 1);
   }
-  if (ok) {
-    const int64_t row = 4 * band0 + 32 * (warp & 3) + (t & 31);  // coefficient row of the tile
-    const int c0 = HALF * (warp >> 2);
-    if (row < Mpad) {
-#pragma unroll
-      for (int r = 0; r < HALF; ++r)
-        if (c0 + r < R) ws[((int64_t)split * R + c0 + r) * Mpad + row] = (double)hi[r] + (double)lo[r];
+  if (alive && n > 0) alive = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (alive && n > 0) {  // the last stage, which always closes its group
+    const int buf = (int)((n - 1) & 1);
+    if (__all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * buf, (uint32_t)(((n - 1) >> 1) & 1)))) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      drain(p_acc, p_tile);
+      flush();
+    } else {
+      if (lane == 0) atomicExch(status, WHFF_ETIMEOUT);
+      ok = false;
     }
+  }
+  if (!alive && t == 0) {  // give the MMAs and the copy in flight a second bounded chance
+    if (committed >= 0) (void)mbar_wait(mma_bar + 8 * (int)(committed & 1), (uint32_t)((committed >> 1) & 1));
+    if (copied >= 0) (void)mbar_wait(b_bar + 8 * (int)(copied & 1), (uint32_t)((copied >> 1) & 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NR < 32 ? 32 : NR));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));
   }
 }
 
-// Sum the column splits of Z in order, map each band's 4 coefficient rows to
-// y (2G mix and 2^-3 with the lift, 2^3 without) and update the state in
-// column order.  Thread per band.
+// Sum each band's segment partials in order, map its 4 coefficient rows to y
+// (2G mix and 2^-3 with the lift, 2^3 without) and update the state in column
+// order.  Thread per band.
 template <bool LIFT>
-__global__ void wz2_mma_finish(const double* __restrict__ ws, int ksplit, int R, int64_t Mpad, int64_t M,
+__global__ void wz2_mma_finish(const double* __restrict__ ws, int64_t S, int64_t L, int maxseg, int R, int64_t M,
                                double* __restrict__ y, int64_t ldy, double* __restrict__ state, double decay) {
   const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (4 * I >= M) return;
+  const int64_t tile = I / 32;
+  const int bl = (int)(I % 32);
+  const int nseg = (int)(((tile + 1) * S - 1) / L - (tile * S) / L + 1);
   double s[4] = {0, 0, 0, 0};
   if (state)
     for (int i = 0; i < 4; ++i)
       if (4 * I + i < M) s[i] = state[4 * I + i];
   for (int r = 0; r < R; ++r) {
     double z[4];
-    for (int i = 0; i < 4; ++i) {
-      double t = 0.0;
-      for (int k = 0; k < ksplit; ++k) t += ws[((int64_t)k * R + r) * Mpad + 4 * I + i];
-      z[i] = t;
+    for (int a = 0; a < 4; ++a) {
+      double acc = 0.0;
+      for (int g = 0; g < nseg; ++g) acc += ws[((tile * maxseg + g) * R + r) * 128 + 32 * a + bl];
+      z[a] = acc;
     }
     double yy[4];
     if (LIFT) {

@@ -50,12 +50,13 @@ struct whff_handle {
   int64_t range_len = 0;        // WZ2: blocks per warp range
   int maxseg = 1;               // WZ2: most ranges sharing one band (1 = none shared)
   int ws_rhs = 8;               // right-hand sides the workspace is sized for
-  double* d_ws_mma = nullptr;   // WZ2 tensor-core passes: ksplit x 32 x Mpad partials
+  double* d_ws_mma = nullptr;   // WZ2 tensor-core passes: tiles x maxseg x 32 x 128 partials
   uint8_t* d_btiles = nullptr;  // WZ2 tensor-core passes: B operand pieces per stage
   size_t ws_mma_bytes = 0;
-  int mma_ksplit = 1;
-  int64_t mma_jchunk = 0;
-  int mma_min_rhs = 9;          // passes of at least this many columns use tcgen05
+  int64_t mma_L = 0;            // (tile, stage) items per CTA of the persistent tensor-core grid
+  int mma_ctas = 0;
+  int mma_maxseg = 1;
+  int mma_min_rhs = 9;          // passes of at least this many columns use tcgen05 (whff_set_crossover)
   cudaStream_t create_stream = nullptr;
 };
 
@@ -294,15 +295,23 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
   if (h->maxseg > 1)
     h->ws_bytes = (size_t)h->BM * (size_t)h->maxseg * (size_t)std::min(max_rhs, kMaxRhsKernel) * 4 * 8;
   h->ws_rhs = std::min(max_rhs, kMaxRhsKernel);
-  if ((info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) && max_rhs >= h->mma_min_rhs) {
-    // tensor-core passes: tiles of 32 bands; split the columns so that about two waves of
-    // CTAs (3 resident per SM) are in flight, chunks a multiple of the 16-block stage
-    const int64_t tiles = ceil_div(h->BM, 32);
-    int64_t ks = std::max<int64_t>(1, ceil_div((int64_t)h->sm_count * 3 * 2, tiles));
-    ks = std::min<int64_t>(ks, std::max<int64_t>(1, h->BN / 64));
-    h->mma_jchunk = ceil_div(ceil_div(h->BN, ks), 16) * 16;
-    h->mma_ksplit = (int)ceil_div(h->BN, h->mma_jchunk);
-    h->ws_mma_bytes = (size_t)h->mma_ksplit * (size_t)std::min(max_rhs, 32) * (size_t)h->Mpad * 8;
+  if ((info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) && max_rhs >= 2) {
+    // tensor-core passes: a persistent grid (all resident CTAs) over the items
+    // (tile of 32 bands, stage of 16 blocks), equal contiguous ranges per CTA
+    const bool lift = info.fmt == WHFF_FMT_FIXED_LIFT;
+    const int occ = std::min(mma_occupancy(info.rate, lift, 16), mma_occupancy(info.rate, lift, 32));
+    if (occ < 1) {
+      set_error("whff_create: the tensor-core kernel cannot be resident");
+      return fail(WHFF_ECUDA);
+    }
+    const int64_t tiles = ceil_div(h->BM, 32), stages = ceil_div(h->BN, 16), items = tiles * stages;
+    h->mma_L = ceil_div(items, (int64_t)h->sm_count * occ);
+    h->mma_ctas = (int)ceil_div(items, h->mma_L);
+    h->mma_maxseg = 1;
+    for (int64_t tl = 0; tl < tiles; ++tl)
+      h->mma_maxseg = std::max<int>(h->mma_maxseg, (int)(((tl + 1) * stages - 1) / h->mma_L -
+                                                         (tl * stages) / h->mma_L + 1));
+    h->ws_mma_bytes = (size_t)tiles * (size_t)h->mma_maxseg * (size_t)std::min(max_rhs, 32) * 128 * 8;
     const size_t btile_bytes = (size_t)ceil_div(h->BN, 16) * 3 * 4 * 32 * 16 * 2;  // stages x pieces x ksteps x NR<=32 tile
     h->ws_mma_bytes += btile_bytes;
     if (cudaMalloc(&h->d_ws_mma, h->ws_mma_bytes - btile_bytes) != cudaSuccess ||
@@ -351,7 +360,7 @@ namespace {
 int launch_mma(const whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
                double decay, cudaStream_t st) {
   MmaStep a{h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, h->d_stream, h->info.M, h->info.N, h->BM, h->BN,
-            h->Mpad, x, ldx, R, h->mma_ksplit, h->mma_jchunk, h->d_ws_mma, h->d_btiles, y, ldy, state, decay,
+            x, ldx, R, h->mma_L, h->mma_ctas, h->mma_maxseg, h->d_ws_mma, h->d_btiles, y, ldy, state, decay,
             h->d_status};
   if (mma_launch(a, st)) {
     set_error("whff_step: tensor-core pass failed to launch");
@@ -674,6 +683,24 @@ extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm) {
     return WHFF_EINVAL;
   }
   return apply_config(h, unroll, ctas_per_sm);
+}
+
+extern "C" int whff_get_crossover(const whff_handle* h, int* min_rhs) {
+  if (!h || !min_rhs) {
+    set_error("whff_get_crossover: null argument");
+    return WHFF_EINVAL;
+  }
+  *min_rhs = h->d_ws_mma ? h->mma_min_rhs : 33;
+  return WHFF_OK;
+}
+
+extern "C" int whff_set_crossover(whff_handle* h, int min_rhs) {
+  if (!h || min_rhs < 2 || min_rhs > 33 || (!h->d_ws_mma && min_rhs != 33)) {
+    set_error("whff_set_crossover: WZ2 handles created with max_rhs >= 2; min_rhs in [2, 33]");
+    return WHFF_EINVAL;
+  }
+  h->mma_min_rhs = min_rhs;
+  return WHFF_OK;
 }
 
 // Time every (unroll, CTAs per SM) candidate on this matrix with R = 1 and

@@ -69,13 +69,14 @@ struct MmaStep {
   int rate;
   bool lift;
   const uint8_t* stream;
-  int64_t M, N, BM, BN, Mpad;
+  int64_t M, N, BM, BN;
   const float* x;
   int64_t ldx;
   int R;           // 1..32 (padded to 16 or 32 inside)
-  int ksplit;
-  int64_t jchunk;  // blocks per column split (a multiple of 16)
-  double* ws;      // ksplit x R x Mpad
+  int64_t L;       // (tile, stage) items per CTA: tile = 32 bands, stage = 16 blocks
+  int ctas;        // persistent grid, ceil(items / L)
+  int maxseg;      // most CTAs sharing one tile
+  double* ws;      // tiles x maxseg x R x 128 FP64 partials
   uint8_t* btiles; // B operand pieces of every 16-block stage (built per pass)
   double* y;
   int64_t ldy;
@@ -84,6 +85,8 @@ struct MmaStep {
   int* status;
 };
 int mma_launch(const MmaStep& a, cudaStream_t st);
+// resident CTAs per SM of the tensor-core kernel at this rate for R <= nr (0 on error)
+int mma_occupancy(int rate, bool lift, int nr);
 int scaled_occupancy(int fmt);
 
 template <int RATE>

@@ -81,6 +81,8 @@ def library() -> ctypes.CDLL:
         "whff_tune": (c_int, [P, c_int, P, ctypes.POINTER(dbl)]),
         "whff_get_config": (c_int, [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
         "whff_set_config": (c_int, [P, c_int, c_int]),
+        "whff_get_crossover": (c_int, [P, ctypes.POINTER(c_int)]),
+        "whff_set_crossover": (c_int, [P, c_int]),
         "whff_batch_create": (c_int, [P, P, c_int, ctypes.POINTER(P)]),
         "whff_batch_step": (c_int, [P, P, P, P, P, P, dbl, P]),
         "whff_batch_destroy": (None, [P]),
@@ -207,6 +209,17 @@ class Handle:
 
     def set_config(self, unroll: int, ctas_per_sm: int):
         _check(library().whff_set_config(self._ptr, unroll, ctas_per_sm))
+
+    @property
+    def crossover(self) -> int:
+        """Fewest right-hand sides of a tensor-core pass (33: CUDA cores only)."""
+        v = ctypes.c_int()
+        _check(library().whff_get_crossover(self._ptr, ctypes.byref(v)))
+        return v.value
+
+    @crossover.setter
+    def crossover(self, min_rhs: int):
+        _check(library().whff_set_crossover(self._ptr, int(min_rhs)))
 
     def plan(self):
         """(ksplit, kernel launches per pass of up to 8 right-hand sides)."""

@@ -41,6 +41,8 @@ def _rel(a, b):
     (5, 8, 1500, 1200, 9),
     (5, 24, 64, 20000, 32),    # wide: split columns
     (6, 20, 2050, 700, 40),    # 32 on tensor cores + 8 on CUDA cores
+    (5, 16, 3000, 5000, 24),   # several stages per CTA, CTA ranges crossing tiles
+    (6, 8, 4100, 9000, 16),
 ])
 def test_tensor_core_passes_match_oracle(env, orc, fmt, rate, M, N, R):
     W, torch = env
@@ -62,3 +64,50 @@ def test_tensor_core_passes_match_oracle(env, orc, fmt, rate, M, N, R):
         assert _rel(Y[r], ref[:, r]) <= TOL, (r, _rel(Y[r], ref[:, r]))
     s_ref = orc.state_update(np.ones(M), ref, 0.95)
     assert _rel(s.cpu().numpy(), s_ref) <= TOL
+
+
+@pytest.mark.parametrize("R", [2, 5, 8])
+def test_low_crossover_matches_oracle(env, orc, R):
+    """With the crossover lowered, passes of 2..8 columns run on the tensor
+    cores and meet the same bar."""
+    W, torch = env
+    M, N = 1100, 2300
+    blob = W.whff_compress(_matrix(M, N, 11), 5, 16)
+    Ahat = orc.decode(blob.tobytes())
+    X = np.random.default_rng(R + 100).standard_normal((R, N)).astype(np.float32)
+    ref = orc.gemv64(Ahat, X.T.astype(np.float64))
+    with W.whff_create(blob, max_rhs=8) as h:
+        assert h.crossover == 9
+        h.crossover = 2
+        assert h.crossover == 2
+        x = torch.from_numpy(X).cuda()
+        y = torch.zeros((R, M), dtype=torch.float64, device="cuda")
+        h.step(x, y)
+        torch.cuda.synchronize()
+        assert h.sync_status() == 0
+        Y = y.cpu().numpy()
+        for r in range(R):
+            assert _rel(Y[r], ref[:, r]) <= TOL, r
+        h.crossover = 33  # CUDA cores only: another rounding, the same bar
+        y2 = torch.zeros_like(y)
+        h.step(x, y2)
+        torch.cuda.synchronize()
+        Y2 = y2.cpu().numpy()
+        for r in range(R):
+            assert _rel(Y2[r], ref[:, r]) <= TOL, r
+
+
+def test_crossover_needs_tensor_core_workspace(env):
+    W, torch = env
+    blob = W.whff_compress(_matrix(64, 64, 3), 5, 16)
+    with W.whff_create(blob, max_rhs=1) as h:
+        assert h.crossover == 33
+        with pytest.raises(W.WhffError):
+            h.crossover = 4
+        h.crossover = 33
+    with W.whff_create(blob, max_rhs=4) as h:
+        for bad in (1, 34):
+            with pytest.raises(W.WhffError):
+                h.crossover = bad
+    with W.whff_create(W.whff_compress(_matrix(64, 64, 3), 1, 16), max_rhs=16) as h:
+        assert h.crossover == 33  # WZ1 has no tensor-core passes
