@@ -61,7 +61,7 @@ def parse_args():
     p.add_argument("--sweep-steps", type=int, default=400)
     p.add_argument("--e2e-steps", type=int, default=200)
     p.add_argument("--rhs-sweep", default="8,16,32",
-                   help="right-hand-side counts timed on the headline matrix (R >= 9 runs on tcgen05)")
+                   help="right-hand-side counts timed on the headline matrix, on both engines")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-baseline", action="store_true")
     p.add_argument("--json-out", default=None)

@@ -118,7 +118,7 @@ int whff_plan(const whff_handle* h, int* ksplit, int* launches);
 
 /* One control step (Sec. 2.1 / Sec. 4.4): y[:,r] = Ahat * x[:,r] for r < R,
  * taken in passes: with a WZ2 matrix whose handle allows max_rhs >= 2, passes
- * of crossover..32 columns (default crossover 9, see whff_set_crossover) run
+ * of crossover..32 columns (default crossover 5, see whff_set_crossover) run
  * on the tensor cores (tcgen05: the stored coefficients split exactly into
  * 1-3 BF16 pieces by field width and the transformed x into three, the
  * piece products above 2^-24 accumulate in FP32 TMEM, drained every 64
@@ -176,7 +176,8 @@ int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm);
 
 /* Crossover of the two engines (Sec. 4.4's GEMV with many right-hand sides is
  * a GEMM): passes of at least min_rhs columns run on the tensor cores, smaller
- * ones on the CUDA cores.  Default 9; 33 = CUDA cores only.  Tensor-core
+ * ones on the CUDA cores.  Default 5 (from 5 columns on, one tensor-core
+ * pass is faster than the CUDA cores on GB300); 33 = CUDA cores only.  Tensor-core
  * passes need a WZ2 handle created with max_rhs >= 2 (WHFF_EINVAL otherwise,
  * unless min_rhs = 33); whff_get_crossover reports 33 for handles without
  * them.  Both engines meet the same accuracy bar; their roundings differ. */

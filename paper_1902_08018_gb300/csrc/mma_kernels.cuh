@@ -1,7 +1,7 @@
 // mma_kernels.cuh -- many right-hand sides on the 5th-generation tensor cores.
 //
 // With R right-hand sides the step Y = A X is a dense contraction (Sec. 4.4's
-// GEMV becomes a GEMM), so for R >= 9 the fixed-allocation (WZ2) kernels run
+// GEMV becomes a GEMM), so for R >= 5 (the default crossover) the WZ2 kernels run
 // it on tcgen05.  In the transform domain the contraction is
 //     Z_band = sum_J (s_J V_J) ((2G)^T X_J),   Y_band = (2G) Z_band * 2^-3,
 // a GEMM whose A operand is the stored integer coefficients times a
@@ -35,6 +35,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "whff.h"
 #include "wz2_kernels.cuh"
@@ -46,7 +47,7 @@ constexpr int kMmaThreads = 256;       // 8 warps; warps w and w+4 share TMEM la
 constexpr int kMmaBands = 32;         // 128 coefficient rows per tile
 constexpr int kMmaStageBlocks = 16;   // K = 64 per stage
 constexpr int kMmaKSteps = 4;         // K = 16 per instruction
-constexpr int kMmaDrainStages = 1;    // stages of one tile accumulated in TMEM between drains
+constexpr int kMmaDrainStages = 2;    // stages of one tile accumulated in TMEM between drains
 constexpr uint32_t kMmaSpinLimit = 1u << 22;  // try_wait polls: bounded to seconds
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -233,6 +234,53 @@ __global__ void wz2_mma_btiles(const float* __restrict__ x, int64_t ldx, int64_t
 }
 
 
+// Field k of a block, already times the block scale s = 2^e: the field is
+// OR-ed into the mantissa of 2^(e+23) (creg = its exponent bits) and
+// 2^e (2^23 + 2^(W-1)) (bias) is subtracted -- both exact, so this is
+// (field - 2^(W-1)) * s with one logic op and one add.  A zero block passes
+// mreg = creg = 0 and bias = 0.
+template <int RATE, int K>
+__device__ __forceinline__ float wz2_field_scaled(const uint32_t (&w)[Wz2Layout<RATE>::kWords], uint32_t mreg,
+                                                  uint32_t creg, float bias) {
+  using Lay = Wz2Layout<RATE>;
+  constexpr int off = 13 + Lay::kW * K;
+  constexpr int wi = off / 32, sh = off % 32;
+  uint32_t u;
+  if constexpr (sh + Lay::kW <= 32) {
+    u = w[wi] >> sh;
+  } else {
+    u = __funnelshift_r(w[wi], w[wi + 1], sh);
+  }
+  return __uint_as_float((u & mreg) | creg) - bias;
+}
+
+template <int RATE, int... Ks>
+__device__ __forceinline__ void wz2_fields_scaled_impl(const uint32_t (&w)[Wz2Layout<RATE>::kWords], uint32_t mreg,
+                                                       uint32_t creg, float bias, float (&f)[16],
+                                                       std::integer_sequence<int, Ks...>) {
+  ((f[Ks] = wz2_field_scaled<RATE, Ks>(w, mreg, creg, bias)), ...);
+}
+
+// The 16 coefficients of a block times its scale 2^(E+K-154): the exponent
+// trick needs E + K - 4 <= 254 (|a| below about 2^103); larger blocks take
+// the exact multiply.
+template <int RATE>
+__device__ __forceinline__ void wz2_fields_times_scale(const uint32_t (&w)[Wz2Layout<RATE>::kWords], float (&f)[16]) {
+  using Lay = Wz2Layout<RATE>;
+  const uint32_t E = w[0] & 0xFFu, K = (w[0] >> 8) & 31u;
+  if (E + K <= 258u) {
+    const uint32_t creg = E ? (E + K - 4u) << 23 : 0u;
+    const uint32_t mreg = E ? Lay::kMask : 0u;
+    const float bias = E ? __uint_as_float(creg | (1u << (Lay::kW - 1))) : 0.f;
+    wz2_fields_scaled_impl<RATE>(w, mreg, creg, bias, f, std::make_integer_sequence<int, 16>{});
+  } else {
+    const float s = __uint_as_float((E + K - 27u) << 23);
+    wz2_fields<RATE>(w, f);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) f[k] *= s;
+  }
+}
+
 // cvt.rn.bf16x2.f32: the packed pair (lo in bits 0-15, hi in bits 16-31).
 __device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
   uint32_t d;
@@ -303,6 +351,9 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
   const uint32_t mma_bar = s_base + SM::kBars;  // two mbarriers: MMAs of buffer 0, 1 done
   const uint32_t b_bar = mma_bar + 16;          // two mbarriers: B tile of buffer 0, 1 landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SM::kBars + 32);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SM::kBars + 36);
+  int64_t* last_commit = reinterpret_cast<int64_t*>(smem + SM::kBars + 48);  // last stage whose MMAs were committed
+  int64_t* last_copy = reinterpret_cast<int64_t*>(smem + SM::kBars + 56);    // last stage whose B copy was started
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t it0 = (int64_t)blockIdx.x * L;
@@ -314,6 +365,8 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
     mbar_init(b_bar, 1);
     mbar_init(b_bar + 8, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    *abort_flag = 0;
+    *last_commit = *last_copy = -1;
   }
   if (warp == 0) {  // TMEM: four accumulators of NR fp32 columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tslot)),
@@ -336,30 +389,42 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
   // Cursors (tile, stage) of the next item to fetch, to copy B for and to
   // issue; they advance in item order, so the loop has no divisions.
   const int tile0 = (int)(it0 / S), st0 = (int)(it0 - (int64_t)tile0 * S);
-  int f_tile = tile0, f_st = st0, b_st = st0, m_tile = tile0, m_st = st0;
+  int f_tile = tile0, f_st = st0, m_tile = tile0, m_st = st0;
 
   uint32_t w[2][2][NW];  // compressed words of two stages (ring), 2 blocks each
+  constexpr int64_t kBlockBytes = 4 * NW;
+  // this thread's first block of the next fetch: band 32 f_tile + band_l, block 16 f_st + jl0
+  bool f_band_ok = 32 * (int64_t)f_tile + band_l < BM;
+  const uint8_t* f_ptr = stream + ((32 * (int64_t)f_tile + band_l) * BN + 16 * (int64_t)f_st + jl0) * kBlockBytes;
   auto fetch = [&](int slot) {
-    const int64_t band = 32 * (int64_t)f_tile + band_l;
     const int64_t J = 16 * (int64_t)f_st + jl0;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      if (band < BM && J + 4 * u < BN) {
-        wz2_load<RATE>(stream, band * BN + J + 4 * u, w[slot][u]);
+      if (f_band_ok && J + 4 * u < BN) {
+        wz2_load<RATE>(f_ptr, 4 * u, w[slot][u]);
       } else {
 #pragma unroll
         for (int i = 0; i < NW; ++i) w[slot][u][i] = 0u;  // a zero block: E = 0, scale 0
       }
     }
-    if (++f_st == S) f_st = 0, ++f_tile;
+    if (++f_st == S) {
+      f_st = 0, ++f_tile;
+      f_band_ok = 32 * (int64_t)f_tile + band_l < BM;
+      f_ptr = stream + ((32 * (int64_t)f_tile + band_l) * BN + jl0) * kBlockBytes;
+    } else {
+      f_ptr += 16 * kBlockBytes;
+    }
   };
-  int64_t copied = -1;  // thread 0: last stage whose B tile copy was started
-  auto b_copy = [&](int64_t k) {  // thread 0 only: B tile of stage k into buffer k % 2
+  auto b_copy = [&](int64_t k) {  // thread 0: B tile of stage k into buffer k % 2
     const int buf = (int)(k & 1);
-    bulk_copy_g2s(s_base + 2 * SM::kA + buf * SM::kB, btiles + (int64_t)b_st * SM::kB, (uint32_t)SM::kB,
+    const int64_t st = (it0 + k) % S;
+    bulk_copy_g2s(s_base + 2 * SM::kA + buf * SM::kB, btiles + st * (int64_t)SM::kB, (uint32_t)SM::kB,
                   b_bar + 8 * buf);
-    if (++b_st == S) b_st = 0;
-    copied = k;
+    *last_copy = k;
+  };
+  auto fail = [&]() {  // a wait ran out: the CTA stops at its next barrier
+    atomicExch(status, WHFF_ETIMEOUT);
+    *abort_flag = 1;
   };
 
   float hi[HALF], lo[HALF];
@@ -393,14 +458,13 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
 
   const uint64_t a_desc0 = smem_desc(s_base, 128, 256);
   const uint64_t b_desc0 = smem_desc(s_base + 2 * SM::kA, 128, 256);
-  bool ok = true;          // this thread's waits all ended in time
-  int64_t committed = -1;  // thread 0: last stage whose MMAs were committed
+  bool ok = true;  // this thread's waits all ended in time
   // accumulator groups: up to kMmaDrainStages consecutive stages of one tile
-  // share a TMEM accumulator (alternating 0, 1); a group is drained after its
-  // last stage's MMAs complete
+  // share a TMEM accumulator pair (alternating 0, 1); a group is drained after
+  // its last stage's MMAs complete
   int gpos = 0, gacc = 0;
   bool p_ends = false;  // stage k-1 closed its group ...
-  int p_acc = 0, p_tile = tile0;  // ... in accumulator p_acc, of tile p_tile
+  int p_acc = 0, p_tile = tile0;  // ... in accumulator pair p_acc, of tile p_tile
   if (n > 0) {
     fetch(0);
     if (t == 0) b_copy(0);
@@ -414,16 +478,13 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int jl = jl0 + 4 * u;
-      uint32_t (&wu)[NW] = w[buf][u];
-      const uint32_t E = wu[0] & 0xFFu, K = (wu[0] >> 8) & 31u;
-      const float s = E ? __uint_as_float((E + K - 27u) << 23) : 0.f;
       float f[16], V[16];
-      wz2_fields<RATE>(wu, f);
+      wz2_fields_times_scale<RATE>(w[buf][u], f);
       wz2_unpermute<LIFT>(f, V);
       const int kstep = jl >> 2, kk = (jl & 3) * 4;
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const float v[4] = {V[4 * a] * s, V[4 * a + 1] * s, V[4 * a + 2] * s, V[4 * a + 3] * s};
+        const float v[4] = {V[4 * a], V[4 * a + 1], V[4 * a + 2], V[4 * a + 3]};
         uint32_t d[PA][2];
         split_row<PA>(v, d);
         const uint32_t off = tile_off(32 * a + band_l, kk);
@@ -444,7 +505,7 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
     if (t == 0) {
       if (!mbar_wait(b_bar + 8 * buf, (uint32_t)((k >> 1) & 1))) {
         ok = false;
-        atomicExch(status, WHFF_ETIMEOUT);
+        fail();
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         constexpr uint32_t idesc = mma_idesc<NR>();
@@ -472,7 +533,7 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                          mma_bar + 8 * buf)
                      : "memory");
-        committed = k;
+        *last_commit = k;
       }
     }
     // this ring slot is free: the words of stage k+2 are loaded while the MMAs run
@@ -480,7 +541,7 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
     if (k >= 1) {  // stage k-1 (other buffer): wait for its MMAs; drain its group if it closed one
       const bool done = __all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * (buf ^ 1), (uint32_t)(((k - 1) >> 1) & 1)));
       if (!done) {
-        if (ok && lane == 0) atomicExch(status, WHFF_ETIMEOUT);
+        if (ok && lane == 0) fail();
         ok = false;
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -509,17 +570,17 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       drain(p_acc, p_tile);
       flush();
-    } else {
-      if (lane == 0) atomicExch(status, WHFF_ETIMEOUT);
-      ok = false;
+    } else if (lane == 0) {
+      fail();
     }
-  }
-  if (!alive && t == 0) {  // give the MMAs and the copy in flight a second bounded chance
-    if (committed >= 0) (void)mbar_wait(mma_bar + 8 * (int)(committed & 1), (uint32_t)((committed >> 1) & 1));
-    if (copied >= 0) (void)mbar_wait(b_bar + 8 * (int)(copied & 1), (uint32_t)((copied >> 1) & 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
+  if (t == 0 && *abort_flag) {  // give the MMAs and the copy in flight a second bounded chance
+    const int64_t c = *last_commit, b = *last_copy;
+    if (c >= 0) (void)mbar_wait(mma_bar + 8 * (int)(c & 1), (uint32_t)((c >> 1) & 1));
+    if (b >= 0) (void)mbar_wait(b_bar + 8 * (int)(b & 1), (uint32_t)((b >> 1) & 1));
+  }
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kCols));

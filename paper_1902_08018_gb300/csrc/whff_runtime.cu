@@ -56,7 +56,7 @@ struct whff_handle {
   int64_t mma_L = 0;            // (tile, stage) items per CTA of the persistent tensor-core grid
   int mma_ctas = 0;
   int mma_maxseg = 1;
-  int mma_min_rhs = 9;          // passes of at least this many columns use tcgen05 (whff_set_crossover)
+  int mma_min_rhs = 5;          // passes of at least this many columns use tcgen05 (whff_set_crossover)
   cudaStream_t create_stream = nullptr;
 };
 

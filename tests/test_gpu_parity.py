@@ -112,10 +112,14 @@ def test_step_matches_fp64_oracle(env, orc, fmt, rate, M, N, R):
         Y = run_step(W, torch, h, X)
         Y1 = run_step(W, torch, h, X[:1])
         Y2 = run_step(W, torch, h, X)
+        same_engine = R < h.crossover  # R columns and 1 column both on the CUDA cores
     for r in range(R):
         assert rel_l2(Y[r], ref[:, r]) <= TOL, (r, rel_l2(Y[r], ref[:, r]))
     assert (Y == Y2).all()  # deterministic
-    assert (Y1[0] == Y[0]).all()  # the first column does not depend on the others
+    if same_engine:
+        assert (Y1[0] == Y[0]).all()  # the first column does not depend on the others
+    else:  # a tensor-core pass: another rounding of the same sum
+        assert rel_l2(Y1[0], Y[0]) <= TOL
 
 
 def test_unit_vectors_give_decoded_columns(env, orc):

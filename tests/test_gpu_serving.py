@@ -1,7 +1,9 @@
 """Graph-captured steps and the request server, through the C ABI.
 
   * a captured step replays to exactly the result of whff_step;
-  * served requests get exactly the y they would get alone, in any batch;
+  * served requests get exactly the y they would get alone when their pass
+    ran on the same engine (CUDA cores below the handle's crossover), and y
+    within relative L2 1e-6 of it when a wide pass ran on the tensor cores;
   * the carried state after a bursty trace equals the oracle's recursion
     s <- decay*s + y over the requests in arrival order;
   * models beyond the device-memory budget are refused (WHFF_EBUSY).
@@ -29,6 +31,14 @@ def _matrix(n, seed):
 
     g = int(np.ceil(np.sqrt(n)))
     return workloads.KernelMatrix(n, g, n, 0.1, seed).dense()
+
+
+def _same_as_alone(y, alone, batch, h):
+    """Bit-exact when the pass used the CUDA cores like the single step, else
+    within the accuracy bar (another rounding)."""
+    if batch < h.crossover:
+        return (y == alone).all()
+    return np.linalg.norm(y - alone) <= 1e-6 * np.linalg.norm(alone)
 
 
 def _step_alone(W, torch, h, x):
@@ -101,8 +111,8 @@ def test_server_batches_give_the_results_of_single_service(env, orc):
     assert bat.max() > 1  # some passes were batched
     assert (lat > 0).all()
     for i in range(n_req):
-        alone = _step_alone(W, torch, handles[model[i]], xs[i])
-        assert (ys[i] == alone).all(), i
+        h = handles[model[i]]
+        assert _same_as_alone(ys[i], _step_alone(W, torch, h, xs[i]), bat[i], h), i
     for m, (n, fmt, rate) in enumerate(sizes):
         Ahat = orc.decode(blobs[m].tobytes())
         s = np.zeros(n)
@@ -150,7 +160,7 @@ def test_firm_mode_drops_expired_requests(env, orc):
     Ahat = orc.decode(blob.tobytes())
     s = np.zeros(n)
     for i in np.nonzero(status != 2)[0]:
-        assert (ys[i] == _step_alone(W, torch, h, xs[i])).all()
+        assert _same_as_alone(ys[i], _step_alone(W, torch, h, xs[i]), bat[i], h), i
         s = orc.state_update(s, orc.gemv64(Ahat, xs[i].astype(np.float64)).reshape(n, 1), 0.9)
     assert np.linalg.norm(state - s) <= 1e-6 * np.linalg.norm(s)
     h.destroy()
