@@ -42,7 +42,7 @@ METRIC = "compressed GEMV: HBM GB/s & % peak; p99 control-step latency at rel.er
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 DECAY = 0.99
-FMT_CODES = {"wz1": 1, "bf16": 2, "fp16": 3, "fp8": 4, "wz2-lift": 5, "wz2-bfp": 6}
+FMT_CODES = {"wz1": 1, "bf16": 2, "fp16": 3, "fp8": 4, "wz2-lift": 5, "wz2-bfp": 6, "fp32": 7}
 FMT_NAMES = {v: k for k, v in FMT_CODES.items()}
 ERR_TARGET = 1e-5
 
@@ -72,6 +72,9 @@ def parse_args():
     p.add_argument("--serve-hz", type=float, default=2000.0)
     p.add_argument("--deadline-us", type=float, default=500.0)
     p.add_argument("--firm", type=int, default=1, help="1: drop requests past their deadline (firm real time)")
+    p.add_argument("--shapes", action="store_true",
+                   help="the paper's three GEMV shapes (wide, tall, square) in FP32 and compressed formats")
+    p.add_argument("--shapes-fmts", default="fp32:0,wz2-lift:16,wz2-lift:12,wz1:16,bf16:0")
     p.add_argument("--batched", action="store_true", help="run the batched uneven-instances workload")
     p.add_argument("--batched-fmt", default="wz2-lift:12")
     return p.parse_args()
@@ -608,7 +611,14 @@ def run_batched(args, rank, world, local_rank):
     torch.cuda.synchronize()
     single_ms = e0.elapsed_time(e1) / max(1, steps // 5)
     once = sum(sizes)
-    streamed = sum(sz * max(1, (R + 7) // 8) if R >= 8 else sz for sz, R in zip(sizes, Rs))
+    # bytes read per step: a matrix stepped on the tensor cores (R >= its crossover) is read once per
+    # 32 columns; the CUDA-core classes read it once per class (8, 4, 2, 1) that R uses
+    streamed = 0
+    for sz, R, h in zip(sizes, Rs, handles):
+        if R >= h.crossover:
+            streamed += sz * ((R + 31) // 32)
+        else:
+            streamed += sz * (R // 8 + bin(R % 8).count("1"))
     peak, peak_kind = measured_peaks()
     flops = sum(R * N * (2 * N - 1) for N, R in inst)
     for h in handles:
@@ -627,6 +637,85 @@ def run_batched(args, rank, world, local_rank):
         "one_matrix_at_a_time_ms": round(single_ms, 4), "batch_speedup": round(single_ms / batch_ms, 2),
         "clocks": clk.summary(), "setup_s": round(setup_s, 1),
     }
+
+
+def run_shapes(args, rank, world, local_rank):
+    """The paper's three GEMV shapes (Sec. 5.1, Fig. results_throughput): wide 378 x 256000, tall
+    256000 x 378, square 10000 x 10000, each stored uncompressed in FP32 (the
+    paper's mixed precision, Sec. 4.4) and compressed, against plain FP64 GEMV
+    on the same GPU.  One right-hand side; every timed step reads a matrix that
+    is not in L2 (a 512 MB buffer is written between steps, outside the
+    events).  rel_err: y against FP64 A x on the uncompressed matrix."""
+    import torch
+
+    import paper_1902_08018_gb300 as W
+    import workloads
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = measured_peaks()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    steps = max(5, min(args.steps, 100))
+    specs = []
+    for item in filter(None, args.shapes_fmts.split(",")):
+        name, rate = item.split(":")
+        specs.append((name, FMT_CODES[name], int(rate)))
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    # the paper's P100 figures (Sec. 5.1, Fig. results_throughput), GFLOP/s: context, not a target
+    p100 = {"wide": {"gpu_mp_cuda": 198.3, "cublas_dgemv": 14.59},
+            "tall": {"gpu_mp_cuda": 65.9, "cublas_dgemv": 99.69},
+            "square": {"gpu_mp_cuda": 202.62, "cublas_dgemv": 87.83}}
+    out = {}
+    for sname, M, N in workloads.PAPER_SHAPES:
+        A = workloads.RectKernelMatrix(M, N, 0.05, workloads.SEED_BASE + 70).dense()
+        x64 = np.random.default_rng(workloads.SEED_BASE + 71).standard_normal(N)
+        y_star = A @ x64
+        flops = M * (2 * N - 1)
+        entry = {"M": M, "N": N, "paper_p100_gflops": p100[sname]}
+        xd = torch.from_numpy(x64.astype(np.float32)).to(dev)
+        yd = torch.zeros(M, dtype=torch.float64, device=dev)
+        for name, fmt, rate in specs:
+            blob = W.whff_compress(A, fmt, rate if rate else 16)
+            nbytes = blob.size - 64
+            with W.whff_create(blob, max_rhs=1) as h:
+                ms = timed(lambda: h.step(xd, yd, None, DECAY, stream))
+                torch.cuda.synchronize()
+                y = yd.cpu().numpy()
+            key = f"{name}-{rate}" if rate else name
+            entry[key] = {"ms": round(ms, 4), "bytes": int(nbytes), "GB_s": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                          "pct_hbm": round(100 * nbytes / (ms * 1e-3) / 1e9 / peak, 2),
+                          "effective_gflops": round(flops / (ms * 1e-3) / 1e9, 1),
+                          "rel_err": float(np.linalg.norm(y - y_star) / np.linalg.norm(y_star))}
+            del blob
+        if not args.no_fp64_baseline:
+            Ad = torch.from_numpy(A).to(dev)
+            xd64 = torch.from_numpy(x64).to(dev)
+            ms = timed(lambda: torch.mv(Ad, xd64))
+            entry["fp64_torch_mv"] = {"ms": round(ms, 4), "bytes": A.nbytes,
+                                      "GB_s": round(A.nbytes / (ms * 1e-3) / 1e9, 1),
+                                      "effective_gflops": round(flops / (ms * 1e-3) / 1e9, 1)}
+            del Ad
+        out[sname] = entry
+        del A
+    return {"mode": "shapes", "metric": "compressed GEMV on the paper's shapes: GB/s, GFLOP/s, % HBM peak",
+            "unit": "GB/s", "higher_is_better": True, "n_gpus": world, "steps": steps, "peak_GB_s": peak,
+            "peak_kind": peak_kind, "data": "synthetic smooth-kernel matrices of the paper's shapes",
+            "l2": "flushed between steps (512 MB write, outside the events)", "shapes": out}
 
 
 # ------------------------------------------------------------ reference arm
@@ -683,6 +772,8 @@ def main():
         res = run_serve(args, rank, world, local_rank)
     elif args.batched:
         res = run_batched(args, rank, world, local_rank)
+    elif args.shapes:
+        res = run_shapes(args, rank, world, local_rank)
     else:
         if world > 1:
             import torch

@@ -59,6 +59,12 @@ extern "C" {
  *    round-half-even(C / 2^K).  rate: 8..24, multiple of 4. */
 #define WHFF_FMT_FIXED_LIFT 5
 #define WHFF_FMT_FIXED_BFP 6
+/*  WHFF_FMT_FP32: the matrix uncompressed, A rounded to FP32 (scales all 1),
+ *    for the like-for-like comparison of Sec. 5.1: the step then follows the
+ *    paper's mixed precision (Sec. 4.4) -- every product a*x rounded to FP32,
+ *    the products summed without further rounding error (compensated FP32
+ *    sums, FP64 across lanes) -- up to the order of the additions. */
+#define WHFF_FMT_FP32 7
 
 #define WHFF_OK 0
 #define WHFF_EINVAL -1     /* bad argument (null, size, leading dimension, rate) */
@@ -78,7 +84,8 @@ typedef struct whff_handle whff_handle;
 
 /* Bytes of the blob (64-byte header + stream) for a format, rate and shape;
  * 0 if the combination is invalid.  WZ1 (fmt 1): 64 + ceil(M/4)*ceil(N/4)*2*rate.
- * Scaled formats: 64 + M*roundup(N,16)*elem_bytes + ceil(M/128)*ceil(N/128)*4. */
+ * Scaled formats: 64 + M*roundup(N,16)*elem_bytes + ceil(M/128)*ceil(N/128)*4
+ * (elem_bytes 2, 2, 1, 4 for BF16, FP16, FP8 E4M3, FP32). */
 size_t whff_compressed_size(int fmt, int rate, int64_t M, int64_t N);
 
 /* Compress all of A (offline encoding, Sec. 4.3: "compression can be done
@@ -132,6 +139,21 @@ int whff_plan(const whff_handle* h, int* ksplit, int* launches);
  * bad ld), WHFF_ECUDA. */
 int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
               double decay, void* stream);
+
+/* The step on a slit (Sec. 2.1, divide and conquer: the deformation of the
+ * slit under scan needs only C_slit, a block of rows of the resident C_field;
+ * Fig. whff_algo fetches it from C_field every millisecond):
+ * y[:,r] = Ahat[row0:row0+nrows, :] * x[:,r] for r < R.  Block formats need
+ * row0 % 4 == 0, scaled formats row0 % 128 == 0; the slit's rows are one
+ * contiguous range of the resident stream, so nothing is copied.  y is
+ * nrows x R (ldy >= nrows) and state, if not NULL, has nrows entries (the
+ * slit's own state); both are device pointers.  Same passes, engines and
+ * accuracy as whff_step; the launch plan is the slit's own (its roundings
+ * can differ from the same rows of a whole-matrix step within the bar).
+ * Capturable in a graph.  Errors: WHFF_EINVAL (rows outside the matrix,
+ * misaligned row0, R > max_rhs, bad ld), WHFF_ECUDA. */
+int whff_step_rows(whff_handle* h, int64_t row0, int64_t nrows, const float* x, int R, int64_t ldx, double* y,
+                   int64_t ldy, double* state, double decay, void* stream);
 
 /* The same step on HOST buffers: copies x (N x R, ldx) host->device, runs
  * whff_step into handle-owned device buffers, copies y (M x R, ldy) back, all

@@ -29,6 +29,7 @@ FMT_FP16 = 3
 FMT_FP8E4M3 = 4
 FMT_FIXED_LIFT = 5
 FMT_FIXED_BFP = 6
+FMT_FP32 = 7
 HEADER_BYTES = 64
 
 

@@ -378,7 +378,8 @@ void orc_wz2_decode_block(const uint64_t* words, int rate, int lift, double out[
 /* --------------------------------------------------------- scaled formats */
 /* Per 128x128 tile b: amax = max |a| (FP64); s = RN_fp32(amax / FMTMAX),
  * s = 1 when amax = 0; q = RN_fmt(a / s) with the quotient in FP64 and
- * saturation to +-FMTMAX; decoded value s * q (exact in FP64). */
+ * saturation to +-FMTMAX; decoded value s * q (exact in FP64).  FP32 is
+ * stored unscaled: s = 1 and q = RN_fp32(a). */
 #define SC_TILE 128
 
 typedef struct {
@@ -389,13 +390,17 @@ typedef struct {
   double fmtmax; /* the value that the tile amax is scaled to */
   double satmax; /* saturation bound for q */
   int bytes;
+  int unscaled;  /* 1: every tile scale is 1 */
 } fmtdesc;
 
 static int fmt_desc(int fmt, fmtdesc* d) {
   switch (fmt) {
-    case ORC_FMT_BF16: *d = (fmtdesc){7, -126, 8, 127, 1.0, 1.0, 2}; return 1;
-    case ORC_FMT_FP16: *d = (fmtdesc){10, -14, 5, 15, 32768.0, 32768.0, 2}; return 1;
-    case ORC_FMT_FP8E4M3: *d = (fmtdesc){3, -6, 4, 7, 448.0, 448.0, 1}; return 1;
+    case ORC_FMT_BF16: *d = (fmtdesc){7, -126, 8, 127, 1.0, 1.0, 2, 0}; return 1;
+    case ORC_FMT_FP16: *d = (fmtdesc){10, -14, 5, 15, 32768.0, 32768.0, 2, 0}; return 1;
+    case ORC_FMT_FP8E4M3: *d = (fmtdesc){3, -6, 4, 7, 448.0, 448.0, 1, 0}; return 1;
+    case ORC_FMT_FP32: /* largest finite FP32: (2 - 2^-23) 2^127 */
+      *d = (fmtdesc){23, -126, 8, 127, 1.0, ldexp(2.0 - ldexp(1.0, -23), 127), 4, 1};
+      return 1;
     default: return 0;
   }
 }
@@ -565,7 +570,7 @@ static int encode_scaled(int fmt, const double* A, int64_t M, int64_t N, int64_t
           double a = fabs(A[i * lda + j]);
           if (a > amax) amax = a;
         }
-      float s = amax == 0.0 ? 1.0f : (float)(amax / d.fmtmax);
+      float s = amax == 0.0 || d.unscaled ? 1.0f : (float)(amax / d.fmtmax);
       if (s == 0.0f) s = 1.0f; /* amax so small that the scale underflows */
       union {
         float f;

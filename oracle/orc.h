@@ -55,6 +55,7 @@ extern "C" {
 #define ORC_FMT_FP8E4M3 4
 #define ORC_FMT_FIXED_LIFT 5 /* WZ2: fixed-width fields of the linear lift's coefficients */
 #define ORC_FMT_FIXED_BFP 6  /* WZ2 without transform: fixed-width block floating point */
+#define ORC_FMT_FP32 7       /* A rounded to FP32, every tile scale 1 (the uncompressed comparison) */
 
 /* Error codes (same meaning as the library's, separate definitions). */
 #define ORC_OK 0

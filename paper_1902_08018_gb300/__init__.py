@@ -13,6 +13,7 @@ from .whff import (  # noqa: F401
     FMT_FIXED_LIFT,
     FMT_FP8E4M3,
     FMT_FP16,
+    FMT_FP32,
     FMT_ZFP,
     Graph,
     Handle,
@@ -30,4 +31,5 @@ from .whff import (  # noqa: F401
     whff_step,
     whff_step_host,
     whff_step_noalloc,
+    whff_step_rows,
 )

@@ -33,10 +33,23 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p) {
   lo += err;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+// Sum of the 32 lanes' compensated (hi, lo) pairs, in a fixed butterfly:
+// each level adds the partner's hi with TwoSum (its error is exact whatever
+// the operand order) and the partner's lo plainly, so every lane ends with
+// the same pair, good to about 2^-48.  FP32 work only: on GB300 the FP64
+// pipe is a small fraction of the FP32 one, and only the result is widened.
+__device__ __forceinline__ double warp_sum_pair(float hi, float lo) {
 #pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int o = 16; o; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = hi + h2;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (h2 - bp);
+    hi = s;
+    lo = (lo + l2) + e;
+  }
+  return (double)hi + (double)lo;
 }
 
 // Fold a lane's (hi, lo) sums for 4 rows x R columns and write either the
@@ -50,7 +63,7 @@ __device__ __forceinline__ void finish_band(const float (&hi)[4][R], const float
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int r = 0; r < R; ++r) tot[i][r] = warp_sum((double)hi[i][r] + (double)lo[i][r]);
+    for (int r = 0; r < R; ++r) tot[i][r] = warp_sum_pair(hi[i][r], lo[i][r]);
   // lane (i*R + r) writes value (i, r)
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -192,6 +205,24 @@ struct ScaledTraits<4> {
   }
 };
 
+// FP32 storage (the uncompressed comparison): four values per 16 bytes.
+template <>
+struct ScaledTraits<7> {
+  static constexpr int V = 4;
+  __device__ static __forceinline__ void decode(uint4 raw, float (&f)[4]) {
+    f[0] = __uint_as_float(raw.x);
+    f[1] = __uint_as_float(raw.y);
+    f[2] = __uint_as_float(raw.z);
+    f[3] = __uint_as_float(raw.w);
+  }
+};
+
+// bytes per element of a scaled format
+template <int FMT>
+__host__ __device__ constexpr int scaled_elem_bytes() {
+  return FMT == 4 ? 1 : FMT == 7 ? 4 : 2;
+}
+
 // --------------------------------------------------- split-K epilogue (FP64)
 static __global__ void splitk_epilogue_kernel(const double* __restrict__ ws, int ksplit, int R, int64_t Mpad, int64_t M,
                                        double* __restrict__ y, int64_t ldy, double* __restrict__ state,
@@ -239,7 +270,7 @@ __global__ void scaled_decompress_kernel(const uint8_t* __restrict__ payload, co
                                          int64_t ldo) {
   using T = ScaledTraits<FMT>;
   constexpr int V = T::V;
-  constexpr int EB = FMT == 4 ? 1 : 2;
+  constexpr int EB = scaled_elem_bytes<FMT>();
   const int64_t chunks_per_row = ld / V;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= M * chunks_per_row) return;

@@ -1,5 +1,6 @@
-// Scaled-format GEMV launches (BF16, FP16, FP8 E4M3): instantiation unit.
+// Scaled-format GEMV launches (BF16, FP16, FP8 E4M3, FP32): instantiation unit.
 #include "scaled_kernels.cuh"
+#include "whff_blob.h"
 #include "wz2_dispatch.h"
 
 namespace whff {
@@ -29,11 +30,12 @@ int scaled_launch(const ScaledStep& a, cudaStream_t st) {
     case 2: e = scaled_fmt<2>(a, st); break;
     case 3: e = scaled_fmt<3>(a, st); break;
     case 4: e = scaled_fmt<4>(a, st); break;
+    case 7: e = scaled_fmt<7>(a, st); break;
     default: return -1;
   }
   if (e) return e;
   if (a.maxseg > 1) {  // shared bands: the chunks of a band are the "blocks" of the segment epilogue
-    const int V = a.fmt == 4 ? 16 : 8;
+    const int V = scaled_vec(a.fmt);
     dev::wz2_segment_epilogue<<<(unsigned)((a.M + 255) / 256), 256, 0, st>>>(a.ws, a.M, a.ld / V, a.L, a.maxseg,
                                                                             a.R, a.y, a.ldy, a.state, a.decay);
   }
@@ -47,6 +49,7 @@ int scaled_occupancy(int fmt) {
   if (fmt == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<2, 1>, threads, 0);
   if (fmt == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<3, 1>, threads, 0);
   if (fmt == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<4, 1>, threads, 0);
+  if (fmt == 7) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<7, 1>, threads, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -5,7 +5,9 @@
 // grid split the band-major sequence of 16-byte column chunks of all 4-row
 // bands into equal contiguous ranges; a lane keeps two chunks (4 rows each) in
 // flight; each group of 4 products enters a TwoSum accumulator together with
-// the exact rounding error of its product with the tile scale.
+// the exact rounding error of its product with the tile scale.  FP32 storage
+// (FMT 7, unit scales) follows the paper's mixed precision instead (Sec. 4.4):
+// every product is rounded to FP32 on its own and enters the TwoSum alone.
 #pragma once
 #include <cstdint>
 
@@ -52,6 +54,13 @@ __device__ __forceinline__ void scaled_chunk(const uint8_t* __restrict__ payload
     if (row >= M) break;
     float f[V];
     T::decode(raw[i], f);
+    if constexpr (FMT == 7) {  // products rounded one by one, summed without loss
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int v = 0; v < V; ++v) two_sum_acc(hi[i][r], lo[i][r], __fmul_rn(f[v], xv[r][v]));
+      continue;
+    }
     const float s = __ldg(scales + (row / 128) * TN + tcol);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -72,7 +81,7 @@ __device__ __forceinline__ void scaled_chunk(const uint8_t* __restrict__ payload
 template <int FMT>
 __device__ __forceinline__ void scaled_load(const uint8_t* __restrict__ payload, int64_t M, int64_t ld,
                                             int64_t row0, int64_t c, uint4 (&raw)[4]) {
-  constexpr int EB = FMT == 4 ? 1 : 2;
+  constexpr int EB = scaled_elem_bytes<FMT>();
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int64_t row = row0 + i;

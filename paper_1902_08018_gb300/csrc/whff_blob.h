@@ -9,7 +9,7 @@
 // (I*ceil(N/4) + J) * 2*rate, i.e. row-major block order, so a band of block
 // rows is one contiguous byte range.
 // Scaled stream: payload M x ld elements (ld = roundup(N, 16)), row-major,
-// then FP32 scales, ceil(M/128) x ceil(N/128), row-major.
+// then FP32 scales, ceil(M/128) x ceil(N/128), row-major (all 1 for FP32).
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -32,7 +32,9 @@ struct BlobInfo {
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t scaled_ld(int64_t N) { return ceil_div(N, 16) * 16; }
 
-int elem_bytes(int fmt);  // 2, 2, 1 for BF16, FP16, FP8; 0 otherwise
+int elem_bytes(int fmt);  // 2, 2, 1, 4 for BF16, FP16, FP8, FP32; 0 otherwise
+// values per 16-byte chunk of a scaled format's row
+inline int scaled_vec(int fmt) { return 16 / (fmt == 4 ? 1 : fmt == 7 ? 4 : 2); }
 bool rate_valid(int rate);       // WZ1: 4..64, multiple of 4
 bool wz2_rate_valid(int rate);   // WZ2: 8..24, multiple of 4
 bool is_blocked(int fmt);        // 4x4-block formats (WZ1, WZ2)

@@ -29,6 +29,8 @@ int elem_bytes(int fmt) {
       return 2;
     case WHFF_FMT_FP8E4M3:
       return 1;
+    case WHFF_FMT_FP32:
+      return 4;
     default:
       return 0;
   }
@@ -344,13 +346,14 @@ int encode_block_wz2(const float* vals, int rate, bool lift, uint64_t* out) {
 // --------------------------------------------------------- scaled formats
 struct FmtSpec {
   int mant, emin, bias, ebits;
-  double fmtmax;
+  double fmtmax;  // the value a tile's amax is scaled to; 0: no scaling (scale 1)
 };
 bool fmt_spec(int fmt, FmtSpec* s) {
   switch (fmt) {
     case WHFF_FMT_BF16: *s = {7, -126, 127, 8, 1.0}; return true;
     case WHFF_FMT_FP16: *s = {10, -14, 15, 5, 32768.0}; return true;
     case WHFF_FMT_FP8E4M3: *s = {3, -6, 7, 4, 448.0}; return true;
+    case WHFF_FMT_FP32: *s = {23, -126, 127, 8, 0.0}; return true;
     default: return false;
   }
 }
@@ -364,9 +367,10 @@ uint32_t round_to_format(double v, const FmtSpec& f) {
   uint32_t sign_bit = sign << (f.mant + f.ebits);
   int E = (int)((db >> 52) & 0x7FF);
   uint64_t frac = db & ((1ull << 52) - 1);
-  // saturation pattern (fmtmax is a normal value of the format)
+  // saturation pattern (the format's largest finite value when it is unscaled)
+  const double fmtmax = f.fmtmax > 0.0 ? f.fmtmax : std::ldexp(2.0 - std::ldexp(1.0, -f.mant), (1 << f.ebits) - 2 - f.bias);
   int sat_e;
-  double sat_m = std::frexp(f.fmtmax, &sat_e);  // fmtmax = sat_m * 2^sat_e
+  double sat_m = std::frexp(fmtmax, &sat_e);  // fmtmax = sat_m * 2^sat_e
   uint32_t sat_pat = ((uint32_t)(sat_e - 1 + f.bias) << f.mant) |
                      (uint32_t)(std::ldexp(sat_m, f.mant + 1) - std::ldexp(1.0, f.mant));
   if (E == 0) return sign_bit;  // zero or FP64 subnormal: far below every format's quantum
@@ -388,7 +392,7 @@ uint32_t round_to_format(double v, const FmtSpec& f) {
     ++ex;
   }
   // compare against fmtmax: value = q * 2^(ex - mant)
-  if (std::ldexp((double)q, ex - f.mant) > f.fmtmax) return sign_bit | sat_pat;
+  if (std::ldexp((double)q, ex - f.mant) > fmtmax) return sign_bit | sat_pat;
   if (q < (1ull << f.mant)) return sign_bit | (uint32_t)q;  // subnormal of the format
   return sign_bit | ((uint32_t)(ex + f.bias) << f.mant) | (uint32_t)(q - (1ull << f.mant));
 }
@@ -465,7 +469,7 @@ int encode_band_scaled(uint8_t* stream, const BlobInfo& b, const double* band, i
         }
         amax = std::max(amax, std::fabs(a));
       }
-    float s = amax == 0.0 ? 1.0f : (float)(amax / f.fmtmax);
+    float s = amax == 0.0 || f.fmtmax == 0.0 ? 1.0f : (float)(amax / f.fmtmax);
     if (s == 0.0f) s = 1.0f;
     uint32_t sb;
     std::memcpy(&sb, &s, 4);
@@ -474,8 +478,7 @@ int encode_band_scaled(uint8_t* stream, const BlobInfo& b, const double* band, i
       for (int64_t j = j0; j < j1; ++j) {
         uint32_t pat = round_to_format(band[(i - row0) * lda + j] / (double)s, f);
         uint8_t* p = stream + ((uint64_t)i * (uint64_t)ld + (uint64_t)j) * (uint64_t)eb;
-        p[0] = uint8_t(pat);
-        if (eb == 2) p[1] = uint8_t(pat >> 8);
+        for (int k = 0; k < eb; ++k) p[k] = uint8_t(pat >> (8 * k));
       }
   });
   return err.load();

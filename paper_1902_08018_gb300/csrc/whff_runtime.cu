@@ -57,6 +57,9 @@ struct whff_handle {
   int mma_ctas = 0;
   int mma_maxseg = 1;
   int mma_min_rhs = 5;          // passes of at least this many columns use tcgen05 (whff_set_crossover)
+  int mma_occ = 0;              // resident tensor-core CTAs per SM
+  size_t ws_mma_cap = 0;        // bytes of d_ws_mma
+  const float* d_scales = nullptr;  // scaled formats: the tile scales after the payload
   cudaStream_t create_stream = nullptr;
 };
 
@@ -74,7 +77,7 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 void choose_ranges(whff_handle* h) {
   if (!is_blocked(h->info.fmt)) {  // scaled formats: units are 16-byte column chunks of a 4-row band
     h->BM = ceil_div(h->info.M, 4);
-    h->BN = scaled_ld(h->info.N) / (h->info.fmt == WHFF_FMT_FP8E4M3 ? 16 : 8);
+    h->BN = scaled_ld(h->info.N) / scaled_vec(h->info.fmt);
   }
   const int64_t total = h->BM * h->BN;
   const int64_t warps_cap = (int64_t)h->sm_count * h->ctas_per_sm * dev::kWarpsPerCta;
@@ -106,7 +109,7 @@ void choose_split(whff_handle* h) {
     h->ksplit = (int)std::min<int64_t>(ks, 256);
     h->chunk = (h->BN + h->ksplit - 1) / h->ksplit;
   } else {
-    const int V = h->info.fmt == WHFF_FMT_FP8E4M3 ? 16 : 8;
+    const int V = scaled_vec(h->info.fmt);
     const int64_t ld = scaled_ld(h->info.N);
     const int64_t unit = 32 * V;  // columns per warp iteration
     const int64_t units = (ld + unit - 1) / unit;
@@ -115,6 +118,29 @@ void choose_split(whff_handle* h) {
     h->chunk = ((units + h->ksplit - 1) / h->ksplit) * unit;
     h->ksplit = (int)((ld + h->chunk - 1) / h->chunk);
   }
+}
+
+// Persistent tensor-core grid: `ctas` CTAs at most over the items (tile of
+// 32 bands, stage of 16 blocks), equal contiguous ranges.
+void plan_mma(whff_handle* h, int64_t ctas) {
+  const int64_t tiles = ceil_div(h->BM, 32), stages = ceil_div(h->BN, 16), items = tiles * stages;
+  h->mma_L = ceil_div(items, std::max<int64_t>(1, ctas));
+  h->mma_ctas = (int)ceil_div(items, h->mma_L);
+  h->mma_maxseg = 1;
+  for (int64_t tl = 0; tl < tiles; ++tl)
+    h->mma_maxseg = std::max<int>(h->mma_maxseg,
+                                  (int)(((tl + 1) * stages - 1) / h->mma_L - (tl * stages) / h->mma_L + 1));
+}
+
+size_t mma_ws_need(const whff_handle* h, int R) {
+  return (size_t)ceil_div(h->BM, 32) * (size_t)h->mma_maxseg * (size_t)R * 128 * 8;
+}
+
+// Workspace bytes a CUDA-core pass of the plan needs.
+size_t ws_need(const whff_handle* h) {
+  if (h->info.fmt == WHFF_FMT_ZFP)
+    return h->ksplit > 1 ? (size_t)h->ksplit * (size_t)h->ws_rhs * (size_t)h->Mpad * 8 : 0;
+  return h->maxseg > 1 ? (size_t)h->BM * (size_t)h->maxseg * (size_t)h->ws_rhs * 4 * 8 : 0;
 }
 
 template <int NW32>
@@ -192,9 +218,7 @@ int launch_scaled(const whff_handle* h, const float* x, int R, int64_t ldx, bool
                   double* state, double decay, cudaStream_t st) {
   const auto& b = h->info;
   const int64_t ld = scaled_ld(b.N);
-  ScaledStep a{b.fmt, h->d_stream,
-               reinterpret_cast<const float*>(h->d_stream + (uint64_t)b.M * (uint64_t)ld * (uint64_t)elem_bytes(b.fmt)),
-               b.M, b.N, ld, ceil_div(b.N, kScaleTile), x, ldx, vec, h->range_len, h->maxseg, h->d_ws, y, ldy, state,
+  ScaledStep a{b.fmt, h->d_stream, h->d_scales, b.M, b.N, ld, ceil_div(b.N, kScaleTile), x, ldx, vec, h->range_len, h->maxseg, h->d_ws, y, ldy, state,
                decay, h->range_ctas, R};
   if (scaled_launch(a, st)) {
     set_error("whff_step: scaled formats take R 1, 2, 4 or 8 per pass");
@@ -218,6 +242,7 @@ int launch_pass(const whff_handle* h, const float* x, int R, int64_t ldx, double
     case WHFF_FMT_BF16:
     case WHFF_FMT_FP16:
     case WHFF_FMT_FP8E4M3:
+    case WHFF_FMT_FP32:
       e = launch_scaled(h, x, R, ldx, vec, y, ldy, state, decay, st);
       break;
     default:
@@ -304,14 +329,10 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
       set_error("whff_create: the tensor-core kernel cannot be resident");
       return fail(WHFF_ECUDA);
     }
-    const int64_t tiles = ceil_div(h->BM, 32), stages = ceil_div(h->BN, 16), items = tiles * stages;
-    h->mma_L = ceil_div(items, (int64_t)h->sm_count * occ);
-    h->mma_ctas = (int)ceil_div(items, h->mma_L);
-    h->mma_maxseg = 1;
-    for (int64_t tl = 0; tl < tiles; ++tl)
-      h->mma_maxseg = std::max<int>(h->mma_maxseg, (int)(((tl + 1) * stages - 1) / h->mma_L -
-                                                         (tl * stages) / h->mma_L + 1));
-    h->ws_mma_bytes = (size_t)tiles * (size_t)h->mma_maxseg * (size_t)std::min(max_rhs, 32) * 128 * 8;
+    h->mma_occ = occ;
+    plan_mma(h, (int64_t)h->sm_count * occ);
+    h->ws_mma_cap = mma_ws_need(h, std::min(max_rhs, 32));
+    h->ws_mma_bytes = h->ws_mma_cap;
     const size_t btile_bytes = (size_t)ceil_div(h->BN, 16) * 3 * 4 * 32 * 16 * 2;  // stages x pieces x ksteps x NR<=32 tile
     h->ws_mma_bytes += btile_bytes;
     if (cudaMalloc(&h->d_ws_mma, h->ws_mma_bytes - btile_bytes) != cudaSuccess ||
@@ -336,6 +357,9 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
     set_error(std::string("whff_create: upload failed: ") + cudaGetErrorString(cudaGetLastError()));
     return fail(WHFF_ECUDA);
   }
+  if (!is_blocked(info.fmt))
+    h->d_scales = reinterpret_cast<const float*>(h->d_stream + (uint64_t)info.M * (uint64_t)scaled_ld(info.N) *
+                                                                   (uint64_t)elem_bytes(info.fmt));
   *out = h;
   return WHFF_OK;
 }
@@ -382,15 +406,13 @@ extern "C" int whff_plan(const whff_handle* h, int* ksplit, int* launches) {
   return WHFF_OK;
 }
 
-extern "C" int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
-                         double decay, void* stream) {
-  if (!h || !x || !y || R <= 0 || R > h->max_rhs || ldx < h->info.N || ldy < h->info.M) {
-    set_error("whff_step: null pointer, R out of [1, max_rhs], or leading dimension too small");
-    return WHFF_EINVAL;
-  }
-  const cudaStream_t st = as_stream(stream);
-  // right-hand sides go through the kernel in passes of 8, 4, 2, 1; the state
-  // update is applied pass by pass, which keeps the column order r = 0..R-1
+namespace whff {
+namespace {
+// The passes of one step on a handle or on a row view of it: up to 32
+// columns per tensor-core pass, else 8, 4, 2, 1 per CUDA-core pass; the state
+// update is applied pass by pass, which keeps the column order r = 0..R-1.
+int step_passes(const whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
+                double decay, cudaStream_t st) {
   int r0 = 0;
   while (r0 < R) {
     const int left = R - r0;
@@ -407,6 +429,71 @@ extern "C" int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, dou
     if (e) return e;
   }
   return WHFF_OK;
+}
+}  // namespace
+}  // namespace whff
+
+extern "C" int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
+                         double decay, void* stream) {
+  if (!h || !x || !y || R <= 0 || R > h->max_rhs || ldx < h->info.N || ldy < h->info.M) {
+    set_error("whff_step: null pointer, R out of [1, max_rhs], or leading dimension too small");
+    return WHFF_EINVAL;
+  }
+  return step_passes(h, x, R, ldx, y, ldy, state, decay, as_stream(stream));
+}
+
+// A slit (Sec. 2.1, divide and conquer: C_slit is a block of rows of the
+// resident C_field): rows [row0, row0 + nrows) of the matrix, which are
+// one contiguous byte range of its stream.  The view shares the handle's
+// buffers and gets its own launch plan, shrunk until its partials fit the
+// handle's workspaces.
+extern "C" int whff_step_rows(whff_handle* h, int64_t row0, int64_t nrows, const float* x, int R, int64_t ldx,
+                              double* y, int64_t ldy, double* state, double decay, void* stream) {
+  if (!h || !x || !y || R <= 0 || R > h->max_rhs || ldx < h->info.N || row0 < 0 || nrows <= 0 ||
+      row0 + nrows > h->info.M || ldy < nrows) {
+    set_error("whff_step_rows: null pointer, R out of [1, max_rhs], rows outside the matrix, or ld too small");
+    return WHFF_EINVAL;
+  }
+  const int fmt = h->info.fmt;
+  const bool blocked = is_blocked(fmt);
+  if (row0 % (blocked ? 4 : kScaleTile)) {
+    set_error("whff_step_rows: row0 must be a multiple of 4 (block formats) or 128 (scaled formats)");
+    return WHFF_EINVAL;
+  }
+  whff_handle v = *h;
+  v.info.M = nrows;
+  v.Mpad = ceil_div(nrows, 4) * 4;
+  if (blocked) {
+    v.BM = ceil_div(nrows, 4);
+    v.d_stream = h->d_stream + (uint64_t)(row0 / 4) * (uint64_t)h->BN * (uint64_t)(2 * h->info.rate);
+  } else {
+    v.d_stream = h->d_stream + (uint64_t)row0 * (uint64_t)scaled_ld(h->info.N) * (uint64_t)elem_bytes(fmt);
+    v.d_scales = h->d_scales + (row0 / kScaleTile) * ceil_div(h->info.N, kScaleTile);
+  }
+  choose_split(&v);
+  for (int c = v.ctas_per_sm; ws_need(&v) > h->ws_bytes; ) {  // fewer warps: longer ranges, fewer segments
+    if (fmt == WHFF_FMT_ZFP) {
+      v.ksplit = (int)std::max<size_t>(1, h->ws_bytes / ((size_t)v.ws_rhs * (size_t)v.Mpad * 8));
+      v.chunk = ceil_div(v.BN, v.ksplit);
+      v.ksplit = (int)ceil_div(v.BN, v.chunk);
+      if (v.ksplit > 1 && ws_need(&v) > h->ws_bytes) v.ksplit = 1, v.chunk = v.BN;
+      break;
+    }
+    if (c == 1) {
+      set_error("whff_step_rows: the view's partials do not fit the workspace");
+      return WHFF_EINVAL;
+    }
+    v.ctas_per_sm = --c;
+    choose_ranges(&v);
+  }
+  if (h->d_ws_mma) {
+    int64_t ctas = (int64_t)h->sm_count * h->mma_occ;
+    for (plan_mma(&v, ctas); mma_ws_need(&v, std::min(R, 32)) > h->ws_mma_cap && ctas > 1;
+         plan_mma(&v, ctas = ctas * 3 / 4)) {
+    }
+    if (mma_ws_need(&v, std::min(R, 32)) > h->ws_mma_cap) v.mma_min_rhs = 33;  // CUDA cores only
+  }
+  return step_passes(&v, x, R, ldx, y, ldy, state, decay, as_stream(stream));
 }
 
 extern "C" int whff_step_host(whff_handle* h, const float* x_host, int R, int64_t ldx, double* y_host, int64_t ldy,
@@ -589,17 +676,18 @@ extern "C" int whff_decompress(whff_handle* h, double* out, int64_t ldo, void* s
     }
   } else {
     const int64_t ld = scaled_ld(b.N), TN = ceil_div(b.N, kScaleTile);
-    const float* scales =
-        reinterpret_cast<const float*>(h->d_stream + (uint64_t)b.M * (uint64_t)ld * (uint64_t)elem_bytes(b.fmt));
-    const int V = b.fmt == WHFF_FMT_FP8E4M3 ? 16 : 8;
+    const float* scales = h->d_scales;
+    const int V = scaled_vec(b.fmt);
     const int64_t work = b.M * (ld / V);
     const unsigned grid = (unsigned)((work + threads - 1) / threads);
     if (b.fmt == WHFF_FMT_BF16)
       dev::scaled_decompress_kernel<2><<<grid, threads, 0, st>>>(h->d_stream, scales, b.M, b.N, ld, TN, out, ldo);
     else if (b.fmt == WHFF_FMT_FP16)
       dev::scaled_decompress_kernel<3><<<grid, threads, 0, st>>>(h->d_stream, scales, b.M, b.N, ld, TN, out, ldo);
-    else
+    else if (b.fmt == WHFF_FMT_FP8E4M3)
       dev::scaled_decompress_kernel<4><<<grid, threads, 0, st>>>(h->d_stream, scales, b.M, b.N, ld, TN, out, ldo);
+    else
+      dev::scaled_decompress_kernel<7><<<grid, threads, 0, st>>>(h->d_stream, scales, b.M, b.N, ld, TN, out, ldo);
   }
   WHFF_CUDA_TRY(cudaGetLastError());
   return WHFF_OK;

@@ -115,7 +115,7 @@ __device__ __forceinline__ void band_finish(const float (&hi)[4][R], const float
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int r = 0; r < R; ++r) z[i][r] = warp_sum((double)hi[i][r] + (double)lo[i][r]);
+    for (int r = 0; r < R; ++r) z[i][r] = warp_sum_pair(hi[i][r], lo[i][r]);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     double t[4];

@@ -20,6 +20,7 @@ FMT_FP16 = 3
 FMT_FP8E4M3 = 4
 FMT_FIXED_LIFT = 5
 FMT_FIXED_BFP = 6
+FMT_FP32 = 7
 
 _ERRORS = {
     -1: "WHFF_EINVAL",
@@ -82,6 +83,7 @@ def library() -> ctypes.CDLL:
         "whff_get_config": (c_int, [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
         "whff_set_config": (c_int, [P, c_int, c_int]),
         "whff_get_crossover": (c_int, [P, ctypes.POINTER(c_int)]),
+        "whff_step_rows": (c_int, [P, i64, i64, P, c_int, i64, P, i64, P, dbl, P]),
         "whff_set_crossover": (c_int, [P, c_int]),
         "whff_batch_create": (c_int, [P, P, c_int, ctypes.POINTER(P)]),
         "whff_batch_step": (c_int, [P, P, P, P, P, P, dbl, P]),
@@ -157,7 +159,8 @@ def _vec_args(t, rows: int, name: str, dtype):
         return t.data_ptr(), 1, rows
     if t.dim() != 2 or t.stride(1) != 1 or t.shape[1] < rows:
         raise WhffError(-1, f"{name}: shape (R, {rows}) with contiguous rows expected")
-    return t.data_ptr(), t.shape[0], t.stride(0)
+    # one row: its stride is arbitrary (numpy's x[None, :] has stride 0); any ld >= rows works
+    return t.data_ptr(), t.shape[0], t.stride(0) if t.shape[0] > 1 else max(t.stride(0), rows)
 
 
 class Handle:
@@ -230,6 +233,9 @@ class Handle:
     def step(self, x, y, state=None, decay: float = 0.99, stream=None):
         whff_step(self, x, y, state, decay, stream)
 
+    def step_rows(self, row0: int, nrows: int, x, y, state=None, decay: float = 0.99, stream=None):
+        whff_step_rows(self, row0, nrows, x, y, state, decay, stream)
+
     def step_host(self, x_host: np.ndarray, y_host: np.ndarray, state=None, decay: float = 0.99, stream=None):
         whff_step_host(self, x_host, y_host, state, decay, stream)
 
@@ -278,6 +284,23 @@ def whff_step(h: Handle, x, y, state=None, decay: float = 0.99, stream=None):
         if Rs != 1:
             raise WhffError(-1, "state must be a vector")
     _check(library().whff_step(h.ptr, xp, R, ldx, yp, ldy, sp or None, float(decay), _stream_ptr(stream)))
+
+
+def whff_step_rows(h: Handle, row0: int, nrows: int, x, y, state=None, decay: float = 0.99, stream=None):
+    """A slit step: y (nrows,) or (R, nrows) = rows row0 .. row0+nrows-1 of the matrix times x."""
+    import torch
+
+    xp, R, ldx = _vec_args(x, h.N, "x", torch.float32)
+    yp, Ry, ldy = _vec_args(y, nrows, "y", torch.float64)
+    if Ry != R:
+        raise WhffError(-1, "x and y disagree on the number of right-hand sides")
+    sp = 0
+    if state is not None:
+        sp, Rs, _ = _vec_args(state, nrows, "state", torch.float64)
+        if Rs != 1:
+            raise WhffError(-1, "state must be a vector")
+    _check(library().whff_step_rows(h.ptr, int(row0), int(nrows), xp, R, ldx, yp, ldy, sp or None, float(decay),
+                                    _stream_ptr(stream)))
 
 
 def whff_step_host(h: Handle, x_host: np.ndarray, y_host: np.ndarray, state=None, decay: float = 0.99, stream=None):

@@ -40,12 +40,13 @@ def test_compressed_size_formula(W):
     assert W.compressed_size(W.FMT_ZFP, 6, 8, 8) == 0  # rate not a multiple of 4
     assert W.compressed_size(W.FMT_ZFP, 16, 0, 8) == 0
     assert W.compressed_size(W.FMT_BF16, 0, 200, 150) == 64 + 200 * 160 * 2 + 2 * 2 * 4
+    assert W.compressed_size(W.FMT_FP32, 0, 200, 150) == 64 + 200 * 160 * 4 + 2 * 2 * 4
     assert W.compressed_size(W.FMT_FIXED_LIFT, 16, 5, 9) == 64 + 2 * 3 * 32
     assert W.compressed_size(W.FMT_FIXED_LIFT, 4, 8, 8) == 0  # WZ2 rates are 8..24
     assert W.compressed_size(W.FMT_FIXED_BFP, 28, 8, 8) == 0
 
 
-@pytest.mark.parametrize("fmt,rate", [(1, 4), (1, 8), (1, 12), (1, 16), (1, 24), (1, 36), (2, 0), (3, 0), (4, 0),
+@pytest.mark.parametrize("fmt,rate", [(1, 4), (1, 8), (1, 12), (1, 16), (1, 24), (1, 36), (2, 0), (3, 0), (4, 0), (7, 0),
                                       (5, 8), (5, 12), (5, 16), (5, 24), (6, 8), (6, 16), (6, 20)])
 def test_encoder_byte_identical_to_oracle(W, orc, fmt, rate):
     import workloads

@@ -38,7 +38,7 @@ def smooth(M, N, seed=3, length=0.15):
 
     n = max(M, N)
     g = int(np.ceil(np.sqrt(n)))
-    return workloads.KernelMatrix(n, g, n, length, seed).dense()[:M, :N]
+    return workloads.KernelMatrix(n, g, n, length, seed).rows(0, M)[:, :N]
 
 
 def run_step(W, torch, h, X, state=None, decay=0.99):
@@ -65,6 +65,9 @@ CASES = [
     (5, 8, 130, 97),
     (5, 24, 16, 20000),   # wide WZ2: split-K
     (6, 12, 301, 300),
+    (7, 0, 300, 301),     # FP32 storage, the paper's mixed precision
+    (7, 0, 16, 20000),    # wide FP32
+    (7, 0, 3001, 40),     # tall FP32
     (6, 20, 3001, 40),
 ]
 
@@ -219,3 +222,21 @@ def test_invalid_arguments(env):
         with pytest.raises(W.WhffError):
             h.step(torch.zeros(7, dtype=torch.float32, device="cuda"), y[0])  # x too short
         assert h.sync_status() == 0
+
+
+@pytest.mark.parametrize("M,N", [(378, 9000), (5000, 378), (1000, 1000)])
+def test_fp32_storage_follows_the_papers_mixed_precision(env, orc, M, N):
+    """FP32 storage: every product rounded to FP32, the products summed
+    without loss (Sec. 4.4).  Against the paper's rule (FP32 products, FP64
+    running sum, y rounded to FP32): |y - y_mp| <= half an FP32 ulp of y_mp
+    (its final rounding) + 1e-13 * sum_j |p_j| (the two sums' orders)."""
+    W, torch = env
+    A = smooth(M, N)
+    x = np.random.default_rng(M + N).standard_normal(N).astype(np.float32)
+    blob = W.whff_compress(A, W.FMT_FP32)
+    y_mp = orc.gemv_mp(A, x.astype(np.float64)).astype(np.float64)
+    P = np.abs(A.astype(np.float32) * x[None, :]).astype(np.float64).sum(axis=1)
+    with W.whff_create(blob) as h:
+        (y,) = run_step(W, torch, h, x[None, :])
+    ulp = np.spacing(np.abs(y_mp).astype(np.float32)).astype(np.float64)
+    assert (np.abs(y - y_mp) <= 0.5 * ulp + 1e-13 * P).all()

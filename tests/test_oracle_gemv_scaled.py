@@ -157,3 +157,42 @@ def test_scaled_blob_roundtrip_properties(orc, fmt):
     q[::128, ::128] = fmax
     B = s * q
     assert (orc.decode(orc.encode(B, fmt)) == B).all()
+
+
+def test_fp32_storage_is_numpy_float32(orc):
+    """FP32 storage (the uncompressed comparison) decodes to exactly numpy's
+    float32 rounding of A -- normal, subnormal, ties and zero entries -- with
+    every tile scale 1; |a| >= 2^127 and non-finite entries are refused."""
+    rng = np.random.default_rng(71)
+    M, N = 150, 140
+    A = rng.standard_normal((M, N)) * np.exp(rng.uniform(-100, 80, size=(M, N)))
+    A[0, :8] = [0.0, -0.0, 2.0 ** -149, 2.0 ** -150 * 3, 1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, -(2.0 ** 126), 1e-50]
+    blob = orc.encode(A, orc.FMT_FP32)
+    ld = math.ceil(N / 16) * 16
+    assert len(blob) == 64 + M * ld * 4 + 2 * 2 * 4
+    scales = np.frombuffer(blob[64 + M * ld * 4:], dtype=np.float32)
+    assert (scales == 1.0).all()
+    ref = A.astype(np.float32).astype(np.float64)
+    D = orc.decode(blob)
+    assert (D.view(np.uint64) == ref.view(np.uint64)).all()
+    for bad, code in ((2.0 ** 127, -2), (np.inf, -3), (np.nan, -3)):
+        B = A.copy()
+        B[5, 7] = bad
+        with pytest.raises(orc.OracleError):
+            orc.encode(B, orc.FMT_FP32)
+
+
+def test_gemv_mp_follows_the_papers_rounding(orc):
+    """The paper's mixed precision (Sec. 4.4): products rounded to FP32, their
+    sum in FP64, y rounded to FP32 -- checked against the same steps in numpy
+    on a small case where the FP64 sum order is the same."""
+    rng = np.random.default_rng(72)
+    A = rng.standard_normal((9, 31))
+    x = rng.standard_normal(31)
+    y = orc.gemv_mp(A, x)
+    for i in range(9):
+        p = A[i].astype(np.float32) * x.astype(np.float32)  # float32 products, rounded
+        s = 0.0
+        for v in p:
+            s += float(v)
+        assert y[i] == np.float32(s)

@@ -104,6 +104,54 @@ class KernelMatrix:
             yield r0, self.rows(r0, r1)
 
 
+@dataclass(frozen=True)
+class RectKernelMatrix:
+    """M x N smooth-kernel matrix between two point sets over the same square:
+    the first M points of a ceil(sqrt(M))-grid (outputs) and the first N points
+    of a ceil(sqrt(N))-grid (inputs), A_ij = exp(-|p_i - q_j|^2 / l^2) plus
+    1e-3 N(0,1) noise; the noise of rows 64k..64k+63 is one (64, N) draw from
+    Philox keyed by seed at counter (0, k, 1, 0).  The shape of the paper's
+    slit models (Sec. 4.4, Sec. 5.1): wide 378 x 256000 maps heat loads to the slit,
+    tall 256000 x 378 the reverse."""
+
+    M: int
+    N: int
+    length: float
+    seed: int
+    noise: float = 1e-3
+
+    @property
+    def shape(self):
+        return (self.M, self.N)
+
+    def rows(self, r0: int, r1: int) -> np.ndarray:
+        out = np.empty((r1 - r0, self.N), dtype=np.float64)
+        p = grid_points(int(np.ceil(np.sqrt(self.M))), self.M)
+        q = grid_points(int(np.ceil(np.sqrt(self.N))), self.N)
+        inv_l2 = 1.0 / (self.length * self.length)
+
+        def group(k):
+            g0, g1 = 64 * k, min(self.M, 64 * k + 64)
+            gen = np.random.Generator(np.random.Philox(key=self.seed, counter=[0, k, 1, 0]))
+            nz = gen.standard_normal((64, self.N))
+            a, b = max(g0, r0), min(g1, r1)
+            for i in range(a, b):
+                d2 = (q[:, 0] - p[i, 0]) ** 2 + (q[:, 1] - p[i, 1]) ** 2
+                out[i - r0] = np.exp(-d2 * inv_l2) + self.noise * nz[i - g0]
+
+        groups = range(r0 // 64, (r1 + 63) // 64)
+        with ThreadPoolExecutor(_threads()) as ex:
+            list(ex.map(group, groups))
+        return out
+
+    def dense(self) -> np.ndarray:
+        return self.rows(0, self.M)
+
+
+# The paper's GEMV shapes (Sec. 5.1, Fig. results_throughput): (name, M, N)
+PAPER_SHAPES = (("wide", 378, 256000), ("tall", 256000, 378), ("square", 10000, 10000))
+
+
 def gaussian_x(n_valid: int, order: int, seed: int, R: int = 1) -> np.ndarray:
     """FP64 x ~ N(0,1), shape (order, R), zero beyond n_valid; column r from Philox key seed+r."""
     X = np.zeros((order, R), dtype=np.float64)
