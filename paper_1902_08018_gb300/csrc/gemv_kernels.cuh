@@ -33,11 +33,20 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p) {
   lo += err;
 }
 
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Sum of the 32 lanes' compensated (hi, lo) pairs, in a fixed butterfly:
 // each level adds the partner's hi with TwoSum (its error is exact whatever
 // the operand order) and the partner's lo plainly, so every lane ends with
 // the same pair, good to about 2^-48.  FP32 work only: on GB300 the FP64
 // pipe is a small fraction of the FP32 one, and only the result is widened.
+// It pays where bands are short (tall matrices: many band sums per block
+// streamed); on long bands the FP64 butterfly above is a little faster, so
+// the choice is a per-matrix setting (see whff_set_config).
 __device__ __forceinline__ double warp_sum_pair(float hi, float lo) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -63,7 +72,7 @@ __device__ __forceinline__ void finish_band(const float (&hi)[4][R], const float
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int r = 0; r < R; ++r) tot[i][r] = warp_sum_pair(hi[i][r], lo[i][r]);
+    for (int r = 0; r < R; ++r) tot[i][r] = warp_sum((double)hi[i][r] + (double)lo[i][r]);
   // lane (i*R + r) writes value (i, r)
 #pragma unroll
   for (int i = 0; i < 4; ++i)

@@ -21,8 +21,11 @@ static int mma_one(const MmaStep& a, cudaStream_t st) {
                                                                                    a.btiles);
   kern<<<(unsigned)a.ctas, dev::kMmaThreads, S::kBytes, st>>>(a.stream, a.BM, a.BN, a.btiles, a.R, nstages,
                                                              tiles * nstages, a.L, a.maxseg, a.ws, a.status);
-  dev::wz2_mma_finish<LIFT><<<(unsigned)((a.BM + 127) / 128), 128, 0, st>>>(a.ws, nstages, a.L, a.maxseg, a.R, a.M,
-                                                                           a.y, a.ldy, a.state, a.decay);
+  const int64_t fin_threads = tiles * a.R * 32;
+  dev::wz2_mma_finish<LIFT><<<(unsigned)((fin_threads + 255) / 256), 256, 0, st>>>(a.ws, nstages, a.L, a.maxseg, a.R,
+                                                                                  a.M, a.y, a.ldy);
+  if (a.state)
+    dev::wz2_mma_state<<<(unsigned)((a.M + 255) / 256), 256, 0, st>>>(a.y, a.ldy, a.R, a.M, a.state, a.decay);
   return 0;
 }
 

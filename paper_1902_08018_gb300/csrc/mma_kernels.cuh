@@ -30,7 +30,7 @@
 // coefficient row a of band b as m = 32a + b, which makes every warp's tile
 // stores bank-conflict free.  At the end of a tile piece the FP32 sums go to
 // the workspace as one FP64 segment partial; wz2_mma_finish adds a band's
-// segments in order, mixes with 2G and applies the state.
+// segments in order and mixes with 2G, wz2_mma_state applies the state.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -587,47 +587,49 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
   }
 }
 
-// Sum each band's segment partials in order, map its 4 coefficient rows to y
-// (2G mix and 2^-3 with the lift, 2^3 without) and update the state in column
-// order.  Thread per band.
+// Sum each band's segment partials in order and map its 4 coefficient rows to
+// y (2G mix and 2^-3 with the lift, 2^3 without).  Thread per (band, column),
+// the band fastest, so a warp reads 32 consecutive partials of one row and
+// writes 32 consecutive 4-row groups of y.
 template <bool LIFT>
 __global__ void wz2_mma_finish(const double* __restrict__ ws, int64_t S, int64_t L, int maxseg, int R, int64_t M,
-                               double* __restrict__ y, int64_t ldy, double* __restrict__ state, double decay) {
-  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                               double* __restrict__ y, int64_t ldy) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bl = (int)(q & 31);
+  const int64_t tr = q >> 5;  // tile * R + r
+  const int r = (int)(tr % R);
+  const int64_t tile = tr / R;
+  const int64_t I = 32 * tile + bl;
   if (4 * I >= M) return;
-  const int64_t tile = I / 32;
-  const int bl = (int)(I % 32);
   const int nseg = (int)(((tile + 1) * S - 1) / L - (tile * S) / L + 1);
-  double s[4] = {0, 0, 0, 0};
-  if (state)
-    for (int i = 0; i < 4; ++i)
-      if (4 * I + i < M) s[i] = state[4 * I + i];
-  for (int r = 0; r < R; ++r) {
-    double z[4];
-    for (int a = 0; a < 4; ++a) {
-      double acc = 0.0;
-      for (int g = 0; g < nseg; ++g) acc += ws[((tile * maxseg + g) * R + r) * 128 + 32 * a + bl];
-      z[a] = acc;
-    }
-    double yy[4];
-    if (LIFT) {
-      const double a = 2.0 * z[0];
-      yy[0] = (a - z[1] - z[2]) * 0.125;
-      yy[1] = (a - z[1] + z[2]) * 0.125;
-      yy[2] = (a + z[1] - z[2] - z[3]) * 0.125;
-      yy[3] = (a + z[1] + z[2] + z[3]) * 0.125;
-    } else {
-      for (int i = 0; i < 4; ++i) yy[i] = z[i] * 8.0;
-    }
-    for (int i = 0; i < 4; ++i)
-      if (4 * I + i < M) {
-        y[(int64_t)r * ldy + 4 * I + i] = yy[i];
-        s[i] = decay * s[i] + yy[i];
-      }
+  double z[4];
+  for (int a = 0; a < 4; ++a) {
+    double acc = 0.0;
+    for (int g = 0; g < nseg; ++g) acc += ws[((tile * maxseg + g) * R + r) * 128 + 32 * a + bl];
+    z[a] = acc;
   }
-  if (state)
-    for (int i = 0; i < 4; ++i)
-      if (4 * I + i < M) state[4 * I + i] = s[i];
+  double yy[4];
+  if (LIFT) {
+    const double a = 2.0 * z[0];
+    yy[0] = (a - z[1] - z[2]) * 0.125;
+    yy[1] = (a - z[1] + z[2]) * 0.125;
+    yy[2] = (a + z[1] - z[2] - z[3]) * 0.125;
+    yy[3] = (a + z[1] + z[2] + z[3]) * 0.125;
+  } else {
+    for (int i = 0; i < 4; ++i) yy[i] = z[i] * 8.0;
+  }
+  for (int i = 0; i < 4; ++i)
+    if (4 * I + i < M) y[(int64_t)r * ldy + 4 * I + i] = yy[i];
+}
+
+// state <- decay * state + y[:, r] for r = 0..R-1 in order.  Thread per row.
+static __global__ void wz2_mma_state(const double* __restrict__ y, int64_t ldy, int R, int64_t M,
+                                     double* __restrict__ state, double decay) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= M) return;
+  double s = state[row];
+  for (int r = 0; r < R; ++r) s = decay * s + y[(int64_t)r * ldy + row];
+  state[row] = s;
 }
 
 }  // namespace dev

@@ -9,7 +9,7 @@ template <int FMT, int R>
 static void scaled_one(const ScaledStep& a, cudaStream_t st) {
   dev::scaled_range_kernel<FMT, R><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
       a.payload, a.scales, a.M, a.N, a.ld, a.TN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg, a.ws, a.y, a.ldy, a.state,
-      a.decay);
+      a.decay, a.red32);
 }
 
 template <int FMT>

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     scaled_range_kernel(const uint8_t* __restrict__ payload, const float* __restrict__ scales, int64_t M, int64_t N,
                         int64_t ld, int64_t TN, const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int64_t L,
                         int maxseg, double* __restrict__ ws, double* __restrict__ y, int64_t ldy,
-                        double* __restrict__ state, double decay) {
+                        double* __restrict__ state, double decay, bool red32) {
   constexpr int V = ScaledTraits<FMT>::V;
   const int lane = threadIdx.x & 31;
   const int64_t g = (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
@@ -129,9 +129,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       scaled_chunk<FMT, R>(payload, scales, M, N, ld, TN, row0, J * V, r0, x, ldx, x_fast, hi, lo);
     }
     if (g_lo == g_hi) {
-      band_finish<0, R>(hi, lo, lane, row0, M, 0, 1, 4 * BM, ws, y, ldy, state, decay);
+      band_finish<0, R>(hi, lo, lane, row0, M, 0, 1, 4 * BM, ws, y, ldy, state, decay, red32);
     } else {
-      band_finish<0, R>(hi, lo, lane, 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, 2, 0, ws, y, ldy, state, decay);
+      band_finish<0, R>(hi, lo, lane, 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, 2, 0, ws, y, ldy, state, decay,
+                        red32);
     }
     b0 = piece_end;
   }

@@ -45,6 +45,7 @@ struct whff_handle {
   int ksplit = 1;
   int64_t chunk = 0;            // J blocks (WZ1) or columns (scaled) per split
   int ctas_per_sm = 4;          // resident CTAs per SM of the persistent kernels
+  bool red32 = false;           // WZ2 / scaled: fold lanes in FP32 pairs (short bands) instead of FP64
   int unroll = 2;               // WZ2: blocks in flight per lane (R = 1 kernel)
   int64_t range_ctas = 0;       // WZ2: CTAs of the range-partitioned persistent grid
   int64_t range_len = 0;        // WZ2: blocks per warp range
@@ -186,7 +187,8 @@ int launch_wz1(const whff_handle* h, const float* x, int R, int64_t ldx, bool ve
 int launch_wz2(const whff_handle* h, const float* x, int R, int64_t ldx, bool vec, double* y, int64_t ldy,
                double* state, double decay, cudaStream_t st) {
   Wz2Step a{h->d_stream, h->info.M, h->info.N, h->BM, h->BN, x, ldx, vec, h->range_len, h->maxseg, h->d_ws,
-            y, ldy, state, decay, h->range_ctas, R == 1 ? h->unroll : 2, h->info.fmt == WHFF_FMT_FIXED_LIFT, R};
+            y, ldy, state, decay, h->range_ctas, R == 1 ? h->unroll : 2, h->info.fmt == WHFF_FMT_FIXED_LIFT, R,
+            h->red32};
   int e;
   switch (h->info.rate) {
     case 8: e = wz2_launch<8>(a, st); break;
@@ -218,8 +220,8 @@ int launch_scaled(const whff_handle* h, const float* x, int R, int64_t ldx, bool
                   double* state, double decay, cudaStream_t st) {
   const auto& b = h->info;
   const int64_t ld = scaled_ld(b.N);
-  ScaledStep a{b.fmt, h->d_stream, h->d_scales, b.M, b.N, ld, ceil_div(b.N, kScaleTile), x, ldx, vec, h->range_len, h->maxseg, h->d_ws, y, ldy, state,
-               decay, h->range_ctas, R};
+  ScaledStep a{b.fmt, h->d_stream, h->d_scales, b.M, b.N, ld, ceil_div(b.N, kScaleTile), x, ldx, vec,
+               h->range_len, h->maxseg, h->d_ws, y, ldy, state, decay, h->range_ctas, R, h->red32};
   if (scaled_launch(a, st)) {
     set_error("whff_step: scaled formats take R 1, 2, 4 or 8 per pass");
     return WHFF_EINVAL;
@@ -310,6 +312,8 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
     h->BN = ceil_div(info.N, 4);
   }
   choose_split(h);
+  // short bands (tall matrices) fold their lanes in FP32 pairs; long ones in FP64
+  h->red32 = info.fmt != WHFF_FMT_ZFP && h->BN < 4096;
   const cudaStream_t st = as_stream(stream);
   if (cudaMalloc(&h->d_stream, info.stream_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -725,9 +729,10 @@ extern "C" void whff_destroy(whff_handle* h) {
 // ------------------------------------------------------------------ tuning
 namespace {
 
-int apply_config(whff_handle* h, int unroll, int ctas_per_sm) {
+int apply_config(whff_handle* h, int unroll, int ctas_per_sm, bool red32) {
   h->unroll = unroll;
   h->ctas_per_sm = ctas_per_sm;
+  h->red32 = red32;
   choose_ranges(h);
   const size_t need = h->maxseg > 1 ? (size_t)h->BM * (size_t)h->maxseg * (size_t)h->ws_rhs * 4 * 8 : 0;
   if (need > h->ws_bytes) {
@@ -750,19 +755,20 @@ bool is_wz2(const whff_handle* h) {
 
 }  // namespace
 
-extern "C" int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_sm) {
+extern "C" int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_sm, int* reduce32) {
   if (!h) {
     set_error("whff_get_config: null handle");
     return WHFF_EINVAL;
   }
   if (unroll) *unroll = h->unroll;
   if (ctas_per_sm) *ctas_per_sm = h->ctas_per_sm;
+  if (reduce32) *reduce32 = h->red32 ? 1 : 0;
   return WHFF_OK;
 }
 
-extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm) {
-  if (!h || !is_wz2(h) || (unroll != 2 && unroll != 4) || ctas_per_sm < 1) {
-    set_error("whff_set_config: WZ2 handles only; unroll 2 or 4; ctas_per_sm >= 1");
+extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int reduce32) {
+  if (!h || !is_wz2(h) || (unroll != 2 && unroll != 4) || ctas_per_sm < 1 || (reduce32 != 0 && reduce32 != 1)) {
+    set_error("whff_set_config: WZ2 handles only; unroll 2 or 4; ctas_per_sm >= 1; reduce32 0 or 1");
     return WHFF_EINVAL;
   }
   const int occ = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, unroll);
@@ -770,7 +776,7 @@ extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm) {
     set_error("whff_set_config: more CTAs per SM than can be resident");
     return WHFF_EINVAL;
   }
-  return apply_config(h, unroll, ctas_per_sm);
+  return apply_config(h, unroll, ctas_per_sm, reduce32 != 0);
 }
 
 extern "C" int whff_get_crossover(const whff_handle* h, int* min_rhs) {
@@ -791,8 +797,8 @@ extern "C" int whff_set_crossover(whff_handle* h, int min_rhs) {
   return WHFF_OK;
 }
 
-// Time every (unroll, CTAs per SM) candidate on this matrix with R = 1 and
-// keep the fastest.  Uses the handle's own staging buffers (x = 0).
+// Time every (unroll, CTAs per SM, lane fold) candidate on this matrix with
+// R = 1 and keep the fastest.  Uses the handle's own staging buffers (x = 0).
 extern "C" int whff_tune(whff_handle* h, int iters, void* stream, double* best_ms) {
   if (!h || !is_wz2(h) || iters < 1) {
     set_error("whff_tune: WZ2 handles only, iters >= 1");
@@ -804,38 +810,42 @@ extern "C" int whff_tune(whff_handle* h, int iters, void* stream, double* best_m
   WHFF_CUDA_TRY(cudaEventCreate(&e0));
   WHFF_CUDA_TRY(cudaEventCreate(&e1));
   const int orig_u = h->unroll, orig_c = h->ctas_per_sm;
+  const bool orig_r = h->red32;
   double best = 1e30;
   int bu = orig_u, bc = orig_c;
+  bool br = orig_r;
   int err = WHFF_OK;
-  for (int u : {2, 4}) {
-    const int occ = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, u);
-    for (int c = occ; c >= 1 && c >= occ - 2; --c) {
-      if ((err = apply_config(h, u, c)) != WHFF_OK) break;
-      if ((err = whff_step(h, h->d_x, 1, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream)) != WHFF_OK) break;
-      cudaEventRecord(e0, st);
-      for (int k = 0; k < iters && err == WHFF_OK; ++k)
-        err = whff_step(h, h->d_x, 1, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) err = WHFF_ECUDA;
-      if (err) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms / iters < best) {
-        best = ms / iters;
-        bu = u;
-        bc = c;
-      }
-    }
+  // candidates: unroll 2 or 4, the top three CTA counts per SM, FP64 or FP32-pair lane folds
+  for (int cand = 0; cand < 12 && err == WHFF_OK; ++cand) {
+    const int u = cand < 6 ? 2 : 4;
+    const bool red = (cand & 1) != 0;
+    const int c = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, u) - (cand % 6) / 2;
+    if (c < 1) continue;
+    if ((err = apply_config(h, u, c, red)) != WHFF_OK) break;
+    if ((err = whff_step(h, h->d_x, 1, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream)) != WHFF_OK) break;
+    cudaEventRecord(e0, st);
+    for (int k = 0; k < iters && err == WHFF_OK; ++k)
+      err = whff_step(h, h->d_x, 1, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) err = WHFF_ECUDA;
     if (err) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / iters < best) {
+      best = ms / iters;
+      bu = u;
+      bc = c;
+      br = red;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err) {
-    apply_config(h, orig_u, orig_c);
+    apply_config(h, orig_u, orig_c, orig_r);
     return err;
   }
   if (best_ms) *best_ms = best;
-  return apply_config(h, bu, bc);
+  return apply_config(h, bu, bc, br);
 }
 
 // ------------------------------------------------------------------ batches

@@ -9,7 +9,8 @@ namespace whff {
 template <int RATE, bool LIFT, int R, int U>
 static void wz2_launch_one(const Wz2Step& a, cudaStream_t st) {
   dev::wz2_gemv_kernel<RATE, LIFT, R, U><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
-      a.stream, a.M, a.N, a.BM, a.BN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg, a.ws, a.y, a.ldy, a.state, a.decay);
+      a.stream, a.M, a.N, a.BM, a.BN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg, a.ws, a.y, a.ldy, a.state, a.decay,
+      a.red32);
 }
 
 template <int RATE, bool LIFT>

@@ -26,6 +26,7 @@ struct Wz2Step {
   int unroll;      // blocks in flight per lane: 2 or 4 (R = 1), 2 otherwise
   bool lift;
   int R;           // 1, 2, 4 or 8
+  bool red32;      // fold lanes with the FP32 pair butterfly (short bands)
 };
 
 
@@ -61,6 +62,7 @@ struct ScaledStep {
   double decay;
   int64_t ctas;
   int R;
+  bool red32;
 };
 int scaled_launch(const ScaledStep& a, cudaStream_t st);  // scaled.cu
 

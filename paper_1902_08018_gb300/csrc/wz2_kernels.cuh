@@ -103,19 +103,28 @@ template <bool LIFT, int R>
 __device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
                                            int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
                                            double* __restrict__ y, int64_t ldy, double* __restrict__ state,
-                                           double decay);
+                                           double decay, bool red32);
 
+// red32: fold the lanes with the FP32 pair butterfly instead of FP64 (the
+// same bar; another rounding).
 template <int MIX, int R>
 __device__ __forceinline__ void band_finish(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
                                             int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
                                             double* __restrict__ y, int64_t ldy, double* __restrict__ state,
-                                            double decay) {
+                                            double decay, bool red32) {
   constexpr bool LIFT = MIX == 1;
   double z[4][R];
+  if (red32) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int r = 0; r < R; ++r) z[i][r] = warp_sum_pair(hi[i][r], lo[i][r]);
+      for (int r = 0; r < R; ++r) z[i][r] = warp_sum_pair(hi[i][r], lo[i][r]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) z[i][r] = warp_sum((double)hi[i][r] + (double)lo[i][r]);
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     double t[4];
@@ -167,8 +176,8 @@ template <bool LIFT, int R>
 __device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
                                            int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
                                            double* __restrict__ y, int64_t ldy, double* __restrict__ state,
-                                           double decay) {
-  band_finish<LIFT ? 1 : 2, R>(hi, lo, lane, row0, M, split, ksplit, Mpad, ws, y, ldy, state, decay);
+                                           double decay, bool red32) {
+  band_finish<LIFT ? 1 : 2, R>(hi, lo, lane, row0, M, split, ksplit, Mpad, ws, y, ldy, state, decay, red32);
 }
 
 template <int RATE, bool LIFT, int R>
@@ -275,7 +284,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     wz2_gemv_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BM, int64_t BN,
                     const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int64_t L, int maxseg,
                     double* __restrict__ ws, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
-                    double decay) {
+                    double decay, bool red32) {
   constexpr int64_t kBlockBytes = 4 * Wz2Layout<RATE>::kWords;
   const int lane = threadIdx.x & 31;
   const int64_t g = (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
@@ -295,10 +304,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
     wz2_piece<RATE, LIFT, R, UNROLL>(stream + (uint64_t)(I * BN) * kBlockBytes, b0 - I * BN, piece_end - I * BN,
                                      lane, x, ldx, N, x_fast, x_vec_ok, hi, lo);
     if (g_lo == g_hi) {  // the whole band is in this range: finish it here
-      wz2_finish<LIFT, R>(hi, lo, lane, 4 * I, M, 0, 1, 4 * BM, ws, y, ldy, state, decay);
+      wz2_finish<LIFT, R>(hi, lo, lane, 4 * I, M, 0, 1, 4 * BM, ws, y, ldy, state, decay, red32);
     } else {  // one segment of a shared band: ws[(band * maxseg + seg) * R + r][i]
       wz2_finish<LIFT, R>(hi, lo, lane, 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, 2, 0, ws, y, ldy, state,
-                          decay);
+                          decay, red32);
     }
     b0 = piece_end;
   }
@@ -366,10 +375,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
                                      piece_end - e.block_begin - I * e.BN, lane, e.x, e.ldx, e.N, x_fast, x_vec_ok,
                                      hi, lo);
     if (g_lo == g_hi) {
-      wz2_finish<LIFT, R>(hi, lo, lane, 4 * I, e.M, 0, 1, 4 * e.BM, e.ws, e.y, e.ldy, e.state, e.decay);
+      wz2_finish<LIFT, R>(hi, lo, lane, 4 * I, e.M, 0, 1, 4 * e.BM, e.ws, e.y, e.ldy, e.state, e.decay, false);
     } else {
       wz2_finish<LIFT, R>(hi, lo, lane, 4 * ((I * e.maxseg + (g - g_lo)) * R), e.M, 0, 2, 0, e.ws, e.y, e.ldy,
-                          e.state, e.decay);
+                          e.state, e.decay, false);
     }
     b0 = piece_end;
   }

@@ -80,8 +80,8 @@ def library() -> ctypes.CDLL:
         "whff_server_run": (c_int, [P, c_int, P, P, P, P, P, P, P, dbl, dbl]),
         "whff_server_destroy": (None, [P]),
         "whff_tune": (c_int, [P, c_int, P, ctypes.POINTER(dbl)]),
-        "whff_get_config": (c_int, [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
-        "whff_set_config": (c_int, [P, c_int, c_int]),
+        "whff_get_config": (c_int, [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+        "whff_set_config": (c_int, [P, c_int, c_int, c_int]),
         "whff_get_crossover": (c_int, [P, ctypes.POINTER(c_int)]),
         "whff_step_rows": (c_int, [P, i64, i64, P, c_int, i64, P, i64, P, dbl, P]),
         "whff_set_crossover": (c_int, [P, c_int]),
@@ -192,12 +192,12 @@ class Handle:
             with open(cache) as f:
                 db = json.load(f)
         if key in db:
-            self.set_config(db[key]["unroll"], db[key]["ctas_per_sm"])
+            self.set_config(db[key]["unroll"], db[key]["ctas_per_sm"], db[key].get("reduce32", 0))
             return dict(db[key], cached=True)
         ms = ctypes.c_double()
         _check(library().whff_tune(self._ptr, iters, _stream_ptr(stream), ctypes.byref(ms)))
-        u, c = self.config()
-        rec = {"unroll": u, "ctas_per_sm": c, "ms": ms.value}
+        u, c, r = self.config()
+        rec = {"unroll": u, "ctas_per_sm": c, "reduce32": r, "ms": ms.value}
         if cache:
             db[key] = rec
             os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
@@ -206,12 +206,15 @@ class Handle:
         return dict(rec, cached=False)
 
     def config(self):
-        u, c = ctypes.c_int(), ctypes.c_int()
-        _check(library().whff_get_config(self._ptr, ctypes.byref(u), ctypes.byref(c)))
-        return u.value, c.value
+        """(unroll, ctas_per_sm, reduce32) of the WZ2 launch shape."""
+        u, c, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(library().whff_get_config(self._ptr, ctypes.byref(u), ctypes.byref(c), ctypes.byref(r)))
+        return u.value, c.value, r.value
 
-    def set_config(self, unroll: int, ctas_per_sm: int):
-        _check(library().whff_set_config(self._ptr, unroll, ctas_per_sm))
+    def set_config(self, unroll: int, ctas_per_sm: int, reduce32: int | None = None):
+        if reduce32 is None:
+            reduce32 = self.config()[2]
+        _check(library().whff_set_config(self._ptr, unroll, ctas_per_sm, int(reduce32)))
 
     @property
     def crossover(self) -> int:
