@@ -155,6 +155,16 @@ int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, double* y, int
 int whff_step_rows(whff_handle* h, int64_t row0, int64_t nrows, const float* x, int R, int64_t ldx, double* y,
                    int64_t ldy, double* state, double decay, void* stream);
 
+/* Time slicing: with rows > 0, whff_step (and every graph captured from it
+ * afterwards) runs each pass as consecutive slits of `rows` rows (the last
+ * one shorter), each its own launch sequence, so that kernels on other,
+ * higher-priority streams are scheduled between slits instead of waiting for
+ * the persistent grid of a whole pass.  The results are the slits' (within
+ * the bar of a whole-matrix step).  rows = 0 (default) turns it off; rows is
+ * a multiple of 4 (block formats) or 128 (scaled formats), else WHFF_EINVAL. */
+int whff_get_slice_rows(const whff_handle* h, int64_t* rows);
+int whff_set_slice_rows(whff_handle* h, int64_t rows);
+
 /* The same step on HOST buffers: copies x (N x R, ldx) host->device, runs
  * whff_step into handle-owned device buffers, copies y (M x R, ldy) back, all
  * asynchronously on the stream (pinned host memory makes the copies truly
@@ -237,8 +247,13 @@ void whff_batch_destroy(whff_batch* b);
  * extra right-hand sides (continuous batching, batch buckets 1, 2, 4, ...,
  * max_batch), each bucket a captured CUDA graph (H2D x, step, D2H y); the
  * columns of a pass are applied in arrival order, so the carried state and
- * every y are the same as for one-at-a-time service.  Different models run
- * concurrently on nstreams streams.  Models are admitted while the sum of
+ * every y are the same as for one-at-a-time service (bit for bit when both
+ * passes run on the same engine; within the accuracy bar when a wide pass
+ * runs on the tensor cores).  Different models run concurrently on nstreams
+ * streams.  A model whose pass streams more than 512 MB is captured as
+ * consecutive row slits of at most that size (whff_set_slice_rows), so the
+ * kernels of smaller, higher-priority models get SMs between slits instead of
+ * waiting for a whole pass.  Models are admitted while the sum of
  * their device footprints (matrix, workspace, state, staging) stays within
  * hbm_budget bytes; otherwise whff_server_add_model returns WHFF_EBUSY.  The
  * server does not own the handles (destroy it before them). */

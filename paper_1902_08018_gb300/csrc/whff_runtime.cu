@@ -61,6 +61,7 @@ struct whff_handle {
   int mma_occ = 0;              // resident tensor-core CTAs per SM
   size_t ws_mma_cap = 0;        // bytes of d_ws_mma
   const float* d_scales = nullptr;  // scaled formats: the tile scales after the payload
+  int64_t slice_rows = 0;       // > 0: whff_step runs as consecutive slits of this many rows
   cudaStream_t create_stream = nullptr;
 };
 
@@ -437,37 +438,18 @@ int step_passes(const whff_handle* h, const float* x, int R, int64_t ldx, double
 }  // namespace
 }  // namespace whff
 
-extern "C" int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
-                         double decay, void* stream) {
-  if (!h || !x || !y || R <= 0 || R > h->max_rhs || ldx < h->info.N || ldy < h->info.M) {
-    set_error("whff_step: null pointer, R out of [1, max_rhs], or leading dimension too small");
-    return WHFF_EINVAL;
-  }
-  return step_passes(h, x, R, ldx, y, ldy, state, decay, as_stream(stream));
-}
-
-// A slit (Sec. 2.1, divide and conquer: C_slit is a block of rows of the
-// resident C_field): rows [row0, row0 + nrows) of the matrix, which are
-// one contiguous byte range of its stream.  The view shares the handle's
-// buffers and gets its own launch plan, shrunk until its partials fit the
-// handle's workspaces.
-extern "C" int whff_step_rows(whff_handle* h, int64_t row0, int64_t nrows, const float* x, int R, int64_t ldx,
-                              double* y, int64_t ldy, double* state, double decay, void* stream) {
-  if (!h || !x || !y || R <= 0 || R > h->max_rhs || ldx < h->info.N || row0 < 0 || nrows <= 0 ||
-      row0 + nrows > h->info.M || ldy < nrows) {
-    set_error("whff_step_rows: null pointer, R out of [1, max_rhs], rows outside the matrix, or ld too small");
-    return WHFF_EINVAL;
-  }
+namespace whff {
+namespace {
+// Rows [row0, row0 + nrows) of the matrix (row0 aligned to the format's band or
+// scale tile): a view with the handle's buffers and its own launch plan,
+// shrunk until its partials fit the handle's workspaces.
+int step_view(const whff_handle* h, int64_t row0, int64_t nrows, const float* x, int R, int64_t ldx, double* y,
+              int64_t ldy, double* state, double decay, cudaStream_t st) {
   const int fmt = h->info.fmt;
-  const bool blocked = is_blocked(fmt);
-  if (row0 % (blocked ? 4 : kScaleTile)) {
-    set_error("whff_step_rows: row0 must be a multiple of 4 (block formats) or 128 (scaled formats)");
-    return WHFF_EINVAL;
-  }
   whff_handle v = *h;
   v.info.M = nrows;
   v.Mpad = ceil_div(nrows, 4) * 4;
-  if (blocked) {
+  if (is_blocked(fmt)) {
     v.BM = ceil_div(nrows, 4);
     v.d_stream = h->d_stream + (uint64_t)(row0 / 4) * (uint64_t)h->BN * (uint64_t)(2 * h->info.rate);
   } else {
@@ -475,7 +457,7 @@ extern "C" int whff_step_rows(whff_handle* h, int64_t row0, int64_t nrows, const
     v.d_scales = h->d_scales + (row0 / kScaleTile) * ceil_div(h->info.N, kScaleTile);
   }
   choose_split(&v);
-  for (int c = v.ctas_per_sm; ws_need(&v) > h->ws_bytes; ) {  // fewer warps: longer ranges, fewer segments
+  for (int c = v.ctas_per_sm; ws_need(&v) > h->ws_bytes;) {  // fewer warps: longer ranges, fewer segments
     if (fmt == WHFF_FMT_ZFP) {
       v.ksplit = (int)std::max<size_t>(1, h->ws_bytes / ((size_t)v.ws_rhs * (size_t)v.Mpad * 8));
       v.chunk = ceil_div(v.BN, v.ksplit);
@@ -497,7 +479,61 @@ extern "C" int whff_step_rows(whff_handle* h, int64_t row0, int64_t nrows, const
     }
     if (mma_ws_need(&v, std::min(R, 32)) > h->ws_mma_cap) v.mma_min_rhs = 33;  // CUDA cores only
   }
-  return step_passes(&v, x, R, ldx, y, ldy, state, decay, as_stream(stream));
+  return step_passes(&v, x, R, ldx, y, ldy, state, decay, st);
+}
+}  // namespace
+}  // namespace whff
+
+extern "C" int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
+                         double decay, void* stream) {
+  if (!h || !x || !y || R <= 0 || R > h->max_rhs || ldx < h->info.N || ldy < h->info.M) {
+    set_error("whff_step: null pointer, R out of [1, max_rhs], or leading dimension too small");
+    return WHFF_EINVAL;
+  }
+  const cudaStream_t st = as_stream(stream);
+  const int64_t M = h->info.M, slice = h->slice_rows;
+  if (slice <= 0 || slice >= M) return step_passes(h, x, R, ldx, y, ldy, state, decay, st);
+  for (int64_t r0 = 0; r0 < M; r0 += slice) {  // time slices: one launch sequence per slit
+    const int e = step_view(h, r0, std::min(slice, M - r0), x, R, ldx, y + r0, ldy, state ? state + r0 : nullptr,
+                            decay, st);
+    if (e) return e;
+  }
+  return WHFF_OK;
+}
+
+// A slit (Sec. 2.1, divide and conquer: C_slit is a block of rows of the
+// resident C_field): rows [row0, row0 + nrows) of the matrix, which are one
+// contiguous byte range of its stream, so nothing is copied.
+extern "C" int whff_step_rows(whff_handle* h, int64_t row0, int64_t nrows, const float* x, int R, int64_t ldx,
+                              double* y, int64_t ldy, double* state, double decay, void* stream) {
+  if (!h || !x || !y || R <= 0 || R > h->max_rhs || ldx < h->info.N || row0 < 0 || nrows <= 0 ||
+      row0 + nrows > h->info.M || ldy < nrows) {
+    set_error("whff_step_rows: null pointer, R out of [1, max_rhs], rows outside the matrix, or ld too small");
+    return WHFF_EINVAL;
+  }
+  if (row0 % (is_blocked(h->info.fmt) ? 4 : kScaleTile)) {
+    set_error("whff_step_rows: row0 must be a multiple of 4 (block formats) or 128 (scaled formats)");
+    return WHFF_EINVAL;
+  }
+  return step_view(h, row0, nrows, x, R, ldx, y, ldy, state, decay, as_stream(stream));
+}
+
+extern "C" int whff_get_slice_rows(const whff_handle* h, int64_t* rows) {
+  if (!h || !rows) {
+    set_error("whff_get_slice_rows: null argument");
+    return WHFF_EINVAL;
+  }
+  *rows = h->slice_rows;
+  return WHFF_OK;
+}
+
+extern "C" int whff_set_slice_rows(whff_handle* h, int64_t rows) {
+  if (!h || rows < 0 || rows % (is_blocked(h->info.fmt) ? 4 : kScaleTile)) {
+    set_error("whff_set_slice_rows: rows >= 0, a multiple of 4 (block formats) or 128 (scaled formats)");
+    return WHFF_EINVAL;
+  }
+  h->slice_rows = rows;
+  return WHFF_OK;
 }
 
 extern "C" int whff_step_host(whff_handle* h, const float* x_host, int R, int64_t ldx, double* y_host, int64_t ldy,

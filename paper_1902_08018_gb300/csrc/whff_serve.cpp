@@ -9,9 +9,13 @@
 // right-hand sides (continuous batching).  Columns are applied in arrival
 // order, so the carried state s <- decay*s + y evolves exactly as if every
 // request had been served alone, and each column's y is computed by the same
-// kernel arithmetic whatever the batch (the kernels treat right-hand sides
-// independently).  Different models' passes run concurrently on a pool of
-// streams.
+// kernel arithmetic whatever the batch as long as the pass stays on the CUDA
+// cores (the kernels treat right-hand sides independently; a pass wide enough
+// for the tensor cores rounds differently, within the same bar).  Different
+// models' passes run concurrently on a pool of streams; passes longer than
+// kSliceBytes of stream are captured as row slits, so that the persistent
+// grid of a big model releases the SMs between slits to the kernels of
+// smaller, higher-priority models.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,7 +43,10 @@ struct Model {
   double* y_pin = nullptr;   // max_batch x M, pinned
   std::vector<whff_graph*> graphs;  // bucket b -> graph for R = 1 << b
   size_t footprint = 0;
+  int64_t slice_rows = 0;  // rows per slit of a captured pass (0: whole matrix)
 };
+
+constexpr size_t kSliceBytes = size_t(512) << 20;  // about 80 us of HBM streaming per slit
 
 int bucket_of(int n) {  // largest b with 2^b <= n
   int b = 0;
@@ -165,12 +172,27 @@ extern "C" int whff_server_add_model(whff_server* s, whff_handle* h, double deca
   if (cudaMallocHost(&m.x_pin, (size_t)s->max_batch * m.N * 4) != cudaSuccess ||
       cudaMallocHost(&m.y_pin, (size_t)s->max_batch * m.M * 8) != cudaSuccess)
     return fail(WHFF_ENOMEM, "pinned staging allocation failed");
+  // long passes are captured as row slits of at most kSliceBytes each (time
+  // slicing); the handle's own setting is restored afterwards
+  int64_t own_slice = 0;
+  whff_get_slice_rows(h, &own_slice);
+  const int64_t align = (fmt == WHFF_FMT_ZFP || fmt == WHFF_FMT_FIXED_LIFT || fmt == WHFF_FMT_FIXED_BFP) ? 4 : 128;
+  const double row_bytes = (double)whff_compressed_size(fmt, rate, m.M, m.N) / (double)m.M;
+  int64_t slice = 0;
+  if (row_bytes * (double)m.M > (double)kSliceBytes)
+    slice = std::max<int64_t>(align, (int64_t)((double)kSliceBytes / row_bytes) / align * align);
+  if (whff_set_slice_rows(h, slice)) return fail(WHFF_EINVAL, "slice setting failed");
   for (int b = 0; b < s->nbuckets; ++b) {
     whff_graph* g = nullptr;
     int e = whff_graph_create_host(h, m.x_pin, 1 << b, m.N, m.y_pin, m.M, m.d_state, decay, s->streams[0], &g);
-    if (e) return fail(e, "graph capture failed");
+    if (e) {
+      whff_set_slice_rows(h, own_slice);
+      return fail(e, "graph capture failed");
+    }
     m.graphs.push_back(g);
   }
+  whff_set_slice_rows(h, own_slice);
+  m.slice_rows = slice;
   s->used += m.footprint;
   *model_id = (int)s->models.size();
   s->models.push_back(m);

@@ -85,6 +85,8 @@ def library() -> ctypes.CDLL:
         "whff_get_crossover": (c_int, [P, ctypes.POINTER(c_int)]),
         "whff_step_rows": (c_int, [P, i64, i64, P, c_int, i64, P, i64, P, dbl, P]),
         "whff_set_crossover": (c_int, [P, c_int]),
+        "whff_get_slice_rows": (c_int, [P, ctypes.POINTER(i64)]),
+        "whff_set_slice_rows": (c_int, [P, i64]),
         "whff_batch_create": (c_int, [P, P, c_int, ctypes.POINTER(P)]),
         "whff_batch_step": (c_int, [P, P, P, P, P, P, dbl, P]),
         "whff_batch_destroy": (None, [P]),
@@ -226,6 +228,17 @@ class Handle:
     @crossover.setter
     def crossover(self, min_rhs: int):
         _check(library().whff_set_crossover(self._ptr, int(min_rhs)))
+
+    @property
+    def slice_rows(self) -> int:
+        """Rows per slit when whff_step runs a pass as time slices (0: whole matrix)."""
+        v = ctypes.c_int64()
+        _check(library().whff_get_slice_rows(self._ptr, ctypes.byref(v)))
+        return v.value
+
+    @slice_rows.setter
+    def slice_rows(self, rows: int):
+        _check(library().whff_set_slice_rows(self._ptr, int(rows)))
 
     def plan(self):
         """(ksplit, kernel launches per pass of up to 8 right-hand sides)."""

@@ -81,3 +81,46 @@ def test_slit_arguments_are_checked(env):
             h.step_rows(0, 16, x, y)  # a valid slit still works
             torch.cuda.synchronize()
             assert (y.cpu().numpy() == 0).all()
+
+
+@pytest.mark.parametrize("fmt,rate", [(5, 16), (1, 12), (7, 0)])
+def test_time_sliced_step_is_its_slits(env, orc, fmt, rate):
+    """With slice_rows set, whff_step runs the pass as consecutive slits: its
+    y and state equal those of the slit steps bit for bit, meet the bar
+    against the oracle, and a graph captured afterwards replays the same."""
+    W, torch = env
+    M, N, R = 1100, 1500, 3
+    blob = W.whff_compress(_matrix(M, N, 9), fmt, rate or 16)
+    Ahat = orc.decode(blob.tobytes())
+    X = np.random.default_rng(fmt).standard_normal((R, N)).astype(np.float32)
+    x = torch.from_numpy(X).cuda()
+    ref = orc.gemv64(Ahat, X.T.astype(np.float64))
+    slice_rows = 256 if fmt == 7 else 300
+    with W.whff_create(blob, max_rhs=4) as h:
+        assert h.slice_rows == 0
+        h.slice_rows = slice_rows
+        y = torch.zeros((R, M), dtype=torch.float64, device="cuda")
+        s = torch.full((M,), 0.5, dtype=torch.float64, device="cuda")
+        h.step(x, y, s, 0.9)
+        y_sl = torch.zeros_like(y)
+        s_sl = torch.full((M,), 0.5, dtype=torch.float64, device="cuda")
+        for r0 in range(0, M, slice_rows):
+            n = min(slice_rows, M - r0)
+            ys = torch.zeros((R, n), dtype=torch.float64, device="cuda")
+            ss = s_sl[r0:r0 + n].clone()
+            h.step_rows(r0, n, x, ys, ss, 0.9)
+            y_sl[:, r0:r0 + n] = ys
+            s_sl[r0:r0 + n] = ss
+        g = W.whff_graph_create(h, x, (yg := torch.zeros_like(y)))
+        g.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(y, y_sl) and torch.equal(s, s_sl) and torch.equal(yg, y)
+        Y = y.cpu().numpy()
+        for r in range(R):
+            assert _rel(Y[r], ref[:, r]) <= TOL
+        s_ref = orc.state_update(np.full(M, 0.5), ref, 0.9)
+        assert _rel(s.cpu().numpy(), s_ref) <= TOL
+        g.destroy()
+        h.slice_rows = 0
+        with pytest.raises(W.WhffError):
+            h.slice_rows = 6 if fmt != 7 else 64  # not on a band / scale-tile boundary
