@@ -64,6 +64,7 @@ def parse_args():
                    help="right-hand-side counts timed on the headline matrix, on both engines")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-baseline", action="store_true")
+    p.add_argument("--no-host-resident", action="store_true", help="skip the matrix-over-the-link leg")
     p.add_argument("--json-out", default=None)
     p.add_argument("--serve", action="store_true", help="run the serving workload instead of the control loop")
     p.add_argument("--serve-fmt", default="wz2-lift:8")
@@ -405,6 +406,44 @@ def run_whff(args, rank, world, local_rank):
         del A64
         torch.cuda.empty_cache()
 
+    # ---------------- the matrix streamed over the CPU-GPU link every step (Sec. 4.2: the
+    # paper's system moves the matrix over the host link; compression divides its bytes)
+    host = None
+    if not args.no_host_resident:
+        hh = W.whff_create(blobs[head], max_rhs=1, host_resident=True)
+        xs0 = xs[0] if xs.dim() == 2 else xs
+        yh = torch.zeros(order, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            hh.step(xs0, yh, None, DECAY, stream)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        f0.record(stream)
+        for _ in range(reps):
+            hh.step(xs0, yh, None, DECAY, stream)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        hms = f0.elapsed_time(f1) / reps
+        hh.destroy()
+        # the link's plain copy rate (pinned host -> HBM), and what an uncompressed FP64
+        # matrix would cost per step over it
+        hbuf = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+        dbuf = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+        dbuf.copy_(hbuf, non_blocking=True)
+        torch.cuda.synchronize()
+        f0.record(stream)
+        for _ in range(3):
+            dbuf.copy_(hbuf, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        link = 3 * (1 << 30) / (f0.elapsed_time(f1) * 1e-3) / 1e9
+        del hbuf, dbuf
+        torch.cuda.empty_cache()
+        host = {"ms_per_step": round(hms, 4), "GB_s": round(stream_bytes / (hms * 1e-3) / 1e9, 1),
+                "h2d_copy_GB_s": round(link, 1),
+                "fp64_uncompressed_over_link_ms": round(order * order * 8 / (link * 1e9) * 1e3, 3),
+                "note": "compressed stream in pinned host memory, read by the fused kernel over the link"}
+
     algo_bytes = stream_bytes + order * 4 + order * 8 + order * 16
     kernel_ms = float(np.mean(per_ms))  # one launch per step when ksplit == 1
     achieved = algo_bytes / (kernel_ms * 1e-3) / 1e9
@@ -451,6 +490,7 @@ def run_whff(args, rank, world, local_rank):
         "formats": formats,
         "multi_rhs": multi,
         "fp64_uncompressed_gemv": fp64,
+        "host_resident": host,
         "setup_s": round(t_setup, 1),
     }
     if cpu is not None:

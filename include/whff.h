@@ -115,6 +115,17 @@ int whff_blob_seal(void* blob, size_t cap);
  * be freed afterwards.  Errors: WHFF_EFORMAT, WHFF_ENOMEM, WHFF_ECUDA. */
 int whff_create(const void* blob, size_t len, int max_rhs, void* stream, whff_handle** h);
 
+/* As whff_create, with flags.  WHFF_CREATE_HOST_RESIDENT keeps the compressed
+ * stream in pinned, mapped host memory instead of HBM: the fused kernels read
+ * the blocks over the CPU-GPU link (NVLink-C2C on a GB300 superchip) every
+ * step, as the paper's system moves each step's matrix over the host link
+ * (Sec. 4.2; Sec. 5.2 measures the transfer share).  Compression then divides
+ * the bytes that cross the link.  Same results bit for bit as a resident
+ * handle; whff_info's device_bytes leaves the stream out.  Errors: as
+ * whff_create, WHFF_EINVAL for an unknown flag. */
+#define WHFF_CREATE_HOST_RESIDENT 1u
+int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigned flags, void* stream, whff_handle** h);
+
 /* Shape and footprint of a resident matrix (device_bytes = all device memory held). */
 int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, int64_t* N, size_t* device_bytes);
 

@@ -34,7 +34,8 @@ struct whff_handle {
   int device = 0;
   int sm_count = 0;
   int max_rhs = 32;
-  uint8_t* d_stream = nullptr;  // the blob's stream, 256-byte aligned
+  uint8_t* d_stream = nullptr;  // the blob's stream, 256-byte aligned (device address)
+  uint8_t* h_stream = nullptr;  // host-resident handles: the pinned, mapped host copy behind d_stream
   double* d_ws = nullptr;       // split-K partials: ksplit x max_rhs x Mpad
   size_t ws_bytes = 0;
   int* d_status = nullptr;      // device-side error word
@@ -271,8 +272,13 @@ extern "C" const char* whff_last_error(void) { return g_last_error.c_str(); }
 extern "C" const char* whff_version(void) { return "whff 0.1 sm_103a"; }
 
 extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stream, whff_handle** out) {
-  if (!out) {
-    set_error("whff_create: null output handle");
+  return whff_create_ex(blob, len, max_rhs, 0u, stream, out);
+}
+
+extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigned flags, void* stream,
+                              whff_handle** out) {
+  if (!out || (flags & ~(unsigned)WHFF_CREATE_HOST_RESIDENT)) {
+    set_error("whff_create: null output handle or unknown flag");
     return WHFF_EINVAL;
   }
   *out = nullptr;
@@ -316,7 +322,17 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
   // short bands (tall matrices) fold their lanes in FP32 pairs; long ones in FP64
   h->red32 = info.fmt != WHFF_FMT_ZFP && h->BN < 4096;
   const cudaStream_t st = as_stream(stream);
-  if (cudaMalloc(&h->d_stream, info.stream_bytes) != cudaSuccess) {
+  if (flags & WHFF_CREATE_HOST_RESIDENT) {  // pinned host memory, read by the kernels over the CPU link
+    void* dp = nullptr;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&h->h_stream), info.stream_bytes, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&dp, h->h_stream, 0) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("whff_create: pinned mapped host allocation of the compressed stream failed");
+      return fail(WHFF_ENOMEM);
+    }
+    h->d_stream = static_cast<uint8_t*>(dp);
+    std::memcpy(h->h_stream, (const uint8_t*)blob + kHeaderBytes, info.stream_bytes);
+  } else if (cudaMalloc(&h->d_stream, info.stream_bytes) != cudaSuccess) {
     cudaGetLastError();
     set_error("whff_create: cudaMalloc of the compressed stream failed");
     return fail(WHFF_ENOMEM);
@@ -356,8 +372,8 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
     return fail(WHFF_ENOMEM);
   }
   if (cudaMemsetAsync(h->d_status, 0, sizeof(int), st) != cudaSuccess ||
-      cudaMemcpyAsync(h->d_stream, (const uint8_t*)blob + kHeaderBytes, info.stream_bytes, cudaMemcpyHostToDevice,
-                      st) != cudaSuccess ||
+      (!h->h_stream && cudaMemcpyAsync(h->d_stream, (const uint8_t*)blob + kHeaderBytes, info.stream_bytes,
+                                       cudaMemcpyHostToDevice, st) != cudaSuccess) ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     set_error(std::string("whff_create: upload failed: ") + cudaGetErrorString(cudaGetLastError()));
     return fail(WHFF_ECUDA);
@@ -379,8 +395,8 @@ extern "C" int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, 
   if (M) *M = h->info.M;
   if (N) *N = h->info.N;
   if (device_bytes)
-    *device_bytes = h->info.stream_bytes + h->ws_bytes + h->ws_mma_bytes + sizeof(int) + (size_t)h->info.N * h->max_rhs * 4 +
-                    (size_t)h->info.M * h->max_rhs * 8;
+    *device_bytes = (h->h_stream ? 0 : h->info.stream_bytes) + h->ws_bytes + h->ws_mma_bytes + sizeof(int) +
+                    (size_t)h->info.N * h->max_rhs * 4 + (size_t)h->info.M * h->max_rhs * 8;
   return WHFF_OK;
 }
 
@@ -751,7 +767,10 @@ extern "C" void whff_destroy(whff_handle* h) {
   if (!h) return;
   // stream-ordered: outstanding work on the creation stream finishes first
   if (h->create_stream) cudaStreamSynchronize(h->create_stream);
-  cudaFree(h->d_stream);
+  if (h->h_stream)
+    cudaFreeHost(h->h_stream);
+  else
+    cudaFree(h->d_stream);
   cudaFree(h->d_ws);
   cudaFree(h->d_ws_mma);
   cudaFree(h->d_btiles);

@@ -60,6 +60,7 @@ def library() -> ctypes.CDLL:
         "whff_compress_band": (c_int, [P, sz, P, i64, i64, i64, c_int]),
         "whff_blob_seal": (c_int, [P, sz]),
         "whff_create": (c_int, [P, sz, c_int, P, ctypes.POINTER(P)]),
+        "whff_create_ex": (c_int, [P, sz, c_int, ctypes.c_uint, P, ctypes.POINTER(P)]),
         "whff_info": (c_int, [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(i64),
                               ctypes.POINTER(i64), ctypes.POINTER(sz)]),
         "whff_plan": (c_int, [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
@@ -279,11 +280,13 @@ class Handle:
             pass
 
 
-def whff_create(blob, max_rhs: int = 32, stream=None) -> Handle:
+def whff_create(blob, max_rhs: int = 32, stream=None, host_resident: bool = False) -> Handle:
+    """Make a blob resident; host_resident keeps the stream in pinned host memory read over the CPU link."""
     b = np.ascontiguousarray(np.frombuffer(blob, dtype=np.uint8) if isinstance(blob, (bytes, bytearray)) else blob,
                              dtype=np.uint8)
     h = ctypes.c_void_p()
-    _check(library().whff_create(b.ctypes.data, b.size, max_rhs, _stream_ptr(stream), ctypes.byref(h)))
+    _check(library().whff_create_ex(b.ctypes.data, b.size, max_rhs, 1 if host_resident else 0, _stream_ptr(stream),
+                                    ctypes.byref(h)))
     return Handle(h.value)
 
 
