@@ -206,21 +206,25 @@ void whff_graph_destroy(whff_graph* g);
 
 /* ------------------------------------------------------- tuning and batches */
 /* Launch shape of the fixed-allocation (WZ2) kernels: blocks kept in flight
- * per lane (2 or 4), resident CTAs per SM of the persistent grid, and how a
- * warp folds its 32 lanes' compensated sums at the end of a band: reduce32 = 0
- * widens them to FP64 first and adds in FP64, reduce32 = 1 adds the FP32
- * (hi, lo) pairs with TwoSum and widens only the result (cheaper on GB300's
- * small FP64 pipe, which pays on short bands; the default is 1 when a band
- * has fewer than 4096 blocks).  Unroll does not change the arithmetic; CTAs
- * per SM (the warp ranges) and reduce32 change its rounding within the bar.
+ * per lane (2 or 4), resident CTAs per SM of the persistent grid, and the
+ * fold flags: WHFF_FOLD_FP32_PAIRS folds a band's 32 lane sums as FP32
+ * (hi, lo) pairs with TwoSum, widened once, instead of widening to FP64 and
+ * adding in FP64 (cheaper on GB300's small FP64 pipe; pays on short bands);
+ * WHFF_FOLD_LANE_GROUPS lets four 8-lane groups of a warp take four bands at
+ * once (short bands: tall matrices), with unroll 2 only.  Defaults: FP32
+ * pairs below 4096 blocks per band, lane groups below 256.  Unroll does not
+ * change the arithmetic; CTAs per SM (the warp ranges) and the fold flags
+ * change its rounding within the bar.
  * whff_tune times every candidate on the resident matrix (iters steps each,
  * R = 1, CUDA events on the stream) and keeps the fastest; *best_ms (optional)
  * receives its step time.  whff_get_config / whff_set_config read and apply a
  * shape (e.g. from a cache keyed by format, rate, shape and SM count).  WZ2
  * handles only (WHFF_EINVAL otherwise). */
+#define WHFF_FOLD_FP32_PAIRS 1
+#define WHFF_FOLD_LANE_GROUPS 2
 int whff_tune(whff_handle* h, int iters, void* stream, double* best_ms);
-int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_sm, int* reduce32);
-int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int reduce32);
+int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_sm, int* fold);
+int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int fold);
 
 /* Crossover of the two engines (Sec. 4.4's GEMV with many right-hand sides is
  * a GEMM): passes of at least min_rhs columns run on the tensor cores, smaller

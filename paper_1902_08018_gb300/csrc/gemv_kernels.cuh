@@ -33,9 +33,12 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float p) {
   lo += err;
 }
 
+// Sum over aligned groups of GL lanes (GL = 32: the warp); every lane of a
+// group ends with its group's sum.  All 32 lanes must execute it.
+template <int GL = 32>
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = GL / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
@@ -47,9 +50,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 // It pays where bands are short (tall matrices: many band sums per block
 // streamed); on long bands the FP64 butterfly above is a little faster, so
 // the choice is a per-matrix setting (see whff_set_config).
+template <int GL = 32>
 __device__ __forceinline__ double warp_sum_pair(float hi, float lo) {
 #pragma unroll
-  for (int o = 16; o; o >>= 1) {
+  for (int o = GL / 2; o; o >>= 1) {
     const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
     const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
     const float s = hi + h2;

@@ -47,6 +47,7 @@ struct whff_handle {
   int64_t chunk = 0;            // J blocks (WZ1) or columns (scaled) per split
   int ctas_per_sm = 4;          // resident CTAs per SM of the persistent kernels
   bool red32 = false;           // WZ2 / scaled: fold lanes in FP32 pairs (short bands) instead of FP64
+  bool groups8 = false;         // WZ2: four 8-lane groups per warp, one band each (short bands)
   int unroll = 2;               // WZ2: blocks in flight per lane (R = 1 kernel)
   int64_t range_ctas = 0;       // WZ2: CTAs of the range-partitioned persistent grid
   int64_t range_len = 0;        // WZ2: blocks per warp range
@@ -190,7 +191,7 @@ int launch_wz2(const whff_handle* h, const float* x, int R, int64_t ldx, bool ve
                double* state, double decay, cudaStream_t st) {
   Wz2Step a{h->d_stream, h->info.M, h->info.N, h->BM, h->BN, x, ldx, vec, h->range_len, h->maxseg, h->d_ws,
             y, ldy, state, decay, h->range_ctas, R == 1 ? h->unroll : 2, h->info.fmt == WHFF_FMT_FIXED_LIFT, R,
-            h->red32};
+            h->red32, h->groups8};
   int e;
   switch (h->info.rate) {
     case 8: e = wz2_launch<8>(a, st); break;
@@ -321,6 +322,7 @@ extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigne
   choose_split(h);
   // short bands (tall matrices) fold their lanes in FP32 pairs; long ones in FP64
   h->red32 = info.fmt != WHFF_FMT_ZFP && h->BN < 4096;
+  h->groups8 = (info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) && h->BN < 256;
   const cudaStream_t st = as_stream(stream);
   if (flags & WHFF_CREATE_HOST_RESIDENT) {  // pinned host memory, read by the kernels over the CPU link
     void* dp = nullptr;
@@ -784,10 +786,11 @@ extern "C" void whff_destroy(whff_handle* h) {
 // ------------------------------------------------------------------ tuning
 namespace {
 
-int apply_config(whff_handle* h, int unroll, int ctas_per_sm, bool red32) {
+int apply_config(whff_handle* h, int unroll, int ctas_per_sm, int fold) {
   h->unroll = unroll;
   h->ctas_per_sm = ctas_per_sm;
-  h->red32 = red32;
+  h->red32 = (fold & WHFF_FOLD_FP32_PAIRS) != 0;
+  h->groups8 = (fold & WHFF_FOLD_LANE_GROUPS) != 0;
   choose_ranges(h);
   const size_t need = h->maxseg > 1 ? (size_t)h->BM * (size_t)h->maxseg * (size_t)h->ws_rhs * 4 * 8 : 0;
   if (need > h->ws_bytes) {
@@ -810,20 +813,21 @@ bool is_wz2(const whff_handle* h) {
 
 }  // namespace
 
-extern "C" int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_sm, int* reduce32) {
+extern "C" int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_sm, int* fold) {
   if (!h) {
     set_error("whff_get_config: null handle");
     return WHFF_EINVAL;
   }
   if (unroll) *unroll = h->unroll;
   if (ctas_per_sm) *ctas_per_sm = h->ctas_per_sm;
-  if (reduce32) *reduce32 = h->red32 ? 1 : 0;
+  if (fold) *fold = (h->red32 ? WHFF_FOLD_FP32_PAIRS : 0) | (h->groups8 ? WHFF_FOLD_LANE_GROUPS : 0);
   return WHFF_OK;
 }
 
-extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int reduce32) {
-  if (!h || !is_wz2(h) || (unroll != 2 && unroll != 4) || ctas_per_sm < 1 || (reduce32 != 0 && reduce32 != 1)) {
-    set_error("whff_set_config: WZ2 handles only; unroll 2 or 4; ctas_per_sm >= 1; reduce32 0 or 1");
+extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int fold) {
+  if (!h || !is_wz2(h) || (unroll != 2 && unroll != 4) || ctas_per_sm < 1 || fold < 0 || fold > 3 ||
+      (unroll == 4 && (fold & WHFF_FOLD_LANE_GROUPS))) {
+    set_error("whff_set_config: WZ2 handles only; unroll 2 or 4 (2 with lane groups); ctas_per_sm >= 1; fold 0..3");
     return WHFF_EINVAL;
   }
   const int occ = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, unroll);
@@ -831,7 +835,7 @@ extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int 
     set_error("whff_set_config: more CTAs per SM than can be resident");
     return WHFF_EINVAL;
   }
-  return apply_config(h, unroll, ctas_per_sm, reduce32 != 0);
+  return apply_config(h, unroll, ctas_per_sm, fold);
 }
 
 extern "C" int whff_get_crossover(const whff_handle* h, int* min_rhs) {
@@ -865,18 +869,18 @@ extern "C" int whff_tune(whff_handle* h, int iters, void* stream, double* best_m
   WHFF_CUDA_TRY(cudaEventCreate(&e0));
   WHFF_CUDA_TRY(cudaEventCreate(&e1));
   const int orig_u = h->unroll, orig_c = h->ctas_per_sm;
-  const bool orig_r = h->red32;
+  const int orig_f = (h->red32 ? WHFF_FOLD_FP32_PAIRS : 0) | (h->groups8 ? WHFF_FOLD_LANE_GROUPS : 0);
   double best = 1e30;
-  int bu = orig_u, bc = orig_c;
-  bool br = orig_r;
+  int bu = orig_u, bc = orig_c, bf = orig_f;
   int err = WHFF_OK;
-  // candidates: unroll 2 or 4, the top three CTA counts per SM, FP64 or FP32-pair lane folds
-  for (int cand = 0; cand < 12 && err == WHFF_OK; ++cand) {
-    const int u = cand < 6 ? 2 : 4;
-    const bool red = (cand & 1) != 0;
-    const int c = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, u) - (cand % 6) / 2;
+  // candidates: the top three CTA counts per SM x (unroll 2 with each of the four
+  // folds, unroll 4 with the two whole-warp folds)
+  for (int cand = 0; cand < 18 && err == WHFF_OK; ++cand) {
+    const int u = cand < 12 ? 2 : 4;
+    const int f = (cand & 1) | (cand < 12 && (cand & 2) ? WHFF_FOLD_LANE_GROUPS : 0);
+    const int c = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, u) - (cand < 12 ? cand / 4 : (cand - 12) / 2);
     if (c < 1) continue;
-    if ((err = apply_config(h, u, c, red)) != WHFF_OK) break;
+    if ((err = apply_config(h, u, c, f)) != WHFF_OK) break;
     if ((err = whff_step(h, h->d_x, 1, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream)) != WHFF_OK) break;
     cudaEventRecord(e0, st);
     for (int k = 0; k < iters && err == WHFF_OK; ++k)
@@ -890,17 +894,17 @@ extern "C" int whff_tune(whff_handle* h, int iters, void* stream, double* best_m
       best = ms / iters;
       bu = u;
       bc = c;
-      br = red;
+      bf = f;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err) {
-    apply_config(h, orig_u, orig_c, orig_r);
+    apply_config(h, orig_u, orig_c, orig_f);
     return err;
   }
   if (best_ms) *best_ms = best;
-  return apply_config(h, bu, bc, br);
+  return apply_config(h, bu, bc, bf);
 }
 
 // ------------------------------------------------------------------ batches
@@ -1078,11 +1082,12 @@ extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64
   const cudaStream_t st = as_stream(stream);
   // the pinned tables are reused: wait until the previous step's copies ran
   WHFF_CUDA_TRY(cudaEventSynchronize(b->copied));
-  // matrices with many right-hand sides: tensor-core passes of their own (state included)
+  // matrices with many right-hand sides: tensor-core passes of their own (their state is
+  // applied with everyone else's by the batch's state pass at the end)
   for (size_t i = 0; i < b->hs.size(); ++i) {
     whff_handle* h = b->hs[i];
     if (b->R[i] >= h->mma_min_rhs && h->d_ws_mma) {
-      int e = whff_step(h, x[i], b->R[i], ldx[i], y[i], ldy[i], state ? state[i] : nullptr, decay, stream);
+      int e = whff_step(h, x[i], b->R[i], ldx[i], y[i], ldy[i], nullptr, decay, stream);
       if (e) return e;
     }
   }
@@ -1127,10 +1132,8 @@ extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64
   }
   if (state) {
     const int count = (int)b->hs.size();
-    for (int i = 0; i < count; ++i) {
-      const bool own = b->R[i] >= b->hs[i]->mma_min_rhs && b->hs[i]->d_ws_mma;  // state already applied
-      b->state_pinned[i] = dev::BatchState{own ? nullptr : state[i], y[i], ldy[i], b->hs[i]->info.M, b->R[i], decay};
-    }
+    for (int i = 0; i < count; ++i)
+      b->state_pinned[i] = dev::BatchState{state[i], y[i], ldy[i], b->hs[i]->info.M, b->R[i], decay};
     WHFF_CUDA_TRY(cudaMemcpyAsync(b->d_state, b->state_pinned, sizeof(dev::BatchState) * count,
                                   cudaMemcpyHostToDevice, st));
     wz2_batched_state_launch(b->d_state, b->d_state_rows, count, b->state_rows, st);

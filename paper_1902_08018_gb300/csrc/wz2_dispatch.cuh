@@ -6,16 +6,24 @@
 
 namespace whff {
 
-template <int RATE, bool LIFT, int R, int U>
+template <int RATE, bool LIFT, int R, int U, int GL = 32>
 static void wz2_launch_one(const Wz2Step& a, cudaStream_t st) {
-  dev::wz2_gemv_kernel<RATE, LIFT, R, U><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
+  dev::wz2_gemv_kernel<RATE, LIFT, R, U, GL><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
       a.stream, a.M, a.N, a.BM, a.BN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg, a.ws, a.y, a.ldy, a.state, a.decay,
       a.red32);
 }
 
 template <int RATE, bool LIFT>
 static int wz2_launch_lift(const Wz2Step& a, cudaStream_t st) {
-  switch (a.R) {
+  if (a.groups8) {  // short bands: four 8-lane groups per warp, two blocks in flight per lane
+    switch (a.R) {
+      case 1: wz2_launch_one<RATE, LIFT, 1, 2, 8>(a, st); break;
+      case 2: wz2_launch_one<RATE, LIFT, 2, 2, 8>(a, st); break;
+      case 4: wz2_launch_one<RATE, LIFT, 4, 2, 8>(a, st); break;
+      case 8: wz2_launch_one<RATE, LIFT, 8, 2, 8>(a, st); break;
+      default: return -1;
+    }
+  } else switch (a.R) {
     case 1:
       if (a.unroll == 4) wz2_launch_one<RATE, LIFT, 1, 4>(a, st);
       else wz2_launch_one<RATE, LIFT, 1, 2>(a, st);
@@ -75,11 +83,11 @@ int wz2_occupancy(bool lift, int unroll) {
   cudaError_t e;
   const int threads = dev::kWarpsPerCta * 32;
   if (lift)
-    e = unroll == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, true, 1, 4>, threads, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, true, 1, 2>, threads, 0);
+    e = unroll == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, true, 1, 4, 32>, threads, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, true, 1, 2, 32>, threads, 0);
   else
-    e = unroll == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, false, 1, 4>, threads, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, false, 1, 2>, threads, 0);
+    e = unroll == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, false, 1, 4, 32>, threads, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, false, 1, 2, 32>, threads, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;

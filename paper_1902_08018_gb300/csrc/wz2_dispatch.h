@@ -27,6 +27,7 @@ struct Wz2Step {
   bool lift;
   int R;           // 1, 2, 4 or 8
   bool red32;      // fold lanes with the FP32 pair butterfly (short bands)
+  bool groups8;    // four 8-lane groups per warp, one band each (short bands)
 };
 
 

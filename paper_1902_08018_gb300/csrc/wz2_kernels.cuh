@@ -99,32 +99,36 @@ __device__ __forceinline__ void wz2_unpermute(const float (&f)[16], float (&V)[1
 
 // Fold a band's FP64 sums and map them to y: MIX 1 = the lift's 2G mixing
 // and 2^-3, MIX 2 = 2^3 (no transform), MIX 0 = identity (scaled formats).
-template <bool LIFT, int R>
+template <bool LIFT, int R, int GL = 32>
 __device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
                                            int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
                                            double* __restrict__ y, int64_t ldy, double* __restrict__ state,
-                                           double decay, bool red32);
+                                           double decay, bool red32, bool active = true);
 
 // red32: fold the lanes with the FP32 pair butterfly instead of FP64 (the
-// same bar; another rounding).
-template <int MIX, int R>
+// same bar; another rounding).  GL: lanes per band (32, or 8 when a warp
+// works on 4 bands at once); lane is the lane within its group, and a group
+// with no piece (active = false) folds zeros and writes nothing.  All 32
+// lanes must call it together.
+template <int MIX, int R, int GL = 32>
 __device__ __forceinline__ void band_finish(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
                                             int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
                                             double* __restrict__ y, int64_t ldy, double* __restrict__ state,
-                                            double decay, bool red32) {
+                                            double decay, bool red32, bool active = true) {
   constexpr bool LIFT = MIX == 1;
   double z[4][R];
   if (red32) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int r = 0; r < R; ++r) z[i][r] = warp_sum_pair(hi[i][r], lo[i][r]);
+      for (int r = 0; r < R; ++r) z[i][r] = warp_sum_pair<GL>(hi[i][r], lo[i][r]);
   } else {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int r = 0; r < R; ++r) z[i][r] = warp_sum((double)hi[i][r] + (double)lo[i][r]);
+      for (int r = 0; r < R; ++r) z[i][r] = warp_sum<GL>((double)hi[i][r] + (double)lo[i][r]);
   }
+  if (!active) return;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     double t[4];
@@ -141,12 +145,12 @@ __device__ __forceinline__ void band_finish(const float (&hi)[4][R], const float
 #pragma unroll
     for (int i = 0; i < 4; ++i) z[i][r] = t[i];
   }
-  // lane (i*R + r) writes value (i, r)
+  // lane (i*R + r) mod GL writes value (i, r)
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      if (lane != i * R + r) continue;
+      if (lane != (i * R + r) % GL) continue;
       const int64_t row = row0 + i;
       if (ksplit == 2) {  // segment partial: ws[row0 + r*4 + i] (row0 = 4*(band*maxseg+seg)*R)
         ws[row0 + r * 4 + i] = z[i][r];
@@ -172,12 +176,13 @@ __device__ __forceinline__ void band_finish(const float (&hi)[4][R], const float
 }
 
 // One block's contribution, scaled: p[i][r] = s * sum_b V[i][b] xt_r[b].
-template <bool LIFT, int R>
+template <bool LIFT, int R, int GL>
 __device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float (&lo)[4][R], int lane, int64_t row0,
                                            int64_t M, int split, int ksplit, int64_t Mpad, double* __restrict__ ws,
                                            double* __restrict__ y, int64_t ldy, double* __restrict__ state,
-                                           double decay, bool red32) {
-  band_finish<LIFT ? 1 : 2, R>(hi, lo, lane, row0, M, split, ksplit, Mpad, ws, y, ldy, state, decay, red32);
+                                           double decay, bool red32, bool active) {
+  band_finish<LIFT ? 1 : 2, R, GL>(hi, lo, lane, row0, M, split, ksplit, Mpad, ws, y, ldy, state, decay, red32,
+                                   active);
 }
 
 template <int RATE, bool LIFT, int R>
@@ -226,35 +231,35 @@ __device__ __forceinline__ void wz2_block_partial(const uint32_t (&w)[Wz2Layout<
 // last block enters alone.  So every right-hand side gets the same rounding
 // whatever R, UNROLL or the batch it is in.  UNROLL (2 or 4) blocks per lane
 // are kept in flight: their loads are issued before any is decoded.
-template <int RATE, bool LIFT, int R, int UNROLL>
+template <int RATE, bool LIFT, int R, int UNROLL, int STRIDE = 32>
 __device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int64_t J0, int64_t J1, int lane,
                                           const float* __restrict__ x, int64_t ldx, int64_t N, bool x_fast,
                                           bool x_vec_ok, float (&hi)[4][R], float (&lo)[4][R]) {
   static_assert(UNROLL == 2 || UNROLL == 4, "blocks are consumed in pairs");
   constexpr int NW = Wz2Layout<RATE>::kWords;
   int64_t J = J0 + lane;
-  for (; J + 32 * (UNROLL - 1) < J1; J += 32 * UNROLL) {
+  for (; J + STRIDE * (UNROLL - 1) < J1; J += STRIDE * UNROLL) {
     uint32_t w[UNROLL][NW];
 #pragma unroll
-    for (int u = 0; u < UNROLL; ++u) wz2_load<RATE>(base, J + 32 * u, w[u]);
+    for (int u = 0; u < UNROLL; ++u) wz2_load<RATE>(base, J + STRIDE * u, w[u]);
 #pragma unroll
     for (int u = 0; u < UNROLL; u += 2) {
       float p0[4][R], p1[4][R];
-      wz2_block_partial<RATE, LIFT, R>(w[u], x, ldx, 4 * (J + 32 * u), N, x_fast, x_vec_ok, p0);
-      wz2_block_partial<RATE, LIFT, R>(w[u + 1], x, ldx, 4 * (J + 32 * (u + 1)), N, x_fast, x_vec_ok, p1);
+      wz2_block_partial<RATE, LIFT, R>(w[u], x, ldx, 4 * (J + STRIDE * u), N, x_fast, x_vec_ok, p0);
+      wz2_block_partial<RATE, LIFT, R>(w[u + 1], x, ldx, 4 * (J + STRIDE * (u + 1)), N, x_fast, x_vec_ok, p1);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r] + p1[i][r]);
     }
   }
-  for (; J + 32 < J1; J += 64) {  // remaining whole pairs
+  for (; J + STRIDE < J1; J += 2 * STRIDE) {  // remaining whole pairs
     uint32_t w0[NW], w1[NW];
     wz2_load<RATE>(base, J, w0);
-    wz2_load<RATE>(base, J + 32, w1);
+    wz2_load<RATE>(base, J + STRIDE, w1);
     float p0[4][R], p1[4][R];
     wz2_block_partial<RATE, LIFT, R>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
-    wz2_block_partial<RATE, LIFT, R>(w1, x, ldx, 4 * (J + 32), N, x_fast, x_vec_ok, p1);
+    wz2_block_partial<RATE, LIFT, R>(w1, x, ldx, 4 * (J + STRIDE), N, x_fast, x_vec_ok, p1);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -275,41 +280,60 @@ __device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int6
 // Persistent kernel with exact balance: the G warps of the grid split the
 // band-major sequence of all BM*BN blocks into G contiguous ranges of L
 // blocks.  A range covers pieces of one to a few 4-row bands; for every piece
-// the warp folds its lanes' sums and either writes y (and the state) directly,
-// when the band lies inside one range, or stores the piece's partial in
-// ws[band][segment] for wz2_segment_epilogue, which adds a band's segments in
-// order.
-template <int RATE, bool LIFT, int R, int UNROLL>
+// the lanes' sums are folded and either y (and the state) is written
+// directly, when the band lies inside one range, or the piece's partial goes
+// to ws[band][segment] for wz2_segment_epilogue, which adds a band's segments
+// in order.  GL = 32: the warp takes one piece at a time; GL = 8: four lane
+// groups take the next four pieces at once (short bands, where a warp per
+// band would spend its time folding).
+template <int RATE, bool LIFT, int R, int UNROLL, int GL>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
     wz2_gemv_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BM, int64_t BN,
                     const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int64_t L, int maxseg,
                     double* __restrict__ ws, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
                     double decay, bool red32) {
   constexpr int64_t kBlockBytes = 4 * Wz2Layout<RATE>::kWords;
+  constexpr int NG = 32 / GL;  // pieces taken at once
   const int lane = threadIdx.x & 31;
+  const int gl = lane % GL;
   const int64_t g = (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   const int64_t total = BM * BN;
   const bool x_fast = x_vec_ok && (N % 4 == 0);
   int64_t b0 = g * L;
   const int64_t b1 = min(total, b0 + L);
   while (b0 < b1) {
-    const int64_t I = b0 / BN;
-    const int64_t piece_end = min(b1, (I + 1) * BN);
-    const int64_t g_lo = (I * BN) / L, g_hi = ((I + 1) * BN - 1) / L;
     float hi[4][R], lo[4][R];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
-    wz2_piece<RATE, LIFT, R, UNROLL>(stream + (uint64_t)(I * BN) * kBlockBytes, b0 - I * BN, piece_end - I * BN,
-                                     lane, x, ldx, N, x_fast, x_vec_ok, hi, lo);
-    if (g_lo == g_hi) {  // the whole band is in this range: finish it here
-      wz2_finish<LIFT, R>(hi, lo, lane, 4 * I, M, 0, 1, 4 * BM, ws, y, ldy, state, decay, red32);
-    } else {  // one segment of a shared band: ws[(band * maxseg + seg) * R + r][i]
-      wz2_finish<LIFT, R>(hi, lo, lane, 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, 2, 0, ws, y, ldy, state,
-                          decay, red32);
+    if constexpr (GL == 32) {  // the warp takes the piece starting at b0
+      const int64_t I = b0 / BN;
+      const int64_t piece_end = min(b1, (I + 1) * BN);
+      const int64_t g_lo = (I * BN) / L, g_hi = ((I + 1) * BN - 1) / L;
+      wz2_piece<RATE, LIFT, R, UNROLL>(stream + (uint64_t)(I * BN) * kBlockBytes, b0 - I * BN, piece_end - I * BN,
+                                       lane, x, ldx, N, x_fast, x_vec_ok, hi, lo);
+      if (g_lo == g_hi) {  // the whole band is in this range: finish it here
+        wz2_finish<LIFT, R>(hi, lo, lane, 4 * I, M, 0, 1, 4 * BM, ws, y, ldy, state, decay, red32);
+      } else {  // one segment of a shared band: ws[(band * maxseg + seg) * R + r][i]
+        wz2_finish<LIFT, R>(hi, lo, lane, 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, 2, 0, ws, y, ldy, state,
+                            decay, red32);
+      }
+      b0 = piece_end;
+    } else {  // lane group lane / GL takes the piece of band b0 / BN + lane / GL
+      const int64_t I = b0 / BN + lane / GL;
+      const int64_t pb = max(b0, I * BN), pe = min(b1, (I + 1) * BN);
+      const bool active = pb < pe;
+      const int64_t g_lo = (I * BN) / L, g_hi = ((I + 1) * BN - 1) / L;
+      if (active)
+        wz2_piece<RATE, LIFT, R, UNROLL, GL>(stream + (uint64_t)(I * BN) * kBlockBytes, pb - I * BN, pe - I * BN,
+                                             gl, x, ldx, N, x_fast, x_vec_ok, hi, lo);
+      // one call for all groups (the folds shuffle across the whole warp)
+      const bool whole = g_lo == g_hi;
+      wz2_finish<LIFT, R, GL>(hi, lo, gl, whole ? 4 * I : 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, whole ? 1 : 2,
+                              whole ? 4 * BM : 0, ws, y, ldy, state, decay, red32, active);
+      b0 = min(b1, (b0 / BN + NG) * BN);
     }
-    b0 = piece_end;
   }
 }
 

@@ -195,12 +195,12 @@ class Handle:
             with open(cache) as f:
                 db = json.load(f)
         if key in db:
-            self.set_config(db[key]["unroll"], db[key]["ctas_per_sm"], db[key].get("reduce32", 0))
+            self.set_config(db[key]["unroll"], db[key]["ctas_per_sm"], db[key].get("fold", 0))
             return dict(db[key], cached=True)
         ms = ctypes.c_double()
         _check(library().whff_tune(self._ptr, iters, _stream_ptr(stream), ctypes.byref(ms)))
-        u, c, r = self.config()
-        rec = {"unroll": u, "ctas_per_sm": c, "reduce32": r, "ms": ms.value}
+        u, c, f = self.config()
+        rec = {"unroll": u, "ctas_per_sm": c, "fold": f, "ms": ms.value}
         if cache:
             db[key] = rec
             os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
@@ -209,15 +209,15 @@ class Handle:
         return dict(rec, cached=False)
 
     def config(self):
-        """(unroll, ctas_per_sm, reduce32) of the WZ2 launch shape."""
+        """(unroll, ctas_per_sm, fold flags: 1 FP32-pair fold, 2 lane groups) of the WZ2 launch shape."""
         u, c, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(library().whff_get_config(self._ptr, ctypes.byref(u), ctypes.byref(c), ctypes.byref(r)))
         return u.value, c.value, r.value
 
-    def set_config(self, unroll: int, ctas_per_sm: int, reduce32: int | None = None):
-        if reduce32 is None:
-            reduce32 = self.config()[2]
-        _check(library().whff_set_config(self._ptr, unroll, ctas_per_sm, int(reduce32)))
+    def set_config(self, unroll: int, ctas_per_sm: int, fold: int | None = None):
+        if fold is None:
+            fold = self.config()[2]
+        _check(library().whff_set_config(self._ptr, unroll, ctas_per_sm, int(fold)))
 
     @property
     def crossover(self) -> int:
