@@ -100,14 +100,15 @@ struct MmaBTile {
   static constexpr int kB = 3 * kMmaKSteps * kBTile;
 };
 
-// Shared memory: A and B tiles of two stages, then 4 mbarriers and the TMEM slot.
+// Shared memory: A and B tiles of two stages, then 4 mbarriers, the TMEM slot,
+// flags and thread 0's B-copy cursor; the member table follows kBytes.
 template <int RATE, int NR>
 struct MmaSmem {
   static constexpr int kATile = 128 * 16 * 2;  // one piece, one K step
   static constexpr int kA = MmaPieces<RATE>::kA * kMmaKSteps * kATile;
   static constexpr int kB = MmaBTile<NR>::kB;
   static constexpr int kBars = 2 * (kA + kB);
-  static constexpr int kBytes = kBars + 64;
+  static constexpr int kBytes = kBars + 80;  // 4 mbarriers, TMEM slot, flags, cursors
 };
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
@@ -196,21 +197,42 @@ __device__ __forceinline__ void tmem_load_row<16>(uint32_t taddr, float (&v)[16]
 // right-hand side r, (2G)^T x_J (or x_J without the lift) in three BF16
 // pieces, already in the shared-memory tile layout of its 16-block stage:
 // out[stage][piece][kstep] = NR x 16 BF16 tile.  Thread per (stage, J, r).
+// The pass of thread q in a launch-wide grid: `single` when table is null,
+// else the entry with the largest begin <= q (begin = bt_begin or fin_begin).
+template <bool FIN>
+__device__ __forceinline__ MmaPass pass_of(const MmaPass& single, const MmaPass* __restrict__ table, int n,
+                                           int64_t q) {
+  if (!table) return single;
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((FIN ? table[mid].fin_begin : table[mid].bt_begin) <= q) lo = mid;
+    else hi = mid - 1;
+  }
+  return table[lo];
+}
+
+// B tiles of every pass: for stage st, column block J and right-hand side r,
+// (2G)^T x_J (or x_J without the lift) in three BF16 pieces, already in the
+// shared-memory tile layout of the stage: out[st][piece][kstep] = NR x 16 BF16.
+// Thread per (pass, stage, J in the stage, r); total threads given.
 template <bool LIFT, int NR>
-__global__ void wz2_mma_btiles(const float* __restrict__ x, int64_t ldx, int64_t N, int R, int64_t nstages,
-                               uint8_t* __restrict__ out) {
+__global__ void wz2_mma_btiles(MmaPass single, const MmaPass* __restrict__ table, int n, int64_t threads) {
   using S = MmaBTile<NR>;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nstages * kMmaStageBlocks * NR) return;
-  const int r = (int)(q % NR);
-  const int jl = (int)((q / NR) % kMmaStageBlocks);
-  const int64_t stage = q / ((int64_t)NR * kMmaStageBlocks);
+  if (q >= threads) return;
+  const MmaPass ps = pass_of<false>(single, table, n, q);
+  const int64_t ql = q - ps.bt_begin;
+  if (ql >= (int64_t)ps.S * kMmaStageBlocks * NR) return;
+  const int r = (int)(ql % NR);
+  const int jl = (int)((ql / NR) % kMmaStageBlocks);
+  const int64_t stage = ql / ((int64_t)NR * kMmaStageBlocks);
   const int64_t J = stage * kMmaStageBlocks + jl;
   float xt[4] = {0.f, 0.f, 0.f, 0.f};
-  if (r < R) {
+  if (r < ps.R) {
     float xv[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) xv[c] = 4 * J + c < N ? __ldg(x + (int64_t)r * ldx + 4 * J + c) : 0.f;
+    for (int c = 0; c < 4; ++c) xv[c] = 4 * J + c < ps.N ? __ldg(ps.x + (int64_t)r * ps.ldx + 4 * J + c) : 0.f;
     if (LIFT) {
       const float aa = xv[0] + xv[1], bb = xv[2] + xv[3], cc = xv[0] + xv[2], dd = xv[1] + xv[3];
       xt[0] = 2.f * (aa + bb);
@@ -226,7 +248,7 @@ __global__ void wz2_mma_btiles(const float* __restrict__ x, int64_t ldx, int64_t
 #pragma unroll
   for (int b = 0; b < 4; ++b) split3(xt[b], p[0][b], p[1][b], p[2][b]);
   const int kstep = jl >> 2, kk = (jl & 3) * 4;
-  uint8_t* base = out + stage * (int64_t)S::kB;
+  uint8_t* base = ps.btiles + stage * (int64_t)S::kB;
 #pragma unroll
   for (int pc = 0; pc < 3; ++pc)
     *reinterpret_cast<uint2*>(base + (pc * kMmaKSteps + kstep) * S::kBTile + tile_off(r, kk)) =
@@ -331,14 +353,16 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
       : "memory");
 }
 
-// Persistent grid over the item sequence (tile, stage), item = tile * S + stage,
-// CTA g taking items [g L, g L + L).  ws[((tile * maxseg + seg) * R + r) * 128 + m]
-// receives the FP64 partial of tile row m (= 32a + band) for the CTA's segment
-// seg = g - (tile S) / L of the tile.
-template <int RATE, bool LIFT, int NR>
+// Persistent grid over the item sequence of one or more passes (members):
+// member k owns items [item_begin, item_begin + tiles S), item = item_begin +
+// tile S + stage; CTA g takes items [g L, g L + L).  ws[((tile * maxseg + seg)
+// * R + r) * 128 + m] of a member receives the FP64 partial of tile row m
+// (= 32a + band) for the CTA's segment seg = g - (item_begin + tile S) / L.
+// `single` is the only member when table is null (one matrix); otherwise the
+// nmem members of the table (a batch) are copied to shared memory.
+template <int RATE, bool LIFT, int NR, bool TABLE>
 __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)  // 3 A pieces: 120 KB of tiles
-    wz2_mma_kernel(const uint8_t* __restrict__ stream, int64_t BM, int64_t BN, const uint8_t* __restrict__ btiles,
-                   int R, int64_t S, int64_t total, int64_t L, int maxseg, double* __restrict__ ws,
+    wz2_mma_kernel(MmaMember single, const MmaMember* __restrict__ table, int nmem, int64_t total, int64_t L,
                    int* __restrict__ status) {
   using SM = MmaSmem<RATE, NR>;
   constexpr int PA = MmaPieces<RATE>::kA;
@@ -354,10 +378,18 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + SM::kBars + 36);
   int64_t* last_commit = reinterpret_cast<int64_t*>(smem + SM::kBars + 48);  // last stage whose MMAs were committed
   int64_t* last_copy = reinterpret_cast<int64_t*>(smem + SM::kBars + 56);    // last stage whose B copy was started
+  MmaMember* tab = reinterpret_cast<MmaMember*>(smem + SM::kBytes);          // the members
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t it0 = (int64_t)blockIdx.x * L;
   const int64_t n = max((int64_t)0, min(total, it0 + L) - it0);
+  if constexpr (TABLE)
+    for (int i = t; i < nmem; i += kMmaThreads) tab[i] = table[i];
+  // member m (TABLE: of the batch's table; else the one matrix)
+  auto mb = [&](int m) -> const MmaMember& {
+    if constexpr (TABLE) return tab[m];
+    return single;
+  };
 
   if (t == 0) {
     mbar_init(mma_bar, 1);
@@ -386,18 +418,41 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
   const int m_row = 32 * (warp & 3) + lane;
   const int c0 = HALF * (warp >> 2);
 
-  // Cursors (tile, stage) of the next item to fetch, to copy B for and to
-  // issue; they advance in item order, so the loop has no divisions.
-  const int tile0 = (int)(it0 / S), st0 = (int)(it0 - (int64_t)tile0 * S);
-  int f_tile = tile0, f_st = st0, m_tile = tile0, m_st = st0;
+  // Cursors (member, tile, stage) of the next item to fetch, to copy B for
+  // and to issue; they advance in item order, so the loop has no divisions.
+  int mem0 = 0;
+  if constexpr (TABLE)
+    while (mem0 + 1 < nmem && tab[mem0 + 1].item_begin <= it0) ++mem0;
+  const int tile0 = (int)((it0 - mb(mem0).item_begin) / mb(mem0).S);
+  const int st0 = (int)(it0 - mb(mem0).item_begin - (int64_t)tile0 * mb(mem0).S);
+  int f_m = mem0, f_tile = tile0, f_st = st0;  // fetch
+  int m_m = mem0, m_tile = tile0, m_st = st0;  // issue
+  // the B-copy cursor of a batch is thread 0's alone: it lives in shared
+  // memory, not in every thread's registers
+  int* b_cur = reinterpret_cast<int*>(smem + SM::kBars + 64);
+  if (TABLE && t == 0) b_cur[0] = mem0, b_cur[1] = tile0, b_cur[2] = st0;
+  auto advance = [&](int& m, int& tile, int& st) {
+    if (++st == mb(m).S) {
+      st = 0, ++tile;
+      if constexpr (TABLE)
+        if (tile == tab[m].tiles) tile = 0, ++m;
+    }
+  };
 
   uint32_t w[2][2][NW];  // compressed words of two stages (ring), 2 blocks each
   constexpr int64_t kBlockBytes = 4 * NW;
   // this thread's first block of the next fetch: band 32 f_tile + band_l, block 16 f_st + jl0
-  bool f_band_ok = 32 * (int64_t)f_tile + band_l < BM;
-  const uint8_t* f_ptr = stream + ((32 * (int64_t)f_tile + band_l) * BN + 16 * (int64_t)f_st + jl0) * kBlockBytes;
+  bool f_band_ok = false;
+  const uint8_t* f_ptr = nullptr;
+  auto fetch_at = [&]() {
+    const int64_t band = 32 * (int64_t)f_tile + band_l;
+    f_band_ok = band < mb(f_m).BM;
+    f_ptr = mb(f_m).stream + (band * mb(f_m).BN + 16 * (int64_t)f_st + jl0) * kBlockBytes;
+  };
+  if (n > 0) fetch_at();
   auto fetch = [&](int slot) {
     const int64_t J = 16 * (int64_t)f_st + jl0;
+    const int64_t BN = mb(f_m).BN;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (f_band_ok && J + 4 * u < BN) {
@@ -407,19 +462,27 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
         for (int i = 0; i < NW; ++i) w[slot][u][i] = 0u;  // a zero block: E = 0, scale 0
       }
     }
-    if (++f_st == S) {
-      f_st = 0, ++f_tile;
-      f_band_ok = 32 * (int64_t)f_tile + band_l < BM;
-      f_ptr = stream + ((32 * (int64_t)f_tile + band_l) * BN + jl0) * kBlockBytes;
+    const int m_before = f_m, t_before = f_tile;
+    advance(f_m, f_tile, f_st);
+    if (f_m != m_before || f_tile != t_before) {
+      if (f_m < nmem) fetch_at();
     } else {
       f_ptr += 16 * kBlockBytes;
     }
   };
   auto b_copy = [&](int64_t k) {  // thread 0: B tile of stage k into buffer k % 2
     const int buf = (int)(k & 1);
-    const int64_t st = (it0 + k) % S;
-    bulk_copy_g2s(s_base + 2 * SM::kA + buf * SM::kB, btiles + st * (int64_t)SM::kB, (uint32_t)SM::kB,
-                  b_bar + 8 * buf);
+    if constexpr (TABLE) {
+      int bm = b_cur[0], bt = b_cur[1], bs = b_cur[2];
+      bulk_copy_g2s(s_base + 2 * SM::kA + buf * SM::kB, tab[bm].btiles + (int64_t)bs * SM::kB, (uint32_t)SM::kB,
+                    b_bar + 8 * buf);
+      advance(bm, bt, bs);
+      b_cur[0] = bm, b_cur[1] = bt, b_cur[2] = bs;
+    } else {
+      const int64_t st = (it0 + k) % single.S;
+      bulk_copy_g2s(s_base + 2 * SM::kA + buf * SM::kB, single.btiles + st * (int64_t)SM::kB, (uint32_t)SM::kB,
+                    b_bar + 8 * buf);
+    }
     *last_copy = k;
   };
   auto fail = [&]() {  // a wait ran out: the CTA stops at its next barrier
@@ -430,20 +493,23 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
   float hi[HALF], lo[HALF];
 #pragma unroll
   for (int r = 0; r < HALF; ++r) hi[r] = lo[r] = 0.f;
-  int cur_tile = tile0;  // tile of the sums in hi/lo
+  int cur_m = mem0, cur_tile = tile0;  // member and tile of the sums in hi/lo
   auto flush = [&]() {
-    const int64_t seg = (int64_t)blockIdx.x - ((int64_t)cur_tile * S) / L;
-    double* dst = ws + (((int64_t)cur_tile * maxseg + seg) * R) * 128 + m_row;
+    const MmaMember& me = mb(cur_m);
+    const int64_t seg = (int64_t)blockIdx.x - (me.item_begin + (int64_t)cur_tile * me.S) / L;
+    double* dst = me.ws + (((int64_t)cur_tile * me.maxseg + seg) * me.R) * 128 + m_row;
 #pragma unroll
     for (int r = 0; r < HALF; ++r) {
-      if (c0 + r < R) dst[(int64_t)(c0 + r) * 128] = (double)hi[r] + (double)lo[r];
+      if (c0 + r < me.R) dst[(int64_t)(c0 + r) * 128] = (double)hi[r] + (double)lo[r];
       hi[r] = lo[r] = 0.f;
     }
   };
-  // drain accumulator pair `acc` (big + small), which holds a group of stages of tile `tile`
-  auto drain = [&](int acc, int tile) {
-    if (tile != cur_tile) {
+  // drain accumulator pair `acc` (big + small), which holds a group of stages of
+  // tile `tile` of member `mem`
+  auto drain = [&](int acc, int mem, int tile) {
+    if (mem != cur_m || tile != cur_tile) {
       flush();
+      cur_m = mem;
       cur_tile = tile;
     }
     const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(2 * acc * NR + c0);
@@ -464,7 +530,7 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
   // its last stage's MMAs complete
   int gpos = 0, gacc = 0;
   bool p_ends = false;  // stage k-1 closed its group ...
-  int p_acc = 0, p_tile = tile0;  // ... in accumulator pair p_acc, of tile p_tile
+  int p_acc = 0, p_m = mem0, p_tile = tile0;  // ... in accumulator pair p_acc, of member p_m's tile p_tile
   if (n > 0) {
     fetch(0);
     if (t == 0) b_copy(0);
@@ -498,10 +564,10 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
     // group bookkeeping of stage k (the same in every thread)
     const bool init = gpos == 0;
     const int acc = gacc;
-    const int tile_k = m_tile;
-    const bool ends = ++gpos == kMmaDrainStages || m_st == S - 1 || k == n - 1;
+    const int tile_k = m_tile, mem_k = m_m;
+    const bool ends = ++gpos == kMmaDrainStages || m_st == mb(m_m).S - 1 || k == n - 1;
     if (ends) gpos = 0, gacc ^= 1;
-    if (++m_st == S) m_st = 0, ++m_tile;
+    advance(m_m, m_tile, m_st);
     if (t == 0) {
       if (!mbar_wait(b_bar + 8 * buf, (uint32_t)((k >> 1) & 1))) {
         ok = false;
@@ -546,7 +612,7 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (t == 0 && ok && k + 1 < n) b_copy(k + 1);  // its B tile buffer is free now
-        if (p_ends) drain(p_acc, p_tile);
+        if (p_ends) drain(p_acc, p_m, p_tile);
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       }
     } else if (t == 0 && ok && k + 1 < n) {
@@ -554,6 +620,7 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
     }
     p_ends = ends;
     p_acc = acc;
+    p_m = mem_k;
     p_tile = tile_k;
     return true;
   };
@@ -568,7 +635,7 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
     const int buf = (int)((n - 1) & 1);
     if (__all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * buf, (uint32_t)(((n - 1) >> 1) & 1)))) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      drain(p_acc, p_tile);
+      drain(p_acc, p_m, p_tile);
       flush();
     } else if (lane == 0) {
       fail();
@@ -588,24 +655,27 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
 }
 
 // Sum each band's segment partials in order and map its 4 coefficient rows to
-// y (2G mix and 2^-3 with the lift, 2^3 without).  Thread per (band, column),
-// the band fastest, so a warp reads 32 consecutive partials of one row and
-// writes 32 consecutive 4-row groups of y.
+// y (2G mix and 2^-3 with the lift, 2^3 without).  Thread per (pass, tile,
+// column, band of the tile), the band fastest, so a warp reads 32 consecutive
+// partials of one row and writes 32 consecutive 4-row groups of y.
 template <bool LIFT>
-__global__ void wz2_mma_finish(const double* __restrict__ ws, int64_t S, int64_t L, int maxseg, int R, int64_t M,
-                               double* __restrict__ y, int64_t ldy) {
+__global__ void wz2_mma_finish(MmaPass single, const MmaPass* __restrict__ table, int n, int64_t threads, int64_t L) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int bl = (int)(q & 31);
-  const int64_t tr = q >> 5;  // tile * R + r
-  const int r = (int)(tr % R);
-  const int64_t tile = tr / R;
+  if (q >= threads) return;
+  const MmaPass ps = pass_of<true>(single, table, n, q);
+  const int64_t ql = q - ps.fin_begin;
+  const int bl = (int)(ql & 31);
+  const int64_t tr = ql >> 5;  // tile * R + r
+  const int r = (int)(tr % ps.R);
+  const int64_t tile = tr / ps.R;
   const int64_t I = 32 * tile + bl;
-  if (4 * I >= M) return;
-  const int nseg = (int)(((tile + 1) * S - 1) / L - (tile * S) / L + 1);
+  if (tile >= ps.tiles || 4 * I >= ps.M) return;
+  const int64_t first = ps.item_begin + tile * ps.S;
+  const int nseg = (int)((first + ps.S - 1) / L - first / L + 1);
   double z[4];
   for (int a = 0; a < 4; ++a) {
     double acc = 0.0;
-    for (int g = 0; g < nseg; ++g) acc += ws[((tile * maxseg + g) * R + r) * 128 + 32 * a + bl];
+    for (int g = 0; g < nseg; ++g) acc += ps.ws[((tile * ps.maxseg + g) * ps.R + r) * 128 + 32 * a + bl];
     z[a] = acc;
   }
   double yy[4];
@@ -619,7 +689,7 @@ __global__ void wz2_mma_finish(const double* __restrict__ ws, int64_t S, int64_t
     for (int i = 0; i < 4; ++i) yy[i] = z[i] * 8.0;
   }
   for (int i = 0; i < 4; ++i)
-    if (4 * I + i < M) y[(int64_t)r * ldy + 4 * I + i] = yy[i];
+    if (4 * I + i < ps.M) ps.y[(int64_t)r * ps.ldy + 4 * I + i] = yy[i];
 }
 
 // state <- decay * state + y[:, r] for r = 0..R-1 in order.  Thread per row.

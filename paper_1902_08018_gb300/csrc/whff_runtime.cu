@@ -932,6 +932,23 @@ struct whff_batch {
   int64_t state_rows = 0;
   std::vector<int> R;
   cudaEvent_t copied = nullptr;        // the last step's table copies have been read
+  // Matrices with R at or above their crossover: their passes of up to 32
+  // columns, grouped by width class (16 or 32 TMEM columns), each group one
+  // persistent tensor-core launch over the concatenated items of its passes.
+  struct MmaGroup {
+    int nr = 32;
+    std::vector<int> of, col0;                 // handle index and first column of each pass
+    std::vector<dev::MmaMember> members;       // static, on the device in d_members
+    std::vector<dev::MmaPass> passes;          // vectors rewritten per step
+    dev::MmaMember* d_members = nullptr;
+    dev::MmaPass* d_passes = nullptr;
+    dev::MmaPass* pinned = nullptr;
+    double* ws = nullptr;
+    uint8_t* btiles = nullptr;
+    int64_t total = 0, L = 1, bt_threads = 0, fin_threads = 0;
+    int ctas = 1;
+  };
+  std::vector<MmaGroup> mma_groups;
 };
 
 extern "C" void whff_batch_destroy(whff_batch* b) {
@@ -943,6 +960,13 @@ extern "C" void whff_batch_destroy(whff_batch* b) {
     for (double* w : g.ws) cudaFree(w);
   }
   if (b->copied) cudaEventDestroy(b->copied);
+  for (auto& g : b->mma_groups) {
+    cudaFree(g.d_members);
+    cudaFree(g.d_passes);
+    cudaFreeHost(g.pinned);
+    cudaFree(g.ws);
+    cudaFree(g.btiles);
+  }
   cudaFreeHost(b->pinned);
   cudaFreeHost(b->state_pinned);
   cudaFree(b->d_state);
@@ -1044,6 +1068,101 @@ extern "C" int whff_batch_create(whff_handle* const* hs, const int* R, int count
     b->pinned_entries += n;
   }
   b->R.assign(R, R + count);
+  // tensor-core passes: one group per width class and per kMaxMembers passes
+  for (int nr : {16, 32}) {
+    whff_batch::MmaGroup g;
+    g.nr = nr;
+    auto close = [&]() {
+      if (!g.of.empty()) b->mma_groups.push_back(g);
+      g = whff_batch::MmaGroup();
+      g.nr = nr;
+    };
+    for (int i = 0; i < count; ++i) {
+      if (!(R[i] >= hs[i]->mma_min_rhs && hs[i]->d_ws_mma)) continue;
+      for (int c = 0; c < R[i]; c += 32) {
+        const int rp = std::min(32, R[i] - c);
+        if ((rp <= 16 ? 16 : 32) != nr) continue;
+        if ((int)g.of.size() == mma_max_members()) close();
+        g.of.push_back(i);
+        g.col0.push_back(c);
+      }
+    }
+    close();
+  }
+  for (auto& g : b->mma_groups) {
+    const int n = (int)g.of.size();
+    const size_t kB = (size_t)3 * 4 * g.nr * 16 * 2;  // B tile bytes per stage
+    int64_t items = 0, bt = 0, fin = 0;
+    size_t ws_words = 0, bt_bytes = 0;
+    g.members.resize(n);
+    g.passes.resize(n);
+    for (int k = 0; k < n; ++k) {
+      const whff_handle* h = hs[g.of[k]];
+      const int rp = std::min(32, R[g.of[k]] - g.col0[k]);
+      dev::MmaMember& m = g.members[k];
+      m.stream = h->d_stream;
+      m.BM = h->BM;
+      m.BN = h->BN;
+      m.S = (int)ceil_div(h->BN, 16);
+      m.tiles = (int)ceil_div(h->BM, 32);
+      m.R = rp;
+      m.item_begin = items;
+      items += (int64_t)m.tiles * m.S;
+    }
+    g.total = items;
+    g.L = ceil_div(items, (int64_t)h0->sm_count * std::max(1, h0->mma_occ));
+    g.ctas = (int)ceil_div(items, g.L);
+    std::vector<size_t> ws_off(n), bt_off(n);
+    for (int k = 0; k < n; ++k) {
+      dev::MmaMember& m = g.members[k];
+      m.maxseg = 1;
+      for (int64_t tl = 0; tl < m.tiles; ++tl) {
+        const int64_t first = m.item_begin + tl * m.S;
+        m.maxseg = std::max<int>(m.maxseg, (int)((first + m.S - 1) / g.L - first / g.L + 1));
+      }
+      ws_off[k] = ws_words;
+      ws_words += (size_t)m.tiles * m.maxseg * m.R * 128;
+      bt_off[k] = bt_bytes;
+      bt_bytes += (size_t)m.S * kB;
+      dev::MmaPass& ps = g.passes[k];
+      ps = dev::MmaPass{};
+      ps.N = hs[g.of[k]]->info.N;
+      ps.M = hs[g.of[k]]->info.M;
+      ps.item_begin = m.item_begin;
+      ps.bt_begin = bt;
+      ps.fin_begin = fin;
+      ps.S = m.S;
+      ps.tiles = m.tiles;
+      ps.R = m.R;
+      ps.maxseg = m.maxseg;
+      bt += (int64_t)m.S * 16 * g.nr;
+      fin += (int64_t)m.tiles * m.R * 32;
+    }
+    g.bt_threads = bt;
+    g.fin_threads = fin;
+    if (cudaMalloc(&g.ws, ws_words * 8) != cudaSuccess || cudaMalloc(&g.btiles, bt_bytes) != cudaSuccess ||
+        cudaMalloc(&g.d_members, sizeof(dev::MmaMember) * n) != cudaSuccess ||
+        cudaMalloc(&g.d_passes, sizeof(dev::MmaPass) * n) != cudaSuccess ||
+        cudaMallocHost(&g.pinned, sizeof(dev::MmaPass) * n) != cudaSuccess) {
+      cudaGetLastError();
+      whff_batch_destroy(b);
+      set_error("whff_batch_create: tensor-core workspace allocation failed");
+      return WHFF_ENOMEM;
+    }
+    for (int k = 0; k < n; ++k) {
+      g.members[k].ws = g.ws + ws_off[k];
+      g.members[k].btiles = g.btiles + bt_off[k];
+      g.passes[k].ws = g.members[k].ws;
+      g.passes[k].btiles = g.btiles + bt_off[k];
+    }
+    if (cudaMemcpy(g.d_members, g.members.data(), sizeof(dev::MmaMember) * n, cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      whff_batch_destroy(b);
+      set_error("whff_batch_create: tensor-core table upload failed");
+      return WHFF_ECUDA;
+    }
+  }
   std::vector<int64_t> srows(count);
   for (int i = 0; i < count; ++i) {
     srows[i] = b->state_rows;
@@ -1082,13 +1201,26 @@ extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64
   const cudaStream_t st = as_stream(stream);
   // the pinned tables are reused: wait until the previous step's copies ran
   WHFF_CUDA_TRY(cudaEventSynchronize(b->copied));
-  // matrices with many right-hand sides: tensor-core passes of their own (their state is
-  // applied with everyone else's by the batch's state pass at the end)
-  for (size_t i = 0; i < b->hs.size(); ++i) {
-    whff_handle* h = b->hs[i];
-    if (b->R[i] >= h->mma_min_rhs && h->d_ws_mma) {
-      int e = whff_step(h, x[i], b->R[i], ldx[i], y[i], ldy[i], nullptr, decay, stream);
-      if (e) return e;
+  // matrices with many right-hand sides: one persistent tensor-core launch per width class
+  // (their states are applied with everyone else's by the batch's state pass at the end)
+  for (auto& g : b->mma_groups) {
+    const int n = (int)g.of.size();
+    for (int k = 0; k < n; ++k) {
+      const int i = g.of[k];
+      dev::MmaPass ps = g.passes[k];
+      ps.x = x[i] + (int64_t)g.col0[k] * ldx[i];
+      ps.y = y[i] + (int64_t)g.col0[k] * ldy[i];
+      ps.ldx = ldx[i];
+      ps.ldy = ldy[i];
+      g.pinned[k] = ps;
+    }
+    WHFF_CUDA_TRY(cudaMemcpyAsync(g.d_passes, g.pinned, sizeof(dev::MmaPass) * n, cudaMemcpyHostToDevice, st));
+    const whff_handle* h0 = b->hs[g.of[0]];
+    MmaBatchStep a{b->rate, b->lift, g.nr, g.d_members, g.d_passes, n, g.total, g.L, g.ctas, g.bt_threads,
+                   g.fin_threads, h0->d_status};
+    if (mma_batch_launch(a, st)) {
+      set_error("whff_batch_step: tensor-core launch failed");
+      return WHFF_ECUDA;
     }
   }
   size_t off = 0;

@@ -31,5 +31,30 @@ struct BatchState {
   double decay;
 };
 
+// One matrix of a tensor-core launch: a pass of up to NR columns over its
+// (tile of 32 bands, stage of 16 blocks) items, which occupy
+// [item_begin, item_begin + tiles * S) of the launch's item sequence.
+struct MmaMember {
+  const uint8_t* stream;  // compressed stream (WZ2 blocks, band-major)
+  const uint8_t* btiles;  // the pass's B tiles, one per stage
+  double* ws;             // FP64 segment partials: tiles x maxseg x R x 128
+  int64_t BM, BN;         // block grid
+  int64_t item_begin;
+  int S, tiles, R, maxseg;  // stages per tile, tiles, columns of the pass, segments per tile
+};
+
+// The vectors of one tensor-core pass (rewritten every step): B tiles are
+// built from x, the finish writes y.  bt_begin / fin_begin: the member's first
+// thread in the launch-wide B-tile and finish grids.
+struct MmaPass {
+  const float* x;
+  double* y;
+  uint8_t* btiles;
+  const double* ws;
+  int64_t ldx, ldy, N, M;
+  int64_t item_begin, bt_begin, fin_begin;
+  int S, tiles, R, maxseg;
+};
+
 }  // namespace dev
 }  // namespace whff

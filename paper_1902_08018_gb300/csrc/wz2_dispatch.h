@@ -88,6 +88,23 @@ struct MmaStep {
   int* status;
 };
 int mma_launch(const MmaStep& a, cudaStream_t st);
+
+// The tensor-core passes of a batch that share one width class (NR 16 or 32),
+// in one persistent launch (mma.cu).  members / passes: device tables.
+struct MmaBatchStep {
+  int rate;
+  bool lift;
+  int nr;
+  const dev::MmaMember* members;
+  const dev::MmaPass* passes;
+  int nmem;
+  int64_t total, L;  // items of all members, items per CTA
+  int ctas;
+  int64_t bt_threads, fin_threads;
+  int* status;
+};
+int mma_batch_launch(const MmaBatchStep& a, cudaStream_t st);
+int mma_max_members();  // most members of one batched launch
 // resident CTAs per SM of the tensor-core kernel at this rate for R <= nr (0 on error)
 int mma_occupancy(int rate, bool lift, int nr);
 int scaled_occupancy(int fmt);

@@ -117,3 +117,41 @@ def test_tuner_keeps_results(env, orc, tmp_path):
         rec2 = h2.tune(iters=3, cache=cache)
         assert rec2["cached"] and rec2["unroll"] == rec["unroll"]
         assert h2.config() == (rec["unroll"], rec["ctas_per_sm"], rec["fold"])
+
+
+def test_batch_tensor_core_groups_match_oracle(env, orc):
+    """Matrices with R at or above the crossover share one persistent
+    tensor-core launch per width class; CTA ranges cross from one matrix to
+    the next, and a matrix with R = 40 has passes in both classes."""
+    W, torch = env
+    shapes = [(1000, 2200), (3100, 900), (260, 5000), (2048, 2048), (700, 1300)]
+    Rs = [5, 16, 20, 40, 32]
+    rng = np.random.default_rng(77)
+    handles, blobs, X, Y, S = [], [], [], [], []
+    for k, ((M, N), R) in enumerate(zip(shapes, Rs)):
+        blob = W.whff_compress(_matrix(M, N, 200 + k), 5, 16)
+        blobs.append(blob)
+        handles.append(W.whff_create(blob, max_rhs=64))
+        X.append(torch.from_numpy(rng.standard_normal((R, N)).astype(np.float32)).cuda())
+        Y.append(torch.zeros((R, M), dtype=torch.float64, device="cuda"))
+        S.append(torch.full((M,), -0.5, dtype=torch.float64, device="cuda"))
+    with W.Batch(handles, Rs) as b:
+        b.step(X, Y, S, decay=0.95)
+        torch.cuda.synchronize()
+        for h in handles:
+            assert h.sync_status() == 0
+        for k, (M, N) in enumerate(shapes):
+            Ahat = orc.decode(blobs[k].tobytes())
+            ref = orc.gemv64(Ahat, X[k].cpu().numpy().T.astype(np.float64))
+            Yk = Y[k].cpu().numpy()
+            for r in range(Rs[k]):
+                assert _rel(Yk[r], ref[:, r]) <= TOL, (k, r)
+            s_ref = orc.state_update(np.full(M, -0.5), ref, 0.95)
+            assert _rel(S[k].cpu().numpy(), s_ref) <= TOL, k
+        Y2 = [torch.zeros_like(y) for y in Y]
+        b.step(X, Y2, None)
+        torch.cuda.synchronize()
+        for k in range(len(shapes)):
+            assert torch.equal(Y2[k], Y[k])
+    for h in handles:
+        h.destroy()
