@@ -78,6 +78,8 @@ def parse_args():
     p.add_argument("--shapes-fmts", default="fp32:0,wz2-lift:16,wz2-lift:12,wz1:16,bf16:0")
     p.add_argument("--batched", action="store_true", help="run the batched uneven-instances workload")
     p.add_argument("--batched-fmt", default="wz2-lift:12")
+    p.add_argument("--batched-crossover", type=int, default=0,
+                   help="fewest columns of a tensor-core pass for the batch's handles (0: their default)")
     return p.parse_args()
 
 
@@ -617,6 +619,8 @@ def run_batched(args, rank, world, local_rank):
         km = workloads.instance_matrix(N)
         blob = W.whff_compress_bands(N, N, km.bands(2048), fmt, rate)
         handles.append(W.whff_create(blob, max_rhs=32))
+        if args.batched_crossover:
+            handles[-1].crossover = args.batched_crossover
         sizes.append(blob.size - 64)
     setup_s = time.perf_counter() - t0
     rng = np.random.default_rng(4)
@@ -661,6 +665,7 @@ def run_batched(args, rank, world, local_rank):
             streamed += sz * (R // 8 + bin(R % 8).count("1"))
     peak, peak_kind = measured_peaks()
     flops = sum(R * N * (2 * N - 1) for N, R in inst)
+    xover = handles[0].crossover
     for h in handles:
         h.destroy()
     return {
@@ -669,7 +674,8 @@ def run_batched(args, rank, world, local_rank):
         "higher_is_better": True, "n_gpus": world, "steps": steps,
         "config": {"workload": f"batched-64-uneven-{fmt_name}-{rate}", "instances": len(inst),
                    "orders_min_max": [min(n for n, _ in inst), max(n for n, _ in inst)],
-                   "R_counts": {str(r): Rs.count(r) for r in sorted(set(Rs))}},
+                   "R_counts": {str(r): Rs.count(r) for r in sorted(set(Rs))},
+                   "crossover": xover},
         "ms_per_step": round(batch_ms, 4), "compressed_bytes": once, "bytes_streamed_per_step": streamed,
         "streamed_GB_s": round(streamed / (batch_ms * 1e-3) / 1e9, 1),
         "pct_hbm_peak_streamed": round(100 * streamed / (batch_ms * 1e-3) / 1e9 / peak, 2), "peak_kind": peak_kind,

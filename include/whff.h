@@ -136,7 +136,7 @@ int whff_plan(const whff_handle* h, int* ksplit, int* launches);
 
 /* One control step (Sec. 2.1 / Sec. 4.4): y[:,r] = Ahat * x[:,r] for r < R,
  * taken in passes: with a WZ2 matrix whose handle allows max_rhs >= 2, passes
- * of crossover..32 columns (default crossover 5, see whff_set_crossover) run
+ * of crossover..32 columns (default crossover 4, see whff_set_crossover) run
  * on the tensor cores (tcgen05: the stored coefficients split exactly into
  * 1-3 BF16 pieces by field width and the transformed x into three, the
  * piece products above 2^-24 accumulate in FP32 TMEM, drained every 64
@@ -217,7 +217,9 @@ void whff_graph_destroy(whff_graph* g);
  * change its rounding within the bar.
  * whff_tune times every candidate on the resident matrix (iters steps each,
  * R = 1, CUDA events on the stream) and keeps the fastest; *best_ms (optional)
- * receives its step time.  whff_get_config / whff_set_config read and apply a
+ * receives its step time.  With tensor-core passes available it then sets
+ * the engine crossover: the fewest columns (2..8) for which one tensor-core
+ * pass is no slower than the CUDA-core passes, else 9.  whff_get_config / whff_set_config read and apply a
  * shape (e.g. from a cache keyed by format, rate, shape and SM count).  WZ2
  * handles only (WHFF_EINVAL otherwise). */
 #define WHFF_FOLD_FP32_PAIRS 1
@@ -228,8 +230,9 @@ int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int fold);
 
 /* Crossover of the two engines (Sec. 4.4's GEMV with many right-hand sides is
  * a GEMM): passes of at least min_rhs columns run on the tensor cores, smaller
- * ones on the CUDA cores.  Default 5 (from 5 columns on, one tensor-core
- * pass is faster than the CUDA cores on GB300); 33 = CUDA cores only.  Tensor-core
+ * ones on the CUDA cores.  Default 4 (from 4 columns on, one tensor-core
+ * pass is at least as fast as the CUDA cores on GB300; whff_tune measures it
+ * per matrix); 33 = CUDA cores only.  Tensor-core
  * passes need a WZ2 handle created with max_rhs >= 2 (WHFF_EINVAL otherwise,
  * unless min_rhs = 33); whff_get_crossover reports 33 for handles without
  * them.  Both engines meet the same accuracy bar; their roundings differ. */

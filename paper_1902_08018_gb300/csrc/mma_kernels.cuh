@@ -1,7 +1,7 @@
 // mma_kernels.cuh -- many right-hand sides on the 5th-generation tensor cores.
 //
 // With R right-hand sides the step Y = A X is a dense contraction (Sec. 4.4's
-// GEMV becomes a GEMM), so for R >= 5 (the default crossover) the WZ2 kernels run
+// GEMV becomes a GEMM), so for R >= 4 (the default crossover) the WZ2 kernels run
 // it on tcgen05.  In the transform domain the contraction is
 //     Z_band = sum_J (s_J V_J) ((2G)^T X_J),   Y_band = (2G) Z_band * 2^-3,
 // a GEMM whose A operand is the stored integer coefficients times a

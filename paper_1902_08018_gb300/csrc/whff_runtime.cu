@@ -59,7 +59,7 @@ struct whff_handle {
   int64_t mma_L = 0;            // (tile, stage) items per CTA of the persistent tensor-core grid
   int mma_ctas = 0;
   int mma_maxseg = 1;
-  int mma_min_rhs = 5;          // passes of at least this many columns use tcgen05 (whff_set_crossover)
+  int mma_min_rhs = 4;          // passes of at least this many columns use tcgen05 (whff_set_crossover, whff_tune)
   int mma_occ = 0;              // resident tensor-core CTAs per SM
   size_t ws_mma_cap = 0;        // bytes of d_ws_mma
   const float* d_scales = nullptr;  // scaled formats: the tile scales after the payload
@@ -904,7 +904,40 @@ extern "C" int whff_tune(whff_handle* h, int iters, void* stream, double* best_m
     return err;
   }
   if (best_ms) *best_ms = best;
-  return apply_config(h, bu, bc, bf);
+  if ((err = apply_config(h, bu, bc, bf)) != WHFF_OK) return err;
+  // the engine crossover: the fewest columns from which one tensor-core pass is
+  // no slower than the CUDA-core passes (it only grows with R on the CUDA cores)
+  if (h->d_ws_mma && h->max_rhs >= 2) {
+    WHFF_CUDA_TRY(cudaMemsetAsync(h->d_x, 0, (size_t)h->info.N * 4 * std::min(h->max_rhs, 8), st));
+    WHFF_CUDA_TRY(cudaEventCreate(&e0));
+    WHFF_CUDA_TRY(cudaEventCreate(&e1));
+    auto time_r = [&](int R, int cross, double* ms) {
+      h->mma_min_rhs = cross;
+      int e = whff_step(h, h->d_x, R, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream);
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < iters && e == WHFF_OK; ++k)
+        e = whff_step(h, h->d_x, R, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream);
+      cudaEventRecord(e1, st);
+      if (e == WHFF_OK && cudaEventSynchronize(e1) != cudaSuccess) e = WHFF_ECUDA;
+      float f = 0.f;
+      cudaEventElapsedTime(&f, e0, e1);
+      *ms = f;
+      return e;
+    };
+    int cross = 9;  // from 9 columns on the tensor cores always win
+    for (int R = 2; R <= std::min(h->max_rhs, 8) && err == WHFF_OK; ++R) {
+      double cc = 0, tc = 0;
+      if ((err = time_r(R, 33, &cc)) != WHFF_OK || (err = time_r(R, 2, &tc)) != WHFF_OK) break;
+      if (tc <= cc) {
+        cross = R;
+        break;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->mma_min_rhs = cross;
+  }
+  return err;
 }
 
 // ------------------------------------------------------------------ batches

@@ -196,11 +196,13 @@ class Handle:
                 db = json.load(f)
         if key in db:
             self.set_config(db[key]["unroll"], db[key]["ctas_per_sm"], db[key].get("fold", 0))
+            if "crossover" in db[key] and (self.crossover < 33 or db[key]["crossover"] == 33):
+                self.crossover = db[key]["crossover"]
             return dict(db[key], cached=True)
         ms = ctypes.c_double()
         _check(library().whff_tune(self._ptr, iters, _stream_ptr(stream), ctypes.byref(ms)))
         u, c, f = self.config()
-        rec = {"unroll": u, "ctas_per_sm": c, "fold": f, "ms": ms.value}
+        rec = {"unroll": u, "ctas_per_sm": c, "fold": f, "crossover": self.crossover, "ms": ms.value}
         if cache:
             db[key] = rec
             os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)

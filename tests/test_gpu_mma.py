@@ -1,7 +1,7 @@
 """Tensor-core (tcgen05) passes for many right-hand sides on WZ2 matrices,
 through the C ABI: every column within relative L2 1e-6 of the FP64 oracle
 GEMV on the decoded matrix, for ragged shapes, split columns and R that mixes
-tensor-core (>= 5 columns by default) and CUDA-core passes; the carried state follows
+tensor-core (>= 4 columns by default) and CUDA-core passes; the carried state follows
 the oracle recursion in column order."""
 import numpy as np
 import pytest
@@ -78,7 +78,7 @@ def test_low_crossover_matches_oracle(env, orc, R):
     X = np.random.default_rng(R + 100).standard_normal((R, N)).astype(np.float32)
     ref = orc.gemv64(Ahat, X.T.astype(np.float64))
     with W.whff_create(blob, max_rhs=8) as h:
-        assert h.crossover == 5
+        assert h.crossover == 4
         h.crossover = 2
         assert h.crossover == 2
         x = torch.from_numpy(X).cuda()

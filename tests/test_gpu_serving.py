@@ -86,8 +86,8 @@ def test_host_graph_replay(env):
                 xh.numpy()[:] = X
                 g.launch()
                 torch.cuda.synchronize()
-                for r in range(4):
-                    assert (yh.numpy()[r] == _step_alone(W, torch, h, X[r])).all()
+                for r in range(4):  # a 4-column pass may run on the tensor cores
+                    assert _same_as_alone(yh.numpy()[r], _step_alone(W, torch, h, X[r]), 4, h)
 
 
 def test_server_batches_give_the_results_of_single_service(env, orc):
