@@ -65,6 +65,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-baseline", action="store_true")
     p.add_argument("--no-host-resident", action="store_true", help="skip the matrix-over-the-link leg")
+    p.add_argument("--no-tune", action="store_true", help="time the default launch shape instead of whff_tune's")
     p.add_argument("--json-out", default=None)
     p.add_argument("--serve", action="store_true", help="run the serving workload instead of the control loop")
     p.add_argument("--serve-fmt", default="wz2-lift:8")
@@ -303,6 +304,9 @@ def run_whff(args, rank, world, local_rank):
     # ---------------- headline format: the timed control loop
     h = W.whff_create(blobs[head], max_rhs=1)
     stream_bytes = blobs[head].size - 64
+    tuned = None
+    if not args.no_tune and head[0] in (5, 6):  # the library's tuner picks the launch shape on this machine
+        tuned = h.tune(iters=10, stream=stream)
     ksplit, launches = h.plan()
     if world > 1:
         torch.distributed.barrier()
@@ -475,6 +479,8 @@ def run_whff(args, rank, world, local_rank):
         "config": {"workload": f"control-loop-{order}-rate{head[1]}", "M": order, "N": order,
                    "fmt": head_name, "rate_bits_per_value": head[1], "R": 1, "state": "FP64 s <- 0.99 s + y",
                    "compressed_bytes_per_step": int(stream_bytes), "ksplit": ksplit,
+                   "launch_shape": ({k: tuned[k] for k in ("unroll", "ctas_per_sm", "fold")} if tuned
+                                    else "default"),
                    "l2": "inputs larger than L2 (the compressed matrix, >1 GB, is streamed every step)",
                    "parallelism": f"replicas{world}"},
         "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
