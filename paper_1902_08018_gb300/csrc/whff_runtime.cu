@@ -55,6 +55,7 @@ struct whff_handle {
   int ws_rhs = 8;               // right-hand sides the workspace is sized for
   double* d_ws_mma = nullptr;   // WZ2 tensor-core passes: tiles x maxseg x 32 x 128 partials
   uint8_t* d_btiles = nullptr;  // WZ2 tensor-core passes: B operand pieces per stage
+  float* d_xt = nullptr;        // WZ2 lift: (2G)^T x of a CUDA-core pass, 4 BN floats x 8 columns
   size_t ws_mma_bytes = 0;
   int64_t mma_L = 0;            // (tile, stage) items per CTA of the persistent tensor-core grid
   int mma_ctas = 0;
@@ -191,7 +192,7 @@ int launch_wz2(const whff_handle* h, const float* x, int R, int64_t ldx, bool ve
                double* state, double decay, cudaStream_t st) {
   Wz2Step a{h->d_stream, h->info.M, h->info.N, h->BM, h->BN, x, ldx, vec, h->range_len, h->maxseg, h->d_ws,
             y, ldy, state, decay, h->range_ctas, R == 1 ? h->unroll : 2, h->info.fmt == WHFF_FMT_FIXED_LIFT, R,
-            h->red32, h->groups8};
+            h->red32, h->groups8, h->d_xt};
   int e;
   switch (h->info.rate) {
     case 8: e = wz2_launch<8>(a, st); break;
@@ -365,7 +366,9 @@ extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigne
       return fail(WHFF_ENOMEM);
     }
   }
-  if ((h->ws_bytes && cudaMalloc(&h->d_ws, h->ws_bytes) != cudaSuccess) ||
+  if ((info.fmt == WHFF_FMT_FIXED_LIFT &&
+       cudaMalloc(&h->d_xt, (size_t)4 * h->BN * std::min(max_rhs, kMaxRhsKernel) * sizeof(float)) != cudaSuccess) ||
+      (h->ws_bytes && cudaMalloc(&h->d_ws, h->ws_bytes) != cudaSuccess) ||
       cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->d_x, (size_t)info.N * (size_t)max_rhs * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&h->d_y, (size_t)info.M * (size_t)max_rhs * sizeof(double)) != cudaSuccess) {
@@ -398,7 +401,8 @@ extern "C" int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, 
   if (N) *N = h->info.N;
   if (device_bytes)
     *device_bytes = (h->h_stream ? 0 : h->info.stream_bytes) + h->ws_bytes + h->ws_mma_bytes + sizeof(int) +
-                    (size_t)h->info.N * h->max_rhs * 4 + (size_t)h->info.M * h->max_rhs * 8;
+                    (size_t)h->info.N * h->max_rhs * 4 + (size_t)h->info.M * h->max_rhs * 8 +
+                    (h->d_xt ? (size_t)4 * h->BN * std::min(h->max_rhs, kMaxRhsKernel) * sizeof(float) : 0);
   return WHFF_OK;
 }
 
@@ -776,6 +780,7 @@ extern "C" void whff_destroy(whff_handle* h) {
   cudaFree(h->d_ws);
   cudaFree(h->d_ws_mma);
   cudaFree(h->d_btiles);
+  cudaFree(h->d_xt);
   cudaFree(h->d_status);
   cudaFree(h->d_x);
   cudaFree(h->d_y);

@@ -41,7 +41,16 @@ static int wz2_launch_lift(const Wz2Step& a, cudaStream_t st) {
 
 template <int RATE>
 int wz2_launch(const Wz2Step& a, cudaStream_t st) {
-  return a.lift ? wz2_launch_lift<RATE, true>(a, st) : wz2_launch_lift<RATE, false>(a, st);
+  if (!a.lift) return wz2_launch_lift<RATE, false>(a, st);
+  // the lift: transform x once per pass, then the kernels read (2G)^T x as their x
+  const int64_t ldt = 4 * a.BN, n = (int64_t)a.R * a.BN;
+  dev::wz2_xt_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.x, a.ldx, a.N, a.R, a.BN, a.xt, ldt);
+  Wz2Step b = a;
+  b.x = a.xt;
+  b.ldx = ldt;
+  b.N = ldt;
+  b.x_vec_ok = true;
+  return wz2_launch_lift<RATE, true>(b, st);
 }
 
 template <int RATE, bool LIFT, int R>

@@ -28,6 +28,7 @@ struct Wz2Step {
   int R;           // 1, 2, 4 or 8
   bool red32;      // fold lanes with the FP32 pair butterfly (short bands)
   bool groups8;    // four 8-lane groups per warp, one band each (short bands)
+  float* xt;       // lift: scratch for (2G)^T x, 4 BN floats per right-hand side (8 columns)
 };
 
 

@@ -185,7 +185,9 @@ __device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float 
                                    active);
 }
 
-template <int RATE, bool LIFT, int R>
+// PRE: x already holds (2G)^T x per 4-column chunk (wz2_xt_kernel), so the
+// lift's transform of x is not repeated per block.
+template <int RATE, bool LIFT, int R, bool PRE = false>
 __device__ __forceinline__ void wz2_block_partial(const uint32_t (&w)[Wz2Layout<RATE>::kWords],
                                                   const float* __restrict__ x, int64_t ldx, int64_t c0, int64_t N,
                                                   bool x_fast, bool x_vec_ok, float (&p)[4][R]) {
@@ -201,7 +203,7 @@ __device__ __forceinline__ void wz2_block_partial(const uint32_t (&w)[Wz2Layout<
     const float4 xv = x_fast ? __ldg(reinterpret_cast<const float4*>(x + (int64_t)r * ldx + c0))
                              : load_x4(x, ldx, r, c0, N, x_vec_ok);
     float xt[4];
-    if (LIFT) {  // (2G)^T x
+    if (LIFT && !PRE) {  // (2G)^T x
       const float a = xv.x + xv.y, b = xv.z + xv.w, c = xv.x + xv.z, d = xv.y + xv.w;
       xt[0] = 2.f * (a + b);
       xt[1] = b - a;
@@ -231,7 +233,7 @@ __device__ __forceinline__ void wz2_block_partial(const uint32_t (&w)[Wz2Layout<
 // last block enters alone.  So every right-hand side gets the same rounding
 // whatever R, UNROLL or the batch it is in.  UNROLL (2 or 4) blocks per lane
 // are kept in flight: their loads are issued before any is decoded.
-template <int RATE, bool LIFT, int R, int UNROLL, int STRIDE = 32>
+template <int RATE, bool LIFT, int R, int UNROLL, int STRIDE = 32, bool PRE = false>
 __device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int64_t J0, int64_t J1, int lane,
                                           const float* __restrict__ x, int64_t ldx, int64_t N, bool x_fast,
                                           bool x_vec_ok, float (&hi)[4][R], float (&lo)[4][R]) {
@@ -245,8 +247,8 @@ __device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int6
 #pragma unroll
     for (int u = 0; u < UNROLL; u += 2) {
       float p0[4][R], p1[4][R];
-      wz2_block_partial<RATE, LIFT, R>(w[u], x, ldx, 4 * (J + STRIDE * u), N, x_fast, x_vec_ok, p0);
-      wz2_block_partial<RATE, LIFT, R>(w[u + 1], x, ldx, 4 * (J + STRIDE * (u + 1)), N, x_fast, x_vec_ok, p1);
+      wz2_block_partial<RATE, LIFT, R, PRE>(w[u], x, ldx, 4 * (J + STRIDE * u), N, x_fast, x_vec_ok, p0);
+      wz2_block_partial<RATE, LIFT, R, PRE>(w[u + 1], x, ldx, 4 * (J + STRIDE * (u + 1)), N, x_fast, x_vec_ok, p1);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -258,8 +260,8 @@ __device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int6
     wz2_load<RATE>(base, J, w0);
     wz2_load<RATE>(base, J + STRIDE, w1);
     float p0[4][R], p1[4][R];
-    wz2_block_partial<RATE, LIFT, R>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
-    wz2_block_partial<RATE, LIFT, R>(w1, x, ldx, 4 * (J + STRIDE), N, x_fast, x_vec_ok, p1);
+    wz2_block_partial<RATE, LIFT, R, PRE>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
+    wz2_block_partial<RATE, LIFT, R, PRE>(w1, x, ldx, 4 * (J + STRIDE), N, x_fast, x_vec_ok, p1);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -269,12 +271,28 @@ __device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int6
     uint32_t w0[NW];
     wz2_load<RATE>(base, J, w0);
     float p0[4][R];
-    wz2_block_partial<RATE, LIFT, R>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
+    wz2_block_partial<RATE, LIFT, R, PRE>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r]);
   }
+}
+
+// (2G)^T x_J for every 4-column chunk J and right-hand side r, once per pass:
+// xt[r * ldt + 4J + i], the same FP32 operations in the same order as the
+// per-block transform, so the results do not change.  Thread per (r, J).
+static __global__ void wz2_xt_kernel(const float* __restrict__ x, int64_t ldx, int64_t N, int R, int64_t BN,
+                                     float* __restrict__ xt, int64_t ldt) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)R * BN) return;
+  const int r = (int)(q / BN);
+  const int64_t J = q - (int64_t)r * BN;
+  float xv[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) xv[c] = 4 * J + c < N ? x[(int64_t)r * ldx + 4 * J + c] : 0.f;
+  const float a = xv[0] + xv[1], b = xv[2] + xv[3], c = xv[0] + xv[2], d = xv[1] + xv[3];
+  *reinterpret_cast<float4*>(xt + (int64_t)r * ldt + 4 * J) = make_float4(2.f * (a + b), b - a, d - c, xv[3] - xv[2]);
 }
 
 // Persistent kernel with exact balance: the G warps of the grid split the
@@ -285,7 +303,8 @@ __device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int6
 // to ws[band][segment] for wz2_segment_epilogue, which adds a band's segments
 // in order.  GL = 32: the warp takes one piece at a time; GL = 8: four lane
 // groups take the next four pieces at once (short bands, where a warp per
-// band would spend its time folding).
+// band would spend its time folding).  With the lift, x is the transformed
+// vector of wz2_xt_kernel (4 BN floats per right-hand side).
 template <int RATE, bool LIFT, int R, int UNROLL, int GL>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
     wz2_gemv_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BM, int64_t BN,
@@ -311,8 +330,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       const int64_t I = b0 / BN;
       const int64_t piece_end = min(b1, (I + 1) * BN);
       const int64_t g_lo = (I * BN) / L, g_hi = ((I + 1) * BN - 1) / L;
-      wz2_piece<RATE, LIFT, R, UNROLL>(stream + (uint64_t)(I * BN) * kBlockBytes, b0 - I * BN, piece_end - I * BN,
-                                       lane, x, ldx, N, x_fast, x_vec_ok, hi, lo);
+      wz2_piece<RATE, LIFT, R, UNROLL, 32, LIFT>(stream + (uint64_t)(I * BN) * kBlockBytes, b0 - I * BN,
+                                                 piece_end - I * BN, lane, x, ldx, N, x_fast, x_vec_ok, hi, lo);
       if (g_lo == g_hi) {  // the whole band is in this range: finish it here
         wz2_finish<LIFT, R>(hi, lo, lane, 4 * I, M, 0, 1, 4 * BM, ws, y, ldy, state, decay, red32);
       } else {  // one segment of a shared band: ws[(band * maxseg + seg) * R + r][i]
@@ -326,8 +345,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       const bool active = pb < pe;
       const int64_t g_lo = (I * BN) / L, g_hi = ((I + 1) * BN - 1) / L;
       if (active)
-        wz2_piece<RATE, LIFT, R, UNROLL, GL>(stream + (uint64_t)(I * BN) * kBlockBytes, pb - I * BN, pe - I * BN,
-                                             gl, x, ldx, N, x_fast, x_vec_ok, hi, lo);
+        wz2_piece<RATE, LIFT, R, UNROLL, GL, LIFT>(stream + (uint64_t)(I * BN) * kBlockBytes, pb - I * BN,
+                                                   pe - I * BN, gl, x, ldx, N, x_fast, x_vec_ok, hi, lo);
       // one call for all groups (the folds shuffle across the whole warp)
       const bool whole = g_lo == g_hi;
       wz2_finish<LIFT, R, GL>(hi, lo, gl, whole ? 4 * I : 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, whole ? 1 : 2,
