@@ -131,7 +131,9 @@ int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, int64_t* N,
 
 /* Launch plan of a resident matrix: *ksplit = column splits per 4-row band
  * (1 for matrices with enough rows to fill the GPU), *launches = kernel
- * launches of one whff_step pass (1, or 2 with the split-K epilogue). */
+ * launches of one CUDA-core whff_step pass: the fused kernel, the epilogue of
+ * shared bands or split-K if any, and for FIXED_LIFT the (2G)^T x transform of
+ * x that the fused kernel reads. */
 int whff_plan(const whff_handle* h, int* ksplit, int* launches);
 
 /* One control step (Sec. 2.1 / Sec. 4.4): y[:,r] = Ahat * x[:,r] for r < R,

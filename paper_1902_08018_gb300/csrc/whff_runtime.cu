@@ -429,7 +429,8 @@ extern "C" int whff_plan(const whff_handle* h, int* ksplit, int* launches) {
     return WHFF_EINVAL;
   }
   if (ksplit) *ksplit = h->ksplit;
-  if (launches) *launches = (h->ksplit > 1 || h->maxseg > 1) ? 2 : 1;
+  if (launches)
+    *launches = ((h->ksplit > 1 || h->maxseg > 1) ? 2 : 1) + (h->info.fmt == WHFF_FMT_FIXED_LIFT ? 1 : 0);
   return WHFF_OK;
 }
 
