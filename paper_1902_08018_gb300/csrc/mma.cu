@@ -123,7 +123,7 @@ static int mma_occ_one() {
   const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
   const int by_regs = regs_sm / (regs_warp * warps);
   const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + reserved);
-  const int by_tmem = 512 / (4 * NR);
+  const int by_tmem = 512 / (int)dev::mma_tmem_cols<NR>();
   return std::min(std::min(by_regs, by_smem), by_tmem);
 }
 

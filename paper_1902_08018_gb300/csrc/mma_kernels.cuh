@@ -13,11 +13,14 @@
 // BF16 pieces (8+8+8 bits, exact).  The products A_p B_q with p+q <= 2 are
 // issued (kind::f16, BF16 in, FP32 accumulate in TMEM); the dropped ones are
 // below 2^-24 of |a||x|.  The tensor cores' FP32 accumulate is not a
-// round-to-nearest sum, so A_0 B_0 goes to its own accumulator and the cross
-// products, about 2^-8 smaller, to a second one: only a few additions happen
-// at full magnitude.  Both cover at most kMmaDrainStages stages of one tile
-// (16 blocks = 64 columns of K each) and are then added and drained into
-// TwoSum FP32 registers, so FP32 rounding never sees long sums.
+// round-to-nearest sum, so the products go to three accumulators by size:
+// A_0 B_0; the 2^-8 terms A_0 B_1 + A_1 B_0; the 2^-16 terms A_0 B_2 + A_1 B_1
+// + A_2 B_0.  With the B pieces side by side along N, one instruction
+// A_p [B_0 .. B_{2-p}] (N = (3-p) NR) writes accumulators p..2, so a K step
+// takes PA instructions.  The accumulators cover at most kMmaDrainStages
+// stages of one tile (16 blocks = 64 columns of K each) and are then added
+// and drained into TwoSum FP32 registers, so FP32 rounding never sees long
+// sums.
 //
 // CTA = 8 warps = 256 threads, persistent: the grid splits the sequence of
 // (tile, stage) items -- tile = 32 bands = 128 coefficient rows, stage = 16
@@ -62,9 +65,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 
 // Instruction descriptor, kind::f16: F32 accumulator (bits 4-5 = 1), A and B
 // BF16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24.
-template <int NR>
-__device__ __forceinline__ constexpr uint32_t mma_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+__device__ __forceinline__ constexpr uint32_t mma_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 // Byte offset of element (row, k) in a 16-wide K-step tile (no swizzle,
@@ -90,15 +92,22 @@ template <int RATE>
 struct MmaPieces {
   static constexpr int kBits = Wz2Layout<RATE>::kW - 1;
   static constexpr int kA = kBits <= 8 ? 1 : kBits <= 16 ? 2 : 3;
-  static constexpr int kProducts = kA == 1 ? 3 : kA == 2 ? 5 : 6;  // A_p B_q, p + q <= 2
 };
 
-// B operand of one stage: 3 pieces x 4 K steps of NR x 16 BF16.
+// B operand of one stage: per K step, the 3 pieces one after another along N
+// (a 3 NR x 16 BF16 tile).
 template <int NR>
 struct MmaBTile {
-  static constexpr int kBTile = NR * 16 * 2;
+  static constexpr int kBTile = NR * 16 * 2;  // one piece, one K step
   static constexpr int kB = 3 * kMmaKSteps * kBTile;
 };
+
+// TMEM columns: two accumulator groups of three NR-column accumulators,
+// rounded up to the power of two that tcgen05.alloc takes.
+template <int NR>
+__host__ __device__ constexpr uint32_t mma_tmem_cols() {
+  return 6 * NR <= 32 ? 32u : 6 * NR <= 64 ? 64u : 6 * NR <= 128 ? 128u : 256u;
+}
 
 // Shared memory: A and B tiles of two stages, then 4 mbarriers, the TMEM slot,
 // flags and thread 0's B-copy cursor; the member table follows kBytes.
@@ -160,23 +169,29 @@ __device__ __forceinline__ void tmem_load_row<8>(uint32_t taddr, float (&v)[8]) 
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Eight columns from each of two accumulators, summed: one wait for both
-// loads, tied to their registers so no use can move above it.
-__device__ __forceinline__ void tmem_load_sum8(uint32_t ta, uint32_t tb, float (&v)[8]) {
-  uint32_t a[8], b[8];
+// Eight columns of the three accumulators at ta, ta + stride, ta + 2 stride,
+// summed big + (small + smaller): one wait for the three loads, tied to their
+// registers so no use can move above it.
+__device__ __forceinline__ void tmem_load_sum8(uint32_t ta, uint32_t stride, float (&v)[8]) {
+  uint32_t a[8], b[8], c[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
                : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7])
                : "r"(ta));
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
                : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7])
-               : "r"(tb));
+               : "r"(ta + stride));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+               : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7])
+               : "r"(ta + 2 * stride));
   asm volatile("tcgen05.wait::ld.sync.aligned;\n"
                : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
-                 "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7])
+                 "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+                 "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7])
                :
                : "memory");
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(a[i]) + __uint_as_float(b[i]);
+  for (int i = 0; i < 8; ++i)
+    v[i] = __uint_as_float(a[i]) + (__uint_as_float(b[i]) + __uint_as_float(c[i]));
 }
 
 template <>
@@ -214,7 +229,7 @@ __device__ __forceinline__ MmaPass pass_of(const MmaPass& single, const MmaPass*
 
 // B tiles of every pass: for stage st, column block J and right-hand side r,
 // (2G)^T x_J (or x_J without the lift) in three BF16 pieces, already in the
-// shared-memory tile layout of the stage: out[st][piece][kstep] = NR x 16 BF16.
+// shared-memory tile layout of the stage: out[st][kstep][piece] = NR x 16 BF16.
 // Thread per (pass, stage, J in the stage, r); total threads given.
 template <bool LIFT, int NR>
 __global__ void wz2_mma_btiles(MmaPass single, const MmaPass* __restrict__ table, int n, int64_t threads) {
@@ -251,7 +266,7 @@ __global__ void wz2_mma_btiles(MmaPass single, const MmaPass* __restrict__ table
   uint8_t* base = ps.btiles + stage * (int64_t)S::kB;
 #pragma unroll
   for (int pc = 0; pc < 3; ++pc)
-    *reinterpret_cast<uint2*>(base + (pc * kMmaKSteps + kstep) * S::kBTile + tile_off(r, kk)) =
+    *reinterpret_cast<uint2*>(base + (kstep * 3 + pc) * S::kBTile + tile_off(r, kk)) =
         make_uint2(pack2(p[pc][0], p[pc][1]), pack2(p[pc][2], p[pc][3]));
 }
 
@@ -330,16 +345,6 @@ __device__ __forceinline__ void split_row(const float (&v)[4], uint32_t (&d)[PA]
   }
 }
 
-// Products (p, q): m = 0 is (0,0), which goes to the "big" accumulator; the
-// others (0,1) (1,0) (0,2) (1,1) (2,0) -- the first kProducts-1 of them with
-// p < PA -- to the "small" one.
-__device__ __forceinline__ constexpr int mma_prod_a(int PA, int m) {
-  return PA == 1 ? 0 : (m == 2 || m == 4) ? 1 : m == 5 ? 2 : 0;
-}
-__device__ __forceinline__ constexpr int mma_prod_b(int PA, int m) {
-  return PA == 1 ? m : (m == 1 || m == 4) ? 1 : m == 3 ? 2 : 0;
-}
-
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
 }
@@ -366,10 +371,9 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
                    int* __restrict__ status) {
   using SM = MmaSmem<RATE, NR>;
   constexpr int PA = MmaPieces<RATE>::kA;
-  constexpr int NP = MmaPieces<RATE>::kProducts;
   constexpr int NW = Wz2Layout<RATE>::kWords;
   constexpr int HALF = NR / 2;  // TMEM columns drained by each of the two warps on a lane quarter
-  constexpr uint32_t kCols = 4 * NR;  // accumulator pairs (big, small) of two groups: 64 or 128 columns
+  constexpr uint32_t kCols = mma_tmem_cols<NR>();  // two groups of three accumulators
   extern __shared__ __align__(1024) uint8_t smem[];
   const uint32_t s_base = smem_addr(smem);
   const uint32_t mma_bar = s_base + SM::kBars;  // two mbarriers: MMAs of buffer 0, 1 done
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
     *abort_flag = 0;
     *last_commit = *last_copy = -1;
   }
-  if (warp == 0) {  // TMEM: four accumulators of NR fp32 columns
+  if (warp == 0) {  // TMEM: six accumulators of NR fp32 columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tslot)),
                  "r"(kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
@@ -427,10 +431,10 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
   const int st0 = (int)(it0 - mb(mem0).item_begin - (int64_t)tile0 * mb(mem0).S);
   int f_m = mem0, f_tile = tile0, f_st = st0;  // fetch
   int m_m = mem0, m_tile = tile0, m_st = st0;  // issue
-  // the B-copy cursor of a batch is thread 0's alone: it lives in shared
-  // memory, not in every thread's registers
+  // the B-copy cursor (member, tile, stage) is thread 0's alone: it lives in
+  // shared memory, not in every thread's registers
   int* b_cur = reinterpret_cast<int*>(smem + SM::kBars + 64);
-  if (TABLE && t == 0) b_cur[0] = mem0, b_cur[1] = tile0, b_cur[2] = st0;
+  if (t == 0) b_cur[0] = mem0, b_cur[1] = tile0, b_cur[2] = st0;
   auto advance = [&](int& m, int& tile, int& st) {
     if (++st == mb(m).S) {
       st = 0, ++tile;
@@ -472,17 +476,11 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
   };
   auto b_copy = [&](int64_t k) {  // thread 0: B tile of stage k into buffer k % 2
     const int buf = (int)(k & 1);
-    if constexpr (TABLE) {
-      int bm = b_cur[0], bt = b_cur[1], bs = b_cur[2];
-      bulk_copy_g2s(s_base + 2 * SM::kA + buf * SM::kB, tab[bm].btiles + (int64_t)bs * SM::kB, (uint32_t)SM::kB,
-                    b_bar + 8 * buf);
-      advance(bm, bt, bs);
-      b_cur[0] = bm, b_cur[1] = bt, b_cur[2] = bs;
-    } else {
-      const int64_t st = (it0 + k) % single.S;
-      bulk_copy_g2s(s_base + 2 * SM::kA + buf * SM::kB, single.btiles + st * (int64_t)SM::kB, (uint32_t)SM::kB,
-                    b_bar + 8 * buf);
-    }
+    int bm = b_cur[0], bt = b_cur[1], bs = b_cur[2];
+    bulk_copy_g2s(s_base + 2 * SM::kA + buf * SM::kB, mb(bm).btiles + (int64_t)bs * SM::kB, (uint32_t)SM::kB,
+                  b_bar + 8 * buf);
+    advance(bm, bt, bs);
+    b_cur[0] = bm, b_cur[1] = bt, b_cur[2] = bs;
     *last_copy = k;
   };
   auto fail = [&]() {  // a wait ran out: the CTA stops at its next barrier
@@ -504,19 +502,19 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
       hi[r] = lo[r] = 0.f;
     }
   };
-  // drain accumulator pair `acc` (big + small), which holds a group of stages of
-  // tile `tile` of member `mem`
+  // drain accumulator group `acc` (its three accumulators, added), which holds
+  // a group of stages of tile `tile` of member `mem`
   auto drain = [&](int acc, int mem, int tile) {
     if (mem != cur_m || tile != cur_tile) {
       flush();
       cur_m = mem;
       cur_tile = tile;
     }
-    const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(2 * acc * NR + c0);
+    const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(3 * acc * NR + c0);
 #pragma unroll
     for (int h = 0; h < HALF; h += 8) {
       float v[8];
-      tmem_load_sum8(ta + h, ta + NR + h, v);
+      tmem_load_sum8(ta + h, NR, v);
 #pragma unroll
       for (int r = 0; r < 8; ++r) two_sum_acc(hi[h + r], lo[h + r], v[r]);
     }
@@ -574,26 +572,23 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
         fail();
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        constexpr uint32_t idesc = mma_idesc<NR>();
         const uint64_t ad0 = a_desc0 + (uint64_t)((buf * SM::kA) >> 4);
         const uint64_t bd0 = b_desc0 + (uint64_t)((buf * SM::kB) >> 4);
-        const uint32_t d_big = tmem + (uint32_t)(2 * acc * NR), d_small = d_big + NR;
-        // the cross products first (small accumulator), then A_0 B_0 (big one):
-        // a truncating accumulate then loses little
+        const uint32_t d0 = tmem + (uint32_t)(3 * acc * NR);
+        // A_p [B_0 .. B_{2-p}] into accumulators p..2; A_0 of the first K step
+        // of a group starts all three
 #pragma unroll
-        for (int mm = 1; mm <= NP; ++mm) {
-          const int m = mm % NP;
+        for (int ks = 0; ks < kMmaKSteps; ++ks) {
 #pragma unroll
-          for (int ks = 0; ks < kMmaKSteps; ++ks) {
-            const int pa = mma_prod_a(PA, m), pb = mma_prod_b(PA, m);
+          for (int pa = 0; pa < PA; ++pa) {
             const uint64_t ad = ad0 + (uint64_t)(((pa * kMmaKSteps + ks) * SM::kATile) >> 4);
-            const uint64_t bd = bd0 + (uint64_t)(((pb * kMmaKSteps + ks) * MmaBTile<NR>::kBTile) >> 4);
-            const uint32_t accumulate = (init && ks == 0 && (m == 0 || m == 1)) ? 0u : 1u;
+            const uint64_t bd = bd0 + (uint64_t)((3 * ks * MmaBTile<NR>::kBTile) >> 4);
+            const uint32_t accumulate = (init && ks == 0 && pa == 0) ? 0u : 1u;
             asm volatile(
                 "{\n\t.reg .pred p;\n\t"
                 "setp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(m ? d_small : d_big),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d0 + (uint32_t)(pa * NR)),
+                "l"(ad), "l"(bd), "r"(mma_idesc((3 - pa) * NR)), "r"(accumulate));
           }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
