@@ -5,7 +5,8 @@
 // grid split the band-major sequence of 16-byte column chunks of all 4-row
 // bands into equal contiguous ranges; a lane keeps two chunks (4 rows each) in
 // flight; each group of 4 products enters a TwoSum accumulator together with
-// the exact rounding error of its product with the tile scale.  FP32 storage
+// the exact rounding error of its product with the tile scale.  Rows 2h and
+// 2h+1 of a band share one packed FP32 pair instruction per step.  FP32 storage
 // (FMT 7, unit scales) follows the paper's mixed precision instead (Sec. 4.4):
 // every product is rounded to FP32 on its own and enters the TwoSum alone.
 #pragma once
@@ -47,35 +48,65 @@ __device__ __forceinline__ void scaled_chunk(const uint8_t* __restrict__ payload
       for (int v = 0; v < V; ++v) xv[r][v] = c + v < N ? __ldg(xp + v) : 0.f;
     }
   }
-  const int64_t tcol = c / 128;
+  // rows 2h and 2h+1 go through the packed FP32 pair instructions together;
+  // rows past M hold zeros (their y is never written)
+  float f[4][V];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t row = row0 + i;
-    if (row >= M) break;
-    float f[V];
-    T::decode(raw[i], f);
-    if constexpr (FMT == 7) {  // products rounded one by one, summed without loss
+  for (int i = 0; i < 4; ++i) T::decode(raw[i], f[i]);
+  float2 hi2[2][R], lo2[2][R];
 #pragma unroll
-      for (int r = 0; r < R; ++r)
+  for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int v = 0; v < V; ++v) two_sum_acc(hi[i][r], lo[i][r], __fmul_rn(f[v], xv[r][v]));
-      continue;
+    for (int r = 0; r < R; ++r) {
+      hi2[h][r] = make_float2(hi[2 * h][r], hi[2 * h + 1][r]);
+      lo2[h][r] = make_float2(lo[2 * h][r], lo[2 * h + 1][r]);
     }
-    const float s = __ldg(scales + (row / 128) * TN + tcol);
+  // A product that must stay rounded is a scalar mul.rn, which is never
+  // fused into its consumer; a packed multiply feeding a packed add may be.
+  if constexpr (FMT == 7) {  // products rounded one by one, summed without loss
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          two_sum_acc2(hi2[h][r], lo2[h][r],
+                       make_float2(__fmul_rn(f[2 * h][v], xv[r][v]), __fmul_rn(f[2 * h + 1][v], xv[r][v])));
+  } else {
+    // the four rows of a band lie in one 128-row tile: one scale per chunk
+    const float s = __ldg(scales + (row0 / 128) * TN + c / 128);
+    const float2 s2 = make_float2(s, s);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
 #pragma unroll
       for (int g = 0; g < V; g += 4) {
-        float p = f[g] * xv[r][g];
-        p = fmaf(f[g + 1], xv[r][g + 1], p);
-        p = fmaf(f[g + 2], xv[r][g + 2], p);
-        p = fmaf(f[g + 3], xv[r][g + 3], p);
-        const float ps = p * s;
-        two_sum_acc(hi[i][r], lo[i][r], ps);
-        lo[i][r] += fmaf(p, s, -ps);
+        float2 xx[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) xx[e] = make_float2(xv[r][g + e], xv[r][g + e]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float* fa = f[2 * h];
+          const float* fb = f[2 * h + 1];
+          float2 p = mul_f2(make_float2(fa[g], fb[g]), xx[0]);
+          p = fma_f2(make_float2(fa[g + 1], fb[g + 1]), xx[1], p);
+          p = fma_f2(make_float2(fa[g + 2], fb[g + 2]), xx[2], p);
+          p = fma_f2(make_float2(fa[g + 3], fb[g + 3]), xx[3], p);
+          const float2 ps = make_float2(__fmul_rn(p.x, s), __fmul_rn(p.y, s));
+          two_sum_acc2(hi2[h][r], lo2[h][r], ps);
+          lo2[h][r] = add_f2(lo2[h][r], fma_f2(p, s2, make_float2(-ps.x, -ps.y)));
+        }
       }
     }
   }
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      hi[2 * h][r] = hi2[h][r].x;
+      hi[2 * h + 1][r] = hi2[h][r].y;
+      lo[2 * h][r] = lo2[h][r].x;
+      lo[2 * h + 1][r] = lo2[h][r].y;
+    }
 }
 
 template <int FMT>
