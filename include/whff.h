@@ -223,7 +223,9 @@ void whff_graph_destroy(whff_graph* g);
  * the engine crossover: the fewest columns (2..8) for which one tensor-core
  * pass is no slower than the CUDA-core passes, else 9.  whff_get_config / whff_set_config read and apply a
  * shape (e.g. from a cache keyed by format, rate, shape and SM count).  WZ2
- * handles only (WHFF_EINVAL otherwise). */
+ * handles only (WHFF_EINVAL otherwise).  Handles of the scaled formats (BF16,
+ * FP16, FP8, FP32) take the same fold defaults, counting 16-byte column chunks
+ * per band instead of blocks, and are not tunable. */
 #define WHFF_FOLD_FP32_PAIRS 1
 #define WHFF_FOLD_LANE_GROUPS 2
 int whff_tune(whff_handle* h, int iters, void* stream, double* best_ms);

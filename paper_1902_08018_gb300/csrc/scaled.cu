@@ -7,9 +7,14 @@ namespace whff {
 
 template <int FMT, int R>
 static void scaled_one(const ScaledStep& a, cudaStream_t st) {
-  dev::scaled_range_kernel<FMT, R><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
-      a.payload, a.scales, a.M, a.N, a.ld, a.TN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg, a.ws, a.y, a.ldy, a.state,
-      a.decay, a.red32);
+  if (a.groups8)
+    dev::scaled_range_kernel<FMT, R, 8><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
+        a.payload, a.scales, a.M, a.N, a.ld, a.TN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg, a.ws, a.y, a.ldy, a.state,
+        a.decay, a.red32);
+  else
+    dev::scaled_range_kernel<FMT, R, 32><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
+        a.payload, a.scales, a.M, a.N, a.ld, a.TN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg, a.ws, a.y, a.ldy, a.state,
+        a.decay, a.red32);
 }
 
 template <int FMT>
@@ -42,14 +47,20 @@ int scaled_launch(const ScaledStep& a, cudaStream_t st) {
   return 0;
 }
 
-int scaled_occupancy(int fmt) {
+template <int FMT>
+static cudaError_t scaled_occ(int* occ, bool groups8, int threads) {
+  if (groups8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::scaled_range_kernel<FMT, 1, 8>, threads, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::scaled_range_kernel<FMT, 1, 32>, threads, 0);
+}
+
+int scaled_occupancy(int fmt, bool groups8) {
   int occ = 0;
   cudaError_t e = cudaErrorInvalidValue;
   const int threads = dev::kWarpsPerCta * 32;
-  if (fmt == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<2, 1>, threads, 0);
-  if (fmt == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<3, 1>, threads, 0);
-  if (fmt == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<4, 1>, threads, 0);
-  if (fmt == 7) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::scaled_range_kernel<7, 1>, threads, 0);
+  if (fmt == 2) e = scaled_occ<2>(&occ, groups8, threads);
+  if (fmt == 3) e = scaled_occ<3>(&occ, groups8, threads);
+  if (fmt == 4) e = scaled_occ<4>(&occ, groups8, threads);
+  if (fmt == 7) e = scaled_occ<7>(&occ, groups8, threads);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -121,14 +121,41 @@ __device__ __forceinline__ void scaled_load(const uint8_t* __restrict__ payload,
   }
 }
 
-template <int FMT, int R>
+// Chunks [J, J1) of the band at row0, lane stride STRIDE (two in flight,
+// processed in order) into the lane's TwoSum sums.
+template <int FMT, int R, int STRIDE>
+__device__ __forceinline__ void scaled_piece(const uint8_t* __restrict__ payload, const float* __restrict__ scales,
+                                             int64_t M, int64_t N, int64_t ld, int64_t TN, int64_t row0, int64_t J,
+                                             int64_t J1, const float* __restrict__ x, int64_t ldx, bool x_fast,
+                                             float (&hi)[4][R], float (&lo)[4][R]) {
+  constexpr int V = ScaledTraits<FMT>::V;
+  for (; J + STRIDE < J1; J += 2 * STRIDE) {
+    uint4 r0[4], r1[4];
+    scaled_load<FMT>(payload, M, ld, row0, J * V, r0);
+    scaled_load<FMT>(payload, M, ld, row0, (J + STRIDE) * V, r1);
+    scaled_chunk<FMT, R>(payload, scales, M, N, ld, TN, row0, J * V, r0, x, ldx, x_fast, hi, lo);
+    scaled_chunk<FMT, R>(payload, scales, M, N, ld, TN, row0, (J + STRIDE) * V, r1, x, ldx, x_fast, hi, lo);
+  }
+  if (J < J1) {
+    uint4 r0[4];
+    scaled_load<FMT>(payload, M, ld, row0, J * V, r0);
+    scaled_chunk<FMT, R>(payload, scales, M, N, ld, TN, row0, J * V, r0, x, ldx, x_fast, hi, lo);
+  }
+}
+
+// GL = 32: the warp takes one piece of a band at a time; GL = 8: four lane
+// groups take the next four pieces at once (short bands, where a warp per
+// band would spend its time folding).
+template <int FMT, int R, int GL>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
     scaled_range_kernel(const uint8_t* __restrict__ payload, const float* __restrict__ scales, int64_t M, int64_t N,
                         int64_t ld, int64_t TN, const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int64_t L,
                         int maxseg, double* __restrict__ ws, double* __restrict__ y, int64_t ldy,
                         double* __restrict__ state, double decay, bool red32) {
   constexpr int V = ScaledTraits<FMT>::V;
+  constexpr int NG = 32 / GL;  // pieces taken at once
   const int lane = threadIdx.x & 31;
+  const int gl = lane % GL;
   const int64_t g = (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
   const int64_t BM = (M + 3) / 4, CB = ld / V;  // bands, chunks per band
   const int64_t total = BM * CB;
@@ -136,36 +163,38 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   int64_t b0 = g * L;
   const int64_t b1 = min(total, b0 + L);
   while (b0 < b1) {
-    const int64_t I = b0 / CB;
-    const int64_t piece_end = min(b1, (I + 1) * CB);
-    const int64_t g_lo = (I * CB) / L, g_hi = ((I + 1) * CB - 1) / L;
-    const int64_t row0 = 4 * I;
     float hi[4][R], lo[4][R];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
-    int64_t J = b0 - I * CB + lane;
-    const int64_t J1 = piece_end - I * CB;
-    for (; J + 32 < J1; J += 64) {  // two chunks in flight, processed in order
-      uint4 r0[4], r1[4];
-      scaled_load<FMT>(payload, M, ld, row0, J * V, r0);
-      scaled_load<FMT>(payload, M, ld, row0, (J + 32) * V, r1);
-      scaled_chunk<FMT, R>(payload, scales, M, N, ld, TN, row0, J * V, r0, x, ldx, x_fast, hi, lo);
-      scaled_chunk<FMT, R>(payload, scales, M, N, ld, TN, row0, (J + 32) * V, r1, x, ldx, x_fast, hi, lo);
+    if constexpr (GL == 32) {
+      const int64_t I = b0 / CB;
+      const int64_t piece_end = min(b1, (I + 1) * CB);
+      const int64_t g_lo = (I * CB) / L, g_hi = ((I + 1) * CB - 1) / L;
+      scaled_piece<FMT, R, 32>(payload, scales, M, N, ld, TN, 4 * I, b0 - I * CB + lane, piece_end - I * CB, x,
+                               ldx, x_fast, hi, lo);
+      if (g_lo == g_hi) {
+        band_finish<0, R>(hi, lo, lane, 4 * I, M, 0, 1, 4 * BM, ws, y, ldy, state, decay, red32);
+      } else {
+        band_finish<0, R>(hi, lo, lane, 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, 2, 0, ws, y, ldy, state, decay,
+                          red32);
+      }
+      b0 = piece_end;
+    } else {  // lane group lane / GL takes the piece of band b0 / CB + lane / GL
+      const int64_t I = b0 / CB + lane / GL;
+      const int64_t pb = max(b0, I * CB), pe = min(b1, (I + 1) * CB);
+      const bool active = pb < pe;
+      const int64_t g_lo = (I * CB) / L, g_hi = ((I + 1) * CB - 1) / L;
+      if (active)
+        scaled_piece<FMT, R, GL>(payload, scales, M, N, ld, TN, 4 * I, pb - I * CB + gl, pe - I * CB, x, ldx, x_fast,
+                                 hi, lo);
+      // one call for all groups (the folds shuffle across the whole warp)
+      const bool whole = g_lo == g_hi;
+      band_finish<0, R, GL>(hi, lo, gl, whole ? 4 * I : 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, whole ? 1 : 2,
+                            whole ? 4 * BM : 0, ws, y, ldy, state, decay, red32, active);
+      b0 = min(b1, (b0 / CB + NG) * CB);
     }
-    if (J < J1) {
-      uint4 r0[4];
-      scaled_load<FMT>(payload, M, ld, row0, J * V, r0);
-      scaled_chunk<FMT, R>(payload, scales, M, N, ld, TN, row0, J * V, r0, x, ldx, x_fast, hi, lo);
-    }
-    if (g_lo == g_hi) {
-      band_finish<0, R>(hi, lo, lane, row0, M, 0, 1, 4 * BM, ws, y, ldy, state, decay, red32);
-    } else {
-      band_finish<0, R>(hi, lo, lane, 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, 2, 0, ws, y, ldy, state, decay,
-                        red32);
-    }
-    b0 = piece_end;
   }
 }
 

@@ -225,7 +225,7 @@ int launch_scaled(const whff_handle* h, const float* x, int R, int64_t ldx, bool
   const auto& b = h->info;
   const int64_t ld = scaled_ld(b.N);
   ScaledStep a{b.fmt, h->d_stream, h->d_scales, b.M, b.N, ld, ceil_div(b.N, kScaleTile), x, ldx, vec,
-               h->range_len, h->maxseg, h->d_ws, y, ldy, state, decay, h->range_ctas, R, h->red32};
+               h->range_len, h->maxseg, h->d_ws, y, ldy, state, decay, h->range_ctas, R, h->red32, h->groups8};
   if (scaled_launch(a, st)) {
     set_error("whff_step: scaled formats take R 1, 2, 4 or 8 per pass");
     return WHFF_EINVAL;
@@ -312,8 +312,8 @@ extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigne
   if (info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) {
     const int occ = wz2_occ(info.rate, info.fmt == WHFF_FMT_FIXED_LIFT, h->unroll);
     h->ctas_per_sm = occ > 0 ? occ : 4;
-  } else if (!is_blocked(info.fmt)) {
-    const int occ = scaled_occupancy(info.fmt);
+  } else if (!is_blocked(info.fmt)) {  // the kernel the fold default below picks (band length in chunks)
+    const int occ = scaled_occupancy(info.fmt, scaled_ld(info.N) / scaled_vec(info.fmt) < 256);
     h->ctas_per_sm = occ > 0 ? occ : 4;
   }
   if (is_blocked(info.fmt)) {
@@ -321,9 +321,11 @@ extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigne
     h->BN = ceil_div(info.N, 4);
   }
   choose_split(h);
-  // short bands (tall matrices) fold their lanes in FP32 pairs; long ones in FP64
+  // short bands (tall matrices) fold their lanes in FP32 pairs, long ones in
+  // FP64; very short ones give each band a group of 8 lanes.  BN counts a
+  // band's lane work units: 4-column blocks (WZ2) or 16-byte chunks (scaled).
   h->red32 = info.fmt != WHFF_FMT_ZFP && h->BN < 4096;
-  h->groups8 = (info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) && h->BN < 256;
+  h->groups8 = info.fmt != WHFF_FMT_ZFP && h->BN < 256;
   const cudaStream_t st = as_stream(stream);
   if (flags & WHFF_CREATE_HOST_RESIDENT) {  // pinned host memory, read by the kernels over the CPU link
     void* dp = nullptr;

@@ -65,6 +65,7 @@ struct ScaledStep {
   int64_t ctas;
   int R;
   bool red32;
+  bool groups8;  // four 8-lane groups per warp, one band each (short bands)
 };
 int scaled_launch(const ScaledStep& a, cudaStream_t st);  // scaled.cu
 
@@ -108,7 +109,7 @@ int mma_batch_launch(const MmaBatchStep& a, cudaStream_t st);
 int mma_max_members();  // most members of one batched launch
 // resident CTAs per SM of the tensor-core kernel at this rate for R <= nr (0 on error)
 int mma_occupancy(int rate, bool lift, int nr);
-int scaled_occupancy(int fmt);
+int scaled_occupancy(int fmt, bool groups8);  // resident CTAs per SM of the R = 1 kernel
 
 template <int RATE>
 int wz2_launch(const Wz2Step& a, cudaStream_t st);

@@ -68,6 +68,8 @@ CASES = [
     (7, 0, 300, 301),     # FP32 storage, the paper's mixed precision
     (7, 0, 16, 20000),    # wide FP32
     (7, 0, 3001, 40),     # tall FP32
+    (2, 0, 3001, 378),    # tall BF16: 8-lane groups per band
+    (4, 0, 2050, 700),    # tall FP8
     (6, 20, 3001, 40),
 ]
 
