@@ -4,9 +4,10 @@
 // Same schedule as the fixed-allocation kernels: the warps of a persistent
 // grid split the band-major sequence of 16-byte column chunks of all 4-row
 // bands into equal contiguous ranges; a lane keeps two chunks (4 rows each) in
-// flight; each group of 4 products enters a TwoSum accumulator together with
-// the exact rounding error of its product with the tile scale.  Rows 2h and
-// 2h+1 of a band share one packed FP32 pair instruction per step.  FP32 storage
+// flight; 8 consecutive products of one row are chained in FP32 and enter a
+// TwoSum accumulator together with the exact rounding error of their sum's
+// product with the tile scale.  Rows 2h and 2h+1 of a band share one packed
+// FP32 pair instruction per step.  FP32 storage
 // (FMT 7, unit scales) follows the paper's mixed precision instead (Sec. 4.4):
 // every product is rounded to FP32 on its own and enters the TwoSum alone.
 #pragma once
@@ -78,19 +79,19 @@ __device__ __forceinline__ void scaled_chunk(const uint8_t* __restrict__ payload
     const float2 s2 = make_float2(s, s);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+      constexpr int G = 8;  // products per chain
 #pragma unroll
-      for (int g = 0; g < V; g += 4) {
-        float2 xx[4];
+      for (int g = 0; g < V; g += G) {
+        float2 xx[G];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) xx[e] = make_float2(xv[r][g + e], xv[r][g + e]);
+        for (int e = 0; e < G; ++e) xx[e] = make_float2(xv[r][g + e], xv[r][g + e]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const float* fa = f[2 * h];
-          const float* fb = f[2 * h + 1];
-          float2 p = mul_f2(make_float2(fa[g], fb[g]), xx[0]);
-          p = fma_f2(make_float2(fa[g + 1], fb[g + 1]), xx[1], p);
-          p = fma_f2(make_float2(fa[g + 2], fb[g + 2]), xx[2], p);
-          p = fma_f2(make_float2(fa[g + 3], fb[g + 3]), xx[3], p);
+          const float* fa = f[2 * h] + g;
+          const float* fb = f[2 * h + 1] + g;
+          float2 p = mul_f2(make_float2(fa[0], fb[0]), xx[0]);
+#pragma unroll
+          for (int e = 1; e < G; ++e) p = fma_f2(make_float2(fa[e], fb[e]), xx[e], p);
           const float2 ps = make_float2(__fmul_rn(p.x, s), __fmul_rn(p.y, s));
           two_sum_acc2(hi2[h][r], lo2[h][r], ps);
           lo2[h][r] = add_f2(lo2[h][r], fma_f2(p, s2, make_float2(-ps.x, -ps.y)));
