@@ -453,7 +453,7 @@ def run_whff(args, rank, world, local_rank):
     algo_bytes = stream_bytes + order * 4 + order * 8 + order * 16
     kernel_ms = float(np.mean(per_ms))  # one launch per step when ksplit == 1
     achieved = algo_bytes / (kernel_ms * 1e-3) / 1e9
-    kname = {1: "wz1_gemv_kernel", 5: "wz2_gemv_kernel", 6: "wz2_gemv_kernel"}.get(head[0], "scaled_gemv_kernel")
+    kname = {1: "wz1_gemv_kernel", 5: "wz2_gemv_kernel", 6: "wz2_gemv_kernel"}.get(head[0], "scaled_range_kernel")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind}",
                 "traffic": ncu_traffic(f"{head_name}_{order}"), "kernel": kname,
