@@ -77,6 +77,11 @@ def parse_args():
     p.add_argument("--shapes", action="store_true",
                    help="the paper's three GEMV shapes (wide, tall, square) in FP32 and compressed formats")
     p.add_argument("--shapes-fmts", default="fp32:0,wz2-lift:16,wz2-lift:12,wz1:16,bf16:0")
+    p.add_argument("--precision", action="store_true",
+                   help="the precision sweep: every format at 1 and 32 right-hand sides on the control-loop matrix")
+    p.add_argument("--precision-fmts",
+                   default="wz1:8,wz1:12,wz1:16,wz2-lift:8,wz2-lift:12,wz2-lift:16,wz2-bfp:8,wz2-bfp:12,wz2-bfp:16,"
+                           "bf16:0,fp16:0,fp8:0")
     p.add_argument("--batched", action="store_true", help="run the batched uneven-instances workload")
     p.add_argument("--batched-fmt", default="wz2-lift:12")
     p.add_argument("--batched-crossover", type=int, default=0,
@@ -811,6 +816,73 @@ def run_reference(args, rank, world):
     }
 
 
+# ---------------------------------------------------------- precision sweep
+def run_precision(args, rank, world, local_rank):
+    """Every storage format of the precision layer on the control-loop matrix, at one
+    right-hand side (the heat load of step 0) and at 32 (the heat loads of steps 0..31):
+    step time, GB/s of stored bytes, and the relative L2 error of y against FP64 GEMV on
+    the uncompressed matrix (64 sampled rows, the worst of the 32 columns)."""
+    import torch
+
+    import paper_1902_08018_gb300 as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    order = args.order
+    specs = []
+    for item in filter(None, args.precision_fmts.split(",")):
+        name, rate = item.split(":")
+        specs.append((FMT_CODES[name], int(rate) if FMT_CODES[name] in (1, 5, 6) else 0))
+    rng = np.random.default_rng(12345)
+    sample_rows = np.sort(rng.choice(order, size=64, replace=False))
+    t_setup = time.perf_counter()
+    km, blobs, _, sampled = build_workload(order, specs, False, sample_rows, torch, dev)
+    t_setup = time.perf_counter() - t_setup
+    X64 = heat_load_inputs(km, 32)  # (32, N)
+    Y_star = sampled @ X64.T        # (64, 32) FP64 reference on the uncompressed rows
+    X = torch.from_numpy(X64.astype(np.float32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = measured_peaks()
+    table = {}
+    with ClockSampler(local_rank) as clk:
+        for spec in specs:
+            name = f"{FMT_NAMES[spec[0]]}-{spec[1]}" if spec[1] else FMT_NAMES[spec[0]]
+            h = W.whff_create(blobs[spec], max_rhs=32)
+            sb = blobs[spec].size - 64
+            entry = {"bytes": int(sb)}
+            for R, reps in ((1, max(10, args.steps)), (32, max(5, args.steps // 10))):
+                Y = torch.zeros((R, order), dtype=torch.float64, device=dev)
+                for _ in range(3):
+                    h.step(X[:R], Y, None, DECAY, stream)
+                torch.cuda.synchronize()
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+                for _ in range(reps):
+                    h.step(X[:R], Y, None, DECAY, stream)
+                f1.record(stream)
+                torch.cuda.synchronize()
+                ms = f0.elapsed_time(f1) / reps
+                Yh = Y.cpu().numpy()[:, sample_rows].T  # (64, R)
+                err = max(float(np.linalg.norm(Yh[:, r] - Y_star[:, r]) / np.linalg.norm(Y_star[:, r]))
+                          for r in range(R))
+                engine = "tcgen05" if (spec[0] in (2, 3, 4, 5, 6) and R >= h.crossover) else "cuda-core"
+                entry[f"R{R}"] = {"ms_per_step": round(ms, 4), "GB_s": round(sb / (ms * 1e-3) / 1e9, 1),
+                                  "pct_hbm": round(100 * sb / (ms * 1e-3) / 1e9 / peak, 2),
+                                  "effective_tflops": round(R * order * (2 * order - 1) / (ms * 1e-3) / 1e12, 2),
+                                  "rel_err_vs_fp64_uncompressed": err, "engine": engine}
+            table[name] = entry
+            h.destroy()
+    head = table.get("wz2-lift-16", next(iter(table.values())))
+    return {"mode": "precision", "metric": "precision sweep: GB/s & % peak and rel. L2 error vs FP64 per format",
+            "value": head["R1"]["GB_s"], "unit": "GB/s (stored bytes, wz2-lift-16, R = 1)", "higher_is_better": True,
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"precision-sweep-{order}", "order": order, "R": [1, 32],
+                       "x": "heat loads of control steps 0..31 (serpentine path)",
+                       "error_rows": "64 sampled rows, FP64 GEMV on the uncompressed matrix"},
+            "peak_gbs": peak, "peak_kind": peak_kind, "formats": table, "clocks": clk.summary(),
+            "setup_s": round(t_setup, 1)}
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -826,6 +898,8 @@ def main():
         res = run_batched(args, rank, world, local_rank)
     elif args.shapes:
         res = run_shapes(args, rank, world, local_rank)
+    elif args.precision:
+        res = run_precision(args, rank, world, local_rank)
     else:
         if world > 1:
             import torch

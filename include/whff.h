@@ -137,13 +137,14 @@ int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, int64_t* N,
 int whff_plan(const whff_handle* h, int* ksplit, int* launches);
 
 /* One control step (Sec. 2.1 / Sec. 4.4): y[:,r] = Ahat * x[:,r] for r < R,
- * taken in passes: with a WZ2 matrix whose handle allows max_rhs >= 2, passes
- * of crossover..32 columns (default crossover 4, see whff_set_crossover) run
- * on the tensor cores (tcgen05: the stored coefficients split exactly into
- * 1-3 BF16 pieces by field width and the transformed x into three, the
- * piece products above 2^-24 accumulate in FP32 TMEM, drained every 64
- * columns of K into compensated sums); otherwise passes of 8, 4, 2, 1
- * columns run on the CUDA cores.
+ * taken in passes: with a WZ2, BF16, FP16 or FP8 matrix whose handle allows
+ * max_rhs >= 2, passes of crossover..32 columns (default crossover 4, see
+ * whff_set_crossover) run on the tensor cores (tcgen05: the stored values
+ * split exactly into 1-3 BF16 pieces -- WZ2 by field width, FP16 into two,
+ * BF16 and FP8 into one -- and x, transformed for FIXED_LIFT, into three; the
+ * piece products above 2^-24 accumulate in FP32 TMEM, drained every 128
+ * columns of K into compensated sums, the scaled formats' tile scale applied
+ * at the drain); otherwise passes of 8, 4, 2, 1 columns run on the CUDA cores.
  * Ahat = the decoded matrix (exactly whff_decompress's output).  Products and
  * per-lane sums in FP32 (compensated), cross-warp and cross-CTA sums and y in
  * FP64.  If state != NULL, afterwards for r = 0..R-1 in order:

@@ -126,9 +126,9 @@ void choose_split(whff_handle* h) {
 }
 
 // Persistent tensor-core grid: `ctas` CTAs at most over the items (tile of
-// 32 bands, stage of 16 blocks), equal contiguous ranges.
+// 128 rows = 32 bands, stage of 64 columns = 16 blocks), equal contiguous ranges.
 void plan_mma(whff_handle* h, int64_t ctas) {
-  const int64_t tiles = ceil_div(h->BM, 32), stages = ceil_div(h->BN, 16), items = tiles * stages;
+  const int64_t tiles = ceil_div(h->info.M, 128), stages = ceil_div(h->info.N, 64), items = tiles * stages;
   h->mma_L = ceil_div(items, std::max<int64_t>(1, ctas));
   h->mma_ctas = (int)ceil_div(items, h->mma_L);
   h->mma_maxseg = 1;
@@ -138,7 +138,7 @@ void plan_mma(whff_handle* h, int64_t ctas) {
 }
 
 size_t mma_ws_need(const whff_handle* h, int R) {
-  return (size_t)ceil_div(h->BM, 32) * (size_t)h->mma_maxseg * (size_t)R * 128 * 8;
+  return (size_t)ceil_div(h->info.M, 128) * (size_t)h->mma_maxseg * (size_t)R * 128 * 8;
 }
 
 // Workspace bytes a CUDA-core pass of the plan needs.
@@ -346,11 +346,14 @@ extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigne
   if (h->maxseg > 1)
     h->ws_bytes = (size_t)h->BM * (size_t)h->maxseg * (size_t)std::min(max_rhs, kMaxRhsKernel) * 4 * 8;
   h->ws_rhs = std::min(max_rhs, kMaxRhsKernel);
-  if ((info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) && max_rhs >= 2) {
+  const bool wz2 = info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP;
+  const bool scaled16 = info.fmt == WHFF_FMT_BF16 || info.fmt == WHFF_FMT_FP16 || info.fmt == WHFF_FMT_FP8E4M3;
+  if ((wz2 || scaled16) && max_rhs >= 2) {
     // tensor-core passes: a persistent grid (all resident CTAs) over the items
-    // (tile of 32 bands, stage of 16 blocks), equal contiguous ranges per CTA
+    // (tile of 128 rows, stage of 64 columns), equal contiguous ranges per CTA
     const bool lift = info.fmt == WHFF_FMT_FIXED_LIFT;
-    const int occ = std::min(mma_occupancy(info.rate, lift, 16), mma_occupancy(info.rate, lift, 32));
+    const int occ = wz2 ? std::min(mma_occupancy(info.rate, lift, 16), mma_occupancy(info.rate, lift, 32))
+                        : scaled_mma_occupancy(info.fmt);
     if (occ < 1) {
       set_error("whff_create: the tensor-core kernel cannot be resident");
       return fail(WHFF_ECUDA);
@@ -359,7 +362,7 @@ extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigne
     plan_mma(h, (int64_t)h->sm_count * occ);
     h->ws_mma_cap = mma_ws_need(h, std::min(max_rhs, 32));
     h->ws_mma_bytes = h->ws_mma_cap;
-    const size_t btile_bytes = (size_t)ceil_div(h->BN, 16) * 3 * 4 * 32 * 16 * 2;  // stages x pieces x ksteps x NR<=32 tile
+    const size_t btile_bytes = (size_t)ceil_div(info.N, 64) * 3 * 4 * 32 * 16 * 2;  // stages x pieces x ksteps x NR<=32 tile
     h->ws_mma_bytes += btile_bytes;
     if (cudaMalloc(&h->d_ws_mma, h->ws_mma_bytes - btile_bytes) != cudaSuccess ||
         cudaMalloc(&h->d_btiles, btile_bytes) != cudaSuccess) {
@@ -412,10 +415,19 @@ namespace whff {
 namespace {
 int launch_mma(const whff_handle* h, const float* x, int R, int64_t ldx, double* y, int64_t ldy, double* state,
                double decay, cudaStream_t st) {
-  MmaStep a{h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, h->d_stream, h->info.M, h->info.N, h->BM, h->BN,
-            x, ldx, R, h->mma_L, h->mma_ctas, h->mma_maxseg, h->d_ws_mma, h->d_btiles, y, ldy, state, decay,
-            h->d_status};
-  if (mma_launch(a, st)) {
+  int e;
+  if (is_blocked(h->info.fmt)) {
+    MmaStep a{h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, h->d_stream, h->info.M, h->info.N, h->BM, h->BN,
+              x, ldx, R, h->mma_L, h->mma_ctas, h->mma_maxseg, h->d_ws_mma, h->d_btiles, y, ldy, state, decay,
+              h->d_status};
+    e = mma_launch(a, st);
+  } else {
+    ScaledMmaStep a{h->info.fmt, h->d_stream, h->d_scales, h->info.M, h->info.N, scaled_ld(h->info.N),
+                    ceil_div(h->info.N, kScaleTile), x, ldx, R, h->mma_L, h->mma_ctas, h->mma_maxseg,
+                    h->d_ws_mma, h->d_btiles, y, ldy, state, decay, h->d_status};
+    e = scaled_mma_launch(a, st);
+  }
+  if (e) {
     set_error("whff_step: tensor-core pass failed to launch");
     return WHFF_ECUDA;
   }

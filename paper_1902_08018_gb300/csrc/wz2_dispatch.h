@@ -111,6 +111,30 @@ int mma_max_members();  // most members of one batched launch
 int mma_occupancy(int rate, bool lift, int nr);
 int scaled_occupancy(int fmt, bool groups8);  // resident CTAs per SM of the R = 1 kernel
 
+// Tensor-core pass of up to 32 right-hand sides over a BF16 / FP16 / FP8
+// matrix (scaled_mma.cu): items (tile of 128 rows, stage of 64 columns).
+struct ScaledMmaStep {
+  int fmt;
+  const uint8_t* payload;
+  const float* scales;
+  int64_t M, N, ld, TN;
+  const float* x;
+  int64_t ldx;
+  int R;           // 1..32 (padded to 16 or 32 inside)
+  int64_t L;       // items per CTA
+  int ctas;
+  int maxseg;      // most CTAs sharing one tile
+  double* ws;      // tiles x maxseg x R x 128 FP64 partials
+  uint8_t* btiles; // B operand pieces of every stage (built per pass)
+  double* y;
+  int64_t ldy;
+  double* state;
+  double decay;
+  int* status;
+};
+int scaled_mma_launch(const ScaledMmaStep& a, cudaStream_t st);
+int scaled_mma_occupancy(int fmt);  // resident CTAs per SM for R <= 32 (0 on error)
+
 template <int RATE>
 int wz2_launch(const Wz2Step& a, cudaStream_t st);
 template <int RATE>
