@@ -238,7 +238,7 @@ int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int fold);
  * ones on the CUDA cores.  Default 4 (from 4 columns on, one tensor-core
  * pass is at least as fast as the CUDA cores on GB300; whff_tune measures it
  * per matrix); 33 = CUDA cores only.  Tensor-core
- * passes need a WZ2 handle created with max_rhs >= 2 (WHFF_EINVAL otherwise,
+ * passes need a WZ2, BF16, FP16 or FP8 handle created with max_rhs >= 2 (WHFF_EINVAL otherwise,
  * unless min_rhs = 33); whff_get_crossover reports 33 for handles without
  * them.  Both engines meet the same accuracy bar; their roundings differ. */
 int whff_get_crossover(const whff_handle* h, int* min_rhs);
