@@ -56,9 +56,11 @@ def parse_args():
     p.add_argument("--order", type=int, default=32768, help="matrix order (32768 = the control-loop workload)")
     p.add_argument("--fmt", default="wz2-lift", choices=sorted(FMT_CODES))
     p.add_argument("--rate", type=int, default=16)
-    p.add_argument("--sweep", default="wz1:16,wz2-bfp:16,wz2-lift:20,wz2-bfp:20,wz2-lift:24,fp8:0,bf16:0",
+    p.add_argument("--sweep", default="wz1:16,wz2-lift:8,wz2-lift:12,wz2-bfp:16,wz2-lift:20,wz2-bfp:20,wz2-lift:24,"
+                                      "fp8:0,fp16:0,bf16:0",
                    help="extra fmt:rate pairs timed on the same matrix ('' for none)")
     p.add_argument("--sweep-steps", type=int, default=400)
+    p.add_argument("--sweep-rhs", type=int, default=1, help="1: also time every sweep format with 32 right-hand sides")
     p.add_argument("--e2e-steps", type=int, default=200)
     p.add_argument("--rhs-sweep", default="8,16,32",
                    help="right-hand-side counts timed on the headline matrix, on both engines")
@@ -275,6 +277,30 @@ def time_format(h, xs, S, steps, warmup, stream, torch, dev, order, with_clocks=
     return total, per
 
 
+def rhs32_entry(h, spec, sb, X, X64, sampled, sample_rows, peak, stream, torch, dev, order, reps=20):
+    """One pass of 32 right-hand sides: time, stored-byte rate, engine, worst column error vs FP64."""
+    R = X.shape[0]
+    Y = torch.zeros((R, order), dtype=torch.float64, device=dev)
+    for _ in range(3):
+        h.step(X, Y, None, DECAY, stream)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(reps):
+        h.step(X, Y, None, DECAY, stream)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms = f0.elapsed_time(f1) / reps
+    Yh = Y.cpu().numpy()[:, sample_rows].T
+    Ys = sampled @ X64.T
+    err = max(float(np.linalg.norm(Yh[:, r] - Ys[:, r]) / np.linalg.norm(Ys[:, r])) for r in range(R))
+    engine = "tcgen05" if (spec[0] in (2, 3, 4, 5, 6) and R >= h.crossover) else "cuda-core"
+    return {"ms_per_step": round(ms, 4), "GB_s": round(sb / (ms * 1e-3) / 1e9, 1),
+            "pct_hbm": round(100 * sb / (ms * 1e-3) / 1e9 / peak, 2),
+            "effective_tflops": round(R * order * (2 * order - 1) / (ms * 1e-3) / 1e12, 2), "engine": engine,
+            "rel_err": err}
+
+
 def end_to_end_error(h, xs, X64, sampled, sample_rows, stream, torch, dev, order):
     y = torch.zeros(order, dtype=torch.float64, device=dev)
     h.step(xs[0], y, None, DECAY, stream)
@@ -352,7 +378,7 @@ def run_whff(args, rank, world, local_rank):
                           "bytes": int(stream_bytes), "ms_per_step": round(ms_per_step, 5),
                           "p99_us": float(np.percentile(lat, 99)), "rel_err": rel_err}
     for spec in specs[1:]:
-        hh = W.whff_create(blobs[spec], max_rhs=1)
+        hh = W.whff_create(blobs[spec], max_rhs=32 if args.sweep_rhs else 1)
         sb = blobs[spec].size - 64
         tot, per = time_format(hh, xs, S, args.sweep_steps, 5, stream, torch, dev, order)
         err, _ = end_to_end_error(hh, xs, X64, sampled, sample_rows, stream, torch, dev, order)
@@ -361,6 +387,9 @@ def run_whff(args, rank, world, local_rank):
         formats[name] = {"GB_s": round(sb / (ms * 1e-3) / 1e9, 1), "pct_hbm": round(100 * sb / (ms * 1e-3) / 1e9 / peak, 2),
                          "bytes": int(sb), "ms_per_step": round(ms, 5), "p99_us": float(np.percentile(per * 1e3, 99)),
                          "rel_err": err}
+        if args.sweep_rhs:  # the same format with 32 right-hand sides (heat loads of steps 0..31)
+            formats[name]["R32"] = rhs32_entry(hh, spec, sb, xs[:32], X64[:32], sampled, sample_rows, peak, stream,
+                                               torch, dev, order)
         hh.destroy()
     # ---------------- many right-hand sides on the headline matrix, on both engines
     multi = {}
