@@ -176,6 +176,23 @@ class ClockSampler:
                 "power_w_median": statistics.median(pw) if pw else None, "reasons": reasons, "samples": len(rows)}
 
 
+# ------------------------------------------------------------ multi-rank
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time (every rank gets it); one process: x itself."""
+    if world <= 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_per_step_per_rank: float, ms_per_step: float, world: int) -> float:
+    """Replicas: every rank streams its own matrix each step; GB/s of all ranks over the slowest time."""
+    return bytes_per_step_per_rank * world / (ms_per_step * 1e-3) / 1e9
+
+
 # ----------------------------------------------------------------- workload
 def parse_specs(args):
     specs = [(FMT_CODES[args.fmt], args.rate)]
@@ -343,13 +360,10 @@ def run_whff(args, rank, world, local_rank):
         torch.distributed.barrier()
     with ClockSampler(local_rank) as clk:
         total_ms, per_ms = time_format(h, xs, S, args.steps, args.warmup, stream, torch, dev, order)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     clocks = clk.summary()
     ms_per_step = total_ms / args.steps
-    value = stream_bytes / (ms_per_step * 1e-3) / 1e9 * world
+    value = whole_job_gbs(stream_bytes, ms_per_step, world)
     lat = per_ms * 1e3
     rel_err, y_gpu = end_to_end_error(h, xs, X64, sampled, sample_rows, stream, torch, dev, order)
 
