@@ -209,7 +209,7 @@ void whff_graph_destroy(whff_graph* g);
 
 /* ------------------------------------------------------- tuning and batches */
 /* Launch shape of the fixed-allocation (WZ2) kernels: blocks kept in flight
- * per lane (2 or 4), resident CTAs per SM of the persistent grid, and the
+ * per lane (2, 4 or 8), resident CTAs per SM of the persistent grid, and the
  * fold flags: WHFF_FOLD_FP32_PAIRS folds a band's 32 lane sums as FP32
  * (hi, lo) pairs with TwoSum, widened once, instead of widening to FP64 and
  * adding in FP64 (cheaper on GB300's small FP64 pipe; pays on short bands);

@@ -845,9 +845,9 @@ extern "C" int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_
 }
 
 extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int fold) {
-  if (!h || !is_wz2(h) || (unroll != 2 && unroll != 4) || ctas_per_sm < 1 || fold < 0 || fold > 3 ||
-      (unroll == 4 && (fold & WHFF_FOLD_LANE_GROUPS))) {
-    set_error("whff_set_config: WZ2 handles only; unroll 2 or 4 (2 with lane groups); ctas_per_sm >= 1; fold 0..3");
+  if (!h || !is_wz2(h) || (unroll != 2 && unroll != 4 && unroll != 8) || ctas_per_sm < 1 || fold < 0 || fold > 3 ||
+      (unroll != 2 && (fold & WHFF_FOLD_LANE_GROUPS))) {
+    set_error("whff_set_config: WZ2 handles only; unroll 2, 4 or 8 (2 with lane groups); ctas_per_sm >= 1; fold 0..3");
     return WHFF_EINVAL;
   }
   const int occ = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, unroll);
@@ -894,11 +894,12 @@ extern "C" int whff_tune(whff_handle* h, int iters, void* stream, double* best_m
   int bu = orig_u, bc = orig_c, bf = orig_f;
   int err = WHFF_OK;
   // candidates: the top three CTA counts per SM x (unroll 2 with each of the four
-  // folds, unroll 4 with the two whole-warp folds)
-  for (int cand = 0; cand < 18 && err == WHFF_OK; ++cand) {
-    const int u = cand < 12 ? 2 : 4;
+  // folds, unroll 4 and 8 with the two whole-warp folds)
+  for (int cand = 0; cand < 24 && err == WHFF_OK; ++cand) {
+    const int u = cand < 12 ? 2 : cand < 18 ? 4 : 8;
     const int f = (cand & 1) | (cand < 12 && (cand & 2) ? WHFF_FOLD_LANE_GROUPS : 0);
-    const int c = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, u) - (cand < 12 ? cand / 4 : (cand - 12) / 2);
+    const int c = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, u) -
+                  (cand < 12 ? cand / 4 : cand < 18 ? (cand - 12) / 2 : (cand - 18) / 2);
     if (c < 1) continue;
     if ((err = apply_config(h, u, c, f)) != WHFF_OK) break;
     if ((err = whff_step(h, h->d_x, 1, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream)) != WHFF_OK) break;

@@ -25,7 +25,8 @@ static int wz2_launch_lift(const Wz2Step& a, cudaStream_t st) {
     }
   } else switch (a.R) {
     case 1:
-      if (a.unroll == 4) wz2_launch_one<RATE, LIFT, 1, 4>(a, st);
+      if (a.unroll == 8) wz2_launch_one<RATE, LIFT, 1, 8>(a, st);
+      else if (a.unroll == 4) wz2_launch_one<RATE, LIFT, 1, 4>(a, st);
       else wz2_launch_one<RATE, LIFT, 1, 2>(a, st);
       break;
     case 2: wz2_launch_one<RATE, LIFT, 2, 2>(a, st); break;
@@ -86,17 +87,21 @@ int wz2_decompress(const uint8_t* stream, int64_t M, int64_t N, int64_t BN, int6
   return 0;
 }
 
+template <int RATE, bool LIFT>
+static cudaError_t wz2_occ_lift(int* occ, int unroll, int threads) {
+  if (unroll == 8)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::wz2_gemv_kernel<RATE, LIFT, 1, 8, 32>, threads, 0);
+  if (unroll == 4)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::wz2_gemv_kernel<RATE, LIFT, 1, 4, 32>, threads, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::wz2_gemv_kernel<RATE, LIFT, 1, 2, 32>, threads, 0);
+}
+
 template <int RATE>
 int wz2_occupancy(bool lift, int unroll) {
   int occ = 0;
-  cudaError_t e;
   const int threads = dev::kWarpsPerCta * 32;
-  if (lift)
-    e = unroll == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, true, 1, 4, 32>, threads, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, true, 1, 2, 32>, threads, 0);
-  else
-    e = unroll == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, false, 1, 4, 32>, threads, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dev::wz2_gemv_kernel<RATE, false, 1, 2, 32>, threads, 0);
+  const cudaError_t e = lift ? wz2_occ_lift<RATE, true>(&occ, unroll, threads)
+                             : wz2_occ_lift<RATE, false>(&occ, unroll, threads);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;

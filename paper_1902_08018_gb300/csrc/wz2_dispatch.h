@@ -23,7 +23,7 @@ struct Wz2Step {
   double* state;
   double decay;
   int64_t ctas;    // grid size (persistent)
-  int unroll;      // blocks in flight per lane: 2 or 4 (R = 1), 2 otherwise
+  int unroll;      // blocks in flight per lane: 2, 4 or 8 (R = 1), 2 otherwise
   bool lift;
   int R;           // 1, 2, 4 or 8
   bool red32;      // fold lanes with the FP32 pair butterfly (short bands)

@@ -231,13 +231,13 @@ __device__ __forceinline__ void wz2_block_partial(const uint32_t (&w)[Wz2Layout<
 // lane's blocks are taken in pairs (its 1st and 2nd, 3rd and 4th, ...), each
 // pair's two scaled partials are added and the sum enters the TwoSum; an odd
 // last block enters alone.  So every right-hand side gets the same rounding
-// whatever R, UNROLL or the batch it is in.  UNROLL (2 or 4) blocks per lane
+// whatever R, UNROLL or the batch it is in.  UNROLL (2, 4 or 8) blocks per lane
 // are kept in flight: their loads are issued before any is decoded.
 template <int RATE, bool LIFT, int R, int UNROLL, int STRIDE = 32, bool PRE = false>
 __device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int64_t J0, int64_t J1, int lane,
                                           const float* __restrict__ x, int64_t ldx, int64_t N, bool x_fast,
                                           bool x_vec_ok, float (&hi)[4][R], float (&lo)[4][R]) {
-  static_assert(UNROLL == 2 || UNROLL == 4, "blocks are consumed in pairs");
+  static_assert(UNROLL == 2 || UNROLL == 4 || UNROLL == 8, "blocks are consumed in pairs");
   constexpr int NW = Wz2Layout<RATE>::kWords;
   int64_t J = J0 + lane;
   for (; J + STRIDE * (UNROLL - 1) < J1; J += STRIDE * UNROLL) {

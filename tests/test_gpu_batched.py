@@ -88,7 +88,7 @@ def test_tuner_keeps_results(env, orc, tmp_path):
     cache = str(tmp_path / "tune.json")
     with W.whff_create(blob) as h:
         rec = h.tune(iters=3, cache=cache)
-        assert rec["unroll"] in (2, 4) and rec["ctas_per_sm"] >= 1 and rec["fold"] in (0, 1, 2, 3)
+        assert rec["unroll"] in (2, 4, 8) and rec["ctas_per_sm"] >= 1 and rec["fold"] in (0, 1, 2, 3)
         assert not rec["cached"]
         y = torch.zeros(3000, dtype=torch.float64, device="cuda")
         h.step(x, y)
@@ -96,11 +96,19 @@ def test_tuner_keeps_results(env, orc, tmp_path):
         assert _rel(y.cpu().numpy(), ref) <= TOL
         y0 = y.clone()
         c, f = rec["ctas_per_sm"], rec["fold"]
-        for u in ((2, 4) if f < 2 else (2,)):  # blocks in flight change the schedule, not the arithmetic
-            h.set_config(u, c, f)
-            h.step(x, y)
-            torch.cuda.synchronize()
-            assert torch.equal(y, y0)
+        for cc in (c, 1):  # blocks in flight change the schedule, not the arithmetic
+            ys = []
+            for u in ((2, 4, 8) if f < 2 else (2,)):
+                try:
+                    h.set_config(u, cc, f)
+                except W.WhffError:  # more CTAs per SM than this unroll keeps resident
+                    continue
+                h.step(x, y)
+                torch.cuda.synchronize()
+                ys.append(y.clone())
+            assert ys and all(torch.equal(v, ys[0]) for v in ys)
+            if cc == c:
+                assert torch.equal(ys[0], y0)
         for u, c2, r2 in ((2, 1, 0), (2, 1, 1), (2, c, 2), (2, c, 3), (4, c, 1 - (f & 1))):  # other partitions / folds
             h.set_config(u, c2, r2)
             assert h.config() == (u, c2, r2)
@@ -113,6 +121,10 @@ def test_tuner_keeps_results(env, orc, tmp_path):
             h.set_config(2, 1, 4)
         with pytest.raises(W.WhffError):
             h.set_config(4, 1, 2)  # lane groups take unroll 2
+        with pytest.raises(W.WhffError):
+            h.set_config(8, 1, 2)
+        with pytest.raises(W.WhffError):
+            h.set_config(16, 1, 0)
     with W.whff_create(blob) as h2:
         rec2 = h2.tune(iters=3, cache=cache)
         assert rec2["cached"] and rec2["unroll"] == rec["unroll"]
