@@ -577,6 +577,8 @@ def run_serve(args, rank, world, local_rank):
         km = workloads.KernelMatrix(n, g, n, 0.05, workloads.SEED_BASE + 5 + 1000 * k)
         blob = W.whff_compress_bands(n, n, km.bands(2048), fmt, rate)
         handles.append(W.whff_create(blob, max_rhs=8))
+        if not args.no_tune and fmt in (5, 6):  # launch shape and engine crossover per model, on this machine
+            handles[-1].tune(iters=5)
         blobs_bytes.append(blob.size - 64)
         del blob
     setup_s = time.perf_counter() - t0
@@ -632,6 +634,7 @@ def run_serve(args, rank, world, local_rank):
     streamed = sum(blobs_bytes[model[keep][i]] / bat[i] for i in np.nonzero(served)[0])
     wall = float(np.max(arrival[keep] + lat)) if len(arrival) else 0.0
     lat_us = lat_us[served]
+    shapes = [list(h.config()) + [h.crossover] if fmt in (5, 6) else None for h in handles]  # before destroy
     for h in handles:
         h.destroy()
     return {
@@ -640,7 +643,8 @@ def run_serve(args, rank, world, local_rank):
         "n_gpus": world, "config": {"workload": f"serving-{len(orders)}-models-{fmt_name}-{rate}", "orders": orders,
                                     "arrival_hz_per_model": args.serve_hz, "seconds": args.serve_seconds,
                                     "deadline_us": args.deadline_us, "max_batch": 8, "streams": 8,
-                                    "hbm_budget_bytes": budget},
+                                    "hbm_budget_bytes": budget,
+                                    "launch_shapes": shapes},
         "admitted": admitted, "refused": refused, "requests": int(keep.sum()),
         "p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
         "p999_us": float(np.percentile(lat_us, 99.9)), "miss_rate": float(miss.mean()),
