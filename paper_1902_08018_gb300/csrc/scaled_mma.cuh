@@ -176,15 +176,14 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
       hi[r] = lo[r] = 0.f;
     }
   };
-  // drain accumulator group `acc` of tile `tile`, whose stages lie in scale
-  // tile column `tc`: s (sum of the three accumulators) enters the TwoSum sums
-  // with the exact rounding error of the product
-  auto drain = [&](int acc, int tile, int tc) {
+  // drain accumulator group `acc` of tile `tile`, whose tile scale is s:
+  // s (sum of the three accumulators) enters the TwoSum sums with the exact
+  // rounding error of the product
+  auto drain = [&](int acc, int tile, float s) {
     if (tile != cur_tile) {
       flush();
       cur_tile = tile;
     }
-    const float s = __ldg(scales + (int64_t)tile * TN + tc);
     const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(3 * acc * NR + c0);
 #pragma unroll
     for (int h = 0; h < HALF; h += 8) {
@@ -206,7 +205,8 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
   // columns) of one tile share an accumulator group (alternating 0, 1)
   int gpos = 0, gacc = 0;
   bool p_ends = false;
-  int p_acc = 0, p_tile = tile0, p_tc = st0 >> 1;
+  int p_acc = 0, p_tile = tile0;
+  float p_s = 0.f;  // the closed group's tile scale, loaded a stage before its drain
   if (n > 0) {
     fetch(0);
     if (t == 0) b_copy(0);
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (t == 0 && ok && k + 1 < n) b_copy(k + 1);
-        if (p_ends) drain(p_acc, p_tile, p_tc);
+        if (p_ends) drain(p_acc, p_tile, p_s);
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       }
     } else if (t == 0 && ok && k + 1 < n) {
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
     p_ends = ends;
     p_acc = acc;
     p_tile = tile_k;
-    p_tc = tc_k;
+    if (ends) p_s = __ldg(scales + (int64_t)tile_k * TN + tc_k);
     return true;
   };
 
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
     const int buf = (int)((n - 1) & 1);
     if (__all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * buf, (uint32_t)(((n - 1) >> 1) & 1)))) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      drain(p_acc, p_tile, p_tc);
+      drain(p_acc, p_tile, p_s);
       flush();
     } else if (lane == 0) {
       fail();
