@@ -86,6 +86,10 @@ def lib():
             "orc_wz2_width": (c_int, [c_int]),
             "orc_wz2_encode_block": (c_int, [P, c_int, c_int, P]),
             "orc_wz2_decode_block": (None, [P, c_int, c_int, P]),
+            "orc_wz3_block": (c_int, [P, ctypes.c_double, c_int, P, P, P, P]),
+            "orc_wz3_block_bytes": (c_int, [c_int]),
+            "orc_wz3_encode_run": (c_int, [P, c_int, ctypes.c_double, c_int, P, P]),
+            "orc_wz3_decode_block": (None, [P, c_int, c_int, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -195,6 +199,37 @@ def wz2_decode_block(words, rate: int, lift: bool) -> np.ndarray:
     w = np.ascontiguousarray(words, dtype=np.uint64)
     out = np.zeros(16, dtype=np.float64)
     lib().orc_wz2_decode_block(_p(w), int(rate), int(bool(lift)), _p(out))
+    return out.reshape(4, 4)
+
+
+def wz3_block(a, tol: float, lift: bool = True):
+    """(emax, K, v[16] in sequency order, width the block needs) of the fixed-accuracy reading."""
+    f = np.ascontiguousarray(a, dtype=np.float32).reshape(16)
+    v = np.zeros(16, dtype=np.int64)
+    e, k, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().orc_wz3_block(_p(f), float(tol), int(bool(lift)), ctypes.byref(e), ctypes.byref(k), _p(v),
+                               ctypes.byref(w)), "wz3_block")
+    return e.value, k.value, v, w.value
+
+
+def wz3_block_bytes(W: int) -> int:
+    return int(lib().orc_wz3_block_bytes(int(W)))
+
+
+def wz3_encode_run(blocks, tol: float, lift: bool = True):
+    """Encode up to 32 blocks (n x 4 x 4) as one run: (words, W)."""
+    b = np.ascontiguousarray(blocks, dtype=np.float32).reshape(-1, 16)
+    words = np.zeros(b.shape[0] * wz3_block_bytes(31) // 8, dtype=np.uint64)
+    w = ctypes.c_int()
+    _check(lib().orc_wz3_encode_run(_p(b), b.shape[0], float(tol), int(bool(lift)), _p(words), ctypes.byref(w)),
+           "wz3_encode_run")
+    return words[: b.shape[0] * wz3_block_bytes(w.value) // 8].copy(), w.value
+
+
+def wz3_decode_block(words, W: int, lift: bool = True) -> np.ndarray:
+    w = np.ascontiguousarray(words, dtype=np.uint64)
+    out = np.zeros(16, dtype=np.float64)
+    lib().orc_wz3_decode_block(_p(w), int(W), int(bool(lift)), _p(out))
     return out.reshape(4, 4)
 
 

@@ -375,6 +375,108 @@ void orc_wz2_decode_block(const uint64_t* words, int rate, int lift, double out[
   }
 }
 
+/* ------------------------------------------- WZ3 (fixed accuracy, planned) */
+/* The decoded block of WZ2's layout for coefficients v (sequency order with
+ * the lift), shift K and exponent emax: the same formulas as
+ * orc_wz2_decode_block, written once more here for a given v. */
+static void wz3_values(const int64_t v[16], int K, int emax, int lift, double out[16]) {
+  int64_t V[16], T[16];
+  int perm[16];
+  orc_sequency(perm);
+  for (int k = 0; k < 16; k++) V[lift ? perm[k] : k] = v[k];
+  if (lift) {
+    sandwich(G2, V, T);
+    for (int i = 0; i < 16; i++) out[i] = ldexp((double)T[i], K + emax - 30);
+  } else {
+    for (int i = 0; i < 16; i++) out[i] = ldexp((double)V[i], K + emax - WZ2_PREC);
+  }
+}
+
+int orc_wz3_block(const float a[16], double tol, int lift, int* emax_out, int* K_out, int64_t v[16],
+                  int* need_w) {
+  for (int k = 0; k < 16; k++) v[k] = 0;
+  *emax_out = 0;
+  *K_out = 0;
+  *need_w = 0;
+  if (!(tol >= 0.0)) return ORC_EINVAL;
+  int emax = WZ1_EMIN - 1000;
+  for (int i = 0; i < 16; i++) {
+    if (!isfinite(a[i])) return ORC_ENONFINITE;
+    if (fabs((double)a[i]) >= ldexp(1.0, 127)) return ORC_ERANGE;
+    if (a[i] != 0.0f) {
+      int e;
+      frexp((double)a[i], &e);
+      if (e > emax) emax = e;
+    }
+  }
+  if (emax <= WZ1_EMIN) return ORC_OK; /* zero block */
+  int64_t q[16], c[16], seq[16];
+  for (int i = 0; i < 16; i++) q[i] = (int64_t)trunc(ldexp((double)a[i], WZ2_PREC - emax));
+  if (lift)
+    sandwich(F4, q, c);
+  else
+    for (int i = 0; i < 16; i++) c[i] = q[i];
+  int perm[16];
+  orc_sequency(perm);
+  for (int k = 0; k < 16; k++) seq[k] = lift ? c[perm[k]] : c[k];
+  /* the largest shift whose decoded block stays within tol of a (else K = 0) */
+  int K;
+  for (K = WZ2_KMAX; K >= 0; K--) {
+    int64_t t[16];
+    double d[16], err = 0.0;
+    for (int k = 0; k < 16; k++) t[k] = (int64_t)nearbyint(ldexp((double)seq[k], -K));
+    wz3_values(t, K, emax, lift, d);
+    for (int i = 0; i < 16; i++) err = fmax(err, fabs((double)a[i] - d[i]));
+    if (err <= tol || K == 0) {
+      for (int k = 0; k < 16; k++) v[k] = t[k];
+      break;
+    }
+  }
+  int W = 1;
+  for (int k = 0; k < 16; k++)
+    while (v[k] < -((int64_t)1 << (W - 1)) || v[k] > ((int64_t)1 << (W - 1)) - 1) W++;
+  *emax_out = emax;
+  *K_out = K;
+  *need_w = W;
+  return ORC_OK;
+}
+
+int orc_wz3_block_bytes(int W) { return 8 * ((13 + 16 * W + 63) / 64); }
+
+int orc_wz3_encode_run(const float* blocks, int nb, double tol, int lift, uint64_t* words, int* w_run) {
+  if (nb < 1 || nb > 32) return ORC_EINVAL;
+  int emax[32], K[32], need[32];
+  int64_t v[32][16];
+  int W = 0;
+  for (int b = 0; b < nb; b++) {
+    int e = orc_wz3_block(blocks + 16 * b, tol, lift, &emax[b], &K[b], v[b], &need[b]);
+    if (e != ORC_OK) return e;
+    if (need[b] > W) W = need[b];
+  }
+  const int nw = orc_wz3_block_bytes(W) / 8;
+  for (int i = 0; i < nb * nw; i++) words[i] = 0;
+  for (int b = 0; b < nb; b++) {
+    uint64_t* w = words + (int64_t)b * nw;
+    if (need[b] == 0) continue; /* zero block: all bits zero */
+    put_bits(w, 0, (uint64_t)(emax[b] + 127), 8);
+    put_bits(w, 8, (uint64_t)K[b], 5);
+    for (int k = 0; k < 16; k++)
+      put_bits(w, 13 + (int64_t)W * k, (uint64_t)(v[b][k] + ((int64_t)1 << (W - 1))), W);
+  }
+  *w_run = W;
+  return ORC_OK;
+}
+
+void orc_wz3_decode_block(const uint64_t* words, int W, int lift, double out[16]) {
+  for (int i = 0; i < 16; i++) out[i] = 0.0;
+  const int E = (int)get_bits(words, 0, 8);
+  if (E == 0 || W < 1) return;
+  const int K = (int)get_bits(words, 8, 5);
+  int64_t v[16];
+  for (int k = 0; k < 16; k++) v[k] = (int64_t)get_bits(words, 13 + (int64_t)W * k, W) - ((int64_t)1 << (W - 1));
+  wz3_values(v, K, E - 127, lift, out);
+}
+
 /* --------------------------------------------------------- scaled formats */
 /* Per 128x128 tile b: amax = max |a| (FP64); s = RN_fp32(amax / FMTMAX),
  * s = 1 when amax = 0; q = RN_fmt(a / s) with the quotient in FP64 and

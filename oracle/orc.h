@@ -109,6 +109,25 @@ int orc_wz2_width(int rate);
 int orc_wz2_encode_block(const float a[16], int rate, int lift, uint64_t* words);
 void orc_wz2_decode_block(const uint64_t* words, int rate, int lift, double out[16]);
 
+/* ---- WZ3: fixed accuracy (planned device format; oracle and pins only) ----
+ * zfp's fixed-accuracy mode (Sec. 4.3 names zfp; its modes other than fixed
+ * rate are the paper's outlook) read GPU-first: WZ2's blocks, exponent,
+ * transform and bit layout, but per block the LARGEST shift K in 0..27 whose
+ * decoded block stays within tol of the FP32 input (max absolute error; K = 0
+ * when none does: the format's floor, WZ2's truncation), and per run of up to
+ * 32 blocks of a band ONE field width: the largest width the run's blocks
+ * need (a block needs the smallest W >= 1 holding its round-half-even
+ * C/2^K in W-bit two's complement; 0 for a zero block).  Every block of a run
+ * takes 8 * ceil((13 + 16 W) / 64) bytes: header 8 bits emax+127 (0 = zero
+ * block), 5 bits K, then 16 offset-binary W-bit fields from bit 13, the rest
+ * zero -- exactly WZ2's layout with W chosen per run. */
+int orc_wz3_block(const float a[16], double tol, int lift, int* emax, int* K, int64_t v[16], int* need_w);
+int orc_wz3_block_bytes(int W);
+/* Encode nb (1..32) blocks (nb x 16 floats, row-major 4x4 each) as one run;
+ * words receives nb * block_bytes(W)/8 words; *w_run = W. */
+int orc_wz3_encode_run(const float* blocks, int nb, double tol, int lift, uint64_t* words, int* w_run);
+void orc_wz3_decode_block(const uint64_t* words, int W, int lift, double out[16]);
+
 /* ---- whole matrices ---- */
 int orc_rate_ok(int rate);
 size_t orc_blob_size(int fmt, int rate, int64_t M, int64_t N);

@@ -1,0 +1,132 @@
+"""Pins of the oracle's fixed-accuracy reading (WZ3, the planned device format
+for zfp's fixed-accuracy mode): every decoded block within the tolerance of
+its FP32 input, the shift the largest that achieves it, the field width the
+smallest that holds it (the run's width the largest of its blocks), the bit
+layout exactly WZ2's with the width chosen per run, and at WZ2's own error a
+WZ3 block never costs more bits than WZ2's fixed rate."""
+import numpy as np
+import pytest
+
+
+def _blocks(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        kind = k % 4
+        if kind == 0:  # smooth: a plane plus a small bump
+            i, j = np.mgrid[0:4, 0:4]
+            b = 1.0 + 0.1 * i + 0.05 * j + 0.01 * rng.standard_normal((4, 4))
+        elif kind == 1:
+            b = rng.standard_normal((4, 4))
+        elif kind == 2:
+            b = rng.standard_normal((4, 4)) * 2.0 ** rng.integers(-40, 40)
+        else:
+            b = np.exp(-rng.random((4, 4)))  # all positive, like kernel entries
+        out.append(b.astype(np.float32))
+    return out
+
+
+def _err(orc, words, W, a, lift):
+    return float(np.abs(orc.wz3_decode_block(words, W, lift) - a.astype(np.float64)).max())
+
+
+@pytest.mark.parametrize("lift", [True, False])
+@pytest.mark.parametrize("p", [4, 8, 12, 16, 20])
+def test_decoded_block_within_tolerance_when_reachable(orc, lift, p):
+    for a in _blocks(24, p):
+        tol = float(np.abs(a).max()) * 2.0**-p
+        emax, K, v, need = orc.wz3_block(a, tol, lift)
+        words, W = orc.wz3_encode_run(a[None], tol, lift)
+        assert W == need
+        err = _err(orc, words, W, a, lift)
+        if err > tol:  # unreachable: the floor, K = 0, the finest quantisation there is
+            assert K == 0
+            w0, W0 = orc.wz3_encode_run(a[None], 0.0, lift)
+            assert _err(orc, w0, W0, a, lift) == err
+        else:
+            assert err <= tol, (K, err, tol)
+
+
+@pytest.mark.parametrize("lift", [True, False])
+def test_shift_is_the_largest_and_width_the_smallest(orc, lift):
+    for a in _blocks(40, 7):
+        tol = float(np.abs(a).max()) * 2.0**-10
+        emax, K, v, need = orc.wz3_block(a, tol, lift)
+        # width: v fits in `need` bits, not in need - 1
+        assert v.min() >= -(2 ** (need - 1)) and v.max() <= 2 ** (need - 1) - 1
+        if need > 1:
+            assert v.min() < -(2 ** (need - 2)) or v.max() > 2 ** (need - 2) - 1
+        # shift: the block's own error at K is its tolerance's witness; any
+        # tolerance below that error forces a smaller shift
+        words, W = orc.wz3_encode_run(a[None], tol, lift)
+        err = _err(orc, words, W, a, lift)
+        if K > 0 and err > 0:
+            _, K2, _, _ = orc.wz3_block(a, np.nextafter(err, 0.0), lift)
+            assert K2 < K
+        _, K3, _, _ = orc.wz3_block(a, err, lift)
+        assert K3 >= K
+
+
+@pytest.mark.parametrize("lift", [True, False])
+@pytest.mark.parametrize("rate", [8, 12, 16, 20, 24])
+def test_same_layout_as_wz2_and_never_more_bits_at_its_error(orc, lift, rate):
+    W2 = orc.wz2_width(rate)
+    for a in _blocks(16, rate):
+        w2 = orc.wz2_encode_block(a, rate, lift)
+        d2 = orc.wz2_decode_block(w2, rate, lift)
+        # the layouts coincide: WZ2's words read as a WZ3 block of width W2
+        assert np.array_equal(orc.wz3_decode_block(w2, W2, lift), d2)
+        e2 = float(np.abs(d2 - a.astype(np.float64)).max())
+        emax, K, v, need = orc.wz3_block(a, e2, lift)
+        words, W = orc.wz3_encode_run(a[None], e2, lift)
+        assert _err(orc, words, W, a, lift) <= e2
+        assert orc.wz3_block_bytes(need) <= orc.wz3_block_bytes(W2) <= 2 * rate
+
+
+def test_zero_blocks_and_exact_blocks(orc):
+    z = np.zeros((4, 4), dtype=np.float32)
+    emax, K, v, need = orc.wz3_block(z, 1e-3)
+    assert need == 0 and (v == 0).all()
+    words, W = orc.wz3_encode_run(z[None], 1e-3)
+    assert W == 0 and words.size == 1 and words[0] == 0
+    assert (orc.wz3_decode_block(words, W) == 0).all()
+    # dyadic small integers: exact at tolerance 0
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        a = (rng.integers(-8, 8, (4, 4)) * 2.0 ** int(rng.integers(-5, 5))).astype(np.float32)
+        for lift in (True, False):
+            words, W = orc.wz3_encode_run(a[None], 0.0, lift)
+            assert np.array_equal(orc.wz3_decode_block(words, W, lift), a.astype(np.float64))
+
+
+def test_run_width_bytes_and_monotonic_tolerance(orc):
+    blocks = _blocks(32, 11)
+    blocks[5] = np.zeros((4, 4), dtype=np.float32)
+    tol = 1e-4
+    words, W = orc.wz3_encode_run(np.stack(blocks), tol)
+    needs = [orc.wz3_block(b, tol)[3] for b in blocks]
+    assert W == max(needs)
+    nb = orc.wz3_block_bytes(W)
+    assert nb == 8 * ((13 + 16 * W + 63) // 64) and words.size * 8 == 32 * nb
+    for k, b in enumerate(blocks):  # every block decodes from its own slot
+        d = orc.wz3_decode_block(words[k * nb // 8:(k + 1) * nb // 8], W)
+        assert np.array_equal(d, orc.wz3_decode_block(orc.wz3_encode_run(b[None], tol)[0], orc.wz3_block(b, tol)[3]))
+    assert (orc.wz3_decode_block(words[5 * nb // 8:6 * nb // 8], W) == 0).all()
+    for b in blocks[:12]:  # a larger tolerance never takes a smaller shift or a wider field
+        prev_k, prev_w = -1, 99
+        for t in (1e-8, 1e-6, 1e-4, 1e-2, 1.0):
+            _, K, _, need = orc.wz3_block(b, t)
+            assert K >= prev_k and need <= prev_w
+            prev_k, prev_w = K, need
+
+
+def test_errors(orc):
+    a = np.ones((4, 4), dtype=np.float32)
+    with pytest.raises(RuntimeError):
+        orc.wz3_block(a, -1.0)
+    bad = a.copy()
+    bad[0, 0] = np.inf
+    with pytest.raises(RuntimeError):
+        orc.wz3_block(bad, 1e-3)
+    with pytest.raises(RuntimeError):
+        orc.wz3_encode_run(np.ones((33, 4, 4), dtype=np.float32), 1e-3)
