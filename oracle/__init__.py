@@ -30,6 +30,7 @@ FMT_FP8E4M3 = 4
 FMT_FIXED_LIFT = 5
 FMT_FIXED_BFP = 6
 FMT_FP32 = 7
+FMT_FIXED_ACC = 8
 HEADER_BYTES = 64
 
 
@@ -90,6 +91,9 @@ def lib():
             "orc_wz3_block_bytes": (c_int, [c_int]),
             "orc_wz3_encode_run": (c_int, [P, c_int, ctypes.c_double, c_int, P, P]),
             "orc_wz3_decode_block": (None, [P, c_int, c_int, P]),
+            "orc_wz3_max_blob_size": (c_sz, [c_i64, c_i64]),
+            "orc_wz3_encode_matrix": (c_int, [P, c_i64, c_i64, c_i64, ctypes.c_double, P, c_sz, P]),
+            "orc_wz3_decode_matrix": (c_int, [P, c_sz, P, c_i64, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -231,6 +235,28 @@ def wz3_decode_block(words, W: int, lift: bool = True) -> np.ndarray:
     out = np.zeros(16, dtype=np.float64)
     lib().orc_wz3_decode_block(_p(w), int(W), int(bool(lift)), _p(out))
     return out.reshape(4, 4)
+
+
+def wz3_encode(A: np.ndarray, tol: float) -> bytes:
+    """Whole matrix in the fixed-accuracy layout (with the lift): a blob of variable length."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    M, N = A.shape
+    cap = int(lib().orc_wz3_max_blob_size(M, N))
+    buf = np.zeros(cap, dtype=np.uint8)
+    n = ctypes.c_size_t()
+    _check(lib().orc_wz3_encode_matrix(_p(A), M, N, N, float(tol), _p(buf), cap, ctypes.byref(n)), "wz3_encode")
+    return buf[: n.value].tobytes()
+
+
+def wz3_decode(blob: bytes):
+    """(decoded FP64 matrix, tolerance) of a fixed-accuracy blob."""
+    b = np.frombuffer(blob, dtype=np.uint8)
+    M = int(np.frombuffer(blob[16:24], dtype=np.int64)[0])
+    N = int(np.frombuffer(blob[24:32], dtype=np.int64)[0])
+    out = np.zeros((M, N), dtype=np.float64)
+    tol = ctypes.c_double()
+    _check(lib().orc_wz3_decode_matrix(_p(b), b.size, _p(out), N, ctypes.byref(tol)), "wz3_decode")
+    return out, tol.value
 
 
 # ---------------------------------------------------------- whole matrices

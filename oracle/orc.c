@@ -822,3 +822,102 @@ void orc_state_update(double* s, int64_t M, const double* Y, int R, int64_t ldy,
   for (int r = 0; r < R; r++)
     for (int64_t i = 0; i < M; i++) s[i] = decay * s[i] + Y[(size_t)r * ldy + i];
 }
+
+/* ------------------------------------------- WZ3 matrix layout (planned) */
+/* Stream: [tol: f64] [index: one u64 per run, band-major; bits 0..55 the
+ * byte offset of the run's first block within the block area, bits 56..63
+ * its width W] [block area: the runs one after another].  A run is up to 32
+ * consecutive blocks of one band (the last run of a band may be shorter).
+ * Edge blocks replicate the last valid row, then column, as WZ1/WZ2. */
+static int64_t wz3_runs_per_band(int64_t N) { return cdiv(cdiv(N, 4), 32); }
+
+size_t orc_wz3_max_blob_size(int64_t M, int64_t N) {
+  if (M <= 0 || N <= 0) return 0;
+  const int64_t BM = cdiv(M, 4), BN = cdiv(N, 4);
+  return ORC_HEADER_BYTES + 8 + 8 * (size_t)(BM * wz3_runs_per_band(N)) +
+         (size_t)(BM * BN) * (size_t)orc_wz3_block_bytes(31);
+}
+
+int orc_wz3_encode_matrix(const double* A, int64_t M, int64_t N, int64_t lda, double tol, uint8_t* blob, size_t cap,
+                          size_t* len) {
+  if (M <= 0 || N <= 0 || lda < N || !(tol >= 0.0) || cap < orc_wz3_max_blob_size(M, N)) return ORC_EINVAL;
+  const int64_t BM = cdiv(M, 4), BN = cdiv(N, 4), RB = wz3_runs_per_band(N);
+  uint8_t* stream = blob + ORC_HEADER_BYTES;
+  uint8_t* index = stream + 8;
+  uint8_t* area = index + 8 * (size_t)(BM * RB);
+  union {
+    double d;
+    uint64_t u;
+  } t;
+  t.d = tol;
+  wr64(stream, t.u);
+  uint64_t off = 0;
+  float blocks[32 * 16];
+  uint64_t words[32 * 9];
+  for (int64_t I = 0; I < BM; I++)
+    for (int64_t r = 0; r < RB; r++) {
+      const int64_t J0 = 32 * r, nb = (BN - J0) < 32 ? (BN - J0) : 32;
+      for (int64_t b = 0; b < nb; b++)
+        for (int rr = 0; rr < 4; rr++)
+          for (int c = 0; c < 4; c++) {
+            int64_t gi = 4 * I + rr, gj = 4 * (J0 + b) + c;
+            if (gi > M - 1) gi = M - 1;
+            if (gj > N - 1) gj = N - 1;
+            blocks[16 * b + 4 * rr + c] = (float)A[gi * lda + gj];
+          }
+      int W;
+      int e = orc_wz3_encode_run(blocks, (int)nb, tol, 1, words, &W);
+      if (e != ORC_OK) return e;
+      wr64(index + 8 * (size_t)(I * RB + r), off | ((uint64_t)W << 56));
+      const int64_t nbytes = nb * orc_wz3_block_bytes(W);
+      for (int64_t k = 0; k < nbytes / 8; k++) wr64(area + off + 8 * (uint64_t)k, words[k]);
+      off += (uint64_t)nbytes;
+    }
+  const size_t sbytes = 8 + 8 * (size_t)(BM * RB) + (size_t)off;
+  write_header(blob, ORC_FMT_FIXED_ACC, 0, M, N, sbytes);
+  *len = ORC_HEADER_BYTES + sbytes;
+  return ORC_OK;
+}
+
+int orc_wz3_decode_matrix(const uint8_t* blob, size_t len, double* out, int64_t ldo, double* tol) {
+  if (len < ORC_HEADER_BYTES || blob[0] != 'W' || blob[1] != 'Z' || blob[2] != '1' || blob[3] != 0 ||
+      rd32(blob + 4) != 1 || rd32(blob + 44) != orc_crc32(blob, 44) || rd32(blob + 8) != ORC_FMT_FIXED_ACC)
+    return ORC_EFORMAT;
+  const int64_t M = (int64_t)rd64(blob + 16), N = (int64_t)rd64(blob + 24);
+  const uint64_t sb = rd64(blob + 32);
+  if (M <= 0 || N <= 0 || ldo < N || len < ORC_HEADER_BYTES + sb) return ORC_EFORMAT;
+  const uint8_t* stream = blob + ORC_HEADER_BYTES;
+  if (rd32(blob + 40) != orc_crc32(stream, (size_t)sb)) return ORC_EFORMAT;
+  const int64_t BM = cdiv(M, 4), BN = cdiv(N, 4), RB = wz3_runs_per_band(N);
+  if (sb < 8 + 8 * (uint64_t)(BM * RB)) return ORC_EFORMAT;
+  union {
+    double d;
+    uint64_t u;
+  } t;
+  t.u = rd64(stream);
+  if (tol) *tol = t.d;
+  const uint8_t* index = stream + 8;
+  const uint8_t* area = index + 8 * (size_t)(BM * RB);
+  const uint64_t area_bytes = sb - 8 - 8 * (uint64_t)(BM * RB);
+  for (int64_t I = 0; I < BM; I++)
+    for (int64_t r = 0; r < RB; r++) {
+      const uint64_t ent = rd64(index + 8 * (size_t)(I * RB + r));
+      const uint64_t off = ent & ((1ull << 56) - 1);
+      const int W = (int)(ent >> 56);
+      const int64_t J0 = 32 * r, nb = (BN - J0) < 32 ? (BN - J0) : 32;
+      const int bb = orc_wz3_block_bytes(W);
+      if (W > 31 || off + (uint64_t)(nb * bb) > area_bytes) return ORC_EFORMAT;
+      for (int64_t b = 0; b < nb; b++) {
+        uint64_t w[9];
+        for (int k = 0; k < bb / 8; k++) w[k] = rd64(area + off + (uint64_t)(b * bb) + 8 * (uint64_t)k);
+        double v[16];
+        orc_wz3_decode_block(w, W, 1, v);
+        for (int rr = 0; rr < 4; rr++)
+          for (int c = 0; c < 4; c++) {
+            const int64_t gi = 4 * I + rr, gj = 4 * (J0 + b) + c;
+            if (gi < M && gj < N) out[gi * ldo + gj] = v[4 * rr + c];
+          }
+      }
+    }
+  return ORC_OK;
+}

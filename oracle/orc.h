@@ -56,6 +56,7 @@ extern "C" {
 #define ORC_FMT_FIXED_LIFT 5 /* WZ2: fixed-width fields of the linear lift's coefficients */
 #define ORC_FMT_FIXED_BFP 6  /* WZ2 without transform: fixed-width block floating point */
 #define ORC_FMT_FP32 7       /* A rounded to FP32, every tile scale 1 (the uncompressed comparison) */
+#define ORC_FMT_FIXED_ACC 8  /* WZ3: fixed accuracy, variable-length runs (oracle only so far) */
 
 /* Error codes (same meaning as the library's, separate definitions). */
 #define ORC_OK 0
@@ -127,6 +128,15 @@ int orc_wz3_block_bytes(int W);
  * words receives nb * block_bytes(W)/8 words; *w_run = W. */
 int orc_wz3_encode_run(const float* blocks, int nb, double tol, int lift, uint64_t* words, int* w_run);
 void orc_wz3_decode_block(const uint64_t* words, int W, int lift, double out[16]);
+/* Whole matrix, with the lift (fmt ORC_FMT_FIXED_ACC): the usual 64-byte header
+ * (rate 0, M, N, stream bytes, both CRCs), then the stream: the tolerance
+ * (f64), one u64 per run in band-major order (bits 0..55: byte offset of the
+ * run's first block in the block area; bits 56..63: W), then the runs' blocks.
+ * blob must hold orc_wz3_max_blob_size bytes; *len receives the bytes used. */
+size_t orc_wz3_max_blob_size(int64_t M, int64_t N);
+int orc_wz3_encode_matrix(const double* A, int64_t M, int64_t N, int64_t lda, double tol, uint8_t* blob, size_t cap,
+                          size_t* len);
+int orc_wz3_decode_matrix(const uint8_t* blob, size_t len, double* out, int64_t ldo, double* tol);
 
 /* ---- whole matrices ---- */
 int orc_rate_ok(int rate);

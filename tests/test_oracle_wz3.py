@@ -130,3 +130,48 @@ def test_errors(orc):
         orc.wz3_block(bad, 1e-3)
     with pytest.raises(RuntimeError):
         orc.wz3_encode_run(np.ones((33, 4, 4), dtype=np.float32), 1e-3)
+
+
+def _kernel_matrix(M, N, seed):
+    import workloads
+
+    n = max(M, N)
+    g = int(np.ceil(np.sqrt(n)))
+    return workloads.KernelMatrix(n, g, n, 0.1, seed).dense()[:M, :N]
+
+
+@pytest.mark.parametrize("M,N", [(130, 97), (64, 260), (5, 3)])
+def test_matrix_layout_round_trip_and_index(orc, M, N):
+    A = _kernel_matrix(M, N, M + N)
+    A32 = A.astype(np.float32)
+    for tol in (1e-2, 1e-4, 1e-6):
+        blob = orc.wz3_encode(A, tol)
+        D, t = orc.wz3_decode(blob)
+        assert t == tol
+        assert np.abs(D - A32.astype(np.float64)).max() <= tol
+        # the index, read here from the bytes: u64 per run, offset | W << 56
+        BM, BN = -(-M // 4), -(-N // 4)
+        RB = -(-BN // 32)
+        idx = np.frombuffer(blob[64 + 8:64 + 8 + 8 * BM * RB], dtype=np.uint64)
+        off, off_expect = idx & np.uint64((1 << 56) - 1), 0
+        Ws = (idx >> np.uint64(56)).astype(int)
+        # padded blocks replicate the last valid row, then column
+        Ap = np.pad(A32, ((0, 4 * BM - M), (0, 4 * BN - N)), mode="edge")
+        for I in range(BM):
+            for r in range(RB):
+                k = I * RB + r
+                assert int(off[k]) == off_expect
+                blocks = [Ap[4 * I:4 * I + 4, 4 * J:4 * J + 4] for J in range(32 * r, min(BN, 32 * r + 32))]
+                assert Ws[k] == max(orc.wz3_block(b, tol)[3] for b in blocks)
+                off_expect += len(blocks) * orc.wz3_block_bytes(Ws[k])
+        assert len(blob) == 64 + 8 + 8 * BM * RB + off_expect
+
+
+def test_matrix_bytes_fall_with_the_tolerance_and_corruption_is_caught(orc):
+    A = _kernel_matrix(96, 96, 3)
+    sizes = [len(orc.wz3_encode(A, t)) for t in (1e-7, 1e-5, 1e-3, 1e-1)]
+    assert sizes == sorted(sizes, reverse=True)
+    blob = bytearray(orc.wz3_encode(A, 1e-4))
+    blob[200] ^= 1
+    with pytest.raises(RuntimeError):
+        orc.wz3_decode(bytes(blob))
