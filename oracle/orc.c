@@ -376,6 +376,7 @@ void orc_wz2_decode_block(const uint64_t* words, int rate, int lift, double out[
 }
 
 /* ------------------------------------------- WZ3 (fixed accuracy, planned) */
+#define WZ3_WMAX 31 /* widest field: 13 + 16*31 bits fill one 64-byte block */
 /* The decoded block of WZ2's layout for coefficients v (sequency order with
  * the lift), shift K and exponent emax: the same formulas as
  * orc_wz2_decode_block, written once more here for a given v. */
@@ -419,15 +420,28 @@ int orc_wz3_block(const float a[16], double tol, int lift, int* emax_out, int* K
   int perm[16];
   orc_sequency(perm);
   for (int k = 0; k < 16; k++) seq[k] = lift ? c[perm[k]] : c[k];
-  /* the largest shift whose decoded block stays within tol of a (else K = 0) */
+  /* The floor: the smallest shift whose fields fit the widest field the
+   * layout has (WZ3_WMAX bits, one 64-byte block).  With the lift the
+   * coefficients reach 2^32 in magnitude, so K = 0 does not always fit. */
+  int Kfloor;
+  for (Kfloor = 0; Kfloor < WZ2_KMAX; Kfloor++) {
+    int fits = 1;
+    for (int k = 0; k < 16; k++) {
+      const double t = nearbyint(ldexp((double)seq[k], -Kfloor));
+      if (t < -ldexp(1.0, WZ3_WMAX - 1) || t > ldexp(1.0, WZ3_WMAX - 1) - 1.0) fits = 0;
+    }
+    if (fits) break;
+  }
+  /* the largest shift down to the floor whose decoded block stays within tol
+   * of a (else the floor, the finest quantisation the layout holds) */
   int K;
-  for (K = WZ2_KMAX; K >= 0; K--) {
+  for (K = WZ2_KMAX; K >= Kfloor; K--) {
     int64_t t[16];
     double d[16], err = 0.0;
     for (int k = 0; k < 16; k++) t[k] = (int64_t)nearbyint(ldexp((double)seq[k], -K));
     wz3_values(t, K, emax, lift, d);
     for (int i = 0; i < 16; i++) err = fmax(err, fabs((double)a[i] - d[i]));
-    if (err <= tol || K == 0) {
+    if (err <= tol || K == Kfloor) {
       for (int k = 0; k < 16; k++) v[k] = t[k];
       break;
     }

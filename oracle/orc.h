@@ -114,11 +114,13 @@ void orc_wz2_decode_block(const uint64_t* words, int rate, int lift, double out[
  * zfp's fixed-accuracy mode (Sec. 4.3 names zfp; its modes other than fixed
  * rate are the paper's outlook) read GPU-first: WZ2's blocks, exponent,
  * transform and bit layout, but per block the LARGEST shift K in 0..27 whose
- * decoded block stays within tol of the FP32 input (max absolute error; K = 0
- * when none does: the format's floor, WZ2's truncation), and per run of up to
+ * decoded block stays within tol of the FP32 input (max absolute error; when
+ * none does, the floor: the smallest K whose fields fit 31 bits -- the lifted
+ * coefficients reach 2^32, so K = 0 can need 34 -- and the block's error is
+ * then above tol), and per run of up to
  * 32 blocks of a band ONE field width: the largest width the run's blocks
  * need (a block needs the smallest W >= 1 holding its round-half-even
- * C/2^K in W-bit two's complement; 0 for a zero block).  Every block of a run
+ * C/2^K in W-bit two's complement, W <= 31; 0 for a zero block).  Every block of a run
  * takes 8 * ceil((13 + 16 W) / 64) bytes: header 8 bits emax+127 (0 = zero
  * block), 5 bits K, then 16 offset-binary W-bit fields from bit 13, the rest
  * zero -- exactly WZ2's layout with W chosen per run. */

@@ -30,6 +30,26 @@ def _err(orc, words, W, a, lift):
     return float(np.abs(orc.wz3_decode_block(words, W, lift) - a.astype(np.float64)).max())
 
 
+_F4 = np.array([[1, 1, 1, 1], [-2, -2, 2, 2], [-4, 4, 0, 0], [4, -4, -4, 4]], dtype=np.int64)
+
+
+def _floor_shift(a, lift):
+    """The smallest shift whose coefficients, rounded half to even, fit 31-bit fields --
+    computed here from the definition with numpy (24 fraction bits, C = (4F) Q (4F)^T)."""
+    a = a.astype(np.float64)
+    nz = a[a != 0]
+    if nz.size == 0:
+        return 0
+    emax = int(np.frexp(np.abs(nz))[1].max())
+    q = np.trunc(np.ldexp(a, 24 - emax)).astype(np.int64)
+    c = _F4 @ q @ _F4.T if lift else q
+    for K in range(28):
+        v = np.rint(np.ldexp(c.astype(np.float64), -K))
+        if v.min() >= -(2.0**30) and v.max() <= 2.0**30 - 1:
+            return K
+    return 27
+
+
 @pytest.mark.parametrize("lift", [True, False])
 @pytest.mark.parametrize("p", [4, 8, 12, 16, 20])
 def test_decoded_block_within_tolerance_when_reachable(orc, lift, p):
@@ -39,8 +59,8 @@ def test_decoded_block_within_tolerance_when_reachable(orc, lift, p):
         words, W = orc.wz3_encode_run(a[None], tol, lift)
         assert W == need
         err = _err(orc, words, W, a, lift)
-        if err > tol:  # unreachable: the floor, K = 0, the finest quantisation there is
-            assert K == 0
+        if err > tol:  # unreachable: the floor, the finest quantisation 31-bit fields hold
+            assert K == _floor_shift(a, lift)
             w0, W0 = orc.wz3_encode_run(a[None], 0.0, lift)
             assert _err(orc, w0, W0, a, lift) == err
         else:
@@ -175,3 +195,30 @@ def test_matrix_bytes_fall_with_the_tolerance_and_corruption_is_caught(orc):
     blob[200] ^= 1
     with pytest.raises(RuntimeError):
         orc.wz3_decode(bytes(blob))
+
+
+@pytest.mark.parametrize("lift", [True, False])
+def test_full_scale_checkerboard_stays_within_31_bit_fields(orc, lift):
+    """A near-full-scale block whose signs follow the last lift row's pattern drives one
+    lifted coefficient to about 2^32: 34-bit fields at K = 0.  The floor is then the
+    smallest shift that fits 31 bits, the block keeps its 64 bytes, and a whole matrix of
+    such blocks fits the size bound and decodes."""
+    s = np.array([1.0, -1.0, -1.0, 1.0])
+    a = (np.outer(s, s) * (1.0 - 2.0**-20)).astype(np.float32)
+    a[0, 1] = np.float32(-(1.0 - 2.0**-20 - 3 * 2.0**-24))  # an odd fixed-point value: not exact above K = 0
+    emax, K, v, need = orc.wz3_block(a, 0.0, lift)
+    assert need <= 31 and K == _floor_shift(a, lift)
+    if lift:
+        assert K == 2  # about 2^32 needs two shifts to fit in 31 bits
+    words, W = orc.wz3_encode_run(a[None], 0.0, lift)
+    assert W == need and words.size * 8 == orc.wz3_block_bytes(W) <= 64
+    d = orc.wz3_decode_block(words, W, lift)
+    e_floor = float(np.abs(d - a.astype(np.float64)).max())
+    assert e_floor <= 2.0 ** (K - 1) * 25 * 2.0 ** (emax - 30) + 2.0 ** (emax - 24)  # the WZ2 bound at K
+    if not lift:  # the matrix layout takes the lift
+        return
+    A = np.tile(a.astype(np.float64), (2, 2))
+    blob = orc.wz3_encode(A, 0.0)
+    assert len(blob) <= orc.lib().orc_wz3_max_blob_size(8, 8)
+    D, _ = orc.wz3_decode(blob)
+    assert np.array_equal(D[:4, :4], d)
