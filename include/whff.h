@@ -321,8 +321,12 @@ void whff_destroy(whff_handle* h);
  * WHFF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
  * exit; a call whose partials would not fit returns WHFF_EINVAL.  The first
  * call on each device looks up the array's device address (make it before any
- * stream capture).  All calls share the array: calls that overlap on the GPU
- * race and must be serialised by the caller.  Calls no cudaMalloc/cudaFree. */
+ * stream capture); the address is kept for the life of the process, so after
+ * cudaDeviceReset (a new primary context) this entry point must not be used
+ * again in that process.  All calls share the array: calls that overlap on
+ * the GPU race and must be serialised by the caller.  The stream's length is
+ * not passed: stream_dev must hold ceil(M/4)*ceil(N/4)*2*rate bytes, else the
+ * kernel reads past it.  Calls no cudaMalloc/cudaFree. */
 #define WHFF_NOALLOC_SCRATCH_BYTES (4u << 20)
 int whff_step_noalloc(const void* stream_dev, int rate, int64_t M, int64_t N, const float* x, int R, int64_t ldx,
                       double* y, int64_t ldy, double* state, double decay, void* stream);

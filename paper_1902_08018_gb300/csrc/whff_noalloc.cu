@@ -40,6 +40,7 @@ int g_sm_count[kMaxDevices] = {};
 
 // Once per device, with that device current: the device address of the
 // array (the host-side symbol is only a stand-in, not a device address).
+// The address is cached for the process; it does not survive cudaDeviceReset.
 int device_setup(int dev, double** scratch, int* sms) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_scratch_addr[dev]) {

@@ -360,6 +360,10 @@ def whff_step_noalloc(stream_dev, rate: int, M: int, N: int, x, y, state=None, d
 
     if not isinstance(stream_dev, torch.Tensor) or not stream_dev.is_cuda or stream_dev.dtype != torch.uint8:
         raise WhffError(-1, "stream_dev must be a CUDA uint8 tensor")
+    # the C entry point takes no length: a short buffer would be read past its end on the device
+    need = -(-int(M) // 4) * -(-int(N) // 4) * 2 * int(rate)
+    if M <= 0 or N <= 0 or not stream_dev.is_contiguous() or stream_dev.numel() < need:
+        raise WhffError(-1, f"stream_dev holds {stream_dev.numel()} bytes; M={M}, N={N}, rate={rate} need {need}")
     xp, R, ldx = _vec_args(x, N, "x", torch.float32)
     yp, Ry, ldy = _vec_args(y, M, "y", torch.float64)
     if Ry != R:
