@@ -68,6 +68,11 @@ def parse_args():
     p.add_argument("--no-fp64-baseline", action="store_true")
     p.add_argument("--no-host-resident", action="store_true", help="skip the matrix-over-the-link leg")
     p.add_argument("--no-tune", action="store_true", help="time the default launch shape instead of whff_tune's")
+    p.add_argument("--no-slits", action="store_true", help="skip the moving-slit graph leg")
+    p.add_argument("--slit-steps", type=int, default=2000)
+    p.add_argument("--no-fields", action="store_true", help="skip the streamed-field pipeline leg")
+    p.add_argument("--launch-shape", default="",
+                   help="unroll,ctas_per_sm,fold for the headline WZ2 handle instead of tuning (e.g. 4,3,1)")
     p.add_argument("--json-out", default=None)
     p.add_argument("--serve", action="store_true", help="run the serving workload instead of the control loop")
     p.add_argument("--serve-fmt", default="wz2-lift:8")
@@ -353,7 +358,11 @@ def run_whff(args, rank, world, local_rank):
     h = W.whff_create(blobs[head], max_rhs=1)
     stream_bytes = blobs[head].size - 64
     tuned = None
-    if not args.no_tune and head[0] in (5, 6):  # the library's tuner picks the launch shape on this machine
+    if args.launch_shape and head[0] in (5, 6):  # a given shape (e.g. to profile the tuned instantiation alone)
+        u, c, f = (int(v) for v in args.launch_shape.split(","))
+        h.set_config(u, c, f)
+        tuned = {"unroll": u, "ctas_per_sm": c, "fold": f}
+    elif not args.no_tune and head[0] in (5, 6):  # the library's tuner picks the launch shape on this machine
         tuned = h.tune(iters=10, stream=stream)
     ksplit, launches = h.plan()
     if world > 1:
@@ -507,6 +516,12 @@ def run_whff(args, rank, world, local_rank):
                 "traffic": ncu_traffic(f"{head_name}_{order}"), "kernel": kname,
                 "launches_per_step": launches, "frac_of_nominal_8TBs": round(achieved / NOMINAL_HBM_GBS, 4)}
 
+    slits = fields = None
+    if not args.no_slits:
+        slits = slit_graph_leg(W, torch, blobs[head], order, xs, stream, steps=args.slit_steps)
+    if not args.no_fields:
+        fields = field_pipeline_leg(W, torch, dev, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(blobs[head], order, head[1] if head[1] else 16, X64[0], y_gpu)
@@ -547,11 +562,159 @@ def run_whff(args, rank, world, local_rank):
         "multi_rhs": multi,
         "fp64_uncompressed_gemv": fp64,
         "host_resident": host,
+        "slit_graph": slits,
+        "field_pipeline": fields,
         "setup_s": round(t_setup, 1),
     }
     if cpu is not None:
         res["cpu_baseline"] = cpu
     return res
+
+
+# ------------------------------------------------- slits and streamed fields
+def slit_graph_leg(W, torch, blob, order, xs, stream, nrows=378, steps=2000):
+    """One instantiated slit graph moved over the resident control-loop matrix (Sec. 2.1:
+    C_slit of 378 rows, Sec. 5.1's M, fetched from C_field every step): per step the host
+    moves the slit (whff_graph_set_rows: re-capture + in-place parameter update) and
+    replays; device time per replay from CUDA events, host time of the move."""
+    h = W.whff_create(blob, max_rhs=1)
+    y = torch.zeros(order, dtype=torch.float64, device=xs.device)
+    s = torch.zeros(order, dtype=torch.float64, device=xs.device)
+    x = xs[0].clone()
+    offs = [((order - nrows) * (k % 97) // 96) // 4 * 4 for k in range(steps)]
+    g = W.whff_graph_create_rows(h, offs[0], nrows, x, y, s, DECAY, stream)
+    for k in range(20):
+        g.set_rows(offs[k])
+        g.launch(stream)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+    host = []
+    for k in range(steps):
+        t0 = time.perf_counter()
+        g.set_rows(offs[k])
+        host.append(time.perf_counter() - t0)
+        evs[2 * k].record(stream)
+        g.launch(stream)
+        evs[2 * k + 1].record(stream)
+    torch.cuda.synchronize()
+    dev_us = np.array([evs[2 * k].elapsed_time(evs[2 * k + 1]) * 1e3 for k in range(steps)])
+    host_us = np.array(host) * 1e6
+    g.destroy()
+    h.destroy()
+    sb = nrows * order * 2  # rate 16: 2 bytes per value
+    return {"slit_rows": nrows, "field_rows": order, "steps": steps, "bytes_per_step": sb,
+            "replay_us": {"p50": float(np.percentile(dev_us, 50)), "p99": float(np.percentile(dev_us, 99)),
+                          "mean": float(dev_us.mean())},
+            "move_host_us": {"p50": float(np.percentile(host_us, 50)), "p99": float(np.percentile(host_us, 99))},
+            "GB_s_at_p50": round(sb / (np.percentile(dev_us, 50) * 1e-6) / 1e9, 1),
+            "note": "one instantiated graph; the slit offset is updated in place before each replay"}
+
+
+def field_pipeline_leg(W, torch, dev, stream, L=2016, S=256000, slit=378, steps_per_field=20, fields=8):
+    """Sec. 4.3 (Fig. compression_cost, Table comp_metrics) and Sec. 5.2 (Fig.
+    decompression_overhead) on GB300: exposure fields of L x S (the paper's C_field,
+    2067 MB in FP32) cross the CPU-GPU link into two resident slots while the slit steps of
+    the previous field run (20 slits of 378 rows per field).  Measured: the copy of one
+    field (T_tr, compressed and FP32), its 20 slit steps alone (T_comp), the pipelined
+    period and one field's latency, against the table's formulas (T_dec = 0: decode is
+    fused into the step); and the breakdown of Fig. decompression_overhead."""
+    import workloads
+
+    t0 = time.perf_counter()
+    A = workloads.RectKernelMatrix(L, S, 0.05, workloads.SEED_BASE + 80).dense()
+    X = torch.from_numpy(np.random.default_rng(80).standard_normal((steps_per_field, S)).astype(np.float32)).to(dev)
+    offs = [((L - slit) * j // (steps_per_field - 1)) // 4 * 4 for j in range(steps_per_field)]
+    out = {"field": [L, S], "slit_rows": slit, "slit_steps_per_field": steps_per_field, "fields": fields}
+    copy = torch.cuda.Stream(dev)
+    kinds = (("wz2-lift-16", 5, 16), ("fp32", 7, 0))
+    hosts = {}
+    for name, fmt, rate in kinds:
+        blob = W.whff_compress(A, fmt, rate or 16)
+        hosts[name] = torch.from_numpy(blob).pin_memory()
+        del blob
+    del A
+    for name, fmt, rate in kinds:
+        host = hosts.pop(name).numpy()
+        nbytes = host.size - 64
+        x = torch.zeros(S, dtype=torch.float32, device=dev)
+        y = torch.zeros(L, dtype=torch.float64, device=dev)
+        st = torch.zeros(L, dtype=torch.float64, device=dev)
+        align = 4 if fmt in (1, 5, 6) else 128
+        offs_f = [o // align * align for o in offs]
+        F = W.Fields(fmt, rate, L, S, nbuf=2, max_rhs=1, stream=stream)
+        F.load(0, host, copy)
+        h0 = F.acquire(0, stream)
+        g = W.whff_graph_create_rows(h0, offs_f[0], slit, x, y, st, DECAY, stream)
+
+        def field_steps(h):
+            for j, r0 in enumerate(offs_f):
+                x.copy_(X[j], non_blocking=True)
+                g.set_rows(r0, h)
+                g.launch(stream)
+
+        field_steps(h0)
+        F.release(0, stream)
+        torch.cuda.synchronize()
+        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        # the copy alone
+        a, b = ev(), ev()
+        a.record(copy)
+        F.load(1, host, copy)
+        b.record(copy)
+        torch.cuda.synchronize()
+        t_tr = a.elapsed_time(b)
+        # the slit steps of one field alone (resident)
+        h1 = F.acquire(1, stream)
+        field_steps(h1)
+        torch.cuda.synchronize()
+        a.record(stream)
+        field_steps(h1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_comp = a.elapsed_time(b)
+        F.release(1, stream)
+        # one field's latency: its copy starts, then its steps (nothing else in flight)
+        torch.cuda.synchronize()
+        a.record(copy)
+        F.load(0, host, copy)
+        h = F.acquire(0, stream)
+        field_steps(h)
+        b.record(stream)
+        F.release(0, stream)
+        torch.cuda.synchronize()
+        lat = a.elapsed_time(b)
+        # the pipeline: field k+1 crosses the link while field k's slits run
+        done = [ev() for _ in range(fields)]
+        F.load(0, host, copy)
+        for k in range(fields):
+            slot = k % 2
+            if k + 1 < fields:
+                F.load(1 - slot, host, copy)
+            h = F.acquire(slot, stream)
+            field_steps(h)
+            F.release(slot, stream)
+            done[k].record(stream)
+        torch.cuda.synchronize()
+        gaps = [done[k - 1].elapsed_time(done[k]) for k in range(2, fields)]
+        period = float(np.mean(gaps))
+        g.destroy()
+        F.destroy()
+        del host
+        out[name] = {"field_bytes": int(nbytes), "T_transfer_ms": round(t_tr, 3),
+                     "link_GB_s": round(nbytes / (t_tr * 1e-3) / 1e9, 1), "T_comp_ms": round(t_comp, 4),
+                     "period_ms": round(period, 3), "period_model_ms": round(max(t_tr, t_comp), 3),
+                     "latency_ms": round(lat, 3), "latency_model_ms": round(t_tr + t_comp, 3)}
+    c, u = out["wz2-lift-16"], out["fp32"]
+    before = u["T_transfer_ms"] + u["T_comp_ms"]
+    out["ratio_R"] = round(u["field_bytes"] / c["field_bytes"], 3)
+    out["breakdown_normalised"] = {  # Fig. decompression_overhead's bars, before = 100
+        "before": {"computation": round(100 * u["T_comp_ms"] / before, 2),
+                   "transfer": round(100 * u["T_transfer_ms"] / before, 2), "decompression": 0.0},
+        "after": {"computation_with_fused_decode": round(100 * c["T_comp_ms"] / before, 2),
+                  "transfer": round(100 * c["T_transfer_ms"] / before, 2), "decompression": 0.0}}
+    out["period_speedup"] = round(u["period_ms"] / c["period_ms"], 3)
+    out["setup_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 # ------------------------------------------------------------ serving arm

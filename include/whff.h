@@ -207,6 +207,59 @@ int whff_graph_create_host(whff_handle* h, const float* x_host, int R, int64_t l
 int whff_graph_launch(whff_graph* g, void* stream);
 void whff_graph_destroy(whff_graph* g);
 
+/* A slit step captured once and moved from slit to slit (Sec. 2.1, divide and
+ * conquer; Fig. whff_algo fetches a new C_slit from C_field every
+ * millisecond): the graph of whff_step_rows(h, row0, nrows, ...) whose slit
+ * offset is a parameter of the instantiated graph.  y (ldy >= M) and state
+ * (M entries, or NULL) are FIELD-sized device buffers: a replay writes
+ * y[row0 .. row0+nrows-1, r] and updates state[row0 .. row0+nrows-1]; x (N x R,
+ * ldx) is read in place, so the caller rewrites it between replays.
+ * whff_graph_set_rows moves the slit to row0 and, with h != NULL, onto another
+ * resident matrix of the same format, rate, shape and max_rhs (e.g. the next
+ * field of a whff_fields pipeline): the slit step is captured again on the
+ * host (no GPU work) and the kernel arguments of the instantiated graph are
+ * updated in place (cudaGraphExecUpdate) -- the slit height fixes the launch
+ * plan, so every offset has the same nodes.  Replays already enqueued keep
+ * the slit they were launched with; the update applies to later launches.
+ * Same results bit for bit as whff_step_rows on that slit.
+ * Errors: WHFF_EINVAL (rows outside the matrix, row0 not a multiple of 4 for
+ * block formats or 128 for scaled ones, R > max_rhs, a mismatching handle, the
+ * handle's launch shape or crossover changed since the capture), WHFF_ECUDA. */
+int whff_graph_create_rows(whff_handle* h, int64_t row0, int64_t nrows, const float* x, int R, int64_t ldx,
+                           double* y, int64_t ldy, double* state, double decay, void* stream, whff_graph** g);
+int whff_graph_set_rows(whff_graph* g, whff_handle* h, int64_t row0);
+
+/* ------------------------------------------------------------ field pipeline */
+/* Compressed fields streamed over the host link (Sec. 4.2-4.3: the scanner
+ * fetches one C_field per exposure field from host memory and the slits of
+ * that field from it; compression divides the bytes on the link, Fig.
+ * compression_cost, and the pipeline period and latency of Table comp_metrics
+ * follow).  nbuf resident slots (2 = double buffering), each a handle of its
+ * own (device copy of the stream, workspaces, launch plan) for one format,
+ * rate and shape.  whff_fields_load(slot, blob, copy_stream) copies a blob's
+ * stream (header + stream in host memory; pinned memory makes the copy
+ * asynchronous) into the slot on copy_stream, after the work released from
+ * that slot has finished; only the header is checked (its CRC, format, rate
+ * and shape) unless the pipeline was created with WHFF_FIELDS_VERIFY_CRC,
+ * which also checks the stream's CRC on the host before the copy.
+ * whff_fields_acquire(slot, compute_stream) makes compute_stream wait for the
+ * slot's last load and returns its handle, for whff_step / whff_step_rows /
+ * graphs (whff_graph_set_rows moves a slit graph onto it).
+ * whff_fields_release(slot, compute_stream) marks the slot free once the work
+ * enqueued on compute_stream so far has run; the next load of the slot waits
+ * for it.  The host blob must stay valid until its copy has run.  The handles
+ * belong to the pipeline (do not destroy them).  Errors: WHFF_EINVAL (slot,
+ * shape or format mismatch), WHFF_EFORMAT (header or CRC), WHFF_ENOMEM,
+ * WHFF_ECUDA. */
+#define WHFF_FIELDS_VERIFY_CRC 1u
+typedef struct whff_fields whff_fields;
+int whff_fields_create(int fmt, int rate, int64_t M, int64_t N, int nbuf, int max_rhs, unsigned flags, void* stream,
+                       whff_fields** f);
+int whff_fields_load(whff_fields* f, int slot, const void* blob, size_t len, void* copy_stream);
+int whff_fields_acquire(whff_fields* f, int slot, void* compute_stream, whff_handle** h);
+int whff_fields_release(whff_fields* f, int slot, void* compute_stream);
+void whff_fields_destroy(whff_fields* f);
+
 /* ------------------------------------------------------- tuning and batches */
 /* Launch shape of the fixed-allocation (WZ2) kernels: blocks kept in flight
  * per lane (2, 4 or 8), resident CTAs per SM of the persistent grid, and the

@@ -8,6 +8,7 @@ possible the import fails loudly -- there is no CPU fallback.
 """
 from .whff import (  # noqa: F401
     Batch,
+    Fields,
     FMT_BF16,
     FMT_FIXED_BFP,
     FMT_FIXED_LIFT,
@@ -28,6 +29,7 @@ from .whff import (  # noqa: F401
     whff_destroy,
     whff_graph_create,
     whff_graph_create_host,
+    whff_graph_create_rows,
     whff_step,
     whff_step_host,
     whff_step_noalloc,

@@ -625,11 +625,8 @@ __global__ void wz2_mma_finish(MmaPass single, const MmaPass* __restrict__ table
   const int64_t first = ps.item_begin + tile * ps.S;
   const int nseg = (int)((first + ps.S - 1) / L - first / L + 1);
   double z[4];
-  for (int a = 0; a < 4; ++a) {
-    double acc = 0.0;
-    for (int g = 0; g < nseg; ++g) acc += ps.ws[((tile * ps.maxseg + g) * ps.R + r) * 128 + 32 * a + bl];
-    z[a] = acc;
-  }
+  for (int a = 0; a < 4; ++a)
+    z[a] = seq_sum_strided(ps.ws + ((tile * ps.maxseg) * ps.R + r) * 128 + 32 * a + bl, nseg, (int64_t)ps.R * 128);
   double yy[4];
   if (LIFT) {
     const double a = 2.0 * z[0];

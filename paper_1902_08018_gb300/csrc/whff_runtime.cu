@@ -277,6 +277,16 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
   return whff_create_ex(blob, len, max_rhs, 0u, stream, out);
 }
 
+namespace whff {
+namespace {
+// A handle for the matrix `info` describes.  src (host memory, info.stream_bytes)
+// is uploaded on `stream`; with src == nullptr the device stream is allocated and
+// left for the caller to fill (the slots of a field pipeline).
+int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned flags, void* stream,
+                whff_handle** out);
+}  // namespace
+}  // namespace whff
+
 extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigned flags, void* stream,
                               whff_handle** out) {
   if (!out || (flags & ~(unsigned)WHFF_CREATE_HOST_RESIDENT)) {
@@ -290,6 +300,13 @@ extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigne
     set_error("whff_create: blob header, size or CRC check failed");
     return e;
   }
+  return create_impl(info, (const uint8_t*)blob + kHeaderBytes, max_rhs, flags, stream, out);
+}
+
+namespace whff {
+namespace {
+int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned flags, void* stream,
+                whff_handle** out) {
   if (max_rhs <= 0) max_rhs = 32;
   if (max_rhs > 1024) {
     set_error("whff_create: max_rhs > 1024");
@@ -336,7 +353,7 @@ extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigne
       return fail(WHFF_ENOMEM);
     }
     h->d_stream = static_cast<uint8_t*>(dp);
-    std::memcpy(h->h_stream, (const uint8_t*)blob + kHeaderBytes, info.stream_bytes);
+    if (src) std::memcpy(h->h_stream, src, info.stream_bytes);
   } else if (cudaMalloc(&h->d_stream, info.stream_bytes) != cudaSuccess) {
     cudaGetLastError();
     set_error("whff_create: cudaMalloc of the compressed stream failed");
@@ -382,8 +399,8 @@ extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigne
     return fail(WHFF_ENOMEM);
   }
   if (cudaMemsetAsync(h->d_status, 0, sizeof(int), st) != cudaSuccess ||
-      (!h->h_stream && cudaMemcpyAsync(h->d_stream, (const uint8_t*)blob + kHeaderBytes, info.stream_bytes,
-                                       cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      (!h->h_stream && src &&
+       cudaMemcpyAsync(h->d_stream, src, info.stream_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     set_error(std::string("whff_create: upload failed: ") + cudaGetErrorString(cudaGetLastError()));
     return fail(WHFF_ECUDA);
@@ -394,6 +411,8 @@ extern "C" int whff_create_ex(const void* blob, size_t len, int max_rhs, unsigne
   *out = h;
   return WHFF_OK;
 }
+}  // namespace
+}  // namespace whff
 
 extern "C" int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, int64_t* N, size_t* device_bytes) {
   if (!h) {
@@ -502,9 +521,11 @@ int step_view(const whff_handle* h, int64_t row0, int64_t nrows, const float* x,
       if (v.ksplit > 1 && ws_need(&v) > h->ws_bytes) v.ksplit = 1, v.chunk = v.BN;
       break;
     }
-    if (c == 1) {
-      set_error("whff_step_rows: the view's partials do not fit the workspace");
-      return WHFF_EINVAL;
+    if (c == 1) {  // ranges of whole bands: no band is shared, so no partials at all
+      v.range_len = ceil_div(v.range_len, v.BN) * v.BN;
+      v.range_ctas = ceil_div(ceil_div(v.BM * v.BN, v.range_len), dev::kWarpsPerCta);
+      v.maxseg = 1;
+      break;
     }
     v.ctas_per_sm = --c;
     choose_ranges(&v);
@@ -596,6 +617,16 @@ struct whff_graph {
   cudaGraphExec_t exec = nullptr;
   float* d_x = nullptr;   // graph-owned staging (host variant)
   double* d_y = nullptr;
+  // slit graphs (whff_graph_create_rows): what a re-capture for another slit needs
+  whff_handle* h = nullptr;
+  int64_t row0 = -1, nrows = 0;
+  const float* x = nullptr;
+  int R = 0;
+  int64_t ldx = 0, ldy = 0;
+  double* y = nullptr;  // field-sized: the slit writes rows [row0, row0 + nrows)
+  double* state = nullptr;
+  double decay = 0.0;
+  cudaStream_t cap = nullptr;  // private capture stream for the updates
 };
 
 namespace {
@@ -640,6 +671,7 @@ extern "C" void whff_graph_destroy(whff_graph* g) {
   if (!g) return;
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->cap) cudaStreamDestroy(g->cap);
   cudaFree(g->d_x);
   cudaFree(g->d_y);
   cudaGetLastError();
@@ -701,6 +733,114 @@ extern "C" int whff_graph_create_host(whff_handle* h, const float* x_host, int R
     return e;
   }
   *out = g;
+  return WHFF_OK;
+}
+
+namespace {
+int check_slit(const whff_handle* h, int64_t row0, int64_t nrows, const char* who) {
+  if (row0 < 0 || nrows <= 0 || row0 + nrows > h->info.M || row0 % (is_blocked(h->info.fmt) ? 4 : kScaleTile)) {
+    set_error(std::string(who) + ": rows outside the matrix, or row0 not a multiple of 4 (block formats) / 128 "
+                                 "(scaled formats)");
+    return WHFF_EINVAL;
+  }
+  return WHFF_OK;
+}
+
+// The slit step of g (rows [row0, row0 + g->nrows) of handle h) captured into a fresh graph.
+int capture_slit(whff_graph* g, whff_handle* h, int64_t row0, cudaGraph_t* out) {
+  *out = nullptr;
+  if (cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    set_error(std::string("whff_graph: begin capture: ") + cudaGetErrorString(cudaGetLastError()));
+    return WHFF_ECUDA;
+  }
+  int e = step_view(h, row0, g->nrows, g->x, g->R, g->ldx, g->y + row0, g->ldy, g->state ? g->state + row0 : nullptr,
+                    g->decay, g->cap);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(g->cap, &graph);
+  if (e == WHFF_OK && ce != cudaSuccess) {
+    set_error(std::string("whff_graph: end capture: ") + cudaGetErrorString(ce));
+    e = WHFF_ECUDA;
+  }
+  if (e) {
+    if (graph) cudaGraphDestroy(graph);
+    return e;
+  }
+  *out = graph;
+  return WHFF_OK;
+}
+}  // namespace
+
+extern "C" int whff_graph_create_rows(whff_handle* h, int64_t row0, int64_t nrows, const float* x, int R, int64_t ldx,
+                                      double* y, int64_t ldy, double* state, double decay, void* stream,
+                                      whff_graph** out) {
+  (void)stream;
+  if (!out || !h || !x || !y || R <= 0 || R > h->max_rhs || ldx < h->info.N || ldy < h->info.M) {
+    set_error("whff_graph_create_rows: null argument, R out of [1, max_rhs], or leading dimension too small");
+    return WHFF_EINVAL;
+  }
+  *out = nullptr;
+  int e = check_slit(h, row0, nrows, "whff_graph_create_rows");
+  if (e) return e;
+  auto* g = new whff_graph;
+  g->h = h;
+  g->nrows = nrows;
+  g->x = x;
+  g->R = R;
+  g->ldx = ldx;
+  g->y = y;
+  g->ldy = ldy;
+  g->state = state;
+  g->decay = decay;
+  if (cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    set_error("whff_graph_create_rows: cannot create a capture stream");
+    return WHFF_ECUDA;
+  }
+  if ((e = capture_slit(g, h, row0, &g->graph)) != WHFF_OK) {
+    whff_graph_destroy(g);
+    return e;
+  }
+  if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) {
+    set_error(std::string("whff_graph_create_rows: instantiate: ") + cudaGetErrorString(cudaGetLastError()));
+    whff_graph_destroy(g);
+    return WHFF_ECUDA;
+  }
+  g->row0 = row0;
+  *out = g;
+  return WHFF_OK;
+}
+
+extern "C" int whff_graph_set_rows(whff_graph* g, whff_handle* h, int64_t row0) {
+  if (!g || !g->cap) {
+    set_error("whff_graph_set_rows: not a slit graph (whff_graph_create_rows)");
+    return WHFF_EINVAL;
+  }
+  if (!h) h = g->h;
+  if (h != g->h && (h->info.fmt != g->h->info.fmt || h->info.rate != g->h->info.rate || h->info.M != g->h->info.M ||
+                    h->info.N != g->h->info.N || h->max_rhs < g->R)) {
+    set_error("whff_graph_set_rows: the new handle differs in format, rate, shape or max_rhs");
+    return WHFF_EINVAL;
+  }
+  int e = check_slit(h, row0, g->nrows, "whff_graph_set_rows");
+  if (e) return e;
+  if (h == g->h && row0 == g->row0) return WHFF_OK;
+  cudaGraph_t graph = nullptr;
+  if ((e = capture_slit(g, h, row0, &graph)) != WHFF_OK) return e;
+  // same plan (it depends on the slit height and the handle's launch shape, not on
+  // row0), so the same nodes: only kernel arguments change
+  cudaGraphExecUpdateResultInfo info;
+  if (cudaGraphExecUpdate(g->exec, graph, &info) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    set_error("whff_graph_set_rows: the slit's launch sequence differs from the captured one (was the handle's "
+              "launch shape or crossover changed?)");
+    return WHFF_EINVAL;
+  }
+  cudaGraphDestroy(g->graph);
+  g->graph = graph;
+  g->h = h;
+  g->row0 = row0;
   return WHFF_OK;
 }
 
@@ -1326,5 +1466,122 @@ extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64
   }
   WHFF_CUDA_TRY(cudaEventRecord(b->copied, st));
   WHFF_CUDA_TRY(cudaGetLastError());
+  return WHFF_OK;
+}
+
+// ------------------------------------------------------------ field pipeline
+// Sec. 4.3 (Fig. compression_cost, Table comp_metrics): the compressed C_field of
+// the next exposure field crosses the host link while the GPU runs the slit steps
+// of the current one.  nbuf resident slots, each a full handle (device stream,
+// workspaces, launch plan) whose stream is rewritten by whff_fields_load; two
+// events per slot order the copy stream against the compute stream.
+struct whff_fields {
+  BlobInfo info;
+  bool verify = false;
+  std::vector<whff_handle*> slots;
+  std::vector<cudaEvent_t> loaded, released;
+};
+
+extern "C" void whff_fields_destroy(whff_fields* f) {
+  if (!f) return;
+  for (cudaEvent_t e : f->loaded)
+    if (e) cudaEventSynchronize(e);
+  for (cudaEvent_t e : f->released)
+    if (e) cudaEventSynchronize(e);
+  for (whff_handle* h : f->slots) whff_destroy(h);
+  for (cudaEvent_t e : f->loaded)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : f->released)
+    if (e) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete f;
+}
+
+extern "C" int whff_fields_create(int fmt, int rate, int64_t M, int64_t N, int nbuf, int max_rhs, unsigned flags,
+                                  void* stream, whff_fields** out) {
+  if (!out || nbuf < 1 || nbuf > 16 || (flags & ~(unsigned)WHFF_FIELDS_VERIFY_CRC)) {
+    set_error("whff_fields_create: null output, nbuf outside 1..16 or unknown flag");
+    return WHFF_EINVAL;
+  }
+  *out = nullptr;
+  BlobInfo info;
+  info.fmt = fmt;
+  info.rate = is_blocked(fmt) ? rate : 8 * elem_bytes(fmt);
+  info.M = M;
+  info.N = N;
+  info.stream_bytes = stream_size(fmt, info.rate, M, N);
+  if (!info.stream_bytes) {
+    set_error("whff_fields_create: invalid format, rate or shape");
+    return WHFF_EINVAL;
+  }
+  auto* f = new whff_fields;
+  f->info = info;
+  f->verify = (flags & WHFF_FIELDS_VERIFY_CRC) != 0;
+  for (int k = 0; k < nbuf; ++k) {
+    whff_handle* h = nullptr;
+    int e = create_impl(info, nullptr, max_rhs, 0u, stream, &h);
+    if (e) {
+      whff_fields_destroy(f);
+      return e;
+    }
+    f->slots.push_back(h);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (a) cudaEventDestroy(a);
+      whff_fields_destroy(f);
+      set_error("whff_fields_create: event creation failed");
+      return WHFF_ECUDA;
+    }
+    f->loaded.push_back(a);
+    f->released.push_back(b);
+  }
+  *out = f;
+  return WHFF_OK;
+}
+
+extern "C" int whff_fields_load(whff_fields* f, int slot, const void* blob, size_t len, void* copy_stream) {
+  if (!f || slot < 0 || slot >= (int)f->slots.size() || !blob) {
+    set_error("whff_fields_load: null argument or slot out of range");
+    return WHFF_EINVAL;
+  }
+  BlobInfo b;
+  int e = read_header(static_cast<const uint8_t*>(blob), len, &b, f->verify);
+  if (e) {
+    set_error("whff_fields_load: blob header, size or CRC check failed");
+    return e;
+  }
+  if (b.fmt != f->info.fmt || b.rate != f->info.rate || b.M != f->info.M || b.N != f->info.N) {
+    set_error("whff_fields_load: the blob's format, rate or shape differs from the pipeline's");
+    return WHFF_EINVAL;
+  }
+  const cudaStream_t cs = as_stream(copy_stream);
+  whff_handle* h = f->slots[slot];
+  // the slot's previous field is no longer read once its release event has passed
+  WHFF_CUDA_TRY(cudaStreamWaitEvent(cs, f->released[slot], 0));
+  WHFF_CUDA_TRY(cudaMemcpyAsync(h->d_stream, static_cast<const uint8_t*>(blob) + kHeaderBytes, b.stream_bytes,
+                                cudaMemcpyHostToDevice, cs));
+  WHFF_CUDA_TRY(cudaEventRecord(f->loaded[slot], cs));
+  h->info.crc_stream = b.crc_stream;
+  return WHFF_OK;
+}
+
+extern "C" int whff_fields_acquire(whff_fields* f, int slot, void* compute_stream, whff_handle** h) {
+  if (!f || slot < 0 || slot >= (int)f->slots.size() || !h) {
+    set_error("whff_fields_acquire: null argument or slot out of range");
+    return WHFF_EINVAL;
+  }
+  WHFF_CUDA_TRY(cudaStreamWaitEvent(as_stream(compute_stream), f->loaded[slot], 0));
+  *h = f->slots[slot];
+  return WHFF_OK;
+}
+
+extern "C" int whff_fields_release(whff_fields* f, int slot, void* compute_stream) {
+  if (!f || slot < 0 || slot >= (int)f->slots.size()) {
+    set_error("whff_fields_release: null argument or slot out of range");
+    return WHFF_EINVAL;
+  }
+  WHFF_CUDA_TRY(cudaEventRecord(f->released[slot], as_stream(compute_stream)));
   return WHFF_OK;
 }

@@ -356,6 +356,24 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   }
 }
 
+// sum_{k < n} p[k * stride], added in k order; the loads of eight terms are
+// issued before their additions (a band split over many warp ranges -- a slit
+// of a long matrix -- has dozens of segments, and one load per dependent add
+// would serialise their latencies).  Same rounding as the plain loop.
+__device__ __forceinline__ double seq_sum_strided(const double* __restrict__ p, int64_t n, int64_t stride) {
+  double t = 0.0;
+  int64_t k = 0;
+  for (; k + 8 <= n; k += 8) {
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = p[(k + j) * stride];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t += v[j];
+  }
+  for (; k < n; ++k) t += p[k * stride];
+  return t;
+}
+
 // Sum the segments of bands shared by several warp ranges, in segment order,
 // then the state update (bands inside one range were finished by the kernel).
 static __global__ void wz2_segment_epilogue(const double* __restrict__ ws, int64_t M, int64_t BN, int64_t L,
@@ -369,8 +387,7 @@ static __global__ void wz2_segment_epilogue(const double* __restrict__ ws, int64
   if (g_lo == g_hi) return;
   double s = state ? state[row] : 0.0;
   for (int r = 0; r < R; ++r) {
-    double t = 0.0;
-    for (int64_t seg = 0; seg <= g_hi - g_lo; ++seg) t += ws[((I * maxseg + seg) * R + r) * 4 + i];
+    const double t = seq_sum_strided(ws + ((I * maxseg) * R + r) * 4 + i, g_hi - g_lo + 1, (int64_t)R * 4);
     y[(int64_t)r * ldy + row] = t;
     s = decay * s + t;
   }
@@ -466,8 +483,7 @@ static __global__ void wz2_batched_epilogue(const BatchEntry* __restrict__ entri
   if (g_lo == g_hi) return;
   double s = e.state ? e.state[row] : 0.0;
   for (int r = 0; r < R; ++r) {
-    double t = 0.0;
-    for (int64_t seg = 0; seg <= g_hi - g_lo; ++seg) t += e.ws[((I * e.maxseg + seg) * R + r) * 4 + i];
+    const double t = seq_sum_strided(e.ws + ((I * e.maxseg) * R + r) * 4 + i, g_hi - g_lo + 1, (int64_t)R * 4);
     e.y[(int64_t)r * e.ldy + row] = t;
     s = e.decay * s + t;
   }

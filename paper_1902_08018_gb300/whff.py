@@ -73,6 +73,13 @@ def library() -> ctypes.CDLL:
         "whff_graph_create": (c_int, [P, P, c_int, i64, P, i64, P, dbl, P, ctypes.POINTER(P)]),
         "whff_graph_create_host": (c_int, [P, P, c_int, i64, P, i64, P, dbl, P, ctypes.POINTER(P)]),
         "whff_graph_launch": (c_int, [P, P]),
+        "whff_graph_create_rows": (c_int, [P, i64, i64, P, c_int, i64, P, i64, P, dbl, P, ctypes.POINTER(P)]),
+        "whff_graph_set_rows": (c_int, [P, P, i64]),
+        "whff_fields_create": (c_int, [c_int, c_int, i64, i64, c_int, c_int, ctypes.c_uint, P, ctypes.POINTER(P)]),
+        "whff_fields_load": (c_int, [P, c_int, P, sz, P]),
+        "whff_fields_acquire": (c_int, [P, c_int, P, ctypes.POINTER(P)]),
+        "whff_fields_release": (c_int, [P, c_int, P]),
+        "whff_fields_destroy": (None, [P]),
         "whff_graph_destroy": (None, [P]),
         "whff_server_create": (c_int, [sz, c_int, c_int, ctypes.POINTER(P)]),
         "whff_server_add_model": (c_int, [P, P, dbl, ctypes.POINTER(c_int)]),
@@ -376,7 +383,7 @@ def whff_step_noalloc(stream_dev, rate: int, M: int, N: int, x, y, state=None, d
 
 
 class Graph:
-    """A captured control step (whff_graph_create / whff_graph_create_host)."""
+    """A captured control step (whff_graph_create / whff_graph_create_host / whff_graph_create_rows)."""
 
     def __init__(self, ptr: int, keep=()):
         self._ptr = ctypes.c_void_p(ptr)
@@ -384,6 +391,12 @@ class Graph:
 
     def launch(self, stream=None):
         _check(library().whff_graph_launch(self._ptr, _stream_ptr(stream)))
+
+    def set_rows(self, row0: int, h: "Handle | None" = None):
+        """Move a slit graph to rows row0.. (and onto handle h, if given)."""
+        _check(library().whff_graph_set_rows(self._ptr, h.ptr if h is not None else None, int(row0)))
+        if h is not None:
+            self._keep = tuple(self._keep) + (h,)
 
     def destroy(self):
         if self._ptr:
@@ -415,6 +428,22 @@ def whff_graph_create(h: Handle, x, y, state=None, decay: float = 0.99, stream=N
     _check(library().whff_graph_create(h.ptr, xp, R, ldx, yp, ldy, sp or None, float(decay), _stream_ptr(stream),
                                        ctypes.byref(g)))
     return Graph(g.value, (x, y, state))
+
+
+def whff_graph_create_rows(h: Handle, row0: int, nrows: int, x, y, state=None, decay: float = 0.99,
+                           stream=None) -> Graph:
+    """A slit graph: y (M,) or (R, M) and state (M,) are field-sized; a replay writes rows row0..row0+nrows-1."""
+    import torch
+
+    xp, R, ldx = _vec_args(x, h.N, "x", torch.float32)
+    yp, Ry, ldy = _vec_args(y, h.M, "y", torch.float64)
+    if Ry != R:
+        raise WhffError(-1, "x and y disagree on the number of right-hand sides")
+    sp = _vec_args(state, h.M, "state", torch.float64)[0] if state is not None else 0
+    g = ctypes.c_void_p()
+    _check(library().whff_graph_create_rows(h.ptr, int(row0), int(nrows), xp, R, ldx, yp, ldy, sp or None,
+                                            float(decay), _stream_ptr(stream), ctypes.byref(g)))
+    return Graph(g.value, (h, x, y, state))
 
 
 def whff_graph_create_host(h: Handle, x_host: np.ndarray, y_host: np.ndarray, state=None, decay: float = 0.99,
@@ -525,6 +554,53 @@ class Batch:
     def destroy(self):
         if self._ptr:
             library().whff_batch_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.destroy()
+
+
+class _SlotHandle(Handle):
+    """A field pipeline's slot: owned by the pipeline, never destroyed here."""
+
+    def destroy(self):
+        self._ptr = ctypes.c_void_p()
+
+
+class Fields:
+    """Compressed fields streamed into nbuf resident slots (whff_fields_*)."""
+
+    def __init__(self, fmt: int, rate: int, M: int, N: int, nbuf: int = 2, max_rhs: int = 1,
+                 verify_crc: bool = False, stream=None):
+        p = ctypes.c_void_p()
+        _check(library().whff_fields_create(int(fmt), int(rate), int(M), int(N), int(nbuf), int(max_rhs),
+                                            1 if verify_crc else 0, _stream_ptr(stream), ctypes.byref(p)))
+        self._ptr = p
+        self.nbuf = nbuf
+        self._blobs = [None] * nbuf  # the host blob of each slot's last load (kept alive for the copy)
+        self._handles = [None] * nbuf
+
+    def load(self, slot: int, blob: np.ndarray, copy_stream=None):
+        b = blob if isinstance(blob, np.ndarray) else np.frombuffer(blob, dtype=np.uint8)
+        _check(library().whff_fields_load(self._ptr, int(slot), b.ctypes.data, b.size, _stream_ptr(copy_stream)))
+        self._blobs[slot] = b
+
+    def acquire(self, slot: int, stream=None) -> Handle:
+        hp = ctypes.c_void_p()
+        _check(library().whff_fields_acquire(self._ptr, int(slot), _stream_ptr(stream), ctypes.byref(hp)))
+        if self._handles[slot] is None or self._handles[slot].ptr.value != hp.value:
+            self._handles[slot] = _SlotHandle(hp.value)
+        return self._handles[slot]
+
+    def release(self, slot: int, stream=None):
+        _check(library().whff_fields_release(self._ptr, int(slot), _stream_ptr(stream)))
+
+    def destroy(self):
+        if self._ptr:
+            library().whff_fields_destroy(self._ptr)
             self._ptr = ctypes.c_void_p()
 
     def __enter__(self):
