@@ -93,6 +93,8 @@ def parse_args():
     p.add_argument("--batched-fmt", default="wz2-lift:12")
     p.add_argument("--batched-crossover", type=int, default=0,
                    help="fewest columns of a tensor-core pass for the batch's handles (0: their default)")
+    p.add_argument("--no-serve-leg", action="store_true",
+                   help="leave the bounded serving and batched runs out of the default line")
     return p.parse_args()
 
 
@@ -685,25 +687,35 @@ def field_pipeline_leg(W, torch, dev, stream, L=2016, S=256000, slit=378, steps_
         lat = a.elapsed_time(b)
         # the pipeline: field k+1 crosses the link while field k's slits run
         done = [ev() for _ in range(fields)]
+        copied = [ev() for _ in range(fields)]
+        t_start = ev()
+        t_start.record(copy)
         F.load(0, host, copy)
+        copied[0].record(copy)
+        host_t = time.perf_counter()
         for k in range(fields):
             slot = k % 2
             if k + 1 < fields:
                 F.load(1 - slot, host, copy)
+                copied[k + 1].record(copy)
             h = F.acquire(slot, stream)
             field_steps(h)
             F.release(slot, stream)
             done[k].record(stream)
+        host_t = time.perf_counter() - host_t
         torch.cuda.synchronize()
         gaps = [done[k - 1].elapsed_time(done[k]) for k in range(2, fields)]
         period = float(np.mean(gaps))
+        timeline = {"copy_done_ms": [round(t_start.elapsed_time(e), 3) for e in copied],
+                    "steps_done_ms": [round(t_start.elapsed_time(e), 3) for e in done],
+                    "host_issue_ms": round(host_t * 1e3, 3)}
         g.destroy()
         F.destroy()
         del host
         out[name] = {"field_bytes": int(nbytes), "T_transfer_ms": round(t_tr, 3),
                      "link_GB_s": round(nbytes / (t_tr * 1e-3) / 1e9, 1), "T_comp_ms": round(t_comp, 4),
                      "period_ms": round(period, 3), "period_model_ms": round(max(t_tr, t_comp), 3),
-                     "latency_ms": round(lat, 3), "latency_model_ms": round(t_tr + t_comp, 3)}
+                     "latency_ms": round(lat, 3), "latency_model_ms": round(t_tr + t_comp, 3), "timeline": timeline}
     c, u = out["wz2-lift-16"], out["fp32"]
     before = u["T_transfer_ms"] + u["T_comp_ms"]
     out["ratio_R"] = round(u["field_bytes"] / c["field_bytes"], 3)
@@ -745,6 +757,21 @@ def run_serve(args, rank, world, local_rank):
         blobs_bytes.append(blob.size - 64)
         del blob
     setup_s = time.perf_counter() - t0
+    # each model's single pass alone (its tuned shape, R = 1, stream resident): the kernels' own rate
+    dev = torch.device("cuda", local_rank)
+    alone_ms = []
+    for h in handles:
+        xa = torch.zeros(h.N, dtype=torch.float32, device=dev)
+        ya = torch.zeros(h.M, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            h.step(xa, ya, None, DECAY)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            h.step(xa, ya, None, DECAY)
+        e1.record()
+        torch.cuda.synchronize()
+        alone_ms.append(e0.elapsed_time(e1) / 5)
     budget = int(free * 0.9)
     rng = np.random.default_rng(workloads.SEED_BASE + 5)
     events = []
@@ -813,8 +840,11 @@ def run_serve(args, rank, world, local_rank):
         "p999_us": float(np.percentile(lat_us, 99.9)), "miss_rate": float(miss.mean()),
         "dropped": int((status == 2).sum()), "firm": bool(args.firm),
         "passes": round(passes), "mean_batch": float(np.mean(bat[served])),
-        "streamed_GB_s": round(streamed / max(wall, 1e-9) / 1e9, 1), "per_model": per, "clocks": clocks,
-        "setup_s": round(setup_s, 1),
+        "streamed_GB_s": round(streamed / max(wall, 1e-9) / 1e9, 1),
+        "kernels_alone_GB_s": round(sum(blobs_bytes) / (sum(alone_ms) * 1e-3) / 1e9, 1),
+        "pass_alone_ms": [round(v, 4) for v in alone_ms],
+        "round_alone_ms": round(sum(alone_ms), 3),
+        "per_model": per, "clocks": clocks, "setup_s": round(setup_s, 1),
     }
 
 
@@ -1139,6 +1169,13 @@ def main():
             import torch
 
             torch.distributed.destroy_process_group()
+        elif not args.no_serve_leg:  # the serving loop and the batched instances, bounded, same process
+            import torch
+
+            torch.cuda.empty_cache()
+            res["serving"] = run_serve(args, rank, world, local_rank)
+            torch.cuda.empty_cache()
+            res["batched"] = run_batched(args, rank, world, local_rank)
     if rank == 0:
         line = json.dumps(res)
         print(line, flush=True)

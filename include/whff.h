@@ -336,6 +336,20 @@ void whff_batch_destroy(whff_batch* b);
 typedef struct whff_server whff_server;
 int whff_server_create(size_t hbm_budget, int max_batch, int nstreams, whff_server** s);
 int whff_server_add_model(whff_server* s, whff_handle* h, double decay, int* model_id);
+/* As whff_server_add_model; with WHFF_SERVER_WAIT a model that does not fit
+ * the budget (or arrives while earlier models wait) is registered as waiting
+ * (returns WHFF_OK with its id) instead of refused, and is admitted -- state,
+ * staging and graphs allocated and captured -- as soon as removals free
+ * enough memory, in registration order (first come, first served).
+ * whff_server_model_state: 1 admitted, 2 waiting, 0 removed.
+ * whff_server_remove_model waits for the model's stream, frees its state,
+ * staging and graphs (not its handle, which the caller owns), returns its
+ * footprint to the budget and admits waiting models that now fit.  Requests
+ * for a model that is not admitted are refused by whff_server_run (status 3). */
+#define WHFF_SERVER_WAIT 1u
+int whff_server_add_model_ex(whff_server* s, whff_handle* h, double decay, unsigned flags, int* model_id);
+int whff_server_model_state(const whff_server* s, int model_id, int* state);
+int whff_server_remove_model(whff_server* s, int model_id);
 int whff_server_reset_state(whff_server* s, int model_id);
 int whff_server_read_state(whff_server* s, int model_id, double* host_out);
 /* Replay a trace in real time: request i for model[i] arrives arrival_s[i]
@@ -346,7 +360,8 @@ int whff_server_read_state(whff_server* s, int model_id, double* host_out);
  * queued drop_after_s after arrival is discarded.  On return latency_s[i] =
  * completion - arrival as seen by the host (for a dropped request its age
  * when discarded), batch[i] = requests in its pass (0 if dropped), status[i]
- * (optional) = 0 in time, 1 late, 2 dropped, and y[i] (if y and y[i] are not
+ * (optional) = 0 in time, 1 late, 2 dropped, 3 refused (model not admitted),
+ * and y[i] (if y and y[i] are not
  * NULL) holds its M doubles.  WHFF_ETIMEOUT if the run exceeds max_wait_s. */
 int whff_server_run(whff_server* s, int n, const int* model, const double* arrival_s, const float* const* x,
                     double* const* y, double* latency_s, int* batch, int* status, double drop_after_s,

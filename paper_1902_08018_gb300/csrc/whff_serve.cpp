@@ -34,7 +34,10 @@ using whff::set_error;
 
 namespace {
 
+enum ModelState { kRemoved = 0, kAdmitted = 1, kWaiting = 2 };
+
 struct Model {
+  int state = kRemoved;
   whff_handle* h = nullptr;
   int64_t M = 0, N = 0;
   double decay = 0.0;
@@ -98,16 +101,51 @@ int make_model_streams(whff_server* s) {
 
 }  // namespace
 
+namespace {
+void release_model(Model& m) {
+  for (auto* g : m.graphs) whff_graph_destroy(g);
+  m.graphs.clear();
+  cudaFree(m.d_state);
+  cudaFreeHost(m.x_pin);
+  cudaFreeHost(m.y_pin);
+  m.d_state = nullptr;
+  m.x_pin = nullptr;
+  m.y_pin = nullptr;
+  cudaGetLastError();
+}
+
+// Footprint of a model on the device: resident matrix and workspaces, state,
+// one staging pair per batch bucket.
+int model_footprint(const whff_server* s, whff_handle* h, Model& m) {
+  int fmt, rate;
+  size_t dev_bytes = 0;
+  if (whff_info(h, &fmt, &rate, &m.M, &m.N, &dev_bytes)) return WHFF_EINVAL;
+  size_t staging = 0;
+  for (int b = 0; b < s->nbuckets; ++b) staging += (size_t)(1 << b) * (size_t)(m.N * 4 + m.M * 8);
+  m.footprint = dev_bytes + (size_t)m.M * 8 + staging;
+  return WHFF_OK;
+}
+
+int admit(whff_server* s, Model& m);
+
+// Admit waiting models in registration order while the oldest one fits the
+// budget (first come, first served: a small model does not overtake a big one).
+int admit_waiting(whff_server* s) {
+  for (auto& m : s->models) {
+    if (m.state != kWaiting) continue;
+    if (s->used + m.footprint > s->budget) break;
+    const int e = admit(s, m);
+    if (e) return e;
+  }
+  return WHFF_OK;
+}
+}  // namespace
+
 extern "C" void whff_server_destroy(whff_server* s) {
   if (!s) return;
   for (auto& st : s->streams) cudaStreamSynchronize(st);
   for (auto& st : s->model_streams) cudaStreamSynchronize(st);
-  for (auto& m : s->models) {
-    for (auto* g : m.graphs) whff_graph_destroy(g);
-    cudaFree(m.d_state);
-    cudaFreeHost(m.x_pin);
-    cudaFreeHost(m.y_pin);
-  }
+  for (auto& m : s->models) release_model(m);
   for (auto& st : s->streams) cudaStreamDestroy(st);
   for (auto& st : s->model_streams) cudaStreamDestroy(st);
   cudaGetLastError();
@@ -138,32 +176,78 @@ extern "C" int whff_server_create(size_t hbm_budget, int max_batch, int nstreams
   return WHFF_OK;
 }
 
-extern "C" int whff_server_add_model(whff_server* s, whff_handle* h, double decay, int* model_id) {
-  if (!s || !h || !model_id) {
-    set_error("whff_server_add_model: null argument");
+extern "C" int whff_server_add_model_ex(whff_server* s, whff_handle* h, double decay, unsigned flags,
+                                        int* model_id) {
+  if (!s || !h || !model_id || (flags & ~(unsigned)WHFF_SERVER_WAIT)) {
+    set_error("whff_server_add_model: null argument or unknown flag");
     return WHFF_EINVAL;
   }
   Model m;
-  int fmt, rate;
-  size_t dev_bytes = 0;
-  if (whff_info(h, &fmt, &rate, &m.M, &m.N, &dev_bytes)) return WHFF_EINVAL;
-  // resident matrix + state + one staging pair per batch bucket
-  size_t staging = 0;
-  for (int b = 0; b < s->nbuckets; ++b) staging += (size_t)(1 << b) * (size_t)(m.N * 4 + m.M * 8);
-  m.footprint = dev_bytes + (size_t)m.M * 8 + staging;
-  if (s->used + m.footprint > s->budget) {
-    set_error("whff_server_add_model: device-memory budget exceeded (" + std::to_string(s->used + m.footprint) +
-              " > " + std::to_string(s->budget) + " bytes)");
-    return WHFF_EBUSY;
+  if (model_footprint(s, h, m)) {
+    set_error("whff_server_add_model: bad handle");
+    return WHFF_EINVAL;
   }
   m.h = h;
   m.decay = decay;
+  bool waiting_ahead = false;  // registrations are admitted in order
+  for (const auto& o : s->models) waiting_ahead |= o.state == kWaiting;
+  if (s->used + m.footprint > s->budget || waiting_ahead) {
+    if (!(flags & WHFF_SERVER_WAIT)) {
+      set_error("whff_server_add_model: device-memory budget exceeded (" + std::to_string(s->used + m.footprint) +
+                " > " + std::to_string(s->budget) + " bytes)");
+      return WHFF_EBUSY;
+    }
+    m.state = kWaiting;  // admitted by whff_server_remove_model once memory frees up
+    *model_id = (int)s->models.size();
+    s->models.push_back(m);
+    return WHFF_OK;
+  }
+  const int e = admit(s, m);
+  if (e) return e;
+  *model_id = (int)s->models.size();
+  s->models.push_back(m);
+  return WHFF_OK;
+}
+
+extern "C" int whff_server_add_model(whff_server* s, whff_handle* h, double decay, int* model_id) {
+  return whff_server_add_model_ex(s, h, decay, 0u, model_id);
+}
+
+extern "C" int whff_server_model_state(const whff_server* s, int model_id, int* state) {
+  if (!s || !state || model_id < 0 || model_id >= (int)s->models.size()) {
+    set_error("whff_server_model_state: bad argument");
+    return WHFF_EINVAL;
+  }
+  *state = s->models[model_id].state;
+  return WHFF_OK;
+}
+
+extern "C" int whff_server_remove_model(whff_server* s, int model_id) {
+  if (!s || model_id < 0 || model_id >= (int)s->models.size() || s->models[model_id].state == kRemoved) {
+    set_error("whff_server_remove_model: bad or removed model");
+    return WHFF_EINVAL;
+  }
+  Model& m = s->models[model_id];
+  if (m.state == kAdmitted) {
+    if (model_id < (int)s->model_streams.size()) cudaStreamSynchronize(s->model_streams[model_id]);
+    release_model(m);
+    s->used -= m.footprint;
+  }
+  m.state = kRemoved;
+  m.h = nullptr;
+  return admit_waiting(s);
+}
+
+namespace {
+// Allocate a model's state and staging and capture its graphs; on success it
+// counts against the budget.
+int admit(whff_server* s, Model& m) {
+  whff_handle* h = m.h;
+  const double decay = m.decay;
+  int fmt, rate;
+  if (whff_info(h, &fmt, &rate, nullptr, nullptr, nullptr)) return WHFF_EINVAL;
   auto fail = [&](int code, const char* what) {
-    for (auto* g : m.graphs) whff_graph_destroy(g);
-    cudaFree(m.d_state);
-    cudaFreeHost(m.x_pin);
-    cudaFreeHost(m.y_pin);
-    cudaGetLastError();
+    release_model(m);
     set_error(std::string("whff_server_add_model: ") + what);
     return code;
   };
@@ -194,13 +278,13 @@ extern "C" int whff_server_add_model(whff_server* s, whff_handle* h, double deca
   whff_set_slice_rows(h, own_slice);
   m.slice_rows = slice;
   s->used += m.footprint;
-  *model_id = (int)s->models.size();
-  s->models.push_back(m);
+  m.state = kAdmitted;
   return WHFF_OK;
 }
+}  // namespace
 
 extern "C" int whff_server_reset_state(whff_server* s, int model_id) {
-  if (!s || model_id < 0 || model_id >= (int)s->models.size()) {
+  if (!s || model_id < 0 || model_id >= (int)s->models.size() || s->models[model_id].state != kAdmitted) {
     set_error("whff_server_reset_state: bad model");
     return WHFF_EINVAL;
   }
@@ -213,8 +297,9 @@ extern "C" int whff_server_reset_state(whff_server* s, int model_id) {
 }
 
 extern "C" int whff_server_read_state(whff_server* s, int model_id, double* host_out) {
-  if (!s || !host_out || model_id < 0 || model_id >= (int)s->models.size()) {
-    set_error("whff_server_read_state: bad argument");
+  if (!s || !host_out || model_id < 0 || model_id >= (int)s->models.size() ||
+      s->models[model_id].state != kAdmitted) {
+    set_error("whff_server_read_state: bad argument or model not admitted");
     return WHFF_EINVAL;
   }
   Model& m = s->models[model_id];
@@ -249,6 +334,8 @@ extern "C" int whff_server_run(whff_server* s, int n, const int* model, const do
       set_error("whff_server_run: bad request " + std::to_string(i));
       return WHFF_EINVAL;
     }
+  std::vector<char> live(nm);
+  for (int m = 0; m < nm; ++m) live[m] = s->models[m].state == kAdmitted;
   if ((int)s->model_streams.size() != nm && make_model_streams(s) != WHFF_OK) {
     set_error("whff_server_run: cannot create model streams");
     return WHFF_ECUDA;
@@ -277,8 +364,15 @@ extern "C" int whff_server_run(whff_server* s, int n, const int* model, const do
       break;
     }
     while (next_arrival < n && arrival_s[next_arrival] <= t) {
-      queue[model[next_arrival]].push_back(next_arrival);
-      ++next_arrival;
+      const int r = next_arrival++;
+      if (live[model[r]]) {
+        queue[model[r]].push_back(r);
+      } else {  // the model is waiting for memory or was removed: refused
+        latency_s[r] = 0.0;
+        batch[r] = 0;
+        if (status) status[r] = 3;
+        ++done;
+      }
     }
     for (int m = 0; m < nm; ++m) {  // completions
       Pass& p = inflight[m];

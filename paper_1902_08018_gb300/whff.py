@@ -83,6 +83,9 @@ def library() -> ctypes.CDLL:
         "whff_graph_destroy": (None, [P]),
         "whff_server_create": (c_int, [sz, c_int, c_int, ctypes.POINTER(P)]),
         "whff_server_add_model": (c_int, [P, P, dbl, ctypes.POINTER(c_int)]),
+        "whff_server_add_model_ex": (c_int, [P, P, dbl, ctypes.c_uint, ctypes.POINTER(c_int)]),
+        "whff_server_model_state": (c_int, [P, c_int, ctypes.POINTER(c_int)]),
+        "whff_server_remove_model": (c_int, [P, c_int]),
         "whff_server_reset_state": (c_int, [P, c_int]),
         "whff_server_read_state": (c_int, [P, c_int, P]),
         "whff_server_run": (c_int, [P, c_int, P, P, P, P, P, P, P, dbl, dbl]),
@@ -472,11 +475,21 @@ class Server:
         self._ptr = p
         self.models = []
 
-    def add_model(self, h: Handle, decay: float = 0.99) -> int:
+    def add_model(self, h: Handle, decay: float = 0.99, wait: bool = False) -> int:
+        """Admit a model; with wait=True one that does not fit waits for removals to free memory."""
         mid = ctypes.c_int()
-        _check(library().whff_server_add_model(self._ptr, h.ptr, float(decay), ctypes.byref(mid)))
+        _check(library().whff_server_add_model_ex(self._ptr, h.ptr, float(decay), 1 if wait else 0,
+                                                  ctypes.byref(mid)))
         self.models.append(h)
         return mid.value
+
+    def model_state(self, model_id: int) -> str:
+        v = ctypes.c_int()
+        _check(library().whff_server_model_state(self._ptr, int(model_id), ctypes.byref(v)))
+        return {0: "removed", 1: "admitted", 2: "waiting"}[v.value]
+
+    def remove_model(self, model_id: int):
+        _check(library().whff_server_remove_model(self._ptr, int(model_id)))
 
     def reset_state(self, model_id: int):
         _check(library().whff_server_reset_state(self._ptr, model_id))

@@ -164,3 +164,42 @@ def test_firm_mode_drops_expired_requests(env, orc):
         s = orc.state_update(s, orc.gemv64(Ahat, xs[i].astype(np.float64)).reshape(n, 1), 0.9)
     assert np.linalg.norm(state - s) <= 1e-6 * np.linalg.norm(s)
     h.destroy()
+
+
+def test_waiting_model_admitted_once_memory_frees(env, orc):
+    """North star's serving rule: a model that does not fit waits and is admitted as
+    memory frees up (whff_server_remove_model); meanwhile its requests are refused
+    (status 3), afterwards they are served and its state follows the oracle."""
+    W, torch = env
+    blob = W.whff_compress(_matrix(512, 1), 5, 16)
+    h1 = W.whff_create(blob, max_rhs=8)
+    h2 = W.whff_create(blob, max_rhs=8)
+    Ahat = orc.decode(blob.tobytes())
+    rng = np.random.default_rng(7)
+    xs = [rng.standard_normal(512).astype(np.float32) for _ in range(6)]
+    with W.Server(hbm_budget=int(h1.device_bytes * 1.6), max_batch=8, nstreams=1) as srv:
+        a = srv.add_model(h1, decay=0.9)
+        b = srv.add_model(h2, decay=0.9, wait=True)  # over the budget: waits instead of WHFF_EBUSY
+        assert (srv.model_state(a), srv.model_state(b)) == ("admitted", "waiting")
+        with pytest.raises(W.WhffError) as e:  # without waiting, still refused
+            srv.add_model(h2)
+        assert e.value.code == -8
+        lat, bat, _, status = srv.run(np.array([a, b, a], dtype=np.int32), np.zeros(3), xs[:3],
+                                      return_status=True)
+        assert list(status) == [0, 3, 0] and bat[1] == 0
+        srv.remove_model(a)  # frees the budget: b is admitted
+        assert (srv.model_state(a), srv.model_state(b)) == ("removed", "admitted")
+        lat, bat, ys, status = srv.run(np.array([b, b, b], dtype=np.int32), np.array([0.0, 1e-3, 2e-3]), xs[3:],
+                                       want_y=True, return_status=True)
+        assert (status != 3).all() and (status != 2).all()  # no firm deadline: all served
+        state = srv.read_state(b)
+        with pytest.raises(W.WhffError):  # a removed model has no state
+            srv.read_state(a)
+    s = np.zeros(512)
+    for i in range(3):
+        ref = orc.gemv64(Ahat, xs[3 + i].astype(np.float64))
+        assert np.linalg.norm(ys[i] - ref) <= 1e-6 * np.linalg.norm(ref)
+        s = orc.state_update(s, ref.reshape(512, 1), 0.9)
+    assert np.linalg.norm(state - s) <= 1e-6 * np.linalg.norm(s)
+    h1.destroy()
+    h2.destroy()
