@@ -376,6 +376,18 @@ int whff_decompress(whff_handle* h, double* out, int64_t ldo, void* stream);
 /* Read and clear the handle's device status word (synchronizes the stream). */
 int whff_sync_status(whff_handle* h, void* stream);
 
+/* Failure detection of the tensor-core passes: every device-side wait of
+ * their kernels (an MMA group's commit, a bulk copy's arrival) is bounded; a
+ * wait that runs out records WHFF_ETIMEOUT in the status word, the CTA stops
+ * at its next barrier, waits once more -- with the full limit -- for its MMAs
+ * and copy in flight, frees its tensor memory and returns, so the context
+ * stays usable.  whff_set_wait_limit sets the polls of the in-loop waits of
+ * this handle's passes (default about 2^22, about a second; polls < 0 restores
+ * it; 0 makes every in-loop wait give up at once).  Lowering it is for tests of
+ * failure detection; the y of a pass that timed out is not valid.  Errors:
+ * WHFF_EINVAL. */
+int whff_set_wait_limit(whff_handle* h, int64_t polls);
+
 /* Free every device allocation of the handle (stream-ordered on its stream). */
 void whff_destroy(whff_handle* h);
 

@@ -32,7 +32,7 @@ static int mma_one(const MmaStep& a, cudaStream_t st) {
   const int64_t bthreads = (int64_t)nstages * dev::kMmaStageBlocks * NR;
   dev::wz2_mma_btiles<LIFT, NR><<<(unsigned)((bthreads + 255) / 256), 256, 0, st>>>(pass, nullptr, 1, bthreads);
   dev::wz2_mma_kernel<RATE, LIFT, NR, false><<<(unsigned)a.ctas, dev::kMmaThreads, smem, st>>>(
-      mem, nullptr, 1, (int64_t)tiles * nstages, a.L, a.status);
+      mem, nullptr, 1, (int64_t)tiles * nstages, a.L, a.status, a.spin);
   const int64_t fin_threads = (int64_t)tiles * a.R * 32;
   dev::wz2_mma_finish<LIFT><<<(unsigned)((fin_threads + 255) / 256), 256, 0, st>>>(pass, nullptr, 1, fin_threads,
                                                                                   a.L);
@@ -61,7 +61,8 @@ static int mma_batch_one(const MmaBatchStep& a, cudaStream_t st) {
   dev::wz2_mma_btiles<LIFT, NR><<<(unsigned)((a.bt_threads + 255) / 256), 256, 0, st>>>(p0, a.passes, a.nmem,
                                                                                        a.bt_threads);
   dev::wz2_mma_kernel<RATE, LIFT, NR, true><<<(unsigned)a.ctas, dev::kMmaThreads, smem, st>>>(m0, a.members, a.nmem,
-                                                                                            a.total, a.L, a.status);
+                                                                                            a.total, a.L, a.status,
+                                                                                            a.spin);
   dev::wz2_mma_finish<LIFT><<<(unsigned)((a.fin_threads + 255) / 256), 256, 0, st>>>(p0, a.passes, a.nmem,
                                                                                     a.fin_threads, a.L);
   return 0;

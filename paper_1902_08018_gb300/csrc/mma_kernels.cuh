@@ -132,9 +132,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kMmaSpinLimit; ++it)
+// Bounded wait; false if the limit ran out.  The in-loop waits of the
+// tensor-core kernels take the launch's limit (a handle setting, lowered only
+// to test failure detection); the waits before TMEM is freed take the full one.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit = kMmaSpinLimit) {
+  for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -325,7 +327,7 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
 template <int RATE, bool LIFT, int NR, bool TABLE>
 __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)  // 3 A pieces: 120 KB of tiles
     wz2_mma_kernel(MmaMember single, const MmaMember* __restrict__ table, int nmem, int64_t total, int64_t L,
-                   int* __restrict__ status) {
+                   int* __restrict__ status, uint32_t spin) {
   using SM = MmaSmem<RATE, NR>;
   constexpr int PA = MmaPieces<RATE>::kA;
   constexpr int NW = Wz2Layout<RATE>::kWords;
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
     if (ends) gpos = 0, gacc ^= 1;
     advance(m_m, m_tile, m_st);
     if (t == 0) {
-      if (!mbar_wait(b_bar + 8 * buf, (uint32_t)((k >> 1) & 1))) {
+      if (!mbar_wait(b_bar + 8 * buf, (uint32_t)((k >> 1) & 1), spin)) {
         ok = false;
         fail();
       } else {
@@ -557,7 +559,8 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
     // this ring slot is free: the words of stage k+2 are loaded while the MMAs run
     if (k + 2 < n) fetch(buf);
     if (k >= 1) {  // stage k-1 (other buffer): wait for its MMAs; drain its group if it closed one
-      const bool done = __all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * (buf ^ 1), (uint32_t)(((k - 1) >> 1) & 1)));
+      const bool done =
+          __all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * (buf ^ 1), (uint32_t)(((k - 1) >> 1) & 1), spin));
       if (!done) {
         if (ok && lane == 0) fail();
         ok = false;
@@ -585,7 +588,7 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
   if (alive && n > 0) alive = __syncthreads_and(ok ? 1 : 0) != 0;
   if (alive && n > 0) {  // the last stage, which always closes its group
     const int buf = (int)((n - 1) & 1);
-    if (__all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * buf, (uint32_t)(((n - 1) >> 1) & 1)))) {
+    if (__all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * buf, (uint32_t)(((n - 1) >> 1) & 1), spin))) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       drain(p_acc, p_m, p_tile);
       flush();

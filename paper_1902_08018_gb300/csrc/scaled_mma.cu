@@ -23,7 +23,7 @@ static int scaled_mma_one(const ScaledMmaStep& a, cudaStream_t st) {
   dev::wz2_mma_btiles<false, NR><<<(unsigned)((bthreads + 255) / 256), 256, 0, st>>>(pass, nullptr, 1, bthreads);
   kern<<<(unsigned)a.ctas, dev::kMmaThreads, S::kBytes, st>>>(a.payload, a.scales, a.M, a.ld, a.TN, a.btiles, a.ws,
                                                               nstages, a.R, a.maxseg, (int64_t)tiles * nstages, a.L,
-                                                              a.status);
+                                                              a.status, a.spin);
   const int64_t fin = (int64_t)tiles * a.R * 128;
   dev::scaled_mma_finish<<<(unsigned)((fin + 255) / 256), 256, 0, st>>>(a.ws, a.M, nstages, a.R, a.maxseg, tiles, a.L,
                                                                        a.y, a.ldy);

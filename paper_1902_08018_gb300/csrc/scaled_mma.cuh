@@ -84,7 +84,7 @@ template <int FMT, int NR>
 __global__ void __launch_bounds__(kMmaThreads, 2)
     scaled_mma_kernel(const uint8_t* __restrict__ payload, const float* __restrict__ scales, int64_t M, int64_t ld,
                       int64_t TN, const uint8_t* __restrict__ btiles, double* __restrict__ ws, int S, int R,
-                      int maxseg, int64_t total, int64_t L, int* __restrict__ status) {
+                      int maxseg, int64_t total, int64_t L, int* __restrict__ status, uint32_t spin) {
   using SM = ScaledMmaSmem<FMT, NR>;
   using TR = ScaledMmaTraits<FMT>;
   constexpr int PA = TR::kPA, NL = TR::kLoads, EB = TR::kEB;
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
     if (ends) gpos = 0, gacc ^= 1;
     advance(m_tile, m_st);
     if (t == 0) {
-      if (!mbar_wait(b_bar + 8 * buf, (uint32_t)((k >> 1) & 1))) {
+      if (!mbar_wait(b_bar + 8 * buf, (uint32_t)((k >> 1) & 1), spin)) {
         ok = false;
         fail();
       } else {
@@ -269,7 +269,8 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
     }
     if (k + 2 < n) fetch(buf);
     if (k >= 1) {
-      const bool done = __all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * (buf ^ 1), (uint32_t)(((k - 1) >> 1) & 1)));
+      const bool done =
+          __all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * (buf ^ 1), (uint32_t)(((k - 1) >> 1) & 1), spin));
       if (!done) {
         if (ok && lane == 0) fail();
         ok = false;
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
   if (alive && n > 0) alive = __syncthreads_and(ok ? 1 : 0) != 0;
   if (alive && n > 0) {
     const int buf = (int)((n - 1) & 1);
-    if (__all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * buf, (uint32_t)(((n - 1) >> 1) & 1)))) {
+    if (__all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * buf, (uint32_t)(((n - 1) >> 1) & 1), spin))) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       drain(p_acc, p_tile, p_s);
       flush();

@@ -65,6 +65,7 @@ struct whff_handle {
   size_t ws_mma_cap = 0;        // bytes of d_ws_mma
   const float* d_scales = nullptr;  // scaled formats: the tile scales after the payload
   int64_t slice_rows = 0;       // > 0: whff_step runs as consecutive slits of this many rows
+  uint32_t wait_polls = whff::kWaitPolls;  // in-loop bounded waits of the tensor-core kernels
   cudaStream_t create_stream = nullptr;
 };
 
@@ -438,12 +439,12 @@ int launch_mma(const whff_handle* h, const float* x, int R, int64_t ldx, double*
   if (is_blocked(h->info.fmt)) {
     MmaStep a{h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, h->d_stream, h->info.M, h->info.N, h->BM, h->BN,
               x, ldx, R, h->mma_L, h->mma_ctas, h->mma_maxseg, h->d_ws_mma, h->d_btiles, y, ldy, state, decay,
-              h->d_status};
+              h->d_status, h->wait_polls};
     e = mma_launch(a, st);
   } else {
     ScaledMmaStep a{h->info.fmt, h->d_stream, h->d_scales, h->info.M, h->info.N, scaled_ld(h->info.N),
                     ceil_div(h->info.N, kScaleTile), x, ldx, R, h->mma_L, h->mma_ctas, h->mma_maxseg,
-                    h->d_ws_mma, h->d_btiles, y, ldy, state, decay, h->d_status};
+                    h->d_ws_mma, h->d_btiles, y, ldy, state, decay, h->d_status, h->wait_polls};
     e = scaled_mma_launch(a, st);
   }
   if (e) {
@@ -998,6 +999,15 @@ extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int 
   return apply_config(h, unroll, ctas_per_sm, fold);
 }
 
+extern "C" int whff_set_wait_limit(whff_handle* h, int64_t polls) {
+  if (!h || polls > (int64_t)0x7FFFFFFF) {
+    set_error("whff_set_wait_limit: null handle or polls above 2^31 - 1");
+    return WHFF_EINVAL;
+  }
+  h->wait_polls = polls < 0 ? kWaitPolls : (uint32_t)polls;
+  return WHFF_OK;
+}
+
 extern "C" int whff_get_crossover(const whff_handle* h, int* min_rhs) {
   if (!h || !min_rhs) {
     set_error("whff_get_crossover: null argument");
@@ -1411,7 +1421,7 @@ extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64
     WHFF_CUDA_TRY(cudaMemcpyAsync(g.d_passes, g.pinned, sizeof(dev::MmaPass) * n, cudaMemcpyHostToDevice, st));
     const whff_handle* h0 = b->hs[g.of[0]];
     MmaBatchStep a{b->rate, b->lift, g.nr, g.d_members, g.d_passes, n, g.total, g.L, g.ctas, g.bt_threads,
-                   g.fin_threads, h0->d_status};
+                   g.fin_threads, h0->d_status, h0->wait_polls};
     if (mma_batch_launch(a, st)) {
       set_error("whff_batch_step: tensor-core launch failed");
       return WHFF_ECUDA;

@@ -9,6 +9,10 @@
 
 namespace whff {
 
+// Polls of a bounded device-side wait (tensor-core kernels) before it gives up
+// and records WHFF_ETIMEOUT: about a second of try_wait.
+constexpr uint32_t kWaitPolls = 1u << 22;
+
 struct Wz2Step {
   const uint8_t* stream;
   int64_t M, N, BM, BN;
@@ -88,6 +92,7 @@ struct MmaStep {
   double* state;
   double decay;
   int* status;
+  uint32_t spin;   // polls of an in-loop mbarrier wait before it gives up (kWaitPolls)
 };
 int mma_launch(const MmaStep& a, cudaStream_t st);
 
@@ -104,6 +109,7 @@ struct MmaBatchStep {
   int ctas;
   int64_t bt_threads, fin_threads;
   int* status;
+  uint32_t spin;
 };
 int mma_batch_launch(const MmaBatchStep& a, cudaStream_t st);
 int mma_max_members();  // most members of one batched launch
@@ -131,6 +137,7 @@ struct ScaledMmaStep {
   double* state;
   double decay;
   int* status;
+  uint32_t spin;
 };
 int scaled_mma_launch(const ScaledMmaStep& a, cudaStream_t st);
 int scaled_mma_occupancy(int fmt);  // resident CTAs per SM for R <= 32 (0 on error)

@@ -68,6 +68,7 @@ def library() -> ctypes.CDLL:
         "whff_step_host": (c_int, [P, P, c_int, i64, P, i64, P, dbl, P]),
         "whff_decompress": (c_int, [P, P, i64, P]),
         "whff_sync_status": (c_int, [P, P]),
+        "whff_set_wait_limit": (c_int, [P, i64]),
         "whff_destroy": (None, [P]),
         "whff_step_noalloc": (c_int, [P, c_int, i64, i64, P, c_int, i64, P, i64, P, dbl, P]),
         "whff_graph_create": (c_int, [P, P, c_int, i64, P, i64, P, dbl, P, ctypes.POINTER(P)]),
@@ -273,6 +274,10 @@ class Handle:
 
     def sync_status(self, stream=None) -> int:
         return int(library().whff_sync_status(self._ptr, _stream_ptr(stream)))
+
+    def set_wait_limit(self, polls: int):
+        """Polls of the tensor-core kernels' in-loop waits (< 0: the default); for failure-detection tests."""
+        _check(library().whff_set_wait_limit(self._ptr, int(polls)))
 
     def destroy(self):
         if self._ptr:
