@@ -107,7 +107,7 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCES = ("gemv_kernels.cuh", "wz1_decode.cuh", "wz2_kernels.cuh", "wz2_dispatch.cuh")
+KERNEL_SOURCES = ("gemv_kernels.cuh", "wz1_decode.cuh", "wz2_kernels.cuh", "wz2_dispatch.cuh", "wz2_stream.cuh", "bulk.cuh")
 
 
 def kernel_source_hash():
@@ -513,6 +513,8 @@ def run_whff(args, rank, world, local_rank):
     kernel_ms = float(np.mean(per_ms))  # one launch per step when ksplit == 1
     achieved = algo_bytes / (kernel_ms * 1e-3) / 1e9
     kname = {1: "wz1_gemv_kernel", 5: "wz2_gemv_kernel", 6: "wz2_gemv_kernel"}.get(head[0], "scaled_range_kernel")
+    if tuned and head[0] in (5, 6) and tuned["fold"] & 4:  # bulk-staged kernel
+        kname = "wz2_stream_kernel"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind}",
                 "traffic": ncu_traffic(f"{head_name}_{order}"), "kernel": kname,

@@ -282,6 +282,14 @@ void whff_fields_destroy(whff_fields* f);
  * per band instead of blocks, and are not tunable. */
 #define WHFF_FOLD_FP32_PAIRS 1
 #define WHFF_FOLD_LANE_GROUPS 2
+/* Launch flag (same word as the folds): one-right-hand-side passes stream each
+ * warp's block range through a shared-memory ring filled by 1-D bulk copies
+ * (cp.async.bulk on mbarriers) instead of keeping `unroll` blocks in flight
+ * in registers -- more bytes in flight per SM for the short blocks of low
+ * rates.  Same results bit for bit as the register-fed kernel; not with lane
+ * groups, and device-resident streams only (host-resident handles ignore it).
+ * whff_tune includes it among its candidates. */
+#define WHFF_CONFIG_BULK 4
 int whff_tune(whff_handle* h, int iters, void* stream, double* best_ms);
 int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_sm, int* fold);
 int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int fold);

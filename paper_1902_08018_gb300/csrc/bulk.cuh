@@ -1,0 +1,49 @@
+// bulk.cuh -- shared-memory barriers and 1-D bulk copies (global -> shared)
+// for the kernels that stage their operands with the copy engine: the
+// tensor-core passes (B tiles) and the streamed R = 1 pass (compressed blocks).
+#pragma once
+#include <cstdint>
+
+namespace whff {
+namespace dev {
+
+constexpr uint32_t kMmaSpinLimit = 1u << 22;  // try_wait polls: bounded to seconds
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; false if the limit ran out.  The in-loop waits of the
+// tensor-core kernels take the launch's limit (a handle setting, lowered only
+// to test failure detection); the waits before TMEM is freed take the full one.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit = kMmaSpinLimit) {
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// One thread: expect `bytes` on `bar` and start the bulk copy global -> shared.
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+}  // namespace dev
+}  // namespace whff

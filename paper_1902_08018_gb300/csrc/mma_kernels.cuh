@@ -41,6 +41,7 @@
 #include <utility>
 
 #include "whff.h"
+#include "bulk.cuh"
 #include "wz2_kernels.cuh"
 
 namespace whff {
@@ -51,9 +52,7 @@ constexpr int kMmaBands = 32;         // 128 coefficient rows per tile
 constexpr int kMmaStageBlocks = 16;   // K = 64 per stage
 constexpr int kMmaKSteps = 4;         // K = 16 per instruction
 constexpr int kMmaDrainStages = 2;    // stages of one tile accumulated in TMEM between drains
-constexpr uint32_t kMmaSpinLimit = 1u << 22;  // try_wait polls: bounded to seconds
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // 64-bit shared-memory matrix descriptor: start >> 4 (bits 0-13), leading
 // byte offset >> 4 (16-29), stride byte offset >> 4 (32-45), descriptor
@@ -120,26 +119,7 @@ struct MmaSmem {
   static constexpr int kBytes = kBars + 80;  // 4 mbarriers, TMEM slot, flags, cursors
 };
 
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 
-// Bounded wait; false if the limit ran out.  The in-loop waits of the
-// tensor-core kernels take the launch's limit (a handle setting, lowered only
-// to test failure detection); the waits before TMEM is freed take the full one.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit = kMmaSpinLimit) {
-  for (uint32_t it = 0; it < limit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
 
 // Eight columns of the three accumulators at ta, ta + stride, ta + 2 stride,
 // summed big + (small + smaller): one wait for the three loads, tied to their
@@ -304,18 +284,7 @@ __device__ __forceinline__ void split_row(const float (&v)[4], uint32_t (&d)[PA]
   }
 }
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
-}
 
-// One thread: expect `bytes` on `bar` and start the bulk copy global -> shared.
-__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
 
 // Persistent grid over the item sequence of one or more passes (members):
 // member k owns items [item_begin, item_begin + tiles S), item = item_begin +

@@ -49,6 +49,7 @@ struct whff_handle {
   bool red32 = false;           // WZ2 / scaled: fold lanes in FP32 pairs (short bands) instead of FP64
   bool groups8 = false;         // WZ2: four 8-lane groups per warp, one band each (short bands)
   int unroll = 2;               // WZ2: blocks in flight per lane (R = 1 kernel)
+  bool bulk = false;            // WZ2, R = 1: blocks staged through shared memory by bulk copies
   int64_t range_ctas = 0;       // WZ2: CTAs of the range-partitioned persistent grid
   int64_t range_len = 0;        // WZ2: blocks per warp range
   int maxseg = 1;               // WZ2: most ranges sharing one band (1 = none shared)
@@ -191,9 +192,12 @@ int launch_wz1(const whff_handle* h, const float* x, int R, int64_t ldx, bool ve
 
 int launch_wz2(const whff_handle* h, const float* x, int R, int64_t ldx, bool vec, double* y, int64_t ldy,
                double* state, double decay, cudaStream_t st) {
+  // the staged kernel needs a padded device stream aligned for its bulk copies
+  const bool staged = h->bulk && R == 1 && !h->groups8 && !h->h_stream &&
+                      reinterpret_cast<uintptr_t>(h->d_stream) % (h->info.rate % 8 == 0 ? 16 : 8) == 0;
   Wz2Step a{h->d_stream, h->info.M, h->info.N, h->BM, h->BN, x, ldx, vec, h->range_len, h->maxseg, h->d_ws,
             y, ldy, state, decay, h->range_ctas, R == 1 ? h->unroll : 2, h->info.fmt == WHFF_FMT_FIXED_LIFT, R,
-            h->red32, h->groups8, h->d_xt};
+            h->red32, h->groups8, h->d_xt, staged, h->d_status};
   int e;
   switch (h->info.rate) {
     case 8: e = wz2_launch<8>(a, st); break;
@@ -217,6 +221,17 @@ int wz2_occ(int rate, bool lift, int unroll) {
     case 16: return wz2_occupancy<16>(lift, unroll);
     case 20: return wz2_occupancy<20>(lift, unroll);
     case 24: return wz2_occupancy<24>(lift, unroll);
+    default: return 0;
+  }
+}
+
+int wz2_stream_occ(int rate, bool lift) {
+  switch (rate) {
+    case 8: return wz2_stream_occupancy<8>(lift);
+    case 12: return wz2_stream_occupancy<12>(lift);
+    case 16: return wz2_stream_occupancy<16>(lift);
+    case 20: return wz2_stream_occupancy<20>(lift);
+    case 24: return wz2_stream_occupancy<24>(lift);
     default: return 0;
   }
 }
@@ -355,7 +370,7 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
     }
     h->d_stream = static_cast<uint8_t*>(dp);
     if (src) std::memcpy(h->h_stream, src, info.stream_bytes);
-  } else if (cudaMalloc(&h->d_stream, info.stream_bytes) != cudaSuccess) {
+  } else if (cudaMalloc(&h->d_stream, info.stream_bytes + kStreamPad) != cudaSuccess) {
     cudaGetLastError();
     set_error("whff_create: cudaMalloc of the compressed stream failed");
     return fail(WHFF_ENOMEM);
@@ -952,6 +967,7 @@ int apply_config(whff_handle* h, int unroll, int ctas_per_sm, int fold) {
   h->ctas_per_sm = ctas_per_sm;
   h->red32 = (fold & WHFF_FOLD_FP32_PAIRS) != 0;
   h->groups8 = (fold & WHFF_FOLD_LANE_GROUPS) != 0;
+  h->bulk = (fold & WHFF_CONFIG_BULK) != 0;
   choose_ranges(h);
   const size_t need = h->maxseg > 1 ? (size_t)h->BM * (size_t)h->maxseg * (size_t)h->ws_rhs * 4 * 8 : 0;
   if (need > h->ws_bytes) {
@@ -981,17 +997,22 @@ extern "C" int whff_get_config(const whff_handle* h, int* unroll, int* ctas_per_
   }
   if (unroll) *unroll = h->unroll;
   if (ctas_per_sm) *ctas_per_sm = h->ctas_per_sm;
-  if (fold) *fold = (h->red32 ? WHFF_FOLD_FP32_PAIRS : 0) | (h->groups8 ? WHFF_FOLD_LANE_GROUPS : 0);
+  if (fold)
+    *fold = (h->red32 ? WHFF_FOLD_FP32_PAIRS : 0) | (h->groups8 ? WHFF_FOLD_LANE_GROUPS : 0) |
+            (h->bulk ? WHFF_CONFIG_BULK : 0);
   return WHFF_OK;
 }
 
 extern "C" int whff_set_config(whff_handle* h, int unroll, int ctas_per_sm, int fold) {
-  if (!h || !is_wz2(h) || (unroll != 2 && unroll != 4 && unroll != 8) || ctas_per_sm < 1 || fold < 0 || fold > 3 ||
-      (unroll != 2 && (fold & WHFF_FOLD_LANE_GROUPS))) {
-    set_error("whff_set_config: WZ2 handles only; unroll 2, 4 or 8 (2 with lane groups); ctas_per_sm >= 1; fold 0..3");
+  if (!h || !is_wz2(h) || (unroll != 2 && unroll != 4 && unroll != 8) || ctas_per_sm < 1 || fold < 0 || fold > 7 ||
+      (unroll != 2 && (fold & WHFF_FOLD_LANE_GROUPS)) ||
+      ((fold & WHFF_CONFIG_BULK) && (fold & WHFF_FOLD_LANE_GROUPS))) {
+    set_error("whff_set_config: WZ2 handles only; unroll 2, 4 or 8 (2 with lane groups); ctas_per_sm >= 1; "
+              "flags 0..7, bulk staging not with lane groups");
     return WHFF_EINVAL;
   }
-  const int occ = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, unroll);
+  const bool lift = h->info.fmt == WHFF_FMT_FIXED_LIFT;
+  const int occ = (fold & WHFF_CONFIG_BULK) ? wz2_stream_occ(h->info.rate, lift) : wz2_occ(h->info.rate, lift, unroll);
   if (occ <= 0 || ctas_per_sm > occ) {
     set_error("whff_set_config: more CTAs per SM than can be resident");
     return WHFF_EINVAL;
@@ -1039,17 +1060,21 @@ extern "C" int whff_tune(whff_handle* h, int iters, void* stream, double* best_m
   WHFF_CUDA_TRY(cudaEventCreate(&e0));
   WHFF_CUDA_TRY(cudaEventCreate(&e1));
   const int orig_u = h->unroll, orig_c = h->ctas_per_sm;
-  const int orig_f = (h->red32 ? WHFF_FOLD_FP32_PAIRS : 0) | (h->groups8 ? WHFF_FOLD_LANE_GROUPS : 0);
+  const int orig_f = (h->red32 ? WHFF_FOLD_FP32_PAIRS : 0) | (h->groups8 ? WHFF_FOLD_LANE_GROUPS : 0) |
+                     (h->bulk ? WHFF_CONFIG_BULK : 0);
   double best = 1e30;
   int bu = orig_u, bc = orig_c, bf = orig_f;
   int err = WHFF_OK;
+  const bool lift = h->info.fmt == WHFF_FMT_FIXED_LIFT;
   // candidates: the top three CTA counts per SM x (unroll 2 with each of the four
-  // folds, unroll 4 and 8 with the two whole-warp folds)
-  for (int cand = 0; cand < 24 && err == WHFF_OK; ++cand) {
-    const int u = cand < 12 ? 2 : cand < 18 ? 4 : 8;
-    const int f = (cand & 1) | (cand < 12 && (cand & 2) ? WHFF_FOLD_LANE_GROUPS : 0);
-    const int c = wz2_occ(h->info.rate, h->info.fmt == WHFF_FMT_FIXED_LIFT, u) -
-                  (cand < 12 ? cand / 4 : cand < 18 ? (cand - 12) / 2 : (cand - 18) / 2);
+  // folds, unroll 4 and 8 with the two whole-warp folds, and -- on device-resident
+  // streams -- the bulk-staged kernel with the two whole-warp folds)
+  const int ncand = h->h_stream ? 24 : 30;
+  for (int cand = 0; cand < ncand && err == WHFF_OK; ++cand) {
+    const int u = cand < 12 ? 2 : cand < 18 ? 4 : cand < 24 ? 8 : 2;
+    const int f = (cand & 1) | (cand < 12 && (cand & 2) ? WHFF_FOLD_LANE_GROUPS : 0) | (cand >= 24 ? WHFF_CONFIG_BULK : 0);
+    const int c = (cand >= 24 ? wz2_stream_occ(h->info.rate, lift) : wz2_occ(h->info.rate, lift, u)) -
+                  (cand < 12 ? cand / 4 : cand < 18 ? (cand - 12) / 2 : cand < 24 ? (cand - 18) / 2 : (cand - 24) / 2);
     if (c < 1) continue;
     if ((err = apply_config(h, u, c, f)) != WHFF_OK) break;
     if ((err = whff_step(h, h->d_x, 1, h->info.N, h->d_y, h->info.M, nullptr, 0.0, stream)) != WHFF_OK) break;

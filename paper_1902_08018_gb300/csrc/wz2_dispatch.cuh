@@ -3,6 +3,7 @@
 #pragma once
 #include "wz2_dispatch.h"
 #include "wz2_kernels.cuh"
+#include "wz2_stream.cuh"
 
 namespace whff {
 
@@ -14,8 +15,27 @@ static void wz2_launch_one(const Wz2Step& a, cudaStream_t st) {
 }
 
 template <int RATE, bool LIFT>
+static int wz2_stream_smem_attr() {
+  static int done = 0;  // once per instantiation and process (the attribute is per function)
+  if (!done) {
+    if (cudaFuncSetAttribute(dev::wz2_stream_kernel<RATE, LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             dev::Wz2Stream<RATE>::kSmemBytes) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    done = 1;
+  }
+  return 0;
+}
+
+template <int RATE, bool LIFT>
 static int wz2_launch_lift(const Wz2Step& a, cudaStream_t st) {
-  if (a.groups8) {  // short bands: four 8-lane groups per warp, two blocks in flight per lane
+  if (a.staged && a.R == 1 && !a.groups8) {
+    if (wz2_stream_smem_attr<RATE, LIFT>()) return -1;
+    dev::wz2_stream_kernel<RATE, LIFT><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, dev::Wz2Stream<RATE>::kSmemBytes,
+                                         st>>>(a.stream, a.M, a.N, a.BM, a.BN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg,
+                                               a.ws, a.y, a.ldy, a.state, a.decay, a.red32, a.status);
+  } else if (a.groups8) {  // short bands: four 8-lane groups per warp, two blocks in flight per lane
     switch (a.R) {
       case 1: wz2_launch_one<RATE, LIFT, 1, 2, 8>(a, st); break;
       case 2: wz2_launch_one<RATE, LIFT, 2, 2, 8>(a, st); break;
@@ -97,6 +117,28 @@ static cudaError_t wz2_occ_lift(int* occ, int unroll, int threads) {
 }
 
 template <int RATE>
+int wz2_stream_occupancy(bool lift) {
+  int occ = 0;
+  const int threads = dev::kWarpsPerCta * 32;
+  const int smem = dev::Wz2Stream<RATE>::kSmemBytes;
+  cudaError_t e;
+  if (lift) {
+    e = wz2_stream_smem_attr<RATE, true>() ? cudaErrorInvalidValue
+                                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                                &occ, dev::wz2_stream_kernel<RATE, true>, threads, smem);
+  } else {
+    e = wz2_stream_smem_attr<RATE, false>() ? cudaErrorInvalidValue
+                                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                                 &occ, dev::wz2_stream_kernel<RATE, false>, threads, smem);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ;
+}
+
+template <int RATE>
 int wz2_occupancy(bool lift, int unroll) {
   int occ = 0;
   const int threads = dev::kWarpsPerCta * 32;
@@ -116,4 +158,5 @@ int wz2_occupancy(bool lift, int unroll) {
   template int whff::wz2_batched_launch<RATE>(const whff::Wz2Batch&, cudaStream_t);                           \
   template int whff::wz2_decompress<RATE>(const uint8_t*, int64_t, int64_t, int64_t, int64_t, double*, int64_t, \
                                           bool, cudaStream_t);                                                \
-  template int whff::wz2_occupancy<RATE>(bool, int);
+  template int whff::wz2_occupancy<RATE>(bool, int);                                                         \
+  template int whff::wz2_stream_occupancy<RATE>(bool);

@@ -33,7 +33,13 @@ struct Wz2Step {
   bool red32;      // fold lanes with the FP32 pair butterfly (short bands)
   bool groups8;    // four 8-lane groups per warp, one band each (short bands)
   float* xt;       // lift: scratch for (2G)^T x, 4 BN floats per right-hand side (8 columns)
+  bool staged;     // R = 1: stream each warp's range through shared memory by bulk copies
+  int* status;     // device status word (bounded waits of the staged kernel)
 };
+
+// Bytes a handle's device stream allocation carries past the stream, so that
+// 16-byte-rounded bulk copies of the last blocks stay inside it.
+constexpr int kStreamPad = 256;
 
 
 struct Wz2Batch {
@@ -152,5 +158,8 @@ int wz2_decompress(const uint8_t* stream, int64_t M, int64_t N, int64_t BN, int6
 // resident CTAs per SM of the R = 1 kernel for the given unroll (0 on error)
 template <int RATE>
 int wz2_occupancy(bool lift, int unroll);
+// resident CTAs per SM of the staged R = 1 kernel (0 on error)
+template <int RATE>
+int wz2_stream_occupancy(bool lift);
 
 }  // namespace whff

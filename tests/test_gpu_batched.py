@@ -88,7 +88,7 @@ def test_tuner_keeps_results(env, orc, tmp_path):
     cache = str(tmp_path / "tune.json")
     with W.whff_create(blob) as h:
         rec = h.tune(iters=3, cache=cache)
-        assert rec["unroll"] in (2, 4, 8) and rec["ctas_per_sm"] >= 1 and rec["fold"] in (0, 1, 2, 3)
+        assert rec["unroll"] in (2, 4, 8) and rec["ctas_per_sm"] >= 1 and rec["fold"] in (0, 1, 2, 3, 4, 5)
         assert not rec["cached"]
         y = torch.zeros(3000, dtype=torch.float64, device="cuda")
         h.step(x, y)
@@ -96,12 +96,13 @@ def test_tuner_keeps_results(env, orc, tmp_path):
         assert _rel(y.cpu().numpy(), ref) <= TOL
         y0 = y.clone()
         c, f = rec["ctas_per_sm"], rec["fold"]
-        for cc in (c, 1):  # blocks in flight change the schedule, not the arithmetic
+        fb = f & 3  # the fold without the bulk-staging flag (4)
+        for cc in (c, 1):  # blocks in flight (registers or bulk-staged) change the schedule, not the arithmetic
             ys = []
-            for u in ((2, 4, 8) if f < 2 else (2,)):
+            for u, ff in ([(2, fb), (4, fb), (8, fb), (2, fb | 4)] if fb < 2 else [(2, fb)]):
                 try:
-                    h.set_config(u, cc, f)
-                except W.WhffError:  # more CTAs per SM than this unroll keeps resident
+                    h.set_config(u, cc, ff)
+                except W.WhffError:  # more CTAs per SM than this kernel keeps resident
                     continue
                 h.step(x, y)
                 torch.cuda.synchronize()
@@ -118,7 +119,7 @@ def test_tuner_keeps_results(env, orc, tmp_path):
         with pytest.raises(W.WhffError):
             h.set_config(1, 1)
         with pytest.raises(W.WhffError):
-            h.set_config(2, 1, 4)
+            h.set_config(2, 1, 8)
         with pytest.raises(W.WhffError):
             h.set_config(4, 1, 2)  # lane groups take unroll 2
         with pytest.raises(W.WhffError):
