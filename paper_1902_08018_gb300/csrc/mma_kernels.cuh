@@ -210,53 +210,6 @@ __global__ void wz2_mma_btiles(MmaPass single, const MmaPass* __restrict__ table
 }
 
 
-// Field k of a block, already times the block scale s = 2^e: the field is
-// OR-ed into the mantissa of 2^(e+23) (creg = its exponent bits) and
-// 2^e (2^23 + 2^(W-1)) (bias) is subtracted -- both exact, so this is
-// (field - 2^(W-1)) * s with one logic op and one add.  A zero block passes
-// mreg = creg = 0 and bias = 0.
-template <int RATE, int K>
-__device__ __forceinline__ float wz2_field_scaled(const uint32_t (&w)[Wz2Layout<RATE>::kWords], uint32_t mreg,
-                                                  uint32_t creg, float bias) {
-  using Lay = Wz2Layout<RATE>;
-  constexpr int off = 13 + Lay::kW * K;
-  constexpr int wi = off / 32, sh = off % 32;
-  uint32_t u;
-  if constexpr (sh + Lay::kW <= 32) {
-    u = w[wi] >> sh;
-  } else {
-    u = __funnelshift_r(w[wi], w[wi + 1], sh);
-  }
-  return __uint_as_float((u & mreg) | creg) - bias;
-}
-
-template <int RATE, int... Ks>
-__device__ __forceinline__ void wz2_fields_scaled_impl(const uint32_t (&w)[Wz2Layout<RATE>::kWords], uint32_t mreg,
-                                                       uint32_t creg, float bias, float (&f)[16],
-                                                       std::integer_sequence<int, Ks...>) {
-  ((f[Ks] = wz2_field_scaled<RATE, Ks>(w, mreg, creg, bias)), ...);
-}
-
-// The 16 coefficients of a block times its scale 2^(E+K-154): the exponent
-// trick needs E + K - 4 <= 254 (|a| below about 2^103); larger blocks take
-// the exact multiply.
-template <int RATE>
-__device__ __forceinline__ void wz2_fields_times_scale(const uint32_t (&w)[Wz2Layout<RATE>::kWords], float (&f)[16]) {
-  using Lay = Wz2Layout<RATE>;
-  const uint32_t E = w[0] & 0xFFu, K = (w[0] >> 8) & 31u;
-  if (E + K <= 258u) {
-    const uint32_t creg = E ? (E + K - 4u) << 23 : 0u;
-    const uint32_t mreg = E ? Lay::kMask : 0u;
-    const float bias = E ? __uint_as_float(creg | (1u << (Lay::kW - 1))) : 0.f;
-    wz2_fields_scaled_impl<RATE>(w, mreg, creg, bias, f, std::make_integer_sequence<int, 16>{});
-  } else {
-    const float s = __uint_as_float((E + K - 27u) << 23);
-    wz2_fields<RATE>(w, f);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) f[k] *= s;
-  }
-}
-
 // cvt.rn.bf16x2.f32: the packed pair (lo in bits 0-15, hi in bits 16-31).
 __device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
   uint32_t d;

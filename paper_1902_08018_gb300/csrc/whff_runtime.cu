@@ -143,6 +143,11 @@ size_t mma_ws_need(const whff_handle* h, int R) {
   return (size_t)ceil_div(h->info.M, 128) * (size_t)h->mma_maxseg * (size_t)R * 128 * 8;
 }
 
+// The lift's transformed x: 4 BN floats per right-hand side of a pass (up to 8).
+size_t xt_bytes(const whff_handle* h) {
+  return (size_t)4 * h->BN * std::min(h->max_rhs, kMaxRhsKernel) * sizeof(float);
+}
+
 // Workspace bytes a CUDA-core pass of the plan needs.
 size_t ws_need(const whff_handle* h) {
   if (h->info.fmt == WHFF_FMT_ZFP)
@@ -404,8 +409,7 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
       return fail(WHFF_ENOMEM);
     }
   }
-  if ((info.fmt == WHFF_FMT_FIXED_LIFT &&
-       cudaMalloc(&h->d_xt, (size_t)4 * h->BN * std::min(max_rhs, kMaxRhsKernel) * sizeof(float)) != cudaSuccess) ||
+  if ((info.fmt == WHFF_FMT_FIXED_LIFT && cudaMalloc(&h->d_xt, xt_bytes(h)) != cudaSuccess) ||
       (h->ws_bytes && cudaMalloc(&h->d_ws, h->ws_bytes) != cudaSuccess) ||
       cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->d_x, (size_t)info.N * (size_t)max_rhs * sizeof(float)) != cudaSuccess ||
@@ -442,7 +446,7 @@ extern "C" int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, 
   if (device_bytes)
     *device_bytes = (h->h_stream ? 0 : h->info.stream_bytes) + h->ws_bytes + h->ws_mma_bytes + sizeof(int) +
                     (size_t)h->info.N * h->max_rhs * 4 + (size_t)h->info.M * h->max_rhs * 8 +
-                    (h->d_xt ? (size_t)4 * h->BN * std::min(h->max_rhs, kMaxRhsKernel) * sizeof(float) : 0);
+                    (h->d_xt ? xt_bytes(h) : 0);
   return WHFF_OK;
 }
 

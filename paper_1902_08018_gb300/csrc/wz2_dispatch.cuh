@@ -9,7 +9,7 @@ namespace whff {
 
 template <int RATE, bool LIFT, int R, int U, int GL = 32>
 static void wz2_launch_one(const Wz2Step& a, cudaStream_t st) {
-  dev::wz2_gemv_kernel<RATE, LIFT, R, U, GL><<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
+  dev::wz2_gemv_entry<RATE, LIFT, R, U, GL>()<<<(unsigned)a.ctas, dev::kWarpsPerCta * 32, 0, st>>>(
       a.stream, a.M, a.N, a.BM, a.BN, a.x, a.ldx, a.x_vec_ok, a.L, a.maxseg, a.ws, a.y, a.ldy, a.state, a.decay,
       a.red32);
 }
@@ -110,10 +110,10 @@ int wz2_decompress(const uint8_t* stream, int64_t M, int64_t N, int64_t BN, int6
 template <int RATE, bool LIFT>
 static cudaError_t wz2_occ_lift(int* occ, int unroll, int threads) {
   if (unroll == 8)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::wz2_gemv_kernel<RATE, LIFT, 1, 8, 32>, threads, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::wz2_gemv_entry<RATE, LIFT, 1, 8, 32>(), threads, 0);
   if (unroll == 4)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::wz2_gemv_kernel<RATE, LIFT, 1, 4, 32>, threads, 0);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::wz2_gemv_kernel<RATE, LIFT, 1, 2, 32>, threads, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::wz2_gemv_entry<RATE, LIFT, 1, 4, 32>(), threads, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::wz2_gemv_entry<RATE, LIFT, 1, 2, 32>(), threads, 0);
 }
 
 template <int RATE>

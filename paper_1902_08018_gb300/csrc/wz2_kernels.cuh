@@ -13,7 +13,9 @@
 // the FP64 epilogue.
 #pragma once
 #include <cstdint>
+#include <utility>
 
+#include "f32x2.cuh"
 #include "gemv_kernels.cuh"
 #include "wz2_batch.h"
 
@@ -86,6 +88,53 @@ __device__ __forceinline__ void wz2_load(const uint8_t* __restrict__ base, int64
       w[2 * i] = v.x;
       w[2 * i + 1] = v.y;
     }
+  }
+}
+
+// Field k of a block, already times the block scale s = 2^e: the field is
+// OR-ed into the mantissa of 2^(e+23) (creg = its exponent bits) and
+// 2^e (2^23 + 2^(W-1)) (bias) is subtracted -- both exact, so this is
+// (field - 2^(W-1)) * s with one logic op and one add.  A zero block passes
+// mreg = creg = 0 and bias = 0.
+template <int RATE, int K>
+__device__ __forceinline__ float wz2_field_scaled(const uint32_t (&w)[Wz2Layout<RATE>::kWords], uint32_t mreg,
+                                                  uint32_t creg, float bias) {
+  using Lay = Wz2Layout<RATE>;
+  constexpr int off = 13 + Lay::kW * K;
+  constexpr int wi = off / 32, sh = off % 32;
+  uint32_t u;
+  if constexpr (sh + Lay::kW <= 32) {
+    u = w[wi] >> sh;
+  } else {
+    u = __funnelshift_r(w[wi], w[wi + 1], sh);
+  }
+  return __uint_as_float((u & mreg) | creg) - bias;
+}
+
+template <int RATE, int... Ks>
+__device__ __forceinline__ void wz2_fields_scaled_impl(const uint32_t (&w)[Wz2Layout<RATE>::kWords], uint32_t mreg,
+                                                       uint32_t creg, float bias, float (&f)[16],
+                                                       std::integer_sequence<int, Ks...>) {
+  ((f[Ks] = wz2_field_scaled<RATE, Ks>(w, mreg, creg, bias)), ...);
+}
+
+// The 16 coefficients of a block times its scale 2^(E+K-154): the exponent
+// trick needs E + K - 4 <= 254 (|a| below about 2^103); larger blocks take
+// the exact multiply.
+template <int RATE>
+__device__ __forceinline__ void wz2_fields_times_scale(const uint32_t (&w)[Wz2Layout<RATE>::kWords], float (&f)[16]) {
+  using Lay = Wz2Layout<RATE>;
+  const uint32_t E = w[0] & 0xFFu, K = (w[0] >> 8) & 31u;
+  if (E + K <= 258u) {
+    const uint32_t creg = E ? (E + K - 4u) << 23 : 0u;
+    const uint32_t mreg = E ? Lay::kMask : 0u;
+    const float bias = E ? __uint_as_float(creg | (1u << (Lay::kW - 1))) : 0.f;
+    wz2_fields_scaled_impl<RATE>(w, mreg, creg, bias, f, std::make_integer_sequence<int, 16>{});
+  } else {
+    const float s = __uint_as_float((E + K - 27u) << 23);
+    wz2_fields<RATE>(w, f);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) f[k] *= s;
   }
 }
 
@@ -185,43 +234,139 @@ __device__ __forceinline__ void wz2_finish(const float (&hi)[4][R], const float 
                                    active);
 }
 
+// The stored-order field of row-major coefficient m (the inverse of seq_index).
+__device__ __forceinline__ constexpr int seq_field(int m) {
+  constexpr int t[16] = {0, 1, 4, 5, 2, 3, 8, 9, 6, 10, 12, 13, 7, 11, 14, 15};
+  return t[m];
+}
+
+// Field k's bits with the block exponent OR-ed in (see wz2_field_scaled): a
+// float of value 2^(e+23) + field * 2^e.
+template <int RATE, int K>
+__device__ __forceinline__ uint32_t wz2_field_bits(const uint32_t (&w)[Wz2Layout<RATE>::kWords], uint32_t mreg,
+                                                   uint32_t creg) {
+  using Lay = Wz2Layout<RATE>;
+  constexpr int off = 13 + Lay::kW * K;
+  constexpr int wi = off / 32, sh = off % 32;
+  uint32_t u;
+  if constexpr (sh + Lay::kW <= 32) {
+    u = w[wi] >> sh;
+  } else {
+    u = __funnelshift_r(w[wi], w[wi + 1], sh);
+  }
+  return (u & mreg) | creg;
+}
+
+template <int RATE, int... Ks>
+__device__ __forceinline__ void wz2_field_bits_impl(const uint32_t (&w)[Wz2Layout<RATE>::kWords], uint32_t mreg,
+                                                    uint32_t creg, uint32_t (&u)[16], std::integer_sequence<int, Ks...>) {
+  ((u[Ks] = wz2_field_bits<RATE, Ks>(w, mreg, creg)), ...);
+}
+
+// One block's partial for R right-hand sides: p[i][r] = s * sum_b V[i][b] xt_r[b],
+// s = 2^(E+K-154) the block scale.  Two arithmetics, one per rate class, the
+// same for every R and every kernel at a rate (so a column's bits never depend
+// on the other columns of its pass):
+//  * rates 8 and 12 (decode-bound: short blocks, many per byte): the scale is
+//    folded into the field decode (the exponent trick of
+//    wz2_fields_times_scale) and a row's four products are two packed FP32
+//    pairs of columns, (V0 xt0 + V2 xt2) + (V1 xt1 + V3 xt3) -- 14 fewer
+//    instructions per block and right-hand side.  Working on values scaled by a
+//    power of two rounds exactly like scaling at the end.  Blocks above about
+//    2^103 (the trick's exponent limit) decode unscaled and take s at the end.
+//  * rates 16 and up (HBM-bound): fields by the 2^23 trick, the scalar chain
+//    ((V0 xt0 + V1 xt1) + V2 xt2) + V3 xt3 with FMAs, then s (measured faster
+//    there: the packed form needs more registers per block in flight).
 // PRE: x already holds (2G)^T x per 4-column chunk (wz2_xt_kernel), so the
 // lift's transform of x is not repeated per block.
+template <int RATE>
+__host__ __device__ constexpr bool wz2_packed() {
+  return RATE <= 12;
+}
+
 template <int RATE, bool LIFT, int R, bool PRE = false>
 __device__ __forceinline__ void wz2_block_partial(const uint32_t (&w)[Wz2Layout<RATE>::kWords],
                                                   const float* __restrict__ x, int64_t ldx, int64_t c0, int64_t N,
                                                   bool x_fast, bool x_vec_ok, float (&p)[4][R]) {
+  using Lay = Wz2Layout<RATE>;
   const uint32_t E = w[0] & 0xFFu;
   const uint32_t K = (w[0] >> 8) & 31u;
-  // 2^(emax+K-27) is always a normal float; a zero block (E = 0) scales by 0
-  const float s = E ? __uint_as_float((E + K - 27u) << 23) : 0.f;
-  float f[16], V[16];
-  wz2_fields<RATE>(w, f);
-  wz2_unpermute<LIFT>(f, V);
+  if constexpr (wz2_packed<RATE>()) {
+    const bool trick = E + K <= 258u;
+    // trick: the field OR-ed into the mantissa of 2^(e+23), e = E+K-154; else of
+    // 2^23 (unscaled).  A zero block (E = 0) decodes to 0.
+    const uint32_t creg = trick ? (E ? (E + K - 4u) << 23 : 0u) : 0x4B000000u;
+    const uint32_t mreg = E ? Lay::kMask : 0u;
+    const float bias = E ? __uint_as_float(creg | (1u << (Lay::kW - 1))) : 0.f;
+    uint32_t u[16];
+    wz2_field_bits_impl<RATE>(w, mreg, creg, u, std::make_integer_sequence<int, 16>{});
+    const float2 b2 = make_float2(bias, bias);
+    float2 P[4][2];  // P[i][h] = (V[i][2h], V[i][2h+1])
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const float4 xv = x_fast ? __ldg(reinterpret_cast<const float4*>(x + (int64_t)r * ldx + c0))
-                             : load_x4(x, ldx, r, c0, N, x_vec_ok);
-    float xt[4];
-    if (LIFT && !PRE) {  // (2G)^T x
-      const float a = xv.x + xv.y, b = xv.z + xv.w, c = xv.x + xv.z, d = xv.y + xv.w;
-      xt[0] = 2.f * (a + b);
-      xt[1] = b - a;
-      xt[2] = d - c;
-      xt[3] = xv.w - xv.z;
-    } else {
-      xt[0] = xv.x;
-      xt[1] = xv.y;
-      xt[2] = xv.z;
-      xt[3] = xv.w;
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m0 = 4 * i + 2 * h, m1 = m0 + 1;
+        const int k0 = LIFT ? seq_field(m0) : m0, k1 = LIFT ? seq_field(m1) : m1;
+        P[i][h] = sub_f2(make_float2(__uint_as_float(u[k0]), __uint_as_float(u[k1])), b2);
+      }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float4 xv = x_fast ? __ldg(reinterpret_cast<const float4*>(x + (int64_t)r * ldx + c0))
+                               : load_x4(x, ldx, r, c0, N, x_vec_ok);
+      float2 X0, X1;
+      if (LIFT && !PRE) {  // (2G)^T x
+        const float a = xv.x + xv.y, b = xv.z + xv.w, c = xv.x + xv.z, d = xv.y + xv.w;
+        X0 = make_float2(2.f * (a + b), b - a);
+        X1 = make_float2(d - c, xv.w - xv.z);
+      } else {
+        X0 = make_float2(xv.x, xv.y);
+        X1 = make_float2(xv.z, xv.w);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 q = fma_f2(P[i][1], X1, mul_f2(P[i][0], X0));
+        p[i][r] = __fadd_rn(q.x, q.y);
+      }
     }
+    if (!trick) {
+      const float s = __uint_as_float((E + K - 27u) << 23);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float q = V[4 * i] * xt[0];
-      q = fmaf(V[4 * i + 1], xt[1], q);
-      q = fmaf(V[4 * i + 2], xt[2], q);
-      q = fmaf(V[4 * i + 3], xt[3], q);
-      p[i][r] = q * s;
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int r = 0; r < R; ++r) p[i][r] = __fmul_rn(p[i][r], s);
+    }
+  } else {
+    // 2^(emax+K-27) is always a normal float; a zero block (E = 0) scales by 0
+    const float s = E ? __uint_as_float((E + K - 27u) << 23) : 0.f;
+    float f[16], V[16];
+    wz2_fields<RATE>(w, f);
+    wz2_unpermute<LIFT>(f, V);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float4 xv = x_fast ? __ldg(reinterpret_cast<const float4*>(x + (int64_t)r * ldx + c0))
+                               : load_x4(x, ldx, r, c0, N, x_vec_ok);
+      float xt[4];
+      if (LIFT && !PRE) {  // (2G)^T x
+        const float a = xv.x + xv.y, b = xv.z + xv.w, c = xv.x + xv.z, d = xv.y + xv.w;
+        xt[0] = 2.f * (a + b);
+        xt[1] = b - a;
+        xt[2] = d - c;
+        xt[3] = xv.w - xv.z;
+      } else {
+        xt[0] = xv.x;
+        xt[1] = xv.y;
+        xt[2] = xv.z;
+        xt[3] = xv.w;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float q = V[4 * i] * xt[0];
+        q = fmaf(V[4 * i + 1], xt[1], q);
+        q = fmaf(V[4 * i + 2], xt[2], q);
+        q = fmaf(V[4 * i + 3], xt[3], q);
+        p[i][r] = q * s;
+      }
     }
   }
 }
@@ -306,11 +451,10 @@ static __global__ void wz2_xt_kernel(const float* __restrict__ x, int64_t ldx, i
 // band would spend its time folding).  With the lift, x is the transformed
 // vector of wz2_xt_kernel (4 BN floats per right-hand side).
 template <int RATE, bool LIFT, int R, int UNROLL, int GL>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
-    wz2_gemv_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BM, int64_t BN,
-                    const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int64_t L, int maxseg,
-                    double* __restrict__ ws, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
-                    double decay, bool red32) {
+__device__ __forceinline__ void wz2_gemv_body(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BM,
+                                              int64_t BN, const float* __restrict__ x, int64_t ldx, bool x_vec_ok,
+                                              int64_t L, int maxseg, double* __restrict__ ws, double* __restrict__ y,
+                                              int64_t ldy, double* __restrict__ state, double decay, bool red32) {
   constexpr int64_t kBlockBytes = 4 * Wz2Layout<RATE>::kWords;
   constexpr int NG = 32 / GL;  // pieces taken at once
   const int lane = threadIdx.x & 31;
@@ -354,6 +498,38 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
       b0 = min(b1, (b0 / BN + NG) * BN);
     }
   }
+}
+
+// The persistent kernel (body above).  Its packed unroll-4 instantiation
+// (rates 8 and 12) is held to 3 resident CTAs per SM; every other one keeps
+// the compiler's default register budget.
+template <int RATE, bool LIFT, int R, int UNROLL, int GL>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+    wz2_gemv_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BM, int64_t BN,
+                    const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int64_t L, int maxseg,
+                    double* __restrict__ ws, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                    double decay, bool red32) {
+  wz2_gemv_body<RATE, LIFT, R, UNROLL, GL>(stream, M, N, BM, BN, x, ldx, x_vec_ok, L, maxseg, ws, y, ldy, state,
+                                           decay, red32);
+}
+
+template <int RATE, bool LIFT, int R, int UNROLL, int GL>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 3)
+    wz2_gemv_kernel_o3(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BM, int64_t BN,
+                       const float* __restrict__ x, int64_t ldx, bool x_vec_ok, int64_t L, int maxseg,
+                       double* __restrict__ ws, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                       double decay, bool red32) {
+  wz2_gemv_body<RATE, LIFT, R, UNROLL, GL>(stream, M, N, BM, BN, x, ldx, x_vec_ok, L, maxseg, ws, y, ldy, state,
+                                           decay, red32);
+}
+
+// The instantiation a launch uses.
+template <int RATE, bool LIFT, int R, int UNROLL, int GL>
+constexpr auto wz2_gemv_entry() {
+  if constexpr (wz2_packed<RATE>() && R == 1 && UNROLL == 4)
+    return &wz2_gemv_kernel_o3<RATE, LIFT, R, UNROLL, GL>;
+  else
+    return &wz2_gemv_kernel<RATE, LIFT, R, UNROLL, GL>;
 }
 
 // sum_{k < n} p[k * stride], added in k order; the loads of eight terms are
