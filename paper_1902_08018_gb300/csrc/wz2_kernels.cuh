@@ -371,6 +371,49 @@ __device__ __forceinline__ void wz2_block_partial(const uint32_t (&w)[Wz2Layout<
   }
 }
 
+// A pair of blocks' partials into the lane's TwoSum sums: (p0 + p1) per row
+// and right-hand side.  At the packed rates the rows go in FP32 pairs (rows
+// 0-1, 2-3); each half rounds as the scalar TwoSum, so the bits are the same.
+template <int RATE, int R>
+__device__ __forceinline__ void wz2_acc_pair(float (&hi)[4][R], float (&lo)[4][R], const float (&p0)[4][R],
+                                             const float (&p1)[4][R]) {
+  if constexpr (wz2_packed<RATE>()) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float2 H = make_float2(hi[2 * h][r], hi[2 * h + 1][r]), Lo = make_float2(lo[2 * h][r], lo[2 * h + 1][r]);
+        two_sum_acc2(H, Lo, add_f2(make_float2(p0[2 * h][r], p0[2 * h + 1][r]), make_float2(p1[2 * h][r], p1[2 * h + 1][r])));
+        hi[2 * h][r] = H.x, hi[2 * h + 1][r] = H.y, lo[2 * h][r] = Lo.x, lo[2 * h + 1][r] = Lo.y;
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r] + p1[i][r]);
+  }
+}
+
+// One block's partial alone (a lane's odd last block of a piece).
+template <int RATE, int R>
+__device__ __forceinline__ void wz2_acc_one(float (&hi)[4][R], float (&lo)[4][R], const float (&p0)[4][R]) {
+  if constexpr (wz2_packed<RATE>()) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float2 H = make_float2(hi[2 * h][r], hi[2 * h + 1][r]), Lo = make_float2(lo[2 * h][r], lo[2 * h + 1][r]);
+        two_sum_acc2(H, Lo, make_float2(p0[2 * h][r], p0[2 * h + 1][r]));
+        hi[2 * h][r] = H.x, hi[2 * h + 1][r] = H.y, lo[2 * h][r] = Lo.x, lo[2 * h + 1][r] = Lo.y;
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r]);
+  }
+}
+
 // Accumulate the blocks [J0, J1) of one 4-row band (lane l takes J0+l,
 // J0+l+32, ...) into the lane's TwoSum sums.  The arithmetic is fixed: the
 // lane's blocks are taken in pairs (its 1st and 2nd, 3rd and 4th, ...), each
@@ -394,10 +437,7 @@ __device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int6
       float p0[4][R], p1[4][R];
       wz2_block_partial<RATE, LIFT, R, PRE>(w[u], x, ldx, 4 * (J + STRIDE * u), N, x_fast, x_vec_ok, p0);
       wz2_block_partial<RATE, LIFT, R, PRE>(w[u + 1], x, ldx, 4 * (J + STRIDE * (u + 1)), N, x_fast, x_vec_ok, p1);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r] + p1[i][r]);
+      wz2_acc_pair<RATE, R>(hi, lo, p0, p1);
     }
   }
   for (; J + STRIDE < J1; J += 2 * STRIDE) {  // remaining whole pairs
@@ -407,20 +447,14 @@ __device__ __forceinline__ void wz2_piece(const uint8_t* __restrict__ base, int6
     float p0[4][R], p1[4][R];
     wz2_block_partial<RATE, LIFT, R, PRE>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
     wz2_block_partial<RATE, LIFT, R, PRE>(w1, x, ldx, 4 * (J + STRIDE), N, x_fast, x_vec_ok, p1);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r] + p1[i][r]);
+    wz2_acc_pair<RATE, R>(hi, lo, p0, p1);
   }
   if (J < J1) {  // odd last block
     uint32_t w0[NW];
     wz2_load<RATE>(base, J, w0);
     float p0[4][R];
     wz2_block_partial<RATE, LIFT, R, PRE>(w0, x, ldx, 4 * J, N, x_fast, x_vec_ok, p0);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int r = 0; r < R; ++r) two_sum_acc(hi[i][r], lo[i][r], p0[i][r]);
+    wz2_acc_one<RATE, R>(hi, lo, p0);
   }
 }
 
