@@ -1,18 +1,41 @@
 // Tensor-core (tcgen05) passes for the scaled formats: instantiation unit.
 #include <algorithm>
 
+#include <cudaTypedefs.h>
+
 #include "scaled_mma.cuh"
+#include "scaled_mma_tma.cuh"
 #include "wz2_dispatch.h"
 
 namespace whff {
+
+// The TMA-fed BF16 kernel: its shared-memory attribute, set once per width.
+template <int NR>
+static int scaled_tma_attr() {
+  static int done = 0;
+  if (!done) {
+    auto kern = dev::scaled_mma_tma_kernel<NR>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::TmaSmem<NR>::kBytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    done = 1;
+  }
+  return 0;
+}
 
 template <int FMT, int NR>
 static int scaled_mma_one(const ScaledMmaStep& a, cudaStream_t st) {
   using S = dev::ScaledMmaSmem<FMT, NR>;
   auto kern = dev::scaled_mma_kernel<FMT, NR>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes) != cudaSuccess ||
-      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
-          cudaSuccess) {
+  const bool tma = FMT == 2 && a.tmap != nullptr;
+  if (tma ? scaled_tma_attr<NR>() != 0
+          : (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes) != cudaSuccess ||
+             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared) != cudaSuccess)) {
     cudaGetLastError();
     return -1;
   }
@@ -21,9 +44,15 @@ static int scaled_mma_one(const ScaledMmaStep& a, cudaStream_t st) {
   const dev::MmaPass pass{a.x, a.y, a.btiles, a.ws, a.ldx, a.ldy, a.N, a.M, 0, 0, 0, nstages, tiles, a.R, a.maxseg};
   const int64_t bthreads = (int64_t)nstages * dev::kMmaStageBlocks * NR;
   dev::wz2_mma_btiles<false, NR><<<(unsigned)((bthreads + 255) / 256), 256, 0, st>>>(pass, nullptr, 1, bthreads);
-  kern<<<(unsigned)a.ctas, dev::kMmaThreads, S::kBytes, st>>>(a.payload, a.scales, a.M, a.ld, a.TN, a.btiles, a.ws,
-                                                              nstages, a.R, a.maxseg, (int64_t)tiles * nstages, a.L,
-                                                              a.status, a.spin);
+  if (tma) {
+    dev::scaled_mma_tma_kernel<NR><<<(unsigned)a.ctas, dev::kTmaThreads, dev::TmaSmem<NR>::kBytes, st>>>(
+        *static_cast<const CUtensorMap*>(a.tmap), a.row0, a.scales, a.TN, a.btiles, a.ws, nstages, a.R, a.maxseg,
+        (int64_t)tiles * nstages, a.L, a.status, a.spin);
+  } else {
+    kern<<<(unsigned)a.ctas, dev::kMmaThreads, S::kBytes, st>>>(a.payload, a.scales, a.M, a.ld, a.TN, a.btiles,
+                                                                a.ws, nstages, a.R, a.maxseg,
+                                                                (int64_t)tiles * nstages, a.L, a.status, a.spin);
+  }
   const int64_t fin = (int64_t)tiles * a.R * 128;
   dev::scaled_mma_finish<<<(unsigned)((fin + 255) / 256), 256, 0, st>>>(a.ws, a.M, nstages, a.R, a.maxseg, tiles, a.L,
                                                                        a.y, a.ldy);
@@ -73,13 +102,65 @@ static int scaled_mma_occ_one() {
   return std::min(std::min(by_regs, by_smem), by_tmem);
 }
 
-int scaled_mma_occupancy(int fmt) {
+// Resident CTAs per SM of the TMA-fed BF16 kernel, from its registers, shared
+// memory and TMEM columns (the occupancy API reported one CTA where two fit).
+template <int NR>
+static int scaled_tma_occ_one() {
+  auto kern = dev::scaled_mma_tma_kernel<NR>;
+  cudaFuncAttributes fa;
+  int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
+  if (scaled_tma_attr<NR>() || cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int warps = dev::kTmaThreads / 32;
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+  const int by_regs = regs_sm / (regs_warp * warps);
+  const int by_smem = smem_sm / (dev::TmaSmem<NR>::kBytes + (int)fa.sharedSizeBytes + reserved);
+  const int by_tmem = 512 / (int)dev::mma_tmem_cols<NR>();
+  return std::min(std::min(by_regs, by_smem), by_tmem);
+}
+
+int scaled_mma_occupancy(int fmt, bool tma) {
   switch (fmt) {
-    case 2: return std::min(scaled_mma_occ_one<2, 16>(), scaled_mma_occ_one<2, 32>());
+    case 2:
+      return tma ? std::min(scaled_tma_occ_one<16>(), scaled_tma_occ_one<32>())
+                 : std::min(scaled_mma_occ_one<2, 16>(), scaled_mma_occ_one<2, 32>());
     case 3: return std::min(scaled_mma_occ_one<3, 16>(), scaled_mma_occ_one<3, 32>());
     case 4: return std::min(scaled_mma_occ_one<4, 16>(), scaled_mma_occ_one<4, 32>());
     default: return 0;
   }
+}
+
+}  // namespace whff
+
+namespace whff {
+
+int scaled_tma_map(void* out, const void* payload, int64_t M, int64_t ld) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return -1;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)M};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};  // bytes between rows (a multiple of 16: ld % 16 == 0)
+  const cuuint32_t box[2] = {64, 128};                  // 128 bytes x 128 rows: one stage
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                            const_cast<void*>(payload), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
 }
 
 }  // namespace whff

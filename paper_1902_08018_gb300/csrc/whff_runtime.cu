@@ -66,6 +66,9 @@ struct whff_handle {
   size_t ws_mma_cap = 0;        // bytes of d_ws_mma
   const float* d_scales = nullptr;  // scaled formats: the tile scales after the payload
   int64_t slice_rows = 0;       // > 0: whff_step runs as consecutive slits of this many rows
+  alignas(64) unsigned char tmap[128] = {};  // BF16: TMA map of the stored matrix (tensor-core passes)
+  bool has_tmap = false;
+  int64_t tma_row0 = 0;         // first row of a row view within the map's matrix
   uint32_t wait_polls = whff::kWaitPolls;  // in-loop bounded waits of the tensor-core kernels
   cudaStream_t create_stream = nullptr;
 };
@@ -390,8 +393,10 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
     // tensor-core passes: a persistent grid (all resident CTAs) over the items
     // (tile of 128 rows, stage of 64 columns), equal contiguous ranges per CTA
     const bool lift = info.fmt == WHFF_FMT_FIXED_LIFT;
+    // BF16 in device memory: the TMA-fed kernel (its map is encoded below)
+    const bool tma = info.fmt == WHFF_FMT_BF16 && !(flags & WHFF_CREATE_HOST_RESIDENT);
     const int occ = wz2 ? std::min(mma_occupancy(info.rate, lift, 16), mma_occupancy(info.rate, lift, 32))
-                        : scaled_mma_occupancy(info.fmt);
+                        : scaled_mma_occupancy(info.fmt, tma);
     if (occ < 1) {
       set_error("whff_create: the tensor-core kernel cannot be resident");
       return fail(WHFF_ECUDA);
@@ -428,6 +433,10 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
   if (!is_blocked(info.fmt))
     h->d_scales = reinterpret_cast<const float*>(h->d_stream + (uint64_t)info.M * (uint64_t)scaled_ld(info.N) *
                                                                    (uint64_t)elem_bytes(info.fmt));
+  // BF16 tensor-core passes take their A tiles by TMA from device memory
+  // (if the map cannot be encoded the register-fed kernel runs instead, same results)
+  if (info.fmt == WHFF_FMT_BF16 && h->d_ws_mma && !h->h_stream)
+    h->has_tmap = scaled_tma_map(h->tmap, h->d_stream, info.M, scaled_ld(info.N)) == 0;
   *out = h;
   return WHFF_OK;
 }
@@ -463,7 +472,8 @@ int launch_mma(const whff_handle* h, const float* x, int R, int64_t ldx, double*
   } else {
     ScaledMmaStep a{h->info.fmt, h->d_stream, h->d_scales, h->info.M, h->info.N, scaled_ld(h->info.N),
                     ceil_div(h->info.N, kScaleTile), x, ldx, R, h->mma_L, h->mma_ctas, h->mma_maxseg,
-                    h->d_ws_mma, h->d_btiles, y, ldy, state, decay, h->d_status, h->wait_polls};
+                    h->d_ws_mma, h->d_btiles, y, ldy, state, decay, h->d_status, h->wait_polls,
+                    h->has_tmap ? h->tmap : nullptr, h->tma_row0};
     e = scaled_mma_launch(a, st);
   }
   if (e) {
@@ -531,6 +541,7 @@ int step_view(const whff_handle* h, int64_t row0, int64_t nrows, const float* x,
   } else {
     v.d_stream = h->d_stream + (uint64_t)row0 * (uint64_t)scaled_ld(h->info.N) * (uint64_t)elem_bytes(fmt);
     v.d_scales = h->d_scales + (row0 / kScaleTile) * ceil_div(h->info.N, kScaleTile);
+    v.tma_row0 = h->tma_row0 + row0;
   }
   choose_split(&v);
   for (int c = v.ctas_per_sm; ws_need(&v) > h->ws_bytes;) {  // fewer warps: longer ranges, fewer segments
