@@ -584,24 +584,36 @@ __device__ __forceinline__ double seq_sum_strided(const double* __restrict__ p, 
   return t;
 }
 
-// Sum the segments of bands shared by several warp ranges, in segment order,
-// then the state update (bands inside one range were finished by the kernel).
+// Sum the segments of bands shared by several warp ranges, then the state
+// update (bands inside one range were finished by the kernel).  Eight lanes per
+// row: lane j adds segments j, j + 8, ... in order, then a fixed xor tree over
+// the eight (the same order every time, so the result is deterministic; with
+// one or two segments it is the plain sum).  A slit of a long matrix has dozens
+// of segments per band: eight lanes keep their loads in flight together.
 static __global__ void wz2_segment_epilogue(const double* __restrict__ ws, int64_t M, int64_t BN, int64_t L,
                                             int maxseg, int R, double* __restrict__ y, int64_t ldy,
                                             double* __restrict__ state, double decay) {
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= M) return;
-  const int64_t I = row / 4;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = q >> 3;
+  const int j = (int)(q & 7);
+  const bool valid = row < M;
+  const int64_t I = valid ? row / 4 : 0;
   const int i = (int)(row % 4);
   const int64_t g_lo = (I * BN) / L, g_hi = ((I + 1) * BN - 1) / L;
-  if (g_lo == g_hi) return;
-  double s = state ? state[row] : 0.0;
+  const bool shared = valid && g_lo != g_hi;
+  double s = (shared && state) ? state[row] : 0.0;
   for (int r = 0; r < R; ++r) {
-    const double t = seq_sum_strided(ws + ((I * maxseg) * R + r) * 4 + i, g_hi - g_lo + 1, (int64_t)R * 4);
-    y[(int64_t)r * ldy + row] = t;
-    s = decay * s + t;
+    double t = 0.0;
+    if (shared)
+      for (int64_t seg = j; seg <= g_hi - g_lo; seg += 8) t += ws[((I * maxseg + seg) * R + r) * 4 + i];
+#pragma unroll
+    for (int o = 4; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (shared && j == 0) {
+      y[(int64_t)r * ldy + row] = t;
+      s = decay * s + t;
+    }
   }
-  if (state) state[row] = s;
+  if (shared && j == 0 && state) state[row] = s;
 }
 
 // ------------------------------------------------------------- batched launch
