@@ -42,7 +42,7 @@ METRIC = "compressed GEMV: HBM GB/s & % peak; p99 control-step latency at rel.er
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 DECAY = 0.99
-FMT_CODES = {"wz1": 1, "bf16": 2, "fp16": 3, "fp8": 4, "wz2-lift": 5, "wz2-bfp": 6, "fp32": 7}
+FMT_CODES = {"wz1": 1, "bf16": 2, "fp16": 3, "fp8": 4, "wz2-lift": 5, "wz2-bfp": 6, "fp32": 7, "wz3": 8}
 FMT_NAMES = {v: k for k, v in FMT_CODES.items()}
 ERR_TARGET = 1e-5
 
@@ -57,8 +57,9 @@ def parse_args():
     p.add_argument("--fmt", default="wz2-lift", choices=sorted(FMT_CODES))
     p.add_argument("--rate", type=int, default=16)
     p.add_argument("--sweep", default="wz1:16,wz2-lift:8,wz2-lift:12,wz2-bfp:16,wz2-lift:20,wz2-bfp:20,wz2-lift:24,"
-                                      "fp8:0,fp16:0,bf16:0",
-                   help="extra fmt:rate pairs timed on the same matrix ('' for none)")
+                                      "fp8:0,fp16:0,bf16:0,wz3:1e-7",
+                   help="extra fmt:rate pairs timed on the same matrix ('' for none; wz3 takes its "
+                        "absolute tolerance in place of a rate)")
     p.add_argument("--sweep-steps", type=int, default=400)
     p.add_argument("--sweep-rhs", type=int, default=1, help="1: also time every sweep format with 32 right-hand sides")
     p.add_argument("--e2e-steps", type=int, default=200)
@@ -205,7 +206,8 @@ def parse_specs(args):
     specs = [(FMT_CODES[args.fmt], args.rate)]
     for item in filter(None, args.sweep.split(",")):
         name, rate = item.split(":")
-        spec = (FMT_CODES[name], int(rate) if FMT_CODES[name] in (1, 5, 6) else 0)
+        code = FMT_CODES[name]
+        spec = (code, float(rate) if code == 8 else int(rate) if code in (1, 5, 6) else 0)
         if spec not in specs:
             specs.append(spec)
     return specs
@@ -229,7 +231,11 @@ def build_workload(order: int, specs, keep_fp64_device: bool, sample_rows: np.nd
     km = matrix_for(order)
     L = W.library()
     blobs = {}
+    accuracy = [spec for spec in specs if spec[0] == 8]  # fixed accuracy: encoded from the whole matrix
+    A_host = np.empty((order, order)) if accuracy else None
     for fmt, rate in specs:
+        if fmt == 8:
+            continue
         n = W.compressed_size(fmt, rate, order, order)
         b = np.empty(n, dtype=np.uint8)
         if L.whff_blob_init(b.ctypes.data, n, fmt, rate, order, order) != 0:
@@ -240,6 +246,8 @@ def build_workload(order: int, specs, keep_fp64_device: bool, sample_rows: np.nd
     for r0, rows in km.bands(1024):
         if A64 is not None:
             A64[r0:r0 + rows.shape[0]].copy_(torch.from_numpy(rows))
+        if A_host is not None:
+            A_host[r0:r0 + rows.shape[0]] = rows
         sel = (sample_rows >= r0) & (sample_rows < r0 + rows.shape[0])
         for k in np.nonzero(sel)[0]:
             sampled[k] = rows[sample_rows[k] - r0]
@@ -249,6 +257,9 @@ def build_workload(order: int, specs, keep_fp64_device: bool, sample_rows: np.nd
                 raise RuntimeError(L.whff_last_error().decode())
     for b in blobs.values():
         L.whff_blob_seal(b.ctypes.data, b.size)
+    for spec in accuracy:
+        blobs[spec] = W.whff_compress_accuracy(A_host, spec[1])
+    del A_host
     return km, blobs, A64, sampled
 
 

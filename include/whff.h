@@ -65,6 +65,19 @@ extern "C" {
  *    the products summed without further rounding error (compensated FP32
  *    sums, FP64 across lanes) -- up to the order of the additions. */
 #define WHFF_FMT_FP32 7
+/*  WHFF_FMT_FIXED_ACC ("WZ3"): zfp's fixed-accuracy mode (Sec. 4.3 names zfp;
+ *    Table 2 reports its modes) read GPU-first.  WZ2's blocks, lifted
+ *    coefficients and bit layout, but each block takes the largest shift K in
+ *    0..27 whose decoded block stays within an absolute tolerance tol of the
+ *    FP32 input (max error; when none does, the smallest K whose fields fit 31
+ *    bits), and every run of up to 32 blocks of a band one field width W, the
+ *    widest its blocks need; a block takes 8*ceil((13 + 16 W)/64) bytes.  Blob:
+ *    the 64-byte header (rate 0, variable stream length), then the tolerance
+ *    (f64), one u64 per run in band-major order (bits 0-55: byte offset of the
+ *    run's first block in the block area; bits 56-63: W), then the blocks.
+ *    Written by whff_compress_accuracy; decoded value (2G) V (2G)^T *
+ *    2^(K+emax-30), exact in FP64. */
+#define WHFF_FMT_FIXED_ACC 8
 
 #define WHFF_OK 0
 #define WHFF_EINVAL -1     /* bad argument (null, size, leading dimension, rate) */
@@ -95,6 +108,17 @@ size_t whff_compressed_size(int fmt, int rate, int64_t M, int64_t N);
  * WHFF_ENONFINITE. */
 int whff_compress(const double* A, int64_t M, int64_t N, int64_t lda, int fmt, int rate, void* out, size_t out_cap,
                   size_t* out_len, int nthreads);
+
+/* Fixed-accuracy encoding (WHFF_FMT_FIXED_ACC) of all of A at absolute
+ * tolerance tol >= 0: every decoded entry within tol of A rounded to FP32,
+ * except in blocks where 31-bit fields cannot reach it (near-full-scale blocks
+ * at tiny tolerances: those take the finest quantisation that fits).  out must
+ * hold whff_accuracy_max_size(M, N) bytes; *out_len = the blob's bytes.  All
+ * host threads (nthreads <= 0) or the given number; the bytes do not depend on
+ * the thread count.  Errors: WHFF_EINVAL, WHFF_ERANGE, WHFF_ENONFINITE. */
+size_t whff_accuracy_max_size(int64_t M, int64_t N);
+int whff_compress_accuracy(const double* A, int64_t M, int64_t N, int64_t lda, double tol, void* out, size_t out_cap,
+                           size_t* out_len, int nthreads);
 
 /* Band interface for matrices too large to hold in FP64 at once.
  * whff_blob_init writes the header fields of an empty blob; whff_compress_band

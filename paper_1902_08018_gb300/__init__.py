@@ -10,6 +10,7 @@ from .whff import (  # noqa: F401
     Batch,
     Fields,
     FMT_BF16,
+    FMT_FIXED_ACC,
     FMT_FIXED_BFP,
     FMT_FIXED_LIFT,
     FMT_FP8E4M3,
@@ -23,6 +24,7 @@ from .whff import (  # noqa: F401
     compressed_size,
     library,
     whff_compress,
+    whff_compress_accuracy,
     whff_compress_bands,
     whff_create,
     whff_decompress,

@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-Xcompiler", "-fPIC", f"-I{ROOT / 'include'}", f"-I{CSRC}"]
 
 CUDA_SOURCES = ["whff_runtime.cu", "whff_noalloc.cu", "wz2_r8.cu", "wz2_r12.cu", "wz2_r16.cu", "wz2_r20.cu",
-                "wz2_r24.cu", "scaled.cu", "mma.cu", "scaled_mma.cu"]
+                "wz2_r24.cu", "scaled.cu", "mma.cu", "scaled_mma.cu", "wz3.cu"]
 HOST_SOURCES = ["whff_encode.cpp", "whff_serve.cpp"]
 
 

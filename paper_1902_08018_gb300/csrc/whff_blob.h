@@ -37,7 +37,10 @@ int elem_bytes(int fmt);  // 2, 2, 1, 4 for BF16, FP16, FP8, FP32; 0 otherwise
 inline int scaled_vec(int fmt) { return 16 / (fmt == 4 ? 1 : fmt == 7 ? 4 : 2); }
 bool rate_valid(int rate);       // WZ1: 4..64, multiple of 4
 bool wz2_rate_valid(int rate);   // WZ2: 8..24, multiple of 4
-bool is_blocked(int fmt);        // 4x4-block formats (WZ1, WZ2)
+bool is_blocked(int fmt);        // fixed-size 4x4-block formats (WZ1, WZ2)
+inline bool is_wz3(int fmt) { return fmt == 8; }  // fixed accuracy: 4x4 blocks of variable size, indexed runs
+// row alignment of a row view: a 4-row band (block formats) or a 128-row scale tile
+inline int row_align(int fmt) { return (is_blocked(fmt) || is_wz3(fmt)) ? 4 : kScaleTile; }
 uint64_t stream_size(int fmt, int rate, int64_t M, int64_t N);  // 0 if invalid
 uint32_t crc32_update(uint32_t crc, const uint8_t* p, size_t n);  // crc = 0 to start
 inline uint32_t crc32(const uint8_t* p, size_t n) { return crc32_update(0, p, n); }

@@ -128,8 +128,15 @@ int read_header(const uint8_t* blob, size_t len, BlobInfo* info, bool check_stre
   b.crc_stream = ld32(blob + 40);
   b.crc_header = ld32(blob + 44);
   uint64_t want = stream_size(b.fmt, b.rate, b.M, b.N);
+  if (b.fmt == WHFF_FMT_FIXED_ACC && b.rate == 0 && b.M > 0 && b.N > 0) {  // variable length, within its bounds
+    const int64_t BM = ceil_div(b.M, 4), BN = ceil_div(b.N, 4), RB = ceil_div(BN, 32);
+    const uint64_t lo = 8 + 8 * (uint64_t)(BM * RB) + 8 * (uint64_t)(BM * BN);
+    const uint64_t hi = 8 + 8 * (uint64_t)(BM * RB) + 64 * (uint64_t)(BM * BN);
+    if (b.stream_bytes < lo || b.stream_bytes > hi) return WHFF_EFORMAT;
+    want = b.stream_bytes;
+  }
   if (!want || want != b.stream_bytes || len < kHeaderBytes + want) return WHFF_EFORMAT;
-  if (!is_blocked(b.fmt) && b.rate != 8 * elem_bytes(b.fmt)) return WHFF_EFORMAT;
+  if (!is_blocked(b.fmt) && b.fmt != WHFF_FMT_FIXED_ACC && b.rate != 8 * elem_bytes(b.fmt)) return WHFF_EFORMAT;
   if (check_stream && crc32(blob + kHeaderBytes, want) != b.crc_stream) return WHFF_EFORMAT;
   *info = b;
   return WHFF_OK;
@@ -343,6 +350,96 @@ int encode_block_wz2(const float* vals, int rate, bool lift, uint64_t* out) {
   return WHFF_OK;
 }
 
+// ------------------------------------------------------- WZ3 (fixed accuracy)
+// WZ2's block (emax, shift K, 16 offset-binary fields of the lifted, sequency
+// ordered coefficients) with, per block, the largest K in 0..27 whose decoded
+// block is within tol of the FP32 input (max absolute error) -- never below the
+// smallest K whose fields fit 31 bits -- and one field width per run of up to
+// 32 blocks of a band, the widest its blocks need.
+constexpr int kWz3Wmax = 31;
+
+inline int wz3_block_bytes(int W) { return 8 * ((13 + 16 * W + 63) / 64); }
+
+// (2G) applied to one 4-vector (s, d, d0, e): the exact inverse of lin_fwd4 up
+// to the factor 8 that the decoded value's exponent absorbs.
+inline void lin_inv4(int64_t& a, int64_t& b, int64_t& c, int64_t& d) {
+  const int64_t s2 = 2 * a, x = b, y = c, z = d;
+  a = s2 - x - y;
+  b = s2 - x + y;
+  c = s2 + x - y - z;
+  d = s2 + x + y + z;
+}
+
+struct Wz3Block {
+  int emax = 0, K = 0, need = 0;  // need 0: a zero block
+  int64_t v[16] = {};             // sequency order
+};
+
+// One block of 16 FP32 values (row-major 4x4) at tolerance tol.
+int wz3_block(const float* vals, double tol, Wz3Block* out) {
+  *out = Wz3Block();
+  uint32_t bits[16];
+  int emax = INT32_MIN;
+  for (int i = 0; i < 16; ++i) {
+    std::memcpy(&bits[i], &vals[i], 4);
+    const uint32_t E = (bits[i] >> 23) & 0xFF;
+    if (E == 0xFF) return WHFF_ENONFINITE;
+    if (E >= 254) return WHFF_ERANGE;
+    if (bits[i] & 0x7FFFFFFFu) emax = std::max(emax, f32_exponent(bits[i]));
+  }
+  if (emax <= kWz1Emin) return WHFF_OK;
+  int64_t c[16];
+  for (int i = 0; i < 16; ++i) c[i] = f32_to_fixed(bits[i], emax, kWz2Prec);
+  for (int r = 0; r < 4; ++r) lin_fwd4(c[4 * r], c[4 * r + 1], c[4 * r + 2], c[4 * r + 3]);
+  for (int j = 0; j < 4; ++j) lin_fwd4(c[j], c[4 + j], c[8 + j], c[12 + j]);
+  const int* seq = seq_table().idx;
+  int64_t ord[16];
+  for (int k = 0; k < 16; ++k) ord[k] = c[seq[k]];
+  const int64_t lim_lo = -((int64_t)1 << (kWz3Wmax - 1)), lim_hi = ((int64_t)1 << (kWz3Wmax - 1)) - 1;
+  int Kf = 0;
+  for (; Kf < kWz2Kmax; ++Kf) {
+    bool fits = true;
+    for (int k = 0; k < 16 && fits; ++k) {
+      const int64_t t = shift_round_even(ord[k], Kf);
+      fits = t >= lim_lo && t <= lim_hi;
+    }
+    if (fits) break;
+  }
+  int64_t v[16];
+  int K = kWz2Kmax;
+  for (;; --K) {
+    for (int k = 0; k < 16; ++k) v[k] = shift_round_even(ord[k], K);
+    int64_t T[16];
+    for (int k = 0; k < 16; ++k) T[seq[k]] = v[k];
+    for (int j = 0; j < 4; ++j) lin_inv4(T[j], T[4 + j], T[8 + j], T[12 + j]);
+    for (int r = 0; r < 4; ++r) lin_inv4(T[4 * r], T[4 * r + 1], T[4 * r + 2], T[4 * r + 3]);
+    // |T| < 2^40 and 2^(K+emax-30) is a normal double: the product is exact, as ldexp
+    const double scale = std::ldexp(1.0, K + emax - 30);
+    bool within = true;
+    for (int i = 0; i < 16 && within; ++i) within = std::fabs((double)vals[i] - (double)T[i] * scale) <= tol;
+    if (within || K == Kf) break;
+  }
+  int W = 1;
+  for (int k = 0; k < 16; ++k)
+    while (v[k] < -((int64_t)1 << (W - 1)) || v[k] > ((int64_t)1 << (W - 1)) - 1) ++W;
+  out->emax = emax;
+  out->K = K;
+  out->need = W;
+  for (int k = 0; k < 16; ++k) out->v[k] = v[k];
+  return WHFF_OK;
+}
+
+// Block (emax, K, v) written with field width W (nothing for a zero block).
+void wz3_put(const Wz3Block& b, int W, uint64_t* out) {
+  const int nw = wz3_block_bytes(W) / 8;
+  std::memset(out, 0, sizeof(uint64_t) * nw);
+  if (b.need == 0) return;
+  BitSink bs{out};
+  bs.put((uint64_t)(b.emax + 127), 8);
+  bs.put((uint64_t)b.K, 5);
+  for (int k = 0; k < 16; ++k) bs.put((uint64_t)(b.v[k] + ((int64_t)1 << (W - 1))), W);
+}
+
 // --------------------------------------------------------- scaled formats
 struct FmtSpec {
   int mant, emin, bias, ebits;
@@ -540,6 +637,97 @@ extern "C" int whff_blob_seal(void* blob, size_t cap) {
   }
   uint8_t* p = (uint8_t*)blob;
   write_header(p, b.fmt, b.rate, b.M, b.N, b.stream_bytes, crc32(p + kHeaderBytes, b.stream_bytes));
+  return WHFF_OK;
+}
+
+// ------------------------------------------------------ fixed accuracy (WZ3)
+namespace {
+
+int64_t wz3_runs_per_band(int64_t N) { return ceil_div(ceil_div(N, 4), 32); }
+
+// The 16 FP32 values of block (I, J), edge rows and columns replicated.
+void gather_block(const double* A, int64_t M, int64_t N, int64_t lda, int64_t I, int64_t J, float* vals) {
+  for (int r = 0; r < 4; ++r) {
+    const int64_t gi = std::min(4 * I + r, M - 1);
+    for (int c = 0; c < 4; ++c) vals[4 * r + c] = (float)A[gi * lda + std::min(4 * J + c, N - 1)];
+  }
+}
+
+}  // namespace
+
+extern "C" size_t whff_accuracy_max_size(int64_t M, int64_t N) {
+  if (M <= 0 || N <= 0) return 0;
+  const int64_t BM = ceil_div(M, 4), BN = ceil_div(N, 4);
+  return (size_t)kHeaderBytes + 8 + 8 * (size_t)(BM * wz3_runs_per_band(N)) +
+         (size_t)(BM * BN) * (size_t)wz3_block_bytes(kWz3Wmax);
+}
+
+extern "C" int whff_compress_accuracy(const double* A, int64_t M, int64_t N, int64_t lda, double tol, void* out,
+                                      size_t out_cap, size_t* out_len, int nthreads) {
+  if (!A || !out || M <= 0 || N <= 0 || lda < N || !(tol >= 0.0) || out_cap < whff_accuracy_max_size(M, N)) {
+    set_error("whff_compress_accuracy: null argument, empty shape, lda < N, tol < 0 or capacity below "
+              "whff_accuracy_max_size");
+    return WHFF_EINVAL;
+  }
+  const int64_t BM = ceil_div(M, 4), BN = ceil_div(N, 4), RB = wz3_runs_per_band(N);
+  // pass 1: the width of every run
+  std::vector<uint8_t> width((size_t)(BM * RB));
+  std::atomic<int> err{WHFF_OK};
+  parallel_for(BM, nthreads, [&](int64_t I) {
+    float vals[16];
+    Wz3Block b;
+    for (int64_t r = 0; r < RB; ++r) {
+      int W = 0;
+      for (int64_t J = 32 * r; J < std::min(BN, 32 * r + 32); ++J) {
+        gather_block(A, M, N, lda, I, J, vals);
+        const int e = wz3_block(vals, tol, &b);
+        if (e != WHFF_OK) err.store(e);
+        W = std::max(W, b.need);
+      }
+      width[(size_t)(I * RB + r)] = (uint8_t)W;
+    }
+  });
+  if (err.load() != WHFF_OK) {
+    set_error(err.load() == WHFF_ERANGE ? "whff_compress_accuracy: |a| >= 2^127"
+                                        : "whff_compress_accuracy: non-finite value");
+    return err.load();
+  }
+  // offsets of the runs in band-major order
+  std::vector<uint64_t> off((size_t)(BM * RB));
+  uint64_t area = 0;
+  for (int64_t I = 0; I < BM; ++I)
+    for (int64_t r = 0; r < RB; ++r) {
+      off[(size_t)(I * RB + r)] = area;
+      area += (uint64_t)(std::min(BN, 32 * r + 32) - 32 * r) * (uint64_t)wz3_block_bytes(width[(size_t)(I * RB + r)]);
+    }
+  uint8_t* blob = static_cast<uint8_t*>(out);
+  uint8_t* stream = blob + kHeaderBytes;
+  uint8_t* index = stream + 8;
+  uint8_t* blocks = index + 8 * (size_t)(BM * RB);
+  uint64_t tol_bits;
+  std::memcpy(&tol_bits, &tol, 8);
+  st64(stream, tol_bits);
+  for (int64_t k = 0; k < BM * RB; ++k) st64(index + 8 * k, off[(size_t)k] | ((uint64_t)width[(size_t)k] << 56));
+  // pass 2: every block at its run's width
+  parallel_for(BM, nthreads, [&](int64_t I) {
+    float vals[16];
+    Wz3Block b;
+    uint64_t w[8];
+    for (int64_t r = 0; r < RB; ++r) {
+      const int W = width[(size_t)(I * RB + r)];
+      const int bb = wz3_block_bytes(W);
+      uint8_t* dst = blocks + off[(size_t)(I * RB + r)];
+      for (int64_t J = 32 * r; J < std::min(BN, 32 * r + 32); ++J) {
+        gather_block(A, M, N, lda, I, J, vals);
+        wz3_block(vals, tol, &b);
+        wz3_put(b, W, w);
+        for (int k = 0; k < bb / 8; ++k) st64(dst + (J - 32 * r) * bb + 8 * k, w[k]);
+      }
+    }
+  });
+  const uint64_t sbytes = 8 + 8 * (uint64_t)(BM * RB) + area;
+  write_header(blob, WHFF_FMT_FIXED_ACC, 0, M, N, sbytes, crc32(stream, sbytes));
+  if (out_len) *out_len = (size_t)(kHeaderBytes + sbytes);
   return WHFF_OK;
 }
 

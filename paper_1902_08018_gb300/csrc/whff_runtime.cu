@@ -69,6 +69,10 @@ struct whff_handle {
   alignas(64) unsigned char tmap[128] = {};  // BF16: TMA map of the stored matrix (tensor-core passes)
   bool has_tmap = false;
   int64_t tma_row0 = 0;         // first row of a row view within the map's matrix
+  const uint64_t* wz3_index = nullptr;  // fixed accuracy: the run index and the block area (device)
+  const uint8_t* wz3_area = nullptr;
+  int64_t wz3_RB = 0;           // runs per band
+  int64_t band0 = 0;            // fixed accuracy: first band of a row view
   uint32_t wait_polls = whff::kWaitPolls;  // in-loop bounded waits of the tensor-core kernels
   cudaStream_t create_stream = nullptr;
 };
@@ -106,6 +110,15 @@ void choose_ranges(whff_handle* h) {
 }
 
 void choose_split(whff_handle* h) {
+  if (is_wz3(h->info.fmt)) {  // a warp per (band, range of runs): split the runs when bands are few
+    const int64_t RB = ceil_div(h->BN, 32);
+    const int64_t bands = h->BM;
+    int64_t ks = ((int64_t)h->sm_count * 48 + bands - 1) / bands;
+    ks = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(ks, RB), 256));
+    h->chunk = ceil_div(RB, ks);
+    h->ksplit = (int)ceil_div(RB, h->chunk);
+    return;
+  }
   if (h->info.fmt != WHFF_FMT_ZFP) {  // WZ2 and scaled formats: persistent warp ranges
     choose_ranges(h);
     return;
@@ -153,7 +166,7 @@ size_t xt_bytes(const whff_handle* h) {
 
 // Workspace bytes a CUDA-core pass of the plan needs.
 size_t ws_need(const whff_handle* h) {
-  if (h->info.fmt == WHFF_FMT_ZFP)
+  if (h->info.fmt == WHFF_FMT_ZFP || is_wz3(h->info.fmt))
     return h->ksplit > 1 ? (size_t)h->ksplit * (size_t)h->ws_rhs * (size_t)h->Mpad * 8 : 0;
   return h->maxseg > 1 ? (size_t)h->BM * (size_t)h->maxseg * (size_t)h->ws_rhs * 4 * 8 : 0;
 }
@@ -275,11 +288,18 @@ int launch_pass(const whff_handle* h, const float* x, int R, int64_t ldx, double
     case WHFF_FMT_FP32:
       e = launch_scaled(h, x, R, ldx, vec, y, ldy, state, decay, st);
       break;
+    case WHFF_FMT_FIXED_ACC: {
+      Wz3Step a{h->wz3_index, h->wz3_area, h->band0, h->info.M, h->info.N, h->BM, h->BN, h->wz3_RB, x, ldx,
+                h->d_xt, R, h->ksplit, h->chunk, h->d_ws, y, ldy, state, decay};
+      e = wz3_launch(a, st) ? WHFF_EINVAL : WHFF_OK;
+      if (e) set_error("whff_step: fixed-accuracy passes take 1 or 8 right-hand sides");
+      break;
+    }
     default:
       e = WHFF_EINVAL;
   }
   if (e) return e;
-  if (h->ksplit > 1 && h->info.fmt == WHFF_FMT_ZFP) {
+  if (h->ksplit > 1 && (h->info.fmt == WHFF_FMT_ZFP || is_wz3(h->info.fmt))) {
     const int threads = 256;
     dev::splitk_epilogue_kernel<<<(unsigned)((h->info.M + threads - 1) / threads), threads, 0, st>>>(
         h->d_ws, h->ksplit, R, h->Mpad, h->info.M, y, ldy, state, decay);
@@ -303,6 +323,26 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
 
 namespace whff {
 namespace {
+// Every run of a fixed-accuracy stream (host copy) lies inside its block area
+// and has a width of at most 31: the kernels then read only the stream.
+int wz3_check_index(const uint8_t* stream, uint64_t sbytes, int64_t BM, int64_t BN) {
+  const int64_t RB = ceil_div(BN, 32);
+  const uint64_t head = 8 + 8 * (uint64_t)(BM * RB);
+  if (sbytes < head) return WHFF_EFORMAT;
+  const uint64_t area = sbytes - head;
+  for (int64_t I = 0; I < BM; ++I)
+    for (int64_t r = 0; r < RB; ++r) {
+      uint64_t e;
+      std::memcpy(&e, stream + 8 + 8 * (uint64_t)(I * RB + r), 8);
+      const int W = (int)(e >> 56);
+      const uint64_t off = e & 0x00FFFFFFFFFFFFFFull;
+      const uint64_t nb = (uint64_t)(std::min<int64_t>(BN, 32 * r + 32) - 32 * r);
+      if (W > 31 || off % 8 || off > area || nb * (uint64_t)(8 * ((13 + 16 * W + 63) / 64)) > area - off)
+        return WHFF_EFORMAT;
+    }
+  return WHFF_OK;
+}
+
 // A handle for the matrix `info` describes.  src (host memory, info.stream_bytes)
 // is uploaded on `stream`; with src == nullptr the device stream is allocated and
 // left for the caller to fill (the slots of a field pipeline).
@@ -353,13 +393,20 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
   if (info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) {
     const int occ = wz2_occ(info.rate, info.fmt == WHFF_FMT_FIXED_LIFT, h->unroll);
     h->ctas_per_sm = occ > 0 ? occ : 4;
-  } else if (!is_blocked(info.fmt)) {  // the kernel the fold default below picks (band length in chunks)
+  } else if (!is_blocked(info.fmt) && !is_wz3(info.fmt)) {  // the kernel the fold default below picks
     const int occ = scaled_occupancy(info.fmt, scaled_ld(info.N) / scaled_vec(info.fmt) < 256);
     h->ctas_per_sm = occ > 0 ? occ : 4;
   }
-  if (is_blocked(info.fmt)) {
+  if (is_blocked(info.fmt) || is_wz3(info.fmt)) {
     h->BM = ceil_div(info.M, 4);
     h->BN = ceil_div(info.N, 4);
+  }
+  if (is_wz3(info.fmt)) {  // the run index must stay inside the stream: checked once, here
+    const int e = src ? wz3_check_index(src, info.stream_bytes, h->BM, h->BN) : WHFF_EFORMAT;
+    if (e) {
+      set_error("whff_create: fixed-accuracy run index out of range (width above 31 or run past the stream)");
+      return fail(e);
+    }
   }
   choose_split(h);
   // short bands (tall matrices) fold their lanes in FP32 pairs, long ones in
@@ -414,7 +461,7 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
       return fail(WHFF_ENOMEM);
     }
   }
-  if ((info.fmt == WHFF_FMT_FIXED_LIFT && cudaMalloc(&h->d_xt, xt_bytes(h)) != cudaSuccess) ||
+  if (((info.fmt == WHFF_FMT_FIXED_LIFT || is_wz3(info.fmt)) && cudaMalloc(&h->d_xt, xt_bytes(h)) != cudaSuccess) ||
       (h->ws_bytes && cudaMalloc(&h->d_ws, h->ws_bytes) != cudaSuccess) ||
       cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->d_x, (size_t)info.N * (size_t)max_rhs * sizeof(float)) != cudaSuccess ||
@@ -430,9 +477,14 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
     set_error(std::string("whff_create: upload failed: ") + cudaGetErrorString(cudaGetLastError()));
     return fail(WHFF_ECUDA);
   }
-  if (!is_blocked(info.fmt))
+  if (is_wz3(info.fmt)) {
+    h->wz3_RB = ceil_div(h->BN, 32);
+    h->wz3_index = reinterpret_cast<const uint64_t*>(h->d_stream + 8);
+    h->wz3_area = h->d_stream + 8 + 8 * (uint64_t)(h->BM * h->wz3_RB);
+  } else if (!is_blocked(info.fmt)) {
     h->d_scales = reinterpret_cast<const float*>(h->d_stream + (uint64_t)info.M * (uint64_t)scaled_ld(info.N) *
                                                                    (uint64_t)elem_bytes(info.fmt));
+  }
   // BF16 tensor-core passes take their A tiles by TMA from device memory
   // (if the map cannot be encoded the register-fed kernel runs instead, same results)
   if (info.fmt == WHFF_FMT_BF16 && h->d_ws_mma && !h->h_stream)
@@ -493,7 +545,8 @@ extern "C" int whff_plan(const whff_handle* h, int* ksplit, int* launches) {
   }
   if (ksplit) *ksplit = h->ksplit;
   if (launches)
-    *launches = ((h->ksplit > 1 || h->maxseg > 1) ? 2 : 1) + (h->info.fmt == WHFF_FMT_FIXED_LIFT ? 1 : 0);
+    *launches = ((h->ksplit > 1 || h->maxseg > 1) ? 2 : 1) +
+                (h->info.fmt == WHFF_FMT_FIXED_LIFT || is_wz3(h->info.fmt) ? 1 : 0);
   return WHFF_OK;
 }
 
@@ -513,7 +566,7 @@ int step_passes(const whff_handle* h, const float* x, int R, int64_t ldx, double
       e = launch_mma(h, x + (int64_t)r0 * ldx, pass, ldx, y + (int64_t)r0 * ldy, ldy, state, decay, st);
       r0 += pass;
     } else {
-      const int pass = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+      const int pass = left >= 8 ? 8 : is_wz3(h->info.fmt) ? 1 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
       e = launch_pass(h, x + (int64_t)r0 * ldx, pass, ldx, y + (int64_t)r0 * ldy, ldy, state, decay, st);
       r0 += pass;
     }
@@ -538,6 +591,9 @@ int step_view(const whff_handle* h, int64_t row0, int64_t nrows, const float* x,
   if (is_blocked(fmt)) {
     v.BM = ceil_div(nrows, 4);
     v.d_stream = h->d_stream + (uint64_t)(row0 / 4) * (uint64_t)h->BN * (uint64_t)(2 * h->info.rate);
+  } else if (is_wz3(fmt)) {  // the same index and blocks, from band row0 / 4 on
+    v.BM = ceil_div(nrows, 4);
+    v.band0 = h->band0 + row0 / 4;
   } else {
     v.d_stream = h->d_stream + (uint64_t)row0 * (uint64_t)scaled_ld(h->info.N) * (uint64_t)elem_bytes(fmt);
     v.d_scales = h->d_scales + (row0 / kScaleTile) * ceil_div(h->info.N, kScaleTile);
@@ -545,11 +601,12 @@ int step_view(const whff_handle* h, int64_t row0, int64_t nrows, const float* x,
   }
   choose_split(&v);
   for (int c = v.ctas_per_sm; ws_need(&v) > h->ws_bytes;) {  // fewer warps: longer ranges, fewer segments
-    if (fmt == WHFF_FMT_ZFP) {
+    if (fmt == WHFF_FMT_ZFP || is_wz3(fmt)) {
+      const int64_t units = is_wz3(fmt) ? v.wz3_RB : v.BN;  // split units: runs (WZ3) or blocks
       v.ksplit = (int)std::max<size_t>(1, h->ws_bytes / ((size_t)v.ws_rhs * (size_t)v.Mpad * 8));
-      v.chunk = ceil_div(v.BN, v.ksplit);
-      v.ksplit = (int)ceil_div(v.BN, v.chunk);
-      if (v.ksplit > 1 && ws_need(&v) > h->ws_bytes) v.ksplit = 1, v.chunk = v.BN;
+      v.chunk = ceil_div(units, v.ksplit);
+      v.ksplit = (int)ceil_div(units, v.chunk);
+      if (v.ksplit > 1 && ws_need(&v) > h->ws_bytes) v.ksplit = 1, v.chunk = units;
       break;
     }
     if (c == 1) {  // ranges of whole bands: no band is shared, so no partials at all
@@ -600,7 +657,7 @@ extern "C" int whff_step_rows(whff_handle* h, int64_t row0, int64_t nrows, const
     set_error("whff_step_rows: null pointer, R out of [1, max_rhs], rows outside the matrix, or ld too small");
     return WHFF_EINVAL;
   }
-  if (row0 % (is_blocked(h->info.fmt) ? 4 : kScaleTile)) {
+  if (row0 % row_align(h->info.fmt)) {
     set_error("whff_step_rows: row0 must be a multiple of 4 (block formats) or 128 (scaled formats)");
     return WHFF_EINVAL;
   }
@@ -617,7 +674,7 @@ extern "C" int whff_get_slice_rows(const whff_handle* h, int64_t* rows) {
 }
 
 extern "C" int whff_set_slice_rows(whff_handle* h, int64_t rows) {
-  if (!h || rows < 0 || rows % (is_blocked(h->info.fmt) ? 4 : kScaleTile)) {
+  if (!h || rows < 0 || rows % row_align(h->info.fmt)) {
     set_error("whff_set_slice_rows: rows >= 0, a multiple of 4 (block formats) or 128 (scaled formats)");
     return WHFF_EINVAL;
   }
@@ -769,7 +826,7 @@ extern "C" int whff_graph_create_host(whff_handle* h, const float* x_host, int R
 
 namespace {
 int check_slit(const whff_handle* h, int64_t row0, int64_t nrows, const char* who) {
-  if (row0 < 0 || nrows <= 0 || row0 + nrows > h->info.M || row0 % (is_blocked(h->info.fmt) ? 4 : kScaleTile)) {
+  if (row0 < 0 || nrows <= 0 || row0 + nrows > h->info.M || row0 % row_align(h->info.fmt)) {
     set_error(std::string(who) + ": rows outside the matrix, or row0 not a multiple of 4 (block formats) / 128 "
                                  "(scaled formats)");
     return WHFF_EINVAL;
@@ -906,6 +963,8 @@ extern "C" int whff_decompress(whff_handle* h, double* out, int64_t ldo, void* s
         return WHFF_EINVAL;
     }
 #undef DZ
+  } else if (is_wz3(b.fmt)) {
+    wz3_decompress(h->wz3_index, h->wz3_area, b.M, b.N, out, ldo, st);
   } else if (is_blocked(b.fmt)) {
     const int64_t nb = h->BM * h->BN;
     const bool lift = b.fmt == WHFF_FMT_FIXED_LIFT;

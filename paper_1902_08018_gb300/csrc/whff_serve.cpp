@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "whff.h"
+#include "whff_blob.h"
 
 namespace whff {
 void set_error(const std::string& msg);
@@ -260,8 +261,10 @@ int admit(whff_server* s, Model& m) {
   // slicing); the handle's own setting is restored afterwards
   int64_t own_slice = 0;
   whff_get_slice_rows(h, &own_slice);
-  const int64_t align = (fmt == WHFF_FMT_ZFP || fmt == WHFF_FMT_FIXED_LIFT || fmt == WHFF_FMT_FIXED_BFP) ? 4 : 128;
-  const double row_bytes = (double)whff_compressed_size(fmt, rate, m.M, m.N) / (double)m.M;
+  const int64_t align = whff::row_align(fmt);
+  size_t fixed = whff_compressed_size(fmt, rate, m.M, m.N), held = 0;
+  if (!fixed) whff_info(h, nullptr, nullptr, nullptr, nullptr, &held);  // fixed accuracy: bounded by all it holds
+  const double row_bytes = (double)(fixed ? fixed : held) / (double)m.M;
   int64_t slice = 0;
   if (row_bytes * (double)m.M > (double)kSliceBytes)
     slice = std::max<int64_t>(align, (int64_t)((double)kSliceBytes / row_bytes) / align * align);

@@ -155,6 +155,30 @@ int scaled_tma_map(void* out, const void* payload, int64_t M, int64_t ld);
 // resident CTAs per SM for R <= 32 (0 on error); tma: the TMA-fed BF16 kernel
 int scaled_mma_occupancy(int fmt, bool tma);
 
+// Fixed-accuracy (WZ3) pass of 1 or 8 right-hand sides (wz3.cu): a warp per
+// (band, split), split = ksplit runs ranges of `chunk` runs.  band0 is the
+// first band of a row view within the matrix (its index is the matrix's).
+struct Wz3Step {
+  const uint64_t* index;  // the matrix's run index (BM_total x RB)
+  const uint8_t* area;    // the block area
+  int64_t band0;
+  int64_t M, N, BM, BN, RB;
+  const float* x;
+  int64_t ldx;
+  float* xt;  // scratch: (2G)^T x, 4 BN floats per right-hand side
+  int R;
+  int ksplit;
+  int64_t chunk;  // runs per split
+  double* ws;     // ksplit x R x 4 BM partials when ksplit > 1
+  double* y;
+  int64_t ldy;
+  double* state;
+  double decay;
+};
+int wz3_launch(const Wz3Step& a, cudaStream_t st);
+int wz3_decompress(const uint64_t* index, const uint8_t* area, int64_t M, int64_t N, double* out, int64_t ldo,
+                   cudaStream_t st);
+
 template <int RATE>
 int wz2_launch(const Wz2Step& a, cudaStream_t st);
 template <int RATE>

@@ -1,0 +1,31 @@
+// Fixed-accuracy (WZ3) launches: instantiation unit.
+#include "wz2_dispatch.h"
+#include "wz3_kernels.cuh"
+
+namespace whff {
+
+int wz3_launch(const Wz3Step& a, cudaStream_t st) {
+  if (a.R != 1 && a.R != 8) return -1;
+  // (2G)^T x once per pass, 4 BN floats per right-hand side
+  const int64_t ldt = 4 * a.BN, n = (int64_t)a.R * a.BN;
+  dev::wz2_xt_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.x, a.ldx, a.N, a.R, a.BN, a.xt, ldt);
+  const dim3 grid((unsigned)((a.BM + dev::kWarpsPerCta - 1) / dev::kWarpsPerCta), (unsigned)a.ksplit);
+  if (a.R == 1)
+    dev::wz3_gemv_kernel<1><<<grid, dev::kWarpsPerCta * 32, 0, st>>>(a.index, a.area, a.band0, a.M, a.BM, a.BN, a.RB,
+                                                                   a.xt, ldt, a.ksplit, a.chunk, a.ws, a.y, a.ldy,
+                                                                   a.state, a.decay);
+  else
+    dev::wz3_gemv_kernel<8><<<grid, dev::kWarpsPerCta * 32, 0, st>>>(a.index, a.area, a.band0, a.M, a.BM, a.BN, a.RB,
+                                                                   a.xt, ldt, a.ksplit, a.chunk, a.ws, a.y, a.ldy,
+                                                                   a.state, a.decay);
+  return 0;
+}
+
+int wz3_decompress(const uint64_t* index, const uint8_t* area, int64_t M, int64_t N, double* out, int64_t ldo,
+                   cudaStream_t st) {
+  const int64_t BM = (M + 3) / 4, BN = (N + 3) / 4, RB = (BN + 31) / 32, nb = BM * BN;
+  dev::wz3_decompress_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(index, area, M, N, BN, RB, nb, out, ldo);
+  return 0;
+}
+
+}  // namespace whff

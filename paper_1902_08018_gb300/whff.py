@@ -21,6 +21,7 @@ FMT_FP8E4M3 = 4
 FMT_FIXED_LIFT = 5
 FMT_FIXED_BFP = 6
 FMT_FP32 = 7
+FMT_FIXED_ACC = 8
 
 _ERRORS = {
     -1: "WHFF_EINVAL",
@@ -56,6 +57,8 @@ def library() -> ctypes.CDLL:
     sigs = {
         "whff_compressed_size": (sz, [c_int, c_int, i64, i64]),
         "whff_compress": (c_int, [P, i64, i64, i64, c_int, c_int, P, sz, ctypes.POINTER(sz), c_int]),
+        "whff_accuracy_max_size": (sz, [i64, i64]),
+        "whff_compress_accuracy": (c_int, [P, i64, i64, i64, dbl, P, sz, ctypes.POINTER(sz), c_int]),
         "whff_blob_init": (c_int, [P, sz, c_int, c_int, i64, i64]),
         "whff_compress_band": (c_int, [P, sz, P, i64, i64, i64, c_int]),
         "whff_blob_seal": (c_int, [P, sz]),
@@ -144,6 +147,20 @@ def whff_compress(A: np.ndarray, fmt: int = FMT_ZFP, rate: int = 16, nthreads: i
     _check(library().whff_compress(A.ctypes.data, M, N, N, fmt, rate, out.ctypes.data, n, ctypes.byref(used),
                                    nthreads))
     return out
+
+
+def whff_compress_accuracy(A: np.ndarray, tol: float, nthreads: int = 0) -> np.ndarray:
+    """Fixed-accuracy encode (WZ3) of an FP64 row-major matrix at absolute tolerance tol -> blob."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    M, N = A.shape
+    cap = int(library().whff_accuracy_max_size(M, N))
+    if cap == 0:
+        raise WhffError(-1, "empty shape")
+    out = np.empty(cap, dtype=np.uint8)
+    used = ctypes.c_size_t()
+    _check(library().whff_compress_accuracy(A.ctypes.data, M, N, N, float(tol), out.ctypes.data, cap,
+                                            ctypes.byref(used), nthreads))
+    return out[: used.value].copy()
 
 
 def whff_compress_bands(M: int, N: int, bands, fmt: int = FMT_ZFP, rate: int = 16, nthreads: int = 0) -> np.ndarray:

@@ -107,3 +107,25 @@ def test_create_rejects_corrupt_blob_without_gpu(W):
     with pytest.raises(W.WhffError) as e:
         W.whff_create(blob, stream=0)
     assert e.value.code == -5
+
+
+@pytest.mark.parametrize("M,N", [(130, 97), (64, 260), (5, 3), (257, 1030)])
+@pytest.mark.parametrize("tol", [1e-2, 1e-6, 0.0])
+def test_fixed_accuracy_encoder_byte_identical_to_oracle(W, orc, M, N, tol):
+    """WZ3 (fixed accuracy, Sec. 4.3 read with a per-block shift and per-run field width):
+    the library's blob, index included, equals the oracle's byte for byte, for every
+    thread count."""
+    import workloads
+
+    A = workloads.RectKernelMatrix(M, N, 0.05, M * 7 + N).dense()
+    want = orc.wz3_encode(A, tol)
+    for nt in (1, 3, 0):
+        got = W.whff_compress_accuracy(A, tol, nthreads=nt)
+        assert got.tobytes() == want, nt
+
+
+def test_fixed_accuracy_rejections(W):
+    with pytest.raises(W.WhffError):
+        W.whff_compress_accuracy(np.ones((4, 4)), -1.0)
+    with pytest.raises(W.WhffError):
+        W.whff_compress_accuracy(np.full((4, 4), np.nan), 1e-3)
