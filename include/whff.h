@@ -74,7 +74,9 @@ extern "C" {
  *    widest its blocks need; a block takes 8*ceil((13 + 16 W)/64) bytes.  Blob:
  *    the 64-byte header (rate 0, variable stream length), then the tolerance
  *    (f64), one u64 per run in band-major order (bits 0-55: byte offset of the
- *    run's first block in the block area; bits 56-63: W), then the blocks.
+ *    run in the block area; bits 56-63: W), then the runs back to back, each
+ *    word-interleaved (64-bit word k of its block b at byte 8 (k nb + b) of
+ *    the run, nb its block count) so that a warp loads a run coalesced.
  *    Written by whff_compress_accuracy; decoded value (2G) V (2G)^T *
  *    2^(K+emax-30), exact in FP64. */
 #define WHFF_FMT_FIXED_ACC 8

@@ -839,10 +839,14 @@ void orc_state_update(double* s, int64_t M, const double* Y, int R, int64_t ldy,
 
 /* ------------------------------------------- WZ3 matrix layout (planned) */
 /* Stream: [tol: f64] [index: one u64 per run, band-major; bits 0..55 the
- * byte offset of the run's first block within the block area, bits 56..63
- * its width W] [block area: the runs one after another].  A run is up to 32
- * consecutive blocks of one band (the last run of a band may be shorter).
- * Edge blocks replicate the last valid row, then column, as WZ1/WZ2. */
+ * byte offset of the run within the block area, bits 56..63 its width W]
+ * [block area: the runs one after another].  A run is up to 32 consecutive
+ * blocks of one band (the last run of a band may be shorter); its nb blocks
+ * of nw = bytes(W) / 8 words are stored word-interleaved: word k of block b
+ * at byte 8 (k nb + b) of the run (the same bytes as nb blocks side by side,
+ * in the order in which nb readers each taking one block load them
+ * together).  Edge blocks replicate the last valid row, then column, as
+ * WZ1/WZ2. */
 static int64_t wz3_runs_per_band(int64_t N) { return cdiv(cdiv(N, 4), 32); }
 
 size_t orc_wz3_max_blob_size(int64_t M, int64_t N) {
@@ -883,9 +887,10 @@ int orc_wz3_encode_matrix(const double* A, int64_t M, int64_t N, int64_t lda, do
       int e = orc_wz3_encode_run(blocks, (int)nb, tol, 1, words, &W);
       if (e != ORC_OK) return e;
       wr64(index + 8 * (size_t)(I * RB + r), off | ((uint64_t)W << 56));
-      const int64_t nbytes = nb * orc_wz3_block_bytes(W);
-      for (int64_t k = 0; k < nbytes / 8; k++) wr64(area + off + 8 * (uint64_t)k, words[k]);
-      off += (uint64_t)nbytes;
+      const int nw = orc_wz3_block_bytes(W) / 8;
+      for (int64_t b = 0; b < nb; b++) /* block b's words: words[b nw + k] */
+        for (int k = 0; k < nw; k++) wr64(area + off + 8 * (uint64_t)(k * nb + b), words[b * nw + k]);
+      off += (uint64_t)(nb * nw * 8);
     }
   const size_t sbytes = 8 + 8 * (size_t)(BM * RB) + (size_t)off;
   write_header(blob, ORC_FMT_FIXED_ACC, 0, M, N, sbytes);
@@ -923,7 +928,7 @@ int orc_wz3_decode_matrix(const uint8_t* blob, size_t len, double* out, int64_t 
       if (W > 31 || off + (uint64_t)(nb * bb) > area_bytes) return ORC_EFORMAT;
       for (int64_t b = 0; b < nb; b++) {
         uint64_t w[9];
-        for (int k = 0; k < bb / 8; k++) w[k] = rd64(area + off + (uint64_t)(b * bb) + 8 * (uint64_t)k);
+        for (int k = 0; k < bb / 8; k++) w[k] = rd64(area + off + 8 * (uint64_t)(k * nb + b));
         double v[16];
         orc_wz3_decode_block(w, W, 1, v);
         for (int rr = 0; rr < 4; rr++)

@@ -715,13 +715,15 @@ extern "C" int whff_compress_accuracy(const double* A, int64_t M, int64_t N, int
     uint64_t w[8];
     for (int64_t r = 0; r < RB; ++r) {
       const int W = width[(size_t)(I * RB + r)];
-      const int bb = wz3_block_bytes(W);
+      const int nw = wz3_block_bytes(W) / 8;
+      const int64_t nb = std::min(BN, 32 * r + 32) - 32 * r;
       uint8_t* dst = blocks + off[(size_t)(I * RB + r)];
-      for (int64_t J = 32 * r; J < std::min(BN, 32 * r + 32); ++J) {
+      for (int64_t J = 32 * r; J < 32 * r + nb; ++J) {
         gather_block(A, M, N, lda, I, J, vals);
         wz3_block(vals, tol, &b);
         wz3_put(b, W, w);
-        for (int k = 0; k < bb / 8; ++k) st64(dst + (J - 32 * r) * bb + 8 * k, w[k]);
+        // word-interleaved run: word k of block j at byte 8 (k nb + j)
+        for (int k = 0; k < nw; ++k) st64(dst + 8 * (k * nb + (J - 32 * r)), w[k]);
       }
     }
   });

@@ -88,38 +88,35 @@ cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 // 4-row band; when bands are few (wide matrices), split the columns.
 // WZ2: split the band-major block order into one contiguous range per
 // resident warp (exact balance); bands that straddle ranges get segments.
+// Units of a band that the persistent ranges count: runs of 32 blocks for the
+// fixed-accuracy format, blocks (WZ2) or 16-byte chunks (scaled) otherwise.
+int64_t band_units(const whff_handle* h) { return is_wz3(h->info.fmt) ? ceil_div(h->BN, 32) : h->BN; }
+
 void choose_ranges(whff_handle* h) {
-  if (!is_blocked(h->info.fmt)) {  // scaled formats: units are 16-byte column chunks of a 4-row band
+  if (!is_blocked(h->info.fmt) && !is_wz3(h->info.fmt)) {  // scaled: units are 16-byte chunks of a 4-row band
     h->BM = ceil_div(h->info.M, 4);
     h->BN = scaled_ld(h->info.N) / scaled_vec(h->info.fmt);
   }
-  const int64_t total = h->BM * h->BN;
+  const int64_t U = band_units(h);
+  const int64_t total = h->BM * U;
   const int64_t warps_cap = (int64_t)h->sm_count * h->ctas_per_sm * dev::kWarpsPerCta;
-  int64_t warps = std::min<int64_t>(warps_cap, std::max<int64_t>(1, (total + 63) / 64));  // >= 64 blocks each
+  const int64_t min_units = is_wz3(h->info.fmt) ? 2 : 64;  // >= 64 blocks (2 runs of 32) per warp
+  int64_t warps = std::min<int64_t>(warps_cap, std::max<int64_t>(1, (total + min_units - 1) / min_units));
   warps = (warps + dev::kWarpsPerCta - 1) / dev::kWarpsPerCta * dev::kWarpsPerCta;
   h->range_ctas = warps / dev::kWarpsPerCta;
   h->range_len = (total + warps - 1) / warps;
   int maxseg = 1;
   for (int64_t I = 0; I < h->BM; ++I) {
-    const int64_t lo = (I * h->BN) / h->range_len, hi = ((I + 1) * h->BN - 1) / h->range_len;
+    const int64_t lo = (I * U) / h->range_len, hi = ((I + 1) * U - 1) / h->range_len;
     maxseg = (int)std::max<int64_t>(maxseg, hi - lo + 1);
   }
   h->maxseg = maxseg;
   h->ksplit = 1;
-  h->chunk = h->BN;
+  h->chunk = U;
 }
 
 void choose_split(whff_handle* h) {
-  if (is_wz3(h->info.fmt)) {  // a warp per (band, range of runs): split the runs when bands are few
-    const int64_t RB = ceil_div(h->BN, 32);
-    const int64_t bands = h->BM;
-    int64_t ks = ((int64_t)h->sm_count * 48 + bands - 1) / bands;
-    ks = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(ks, RB), 256));
-    h->chunk = ceil_div(RB, ks);
-    h->ksplit = (int)ceil_div(RB, h->chunk);
-    return;
-  }
-  if (h->info.fmt != WHFF_FMT_ZFP) {  // WZ2 and scaled formats: persistent warp ranges
+  if (h->info.fmt != WHFF_FMT_ZFP) {  // WZ2, WZ3 and scaled formats: persistent warp ranges
     choose_ranges(h);
     return;
   }
@@ -166,7 +163,7 @@ size_t xt_bytes(const whff_handle* h) {
 
 // Workspace bytes a CUDA-core pass of the plan needs.
 size_t ws_need(const whff_handle* h) {
-  if (h->info.fmt == WHFF_FMT_ZFP || is_wz3(h->info.fmt))
+  if (h->info.fmt == WHFF_FMT_ZFP)
     return h->ksplit > 1 ? (size_t)h->ksplit * (size_t)h->ws_rhs * (size_t)h->Mpad * 8 : 0;
   return h->maxseg > 1 ? (size_t)h->BM * (size_t)h->maxseg * (size_t)h->ws_rhs * 4 * 8 : 0;
 }
@@ -290,7 +287,7 @@ int launch_pass(const whff_handle* h, const float* x, int R, int64_t ldx, double
       break;
     case WHFF_FMT_FIXED_ACC: {
       Wz3Step a{h->wz3_index, h->wz3_area, h->band0, h->info.M, h->info.N, h->BM, h->BN, h->wz3_RB, x, ldx,
-                h->d_xt, R, h->ksplit, h->chunk, h->d_ws, y, ldy, state, decay};
+                h->d_xt, R, h->range_len, h->maxseg, h->range_ctas, h->d_ws, y, ldy, state, decay};
       e = wz3_launch(a, st) ? WHFF_EINVAL : WHFF_OK;
       if (e) set_error("whff_step: fixed-accuracy passes take 1 or 8 right-hand sides");
       break;
@@ -299,7 +296,7 @@ int launch_pass(const whff_handle* h, const float* x, int R, int64_t ldx, double
       e = WHFF_EINVAL;
   }
   if (e) return e;
-  if (h->ksplit > 1 && (h->info.fmt == WHFF_FMT_ZFP || is_wz3(h->info.fmt))) {
+  if (h->ksplit > 1 && h->info.fmt == WHFF_FMT_ZFP) {
     const int threads = 256;
     dev::splitk_epilogue_kernel<<<(unsigned)((h->info.M + threads - 1) / threads), threads, 0, st>>>(
         h->d_ws, h->ksplit, R, h->Mpad, h->info.M, y, ldy, state, decay);
@@ -323,13 +320,16 @@ extern "C" int whff_create(const void* blob, size_t len, int max_rhs, void* stre
 
 namespace whff {
 namespace {
-// Every run of a fixed-accuracy stream (host copy) lies inside its block area
-// and has a width of at most 31: the kernels then read only the stream.
+// The runs of a fixed-accuracy stream (host copy) lie back to back in
+// band-major order from the start of the block area, each of width at most 31
+// (a run of width 0 stores 8 zero bytes per block): the kernels then read only
+// the stream.
 int wz3_check_index(const uint8_t* stream, uint64_t sbytes, int64_t BM, int64_t BN) {
   const int64_t RB = ceil_div(BN, 32);
   const uint64_t head = 8 + 8 * (uint64_t)(BM * RB);
   if (sbytes < head) return WHFF_EFORMAT;
   const uint64_t area = sbytes - head;
+  uint64_t next = 0;  // where the next run must start
   for (int64_t I = 0; I < BM; ++I)
     for (int64_t r = 0; r < RB; ++r) {
       uint64_t e;
@@ -337,8 +337,9 @@ int wz3_check_index(const uint8_t* stream, uint64_t sbytes, int64_t BM, int64_t 
       const int W = (int)(e >> 56);
       const uint64_t off = e & 0x00FFFFFFFFFFFFFFull;
       const uint64_t nb = (uint64_t)(std::min<int64_t>(BN, 32 * r + 32) - 32 * r);
-      if (W > 31 || off % 8 || off > area || nb * (uint64_t)(8 * ((13 + 16 * W + 63) / 64)) > area - off)
-        return WHFF_EFORMAT;
+      const uint64_t bytes = nb * (uint64_t)(8 * ((13 + 16 * W + 63) / 64));
+      if (W > 31 || off != next || bytes > area - off) return WHFF_EFORMAT;
+      next = off + bytes;
     }
   return WHFF_OK;
 }
@@ -393,7 +394,10 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
   if (info.fmt == WHFF_FMT_FIXED_LIFT || info.fmt == WHFF_FMT_FIXED_BFP) {
     const int occ = wz2_occ(info.rate, info.fmt == WHFF_FMT_FIXED_LIFT, h->unroll);
     h->ctas_per_sm = occ > 0 ? occ : 4;
-  } else if (!is_blocked(info.fmt) && !is_wz3(info.fmt)) {  // the kernel the fold default below picks
+  } else if (is_wz3(info.fmt)) {
+    const int occ = wz3_occupancy(1);
+    h->ctas_per_sm = occ > 0 ? occ : 4;
+  } else if (!is_blocked(info.fmt)) {  // the kernel the fold default below picks
     const int occ = scaled_occupancy(info.fmt, scaled_ld(info.N) / scaled_vec(info.fmt) < 256);
     h->ctas_per_sm = occ > 0 ? occ : 4;
   }
@@ -417,7 +421,8 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
   const cudaStream_t st = as_stream(stream);
   if (flags & WHFF_CREATE_HOST_RESIDENT) {  // pinned host memory, read by the kernels over the CPU link
     void* dp = nullptr;
-    if (cudaHostAlloc(reinterpret_cast<void**>(&h->h_stream), info.stream_bytes, cudaHostAllocMapped) != cudaSuccess ||
+    if (cudaHostAlloc(reinterpret_cast<void**>(&h->h_stream), info.stream_bytes + kStreamPad, cudaHostAllocMapped) !=
+            cudaSuccess ||
         cudaHostGetDevicePointer(&dp, h->h_stream, 0) != cudaSuccess) {
       cudaGetLastError();
       set_error("whff_create: pinned mapped host allocation of the compressed stream failed");
@@ -601,17 +606,17 @@ int step_view(const whff_handle* h, int64_t row0, int64_t nrows, const float* x,
   }
   choose_split(&v);
   for (int c = v.ctas_per_sm; ws_need(&v) > h->ws_bytes;) {  // fewer warps: longer ranges, fewer segments
-    if (fmt == WHFF_FMT_ZFP || is_wz3(fmt)) {
-      const int64_t units = is_wz3(fmt) ? v.wz3_RB : v.BN;  // split units: runs (WZ3) or blocks
+    if (fmt == WHFF_FMT_ZFP) {
       v.ksplit = (int)std::max<size_t>(1, h->ws_bytes / ((size_t)v.ws_rhs * (size_t)v.Mpad * 8));
-      v.chunk = ceil_div(units, v.ksplit);
-      v.ksplit = (int)ceil_div(units, v.chunk);
-      if (v.ksplit > 1 && ws_need(&v) > h->ws_bytes) v.ksplit = 1, v.chunk = units;
+      v.chunk = ceil_div(v.BN, v.ksplit);
+      v.ksplit = (int)ceil_div(v.BN, v.chunk);
+      if (v.ksplit > 1 && ws_need(&v) > h->ws_bytes) v.ksplit = 1, v.chunk = v.BN;
       break;
     }
     if (c == 1) {  // ranges of whole bands: no band is shared, so no partials at all
-      v.range_len = ceil_div(v.range_len, v.BN) * v.BN;
-      v.range_ctas = ceil_div(ceil_div(v.BM * v.BN, v.range_len), dev::kWarpsPerCta);
+      const int64_t U = band_units(&v);
+      v.range_len = ceil_div(v.range_len, U) * U;
+      v.range_ctas = ceil_div(ceil_div(v.BM * U, v.range_len), dev::kWarpsPerCta);
       v.maxseg = 1;
       break;
     }

@@ -155,9 +155,10 @@ int scaled_tma_map(void* out, const void* payload, int64_t M, int64_t ld);
 // resident CTAs per SM for R <= 32 (0 on error); tma: the TMA-fed BF16 kernel
 int scaled_mma_occupancy(int fmt, bool tma);
 
-// Fixed-accuracy (WZ3) pass of 1 or 8 right-hand sides (wz3.cu): a warp per
-// (band, split), split = ksplit runs ranges of `chunk` runs.  band0 is the
-// first band of a row view within the matrix (its index is the matrix's).
+// Fixed-accuracy (WZ3) pass: (2G)^T x, then persistent warp ranges of L runs
+// over the pass's bands in band-major order, then (maxseg > 1) the segment
+// epilogue for bands shared by several ranges.  band0 is the first band of a
+// row view within the matrix (its index is the matrix's).
 struct Wz3Step {
   const uint64_t* index;  // the matrix's run index (BM_total x RB)
   const uint8_t* area;    // the block area
@@ -166,16 +167,18 @@ struct Wz3Step {
   const float* x;
   int64_t ldx;
   float* xt;  // scratch: (2G)^T x, 4 BN floats per right-hand side
-  int R;
-  int ksplit;
-  int64_t chunk;  // runs per split
-  double* ws;     // ksplit x R x 4 BM partials when ksplit > 1
+  int R;      // 1 or 8
+  int64_t L;      // runs per warp range
+  int maxseg;     // most ranges sharing one band
+  int64_t ctas;   // grid size
+  double* ws;     // BM x maxseg x R x 4 segment partials when maxseg > 1
   double* y;
   int64_t ldy;
   double* state;
   double decay;
 };
 int wz3_launch(const Wz3Step& a, cudaStream_t st);
+int wz3_occupancy(int R);  // resident CTAs per SM of the R-column kernel (0 on error)
 int wz3_decompress(const uint64_t* index, const uint8_t* area, int64_t M, int64_t N, double* out, int64_t ldo,
                    cudaStream_t st);
 

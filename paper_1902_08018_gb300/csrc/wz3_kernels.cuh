@@ -6,9 +6,11 @@
 // block for an absolute tolerance and one field width W per run of up to 32
 // blocks of a band.  A run is exactly what one warp takes in one iteration:
 // lane l decodes block 32 run + l, and since W is the same for the whole run
-// the warp switches once, uniformly, onto a decoder compiled for that width
-// (no per-lane prefix sums, no dynamic register indexing).  The run's first
-// byte comes from one index entry (offset | W << 56) that every lane reads.
+// the warp switches once, uniformly, onto a field extractor compiled for that
+// width (no per-lane prefix sums, no dynamic register indexing).  The run's
+// first byte comes from one index entry (offset | W << 56) that every lane
+// reads, and its words are interleaved across its blocks (word k of block b
+// at word k nb + b), so each of the warp's loads is one coalesced sweep.
 // As for WZ2 with the lift, the product works in the transform domain:
 // y_band = (2G) sum_J s_J V_J ((2G)^T x_J) 2^-3 with s_J = 2^(E+K-154), the
 // (2G) mixing once per band in FP64 (band_finish with the lift's mix).
@@ -40,139 +42,154 @@ __device__ __forceinline__ uint32_t wz3_field(const uint32_t (&w)[NW]) {
   }
 }
 
-// The 16 raw fields of a width-W block in sequency order (offset binary, no
-// conversion): the only part of the decode that depends on W at compile time,
-// so the code that a run's width selects stays small.
+// The 16 fields of a width-W block, placed in block order (t[4 i + j] for
+// coefficient (i, j)): up to 23 bits already OR'd into the mantissa of 2^23
+// (so that one packed subtraction of 2^23 + 2^(W-1) gives the exact value),
+// wider ones raw.  Only this part depends on W at compile time, so the code a
+// run's width selects stays small.
 template <int W, int... Ks>
-__device__ __forceinline__ void wz3_raw_impl(const uint32_t (&w)[16], uint32_t (&u)[16],
-                                             std::integer_sequence<int, Ks...>) {
-  ((u[Ks] = wz3_field<W, Ks>(w)), ...);
+__device__ __forceinline__ void wz3_fields_to(const uint32_t (&w)[16], uint32_t (&t)[16],
+                                              std::integer_sequence<int, Ks...>) {
+  constexpr uint32_t kOr = W <= 23 ? 0x4B000000u : 0u;
+  ((t[seq_index(Ks)] = wz3_field<W, Ks>(w) | kOr), ...);
 }
 
-// Raw fields for the run's width W (1..31), a switch that is uniform over the warp.
-__device__ __forceinline__ void wz3_raw(int W, const uint32_t (&w)[16], uint32_t (&u)[16]) {
+// Fields for the run's width W (1..31), a switch that is uniform over the warp.
+__device__ __forceinline__ void wz3_fields_w(int W, const uint32_t (&w)[16], uint32_t (&t)[16]) {
   switch (W) {
-#define WZ3_RAW(WW) \
-  case WW:          \
-    wz3_raw_impl<WW>(w, u, std::make_integer_sequence<int, 16>{}); \
+#define WZ3_F(WW) \
+  case WW:        \
+    wz3_fields_to<WW>(w, t, std::make_integer_sequence<int, 16>{}); \
     break;
-    WZ3_RAW(1) WZ3_RAW(2) WZ3_RAW(3) WZ3_RAW(4) WZ3_RAW(5) WZ3_RAW(6) WZ3_RAW(7) WZ3_RAW(8) WZ3_RAW(9) WZ3_RAW(10)
-    WZ3_RAW(11) WZ3_RAW(12) WZ3_RAW(13) WZ3_RAW(14) WZ3_RAW(15) WZ3_RAW(16) WZ3_RAW(17) WZ3_RAW(18) WZ3_RAW(19)
-    WZ3_RAW(20) WZ3_RAW(21) WZ3_RAW(22) WZ3_RAW(23) WZ3_RAW(24) WZ3_RAW(25) WZ3_RAW(26) WZ3_RAW(27) WZ3_RAW(28)
-    WZ3_RAW(29) WZ3_RAW(30)
+    WZ3_F(1) WZ3_F(2) WZ3_F(3) WZ3_F(4) WZ3_F(5) WZ3_F(6) WZ3_F(7) WZ3_F(8) WZ3_F(9) WZ3_F(10) WZ3_F(11) WZ3_F(12)
+    WZ3_F(13) WZ3_F(14) WZ3_F(15) WZ3_F(16) WZ3_F(17) WZ3_F(18) WZ3_F(19) WZ3_F(20) WZ3_F(21) WZ3_F(22) WZ3_F(23)
+    WZ3_F(24) WZ3_F(25) WZ3_F(26) WZ3_F(27) WZ3_F(28) WZ3_F(29) WZ3_F(30)
     default:  // 31 (wider runs are refused when the matrix is made resident)
-      wz3_raw_impl<31>(w, u, std::make_integer_sequence<int, 16>{});
-#undef WZ3_RAW
+      wz3_fields_to<31>(w, t, std::make_integer_sequence<int, 16>{});
+#undef WZ3_F
   }
 }
 
-// Offset-binary fields -> values in block order: exact through the 2^23
-// mantissa up to 23 bits, else the integer conversion (round to nearest; the
-// FP32 product rounds anyway).
-__device__ __forceinline__ void wz3_values(int W, const uint32_t (&u)[16], float (&V)[16]) {
-  const uint32_t half = 1u << (W - 1);
-  if (W <= 23) {
-    const float bias = 8388608.0f + (float)half;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) V[seq_index(k)] = __uint_as_float(u[k] | 0x4B000000u) - bias;
-  } else {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) V[seq_index(k)] = __int2float_rn((int32_t)(u[k] - half));
-  }
-}
-
-// The lane's block of a run: its words (zeros past the block or for an idle lane).
-__device__ __forceinline__ void wz3_load_run(const uint8_t* __restrict__ area, uint64_t e, int lane, bool active,
-                                             uint32_t (&w)[16]) {
+// The lane's block of a run of nb blocks (word-interleaved: word k of block
+// b at word k nb + b of the run), so that each load instruction of the warp
+// reads 8 nb consecutive bytes.  An idle lane (past the band's end) and every
+// lane of a zero run load nothing.
+__device__ __forceinline__ void wz3_load_run(const uint8_t* __restrict__ area, uint64_t e, int lane, int nb,
+                                             bool active, uint32_t (&w)[16]) {
   const int W = (int)(e >> 56);
-  const int nw2 = wz3_block_bytes(W) / 8;  // 8-byte words of the block
-  const uint2* p = reinterpret_cast<const uint2*>(area + (e & 0x00FFFFFFFFFFFFFFull) +
-                                                  (uint64_t)lane * (uint64_t)wz3_block_bytes(W));
+  const int nw = wz3_block_bytes(W) / 8;  // 64-bit words of a block (uniform over the warp)
+  const uint2* p = reinterpret_cast<const uint2*>(area + (e & 0x00FFFFFFFFFFFFFFull)) + lane;
+  if (active && W != 0) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    uint2 v = make_uint2(0u, 0u);
-    if (active && i < nw2) v = __ldcs(p + i);
-    w[2 * i] = v.x;
-    w[2 * i + 1] = v.y;
+    for (int k = 0; k < 8; ++k)
+      if (k < nw) {
+        const uint2 v = __ldcs(p + k * nb);
+        w[2 * k] = v.x;
+        w[2 * k + 1] = v.y;
+      }
   }
 }
 
 // A block's products added into the lane's sums: for each r,
 // p_i = s * sum_b V[i][b] xt_r[b] (xt the transformed x of the block's column
-// chunk J, ldt floats per column), then hi/lo[i][r] += p_i by TwoSum.
+// chunk J, ldt floats per column), then hi/lo[i][r] += p_i by TwoSum.  Rows
+// (0, 1) and (2, 3) go in packed FP32 pairs; each half rounds as the scalar
+// chain (product, three FMAs in b order, the scale, TwoSum) would.
 template <int R>
 __device__ __forceinline__ void wz3_accumulate(const uint32_t (&w)[16], int W, const float* __restrict__ xt,
-                                               int64_t ldt, int64_t J, float (&hi)[4][R], float (&lo)[4][R]) {
-  uint32_t u[16];
-  wz3_raw(W, w, u);
-  float V[16];
-  wz3_values(W, u, V);
+                                               int64_t ldt, int J, float (&hi)[4][R], float (&lo)[4][R]) {
+  uint32_t t[16];
+  wz3_fields_w(W, w, t);
+  float2 V[2][4];  // V[h][b] = (value (2h, b), value (2h + 1, b))
+  if (W <= 23) {  // exact: (2^23 + field) - (2^23 + 2^(W-1))
+    const float bias = 8388608.0f + (float)(1u << (W - 1));
+    const float2 b2 = make_float2(bias, bias);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        V[h][b] = sub_f2(make_float2(__uint_as_float(t[8 * h + b]), __uint_as_float(t[8 * h + 4 + b])), b2);
+  } else {  // the integer conversion, round to nearest
+    const uint32_t half = 1u << (W - 1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        V[h][b] = make_float2(__int2float_rn((int32_t)(t[8 * h + b] - half)),
+                              __int2float_rn((int32_t)(t[8 * h + 4 + b] - half)));
+  }
   const uint32_t E = w[0] & 0xFFu, K = (w[0] >> 8) & 31u;
   const float s = E ? __uint_as_float((E + K - 27u) << 23) : 0.f;  // 2^(E+K-154); E >= 28 for a nonzero block
+  const float2 s2 = make_float2(s, s);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const float4 x = __ldg(reinterpret_cast<const float4*>(xt + (int64_t)r * ldt + 4 * J));
+    const float2 x0 = make_float2(x.x, x.x), x1 = make_float2(x.y, x.y), x2 = make_float2(x.z, x.z),
+                 x3 = make_float2(x.w, x.w);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float q = __fmul_rn(V[4 * i], x.x);
-      q = fmaf(V[4 * i + 1], x.y, q);
-      q = fmaf(V[4 * i + 2], x.z, q);
-      q = fmaf(V[4 * i + 3], x.w, q);
-      two_sum_acc(hi[i][r], lo[i][r], __fmul_rn(q, s));
+    for (int h = 0; h < 2; ++h) {
+      float2 q = mul_f2(V[h][0], x0);
+      q = fma_f2(V[h][1], x1, q);
+      q = fma_f2(V[h][2], x2, q);
+      q = fma_f2(V[h][3], x3, q);
+      float2 H = make_float2(hi[2 * h][r], hi[2 * h + 1][r]), Lo = make_float2(lo[2 * h][r], lo[2 * h + 1][r]);
+      two_sum_acc2(H, Lo, mul_f2(q, s2));
+      hi[2 * h][r] = H.x, hi[2 * h + 1][r] = H.y, lo[2 * h][r] = Lo.x, lo[2 * h + 1][r] = Lo.y;
     }
   }
 }
 
-// A warp per (band, split): band I of this pass (band0 + I of the matrix),
-// runs [split chunk, split chunk + chunk) of it, R right-hand sides (1 or 8).
-// With one right-hand side the loop is software-pipelined: while the lanes
-// decode run r, the words of run r + 1 are on their way and the index entry
-// of run r + 2 is read (with eight, the products hide the loads).
-// ksplit > 1: the band's mixed partial goes to ws[(split R + r) Mpad + row]
-// (the split-K epilogue adds the splits in order and applies the state).
+// Persistent warp ranges over the runs in band-major order (units = runs):
+// warp g takes runs [g L, (g + 1) L) of the pass's bands, band I of the pass
+// being band0 + I of the matrix (index points at band0's first entry).  A
+// band whose runs all lie in the range is finished here (y, state); a band
+// shared by several ranges leaves one FP64 partial per range in
+// ws[(I maxseg + seg) R + r][4] for the segment epilogue.  The index entry of
+// the next run is read while the lanes decode the current one.
 template <int R>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, R == 1 ? 4 : 2)
-    wz3_gemv_kernel(const uint64_t* __restrict__ index, const uint8_t* __restrict__ area, int64_t band0, int64_t M,
-                    int64_t BM, int64_t BN, int64_t RB, const float* __restrict__ xt, int64_t ldt, int ksplit,
-                    int64_t chunk, double* __restrict__ ws, double* __restrict__ y, int64_t ldy,
-                    double* __restrict__ state, double decay) {
-  constexpr bool kPipe = R == 1;
+__global__ void __launch_bounds__(kWarpsPerCta * 32, R == 1 ? 4 : 1)
+    wz3_gemv_kernel(const uint64_t* __restrict__ index, const uint8_t* __restrict__ area, int64_t M, int64_t BM,
+                    int BN, int RB, const float* __restrict__ xt, int64_t ldt, int64_t L, int maxseg,
+                    double* __restrict__ ws, double* __restrict__ y, int64_t ldy, double* __restrict__ state,
+                    double decay) {
   const int lane = threadIdx.x & 31;
-  const int64_t I = (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
-  if (I >= BM) return;  // warp-uniform; nothing below synchronises across warps
-  const int split = (int)blockIdx.y;
-  const int64_t r0 = (int64_t)split * chunk, r1 = min(RB, r0 + chunk);
-  const uint64_t* idx = index + (band0 + I) * RB;  // one entry per run, the same word for every lane
+  const int64_t g = (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  const int64_t total = BM * RB;
+  const int64_t u0 = g * L, u1 = min(total, u0 + L);
+  if (u0 >= u1) return;  // warp-uniform; nothing below synchronises across warps
+  int64_t I = u0 / RB;  // band of the current piece
   float hi[4][R], lo[4][R];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
-  uint64_t e_cur = r0 < r1 ? __ldg(idx + r0) : 0ull;
-  uint64_t e_nxt = kPipe && r0 + 1 < r1 ? __ldg(idx + r0 + 1) : 0ull;
-  uint32_t w_cur[16];
-  if constexpr (kPipe) wz3_load_run(area, e_cur, lane, r0 < r1 && 32 * r0 + lane < BN, w_cur);
-  for (int64_t run = r0; run < r1; ++run) {
-    uint32_t w_nxt[16];
-    uint64_t e_after = 0;
-    if constexpr (kPipe) {
-      wz3_load_run(area, e_nxt, lane, run + 1 < r1 && 32 * (run + 1) + lane < BN, w_nxt);
-      e_after = run + 2 < r1 ? __ldg(idx + run + 2) : 0ull;
-    } else {
-      e_cur = __ldg(idx + run);
-      wz3_load_run(area, e_cur, lane, 32 * run + lane < BN, w_cur);
+  uint64_t e_nxt = __ldg(index + u0);  // the same word for every lane
+  for (int64_t ub = u0; ub < u1;) {  // the range's piece of band I: runs [ub, ue)
+    const int64_t ue = min(u1, (I + 1) * RB);
+#pragma unroll 1
+    for (int64_t u = ub; u < ue; ++u) {
+      const uint64_t e = e_nxt;
+      if (u + 1 < u1) e_nxt = __ldg(index + u + 1);
+      const int q = (int)(u - I * RB);  // run within the band
+      const int nb = min(32, BN - 32 * q);
+      const int W = (int)(e >> 56);
+      uint32_t w[16];
+      wz3_load_run(area, e, lane, nb, lane < nb, w);
+      if (W != 0 && lane < nb) wz3_accumulate<R>(w, W, xt, ldt, 32 * q + lane, hi, lo);  // a zero run adds 0
     }
-    const int W = (int)(e_cur >> 56);
-    const int64_t J = 32 * run + lane;
-    if (W != 0 && J < BN) wz3_accumulate<R>(w_cur, W, xt, ldt, J, hi, lo);  // a zero run decodes to zeros
-    if constexpr (kPipe) {
+    const int64_t g_lo = (I * RB) / L, g_hi = ((I + 1) * RB - 1) / L;
+    if (g_lo == g_hi)
+      band_finish<1, R>(hi, lo, lane, 4 * I, M, 0, 1, 4 * BM, ws, y, ldy, state, decay, false);
+    else
+      band_finish<1, R>(hi, lo, lane, 4 * ((I * maxseg + (g - g_lo)) * R), M, 0, 2, 0, ws, y, ldy, state, decay,
+                        false);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) w_cur[k] = w_nxt[k];
-      e_cur = e_nxt;
-      e_nxt = e_after;
-    }
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
+    ++I;
+    ub = ue;
   }
-  band_finish<1, R>(hi, lo, lane, 4 * I, M, split, ksplit, 4 * BM, ws, y, ldy, state, decay, false);
 }
 
 // Decode: thread per block, the exact definition -- T = (2G) V (2G)^T in
@@ -192,12 +209,13 @@ static __global__ void wz3_decompress_kernel(const uint64_t* __restrict__ index,
   int scale_exp = 0;
   bool zero = W == 0;
   if (!zero) {
-    const int bb = wz3_block_bytes(W);
-    const uint64_t* wp =
-        reinterpret_cast<const uint64_t*>(area + (e & 0x00FFFFFFFFFFFFFFull) + (uint64_t)(J - 32 * run) * bb);
+    const int nw = wz3_block_bytes(W) / 8;
+    const int64_t nb = min((int64_t)32, BN - 32 * run);
+    // word-interleaved run: word k of block b at word k nb + b
+    const uint64_t* wp = reinterpret_cast<const uint64_t*>(area + (e & 0x00FFFFFFFFFFFFFFull)) + (J - 32 * run);
     uint64_t w[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) w[k] = k < bb / 8 ? wp[k] : 0ull;
+    for (int k = 0; k < 9; ++k) w[k] = k < nw ? wp[k * nb] : 0ull;
     const int E = (int)(w[0] & 0xFF), K = (int)((w[0] >> 8) & 31);
     zero = E == 0;
     scale_exp = K + (E - 127) - 30;

@@ -183,6 +183,13 @@ def test_matrix_layout_round_trip_and_index(orc, M, N):
                 assert int(off[k]) == off_expect
                 blocks = [Ap[4 * I:4 * I + 4, 4 * J:4 * J + 4] for J in range(32 * r, min(BN, 32 * r + 32))]
                 assert Ws[k] == max(orc.wz3_block(b, tol)[3] for b in blocks)
+                # word-interleaved: word j of block b at byte 8 (j nb + b) of the run
+                nb, nw = len(blocks), orc.wz3_block_bytes(Ws[k]) // 8
+                words, W = orc.wz3_encode_run(np.stack(blocks), tol)
+                assert W == Ws[k]
+                start = 64 + 8 + 8 * BM * RB + int(off[k])
+                run = np.frombuffer(blob[start:start + 8 * nb * nw], dtype=np.uint64)
+                assert np.array_equal(run.reshape(nw, nb).T.reshape(-1), words)
                 off_expect += len(blocks) * orc.wz3_block_bytes(Ws[k])
         assert len(blob) == 64 + 8 + 8 * BM * RB + off_expect
 
