@@ -338,7 +338,10 @@ int whff_set_crossover(whff_handle* h, int min_rhs);
  * a matrix with R[i] at or above its handle's crossover (tensor-core passes
  * available, see whff_set_crossover) is instead stepped by its own
  * tensor-core passes (see whff_step).
- * All matrices must be WZ2 of one format and rate.  whff_batch_step: x[i]
+ * All matrices must be WZ2 of one format and rate, or all of one scaled
+ * format (BF16, FP16, FP8, FP32: units are then the 16-byte column chunks of
+ * a band, and a matrix at or above its crossover is stepped by its own
+ * tensor-core passes within the batch step).  whff_batch_step: x[i]
  * (N_i x R[i], ldx[i]), y[i] (M_i x R[i], ldy[i]), state[i] (M_i, may be NULL,
  * or state itself NULL) are device pointers; each state is updated for
  * r = 0..R[i]-1 in order after all of its matrix's columns are computed.

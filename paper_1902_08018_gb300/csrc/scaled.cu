@@ -48,6 +48,36 @@ int scaled_launch(const ScaledStep& a, cudaStream_t st) {
 }
 
 template <int FMT>
+static int scaled_batched_fmt(const Wz2Batch& b, cudaStream_t st) {
+  const unsigned grid = (unsigned)b.ctas, threads = dev::kWarpsPerCta * 32;
+  switch (b.R) {
+    case 1: dev::scaled_batched_kernel<FMT, 1><<<grid, threads, 0, st>>>(b.entries, b.nentries, b.total_blocks, b.L); break;
+    case 2: dev::scaled_batched_kernel<FMT, 2><<<grid, threads, 0, st>>>(b.entries, b.nentries, b.total_blocks, b.L); break;
+    case 4: dev::scaled_batched_kernel<FMT, 4><<<grid, threads, 0, st>>>(b.entries, b.nentries, b.total_blocks, b.L); break;
+    case 8: dev::scaled_batched_kernel<FMT, 8><<<grid, threads, 0, st>>>(b.entries, b.nentries, b.total_blocks, b.L); break;
+    default: return -1;
+  }
+  return 0;
+}
+
+int scaled_batched_launch(int fmt, const Wz2Batch& b, cudaStream_t st) {
+  int e;
+  switch (fmt) {
+    case 2: e = scaled_batched_fmt<2>(b, st); break;
+    case 3: e = scaled_batched_fmt<3>(b, st); break;
+    case 4: e = scaled_batched_fmt<4>(b, st); break;
+    case 7: e = scaled_batched_fmt<7>(b, st); break;
+    default: return -1;
+  }
+  if (e) return e;
+  if (b.any_shared)
+    dev::wz2_batched_epilogue<<<(unsigned)((b.total_rows + 255) / 256), 256, 0, st>>>(b.entries, b.row_begin,
+                                                                                     b.nentries, b.total_rows, b.L,
+                                                                                     b.R);
+  return 0;
+}
+
+template <int FMT>
 static cudaError_t scaled_occ(int* occ, bool groups8, int threads) {
   if (groups8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::scaled_range_kernel<FMT, 1, 8>, threads, 0);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, dev::scaled_range_kernel<FMT, 1, 32>, threads, 0);

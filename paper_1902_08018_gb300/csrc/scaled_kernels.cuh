@@ -200,5 +200,44 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
   }
 }
 
+// One persistent launch over all matrices of a batch of one scaled format
+// and right-hand-side count (units: the 16-byte column chunks of each 4-row
+// band, BN of them per band; the entries' band-major orders one after
+// another), split into contiguous warp ranges like scaled_range_kernel's.
+template <int FMT, int R>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+    scaled_batched_kernel(const BatchEntry* __restrict__ entries, int nentries, int64_t total, int64_t L) {
+  const int lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  int64_t b0 = g * L;
+  const int64_t b1 = min(total, b0 + L);
+  int ei = 0;
+  while (b0 < b1) {
+    while (ei + 1 < nentries && entries[ei + 1].block_begin <= b0) ++ei;  // warp-uniform
+    const BatchEntry& e = entries[ei];
+    const int64_t local = b0 - e.block_begin;
+    const int64_t I = local / e.BN;
+    const int64_t piece_end = min(b1, e.block_begin + (I + 1) * e.BN);
+    int64_t g_lo, g_hi;
+    batch_band_span(e, I, L, g_lo, g_hi);
+    const bool x_vec_ok = (reinterpret_cast<uintptr_t>(e.x) % 16 == 0) && (e.ldx % 4 == 0);
+    const bool x_fast = x_vec_ok && (e.N % 4 == 0) && (e.ld == e.N);
+    float hi[4][R], lo[4][R];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
+    scaled_piece<FMT, R, 32>(e.stream, e.scales, e.M, e.N, e.ld, e.TN, 4 * I, local - I * e.BN + lane,
+                             piece_end - e.block_begin - I * e.BN, e.x, e.ldx, x_fast, hi, lo);
+    if (g_lo == g_hi) {
+      band_finish<0, R>(hi, lo, lane, 4 * I, e.M, 0, 1, 4 * e.BM, e.ws, e.y, e.ldy, e.state, e.decay, false);
+    } else {
+      band_finish<0, R>(hi, lo, lane, 4 * ((I * e.maxseg + (g - g_lo)) * R), e.M, 0, 2, 0, e.ws, e.y, e.ldy,
+                        e.state, e.decay, false);
+    }
+    b0 = piece_end;
+  }
+}
+
 }  // namespace dev
 }  // namespace whff

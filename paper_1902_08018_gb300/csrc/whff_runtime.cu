@@ -1231,6 +1231,8 @@ struct whff_batch {
   std::vector<whff_handle*> hs;
   int rate = 0;
   bool lift = true;
+  int scaled_fmt = 0;              // a batch of one scaled format (0: WZ2)
+  std::vector<int> own_passes;     // scaled matrices stepped by their own tensor-core passes
   std::vector<Group> groups;
   dev::BatchEntry* pinned = nullptr;   // staging for the table uploads
   size_t pinned_entries = 0;
@@ -1295,15 +1297,30 @@ extern "C" int whff_batch_create(whff_handle* const* hs, const int* R, int count
   *out = nullptr;
   auto* b = new whff_batch;
   b->hs.assign(hs, hs + count);
+  const auto scaled = [](const whff_handle* h) {
+    const int f = h->info.fmt;
+    return f == WHFF_FMT_BF16 || f == WHFF_FMT_FP16 || f == WHFF_FMT_FP8E4M3 || f == WHFF_FMT_FP32;
+  };
+  if (!hs[0]) {
+    whff_batch_destroy(b);
+    set_error("whff_batch_create: null handle");
+    return WHFF_EINVAL;
+  }
   b->rate = hs[0]->info.rate;
   b->lift = hs[0]->info.fmt == WHFF_FMT_FIXED_LIFT;
-  for (int i = 0; i < count; ++i)
-    if (!hs[i] || !is_wz2(hs[i]) || hs[i]->info.rate != b->rate || is_wz2(hs[i]) != is_wz2(hs[0]) ||
-        (hs[i]->info.fmt == WHFF_FMT_FIXED_LIFT) != b->lift || R[i] < 1) {
+  b->scaled_fmt = scaled(hs[0]) ? hs[0]->info.fmt : 0;
+  for (int i = 0; i < count; ++i) {
+    const bool ok = hs[i] && R[i] >= 1 &&
+                    (b->scaled_fmt ? hs[i]->info.fmt == b->scaled_fmt
+                                   : is_wz2(hs[i]) && hs[i]->info.rate == b->rate &&
+                                         (hs[i]->info.fmt == WHFF_FMT_FIXED_LIFT) == b->lift);
+    if (!ok) {
       whff_batch_destroy(b);
-      set_error("whff_batch_create: all matrices must be resident WZ2 of one format and rate, R >= 1");
+      set_error("whff_batch_create: all matrices must be resident WZ2 of one format and rate, or of one scaled "
+                "format; R >= 1");
       return WHFF_EINVAL;
     }
+  }
   const int classes[4] = {8, 4, 2, 1};
   for (int cls : classes) {
     whff_batch::Group g;
@@ -1339,7 +1356,7 @@ extern "C" int whff_batch_create(whff_handle* const* hs, const int* R, int count
     }
     g.total_blocks = blocks;
     g.total_rows = rows;
-    const int occ = wz2_occ(b->rate, b->lift, g.R == 1 ? 2 : 1);
+    const int occ = b->scaled_fmt ? scaled_occupancy(b->scaled_fmt, false) : wz2_occ(b->rate, b->lift, g.R == 1 ? 2 : 1);
     const int64_t warps_cap = (int64_t)h0->sm_count * std::max(occ, 1) * dev::kWarpsPerCta;
     int64_t warps = std::min<int64_t>(warps_cap, std::max<int64_t>(1, (blocks + 63) / 64));
     warps = (warps + dev::kWarpsPerCta - 1) / dev::kWarpsPerCta * dev::kWarpsPerCta;
@@ -1376,8 +1393,13 @@ extern "C" int whff_batch_create(whff_handle* const* hs, const int* R, int count
     b->pinned_entries += n;
   }
   b->R.assign(R, R + count);
+  if (b->scaled_fmt) {  // scaled matrices at or above their crossover take their own tensor-core passes
+    for (int i = 0; i < count; ++i)
+      if (R[i] >= hs[i]->mma_min_rhs && hs[i]->d_ws_mma) b->own_passes.push_back(i);
+  }
   // tensor-core passes: one group per width class and per kMaxMembers passes
   for (int nr : {16, 32}) {
+    if (b->scaled_fmt) break;
     whff_batch::MmaGroup g;
     g.nr = nr;
     auto close = [&]() {
@@ -1531,6 +1553,10 @@ extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64
       return WHFF_ECUDA;
     }
   }
+  for (int i : b->own_passes) {  // scaled matrices with many columns: their own passes, state applied below
+    const int e = step_passes(b->hs[i], x[i], b->R[i], ldx[i], y[i], ldy[i], nullptr, decay, st);
+    if (e) return e;
+  }
   size_t off = 0;
   for (auto& g : b->groups) {
     const int n = (int)g.members.size();
@@ -1550,13 +1576,19 @@ extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64
       e.ldx = ldx[i];
       e.ldy = ldy[i];
       e.decay = decay;
+      if (b->scaled_fmt) {
+        e.scales = h->d_scales;
+        e.ld = scaled_ld(h->info.N);
+        e.TN = ceil_div(h->info.N, kScaleTile);
+      }
       b->pinned[off + k] = e;
     }
     WHFF_CUDA_TRY(cudaMemcpyAsync(g.d_entries, b->pinned + off, sizeof(dev::BatchEntry) * n,
                                   cudaMemcpyHostToDevice, st));
     Wz2Batch a{g.d_entries, g.d_row_begin, n, g.total_blocks, g.total_rows, g.L, g.ctas, g.any_shared, b->lift, g.R};
     int e;
-    switch (b->rate) {
+    if (b->scaled_fmt) e = scaled_batched_launch(b->scaled_fmt, a, st);
+    else switch (b->rate) {
       case 8: e = wz2_batched_launch<8>(a, st); break;
       case 12: e = wz2_batched_launch<12>(a, st); break;
       case 16: e = wz2_batched_launch<16>(a, st); break;

@@ -19,6 +19,8 @@ struct BatchEntry {
   int64_t block_begin;    // first global block index of this entry
   int maxseg;
   double decay;
+  const float* scales;    // scaled formats: the tile scales (stream = the payload)
+  int64_t ld, TN;         // scaled formats: payload row length, 128-column tiles per row
 };
 
 // The carried state of one batched matrix, applied after all its column

@@ -53,6 +53,10 @@ struct Wz2Batch {
   int R;
 };
 
+// A batch of one scaled format (BF16, FP16, FP8, FP32): same tables, units
+// are 16-byte column chunks (BN of them per band), stream = the payload.
+int scaled_batched_launch(int fmt, const Wz2Batch& b, cudaStream_t st);
+
 // state step of a batch (rate independent; defined in the rate-16 unit)
 int wz2_batched_state_launch(const dev::BatchState* table, const int64_t* row_begin, int n, int64_t total_rows,
                              cudaStream_t st);

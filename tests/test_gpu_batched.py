@@ -68,14 +68,57 @@ def test_batch_matches_oracle(env, orc, fmt, rate):
         h.destroy()
 
 
+@pytest.mark.parametrize("fmt", [2, 3, 4, 7])
+def test_scaled_batch_matches_oracle(env, orc, fmt):
+    """One scaled format per batch (BF16, FP16, FP8, FP32; 128 x 128 scale tiles cut
+    by ragged shapes): CUDA-core column groups for few columns, the matrices' own
+    tensor-core passes at or above their crossover (not for FP32), states in order."""
+    W, torch = env
+    shapes = [(130, 97), (1500, 1400), (16, 6000), (777, 777), (2000, 300), (64, 64)]
+    Rs = [1, 3, 8, 13, 4, 32]
+    rng = np.random.default_rng(fmt)
+    handles, blobs, X, Y, S = [], [], [], [], []
+    for k, ((M, N), R) in enumerate(zip(shapes, Rs)):
+        blob = W.whff_compress(_matrix(M, N, 200 + k), fmt, 0)
+        blobs.append(blob)
+        handles.append(W.whff_create(blob, max_rhs=32))
+        X.append(torch.from_numpy(rng.standard_normal((R, N)).astype(np.float32)).cuda())
+        Y.append(torch.full((R, M), float("nan"), dtype=torch.float64, device="cuda"))
+        S.append(torch.full((M,), 0.25, dtype=torch.float64, device="cuda"))
+    with W.Batch(handles, Rs) as b:
+        b.step(X, Y, S, decay=0.9)
+        torch.cuda.synchronize()
+        for k, (M, N) in enumerate(shapes):
+            Ahat = orc.decode(blobs[k].tobytes())
+            ref = orc.gemv64(Ahat, X[k].cpu().numpy().T.astype(np.float64))
+            Yk = Y[k].cpu().numpy()
+            for r in range(Rs[k]):
+                assert _rel(Yk[r], ref[:, r]) <= TOL, (k, r)
+            s_ref = orc.state_update(np.full(M, 0.25), ref, 0.9)
+            assert _rel(S[k].cpu().numpy(), s_ref) <= TOL, k
+        Y2 = [torch.zeros_like(y) for y in Y]
+        b.step(X, Y2, None)  # the plan is reused: the same bits
+        torch.cuda.synchronize()
+        for k in range(len(shapes)):
+            assert torch.equal(Y2[k], Y[k])
+    for h in handles:
+        assert h.sync_status() == 0
+        h.destroy()
+
+
 def test_batch_rejects_mixed_formats(env):
     W, torch = env
     h1 = W.whff_create(W.whff_compress(_matrix(64, 64, 1), 5, 12))
     h2 = W.whff_create(W.whff_compress(_matrix(64, 64, 2), 5, 16))
     with pytest.raises(W.WhffError):
         W.Batch([h1, h2], [1, 1])
-    h1.destroy()
-    h2.destroy()
+    h3 = W.whff_create(W.whff_compress(_matrix(64, 64, 3), 2, 0))  # BF16
+    h4 = W.whff_create(W.whff_compress(_matrix(64, 64, 4), 3, 0))  # FP16
+    for pair in ([h3, h4], [h3, h1], [h1, h3]):
+        with pytest.raises(W.WhffError):
+            W.Batch(pair, [1, 1])
+    for h in (h1, h2, h3, h4):
+        h.destroy()
 
 
 def test_tuner_keeps_results(env, orc, tmp_path):
