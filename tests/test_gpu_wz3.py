@@ -89,7 +89,7 @@ def test_step_against_oracle(env, orc, M, N, tol, R):
 
 
 def test_zero_runs_and_mixed_widths(env, orc):
-    """Whole runs of zero blocks (width 0: nothing stored), runs of tiny values next to
+    """Whole runs of zero blocks (width 0: 8 zero bytes per block), runs of tiny values next to
     runs of large ones (widths from 1 to 31 in one band)."""
     W, torch = env
     M, N = 256, 4096
