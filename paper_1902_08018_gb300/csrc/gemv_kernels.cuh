@@ -138,13 +138,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
 #pragma unroll
     for (int r = 0; r < R; ++r) hi[i][r] = lo[i][r] = 0.f;
 
+  __shared__ uint32_t planes[kPlaneWords];  // the decoder's plane words, a column per thread
+  uint32_t* Ps = planes + threadIdx.x;
   const int64_t rowblk = I * BN;
   for (int64_t J = J0 + lane; J < J1; J += 32) {
     uint32_t w[NW32 + 2];
     load_block<NW32>(stream, rowblk + J, w);
     int32_t q[16];
     int emax;
-    const bool nz = decode_block<NW32>(w, q, emax);
+    const bool nz = decode_block<NW32>(w, Ps, q, emax);
     if (!nz) continue;
     const float scale = __int_as_float((emax - 26 + 127) << 23);  // 2^(emax-26), a normal float
     float a[16];
@@ -256,6 +258,7 @@ static __global__ void splitk_epilogue_kernel(const double* __restrict__ ws, int
 template <int NW32>
 __global__ void wz1_decompress_kernel(const uint8_t* __restrict__ stream, int64_t M, int64_t N, int64_t BN,
                                       int64_t nblocks, double* __restrict__ out, int64_t ldo) {
+  __shared__ uint32_t planes[kPlaneWords];  // the decoder's plane words, a column per thread
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nblocks) return;
   const int64_t I = b / BN, J = b - (b / BN) * BN;
@@ -263,7 +266,7 @@ __global__ void wz1_decompress_kernel(const uint8_t* __restrict__ stream, int64_
   load_block<NW32>(stream, b, w);
   int32_t q[16];
   int emax;
-  const bool nz = decode_block<NW32>(w, q, emax);
+  const bool nz = decode_block<NW32>(w, planes + threadIdx.x, q, emax);
   const double scale = nz ? ldexp(1.0, emax - 26) : 0.0;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {

@@ -47,8 +47,14 @@ __device__ __forceinline__ void dswap(uint32_t& a, uint32_t& b, int s, uint32_t 
 // Decode the plane stream (starting after the 9 header bits) of one block
 // whose NW32 little-endian 32-bit words are in w[0..NW32) followed by two zero
 // words.  Returns the 16 negabinary words u[k] in sequency order.
+//
+// The plane loop is not unrolled (one small loop body instead of 32 copies:
+// the unrolled form spent its time on instruction-cache misses), so the plane
+// words go to the thread's own column of a shared-memory array, Ps[j * ps]
+// for plane kmax - j, and come back for the bit-matrix transpose.
 template <int NW32>
-__device__ __forceinline__ void decode_planes(const uint32_t (&w)[NW32 + 2], uint32_t (&u)[16]) {
+__device__ __forceinline__ void decode_planes(const uint32_t (&w)[NW32 + 2], uint32_t* __restrict__ Ps, int ps,
+                                              uint32_t (&u)[16]) {
   constexpr int kMaxBits = 16 * NW32 * 2 - 9;  // 16*rate - 9, rate = 2*NW32
   uint64_t win = ((uint64_t)w[1] << 32 | w[0]) >> 9;
   int avail = 55;  // valid bits in win
@@ -74,18 +80,14 @@ __device__ __forceinline__ void decode_planes(const uint32_t (&w)[NW32 + 2], uin
   skip(z0);
   const int kmax = 31 - z0;
 
-  uint32_t P[32];  // P[j] = plane kmax - j, bit i = coefficient i
-#pragma unroll
-  for (int j = 0; j < 32; ++j) P[j] = 0;
-
-  int n = 0;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if (j > kmax || bits <= 0) break;
+  int n = 0, j = 0;
+#pragma unroll 1
+  for (; j <= kmax && bits > 0; ++j) {
     refill();
     const int m = min(n, bits);
     uint32_t p = (uint32_t)win & ((1u << m) - 1u);
     skip(m);
+#pragma unroll 1
     while (n < 16 && bits > 0) {
       refill();
       const uint32_t v = (uint32_t)win;
@@ -116,10 +118,14 @@ __device__ __forceinline__ void decode_planes(const uint32_t (&w)[NW32 + 2], uin
       }
       break;
     }
-    P[j] = p;
+    Ps[j * ps] = p;
   }
 
-  // Transpose the 32 (plane) x 16 (coefficient) bit matrix: A[i] bit j = P[j] bit i.
+  // Transpose the 32 (plane) x 16 (coefficient) bit matrix: A[i] bit j = P[j] bit i
+  // (planes past the last decoded one are zero).
+  uint32_t P[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) P[k] = k < j ? Ps[k * ps] : 0u;
   uint32_t A[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) A[i] = __byte_perm(P[i], P[i + 16], 0x5410);
@@ -140,13 +146,20 @@ __device__ __forceinline__ void decode_planes(const uint32_t (&w)[NW32 + 2], uin
   for (int i = 0; i < 16; ++i) u[i] = sh >= 32 ? 0u : (__brev(A[i]) >> sh);
 }
 
+// Shared memory the decoder needs: one 32-word column per thread of a block
+// of kDecodeThreads threads.
+constexpr int kDecodeThreads = 256;
+constexpr int kPlaneWords = 32 * kDecodeThreads;
+
 // Decode one block: q (row-major) after the inverse transform, emax, nonzero.
+// Ps: the thread's column of a kPlaneWords-word shared array (stride kDecodeThreads).
 template <int NW32>
-__device__ __forceinline__ bool decode_block(const uint32_t (&w)[NW32 + 2], int32_t (&q)[16], int& emax) {
+__device__ __forceinline__ bool decode_block(const uint32_t (&w)[NW32 + 2], uint32_t* __restrict__ Ps, int32_t (&q)[16],
+                                             int& emax) {
   const bool nz = w[0] & 1u;
   emax = (int)((w[0] >> 1) & 0xFFu) - 127;
   uint32_t u[16];
-  decode_planes<NW32>(w, u);
+  decode_planes<NW32>(w, Ps, kDecodeThreads, u);
   uint32_t c[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) c[seq_index(k)] = (u[k] ^ 0xAAAAAAAAu) - 0xAAAAAAAAu;
