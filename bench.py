@@ -415,6 +415,10 @@ def run_whff(args, rank, world, local_rank):
                           "p99_us": float(np.percentile(lat, 99)), "rel_err": rel_err}
     for spec in specs[1:]:
         hh = W.whff_create(blobs[spec], max_rhs=32 if args.sweep_rhs else 1)
+        shape = "default"
+        if spec[0] in (5, 6) and not args.no_tune:  # WZ2: the launch shape the tuner picks, as for the headline
+            hh.tune(iters=3, stream=stream)
+            shape = dict(zip(("unroll", "ctas_per_sm", "fold"), hh.config()))
         sb = blobs[spec].size - 64
         tot, per = time_format(hh, xs, S, args.sweep_steps, 5, stream, torch, dev, order)
         err, _ = end_to_end_error(hh, xs, X64, sampled, sample_rows, stream, torch, dev, order)
@@ -422,7 +426,7 @@ def run_whff(args, rank, world, local_rank):
         name = f"{FMT_NAMES[spec[0]]}-{spec[1]}" if spec[1] else FMT_NAMES[spec[0]]
         formats[name] = {"GB_s": round(sb / (ms * 1e-3) / 1e9, 1), "pct_hbm": round(100 * sb / (ms * 1e-3) / 1e9 / peak, 2),
                          "bytes": int(sb), "ms_per_step": round(ms, 5), "p99_us": float(np.percentile(per * 1e3, 99)),
-                         "rel_err": err}
+                         "rel_err": err, "launch_shape": shape}
         if args.sweep_rhs:  # the same format with 32 right-hand sides (heat loads of steps 0..31)
             formats[name]["R32"] = rhs32_entry(hh, spec, sb, xs[:32], X64[:32], sampled, sample_rows, peak, stream,
                                                torch, dev, order)
