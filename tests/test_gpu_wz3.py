@@ -173,3 +173,77 @@ def test_create_refuses_bad_run_index(env):
         with pytest.raises(W.WhffError) as err:
             W.whff_create(_reseal(b), max_rhs=1)
         assert err.value.code == -5, patch
+
+
+def test_host_resident_graph_and_server(env, orc):
+    """The same fixed-accuracy bytes read over the host link give the device-resident
+    results bit for bit; a captured step replays to the result of whff_step; a WZ3 model
+    served among WZ2 ones gets what it gets alone and the oracle's state."""
+    W, torch = env
+    M, N = 700, 1300
+    blob = W.whff_compress_accuracy(_matrix(M, N, 21), 1e-6)
+    Ahat, _ = orc.wz3_decode(blob.tobytes())
+    rng = np.random.default_rng(21)
+    X = torch.from_numpy(rng.standard_normal((9, N)).astype(np.float32)).cuda()
+    out = []
+    for host in (False, True):
+        with W.whff_create(blob, max_rhs=16, host_resident=host) as h:
+            y = torch.zeros((9, M), dtype=torch.float64, device="cuda")
+            s = torch.full((M,), 0.5, dtype=torch.float64, device="cuda")
+            h.step(X, y, s, 0.9)  # a pass of 8 columns, then one of 1
+            ys = torch.zeros((2, 256), dtype=torch.float64, device="cuda")
+            h.step_rows(256, 256, X[:2], ys)
+            D = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+            h.decompress(D)
+            torch.cuda.synchronize()
+            assert h.sync_status() == 0
+            out.append((y, s, ys, D))
+    for u, v in zip(*out):
+        assert torch.equal(u, v)
+    assert np.array_equal(out[0][3].cpu().numpy(), Ahat)
+
+    with W.whff_create(blob, max_rhs=8) as h:
+        x = torch.zeros((2, N), dtype=torch.float32, device="cuda")
+        y = torch.zeros((2, M), dtype=torch.float64, device="cuda")
+        s = torch.zeros(M, dtype=torch.float64, device="cuda")
+        y_ref = torch.zeros((2, M), dtype=torch.float64, device="cuda")
+        s_ref = torch.zeros(M, dtype=torch.float64, device="cuda")
+        with W.whff_graph_create(h, x, y, s, 0.9) as g:
+            for _ in range(3):
+                xv = torch.from_numpy(rng.standard_normal((2, N)).astype(np.float32)).cuda()
+                x.copy_(xv)
+                g.launch()
+                h.step(xv, y_ref, s_ref, 0.9)
+                torch.cuda.synchronize()
+                assert torch.equal(y, y_ref) and torch.equal(s, s_ref)
+
+    import workloads
+
+    other = W.whff_compress(workloads.RectKernelMatrix(512, 512, 0.05, 22).dense(), 5, 16)
+    handles = [W.whff_create(blob, max_rhs=8), W.whff_create(other, max_rhs=8)]
+    n_req = 60
+    model = rng.integers(0, 2, size=n_req)
+    arrival = np.sort(np.repeat(np.arange(n_req // 10) * 2e-3, 10))
+    xs = [rng.standard_normal(handles[m].N).astype(np.float32) for m in model]
+    with W.Server(hbm_budget=8 << 30, max_batch=8, nstreams=2) as srv:
+        ids = [srv.add_model(h, decay=0.95) for h in handles]
+        lat, bat, ys = srv.run(model, arrival, xs, want_y=True)
+        state0 = srv.read_state(ids[0])
+    s = np.zeros(M)
+    for i in range(n_req):
+        if model[i] != 0:
+            continue
+        ref = orc.gemv64(Ahat, xs[i].astype(np.float64))
+        assert _rel(ys[i], ref) <= TOL, i
+        s = orc.state_update(s, ref, 0.95)
+    assert _rel(state0, s) <= TOL
+    for h in handles:
+        h.destroy()
+
+
+def test_batch_refuses_fixed_accuracy(env):
+    W, torch = env
+    h = W.whff_create(W.whff_compress_accuracy(_matrix(64, 64, 5), 1e-4), max_rhs=1)
+    with pytest.raises(W.WhffError):
+        W.Batch([h], [1])
+    h.destroy()
