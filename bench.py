@@ -336,6 +336,27 @@ def rhs32_entry(h, spec, sb, X, X64, sampled, sample_rows, peak, stream, torch, 
             "rel_err": err}
 
 
+def achievable_read(W, torch, dev, stream, nbytes: int, reps: int = 20) -> float:
+    """GB/s of the library's read-only streaming probe over a buffer the size of the
+    compressed stream (larger than L2): the third roofline line, beside the copy peak
+    and the nominal figure."""
+    buf = torch.ones(nbytes // 16 * 16, dtype=torch.uint8, device=dev)
+    out = torch.zeros(1, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        W.whff_read_probe(buf, out, stream)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(reps):
+        W.whff_read_probe(buf, out, stream)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    gbs = buf.numel() * reps / (f0.elapsed_time(f1) * 1e-3) / 1e9
+    del buf
+    torch.cuda.empty_cache()
+    return gbs
+
+
 def end_to_end_error(h, xs, X64, sampled, sample_rows, stream, torch, dev, order):
     y = torch.zeros(order, dtype=torch.float64, device=dev)
     h.step(xs[0], y, None, DECAY, stream)
@@ -534,6 +555,9 @@ def run_whff(args, rank, world, local_rank):
                 "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind}",
                 "traffic": ncu_traffic(f"{head_name}_{order}"), "kernel": kname,
                 "launches_per_step": launches, "frac_of_nominal_8TBs": round(achieved / NOMINAL_HBM_GBS, 4)}
+    read_gbs = achievable_read(W, torch, dev, stream, stream_bytes)
+    roofline["achievable_read_GB_s"] = round(read_gbs, 1)
+    roofline["frac_of_achievable_read"] = round(achieved / read_gbs, 4)
 
     slits = fields = None
     if not args.no_slits:

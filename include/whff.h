@@ -448,6 +448,15 @@ void whff_destroy(whff_handle* h);
 int whff_step_noalloc(const void* stream_dev, int rate, int64_t M, int64_t N, const float* x, int R, int64_t ldx,
                       double* y, int64_t ldy, double* state, double decay, void* stream);
 
+/* Measurement: read a device buffer once at full bandwidth (16-byte streaming
+ * loads, a persistent grid, four loads in flight per thread) and XOR all its
+ * 32-bit words into *d_xor (device memory; XOR-ed into, so zero it first).
+ * This is the achievable-read roofline the fused kernels stream against: a
+ * read-only stream is not a copy, and can exceed the copy bandwidth.
+ * buf must be 16-byte aligned and bytes a multiple of 16 (WHFF_EINVAL
+ * otherwise).  Asynchronous on `stream`. */
+int whff_read_probe(const void* buf, size_t bytes, uint32_t* d_xor, void* stream);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* whff_last_error(void);
 

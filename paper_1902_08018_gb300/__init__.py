@@ -32,6 +32,7 @@ from .whff import (  # noqa: F401
     whff_graph_create,
     whff_graph_create_host,
     whff_graph_create_rows,
+    whff_read_probe,
     whff_step,
     whff_step_host,
     whff_step_noalloc,

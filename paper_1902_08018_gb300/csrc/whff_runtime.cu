@@ -310,6 +310,48 @@ int launch_pass(const whff_handle* h, const float* x, int R, int64_t ldx, double
 
 using namespace whff;
 
+namespace whff {
+namespace dev {
+// The achievable-read probe: each thread keeps four 16-byte streaming loads in
+// flight and folds them into one XOR word; a warp folds its lanes, lane 0 adds
+// its word to the result with one atomic.
+static __global__ void __launch_bounds__(256) read_probe_kernel(const uint4* __restrict__ p, int64_t n16,
+                                                                uint32_t* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t acc = 0;
+  for (; i + 3 * stride < n16; i += 4 * stride) {
+    const uint4 a = __ldcs(p + i), b = __ldcs(p + i + stride), c = __ldcs(p + i + 2 * stride),
+                d = __ldcs(p + i + 3 * stride);
+    acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+  }
+  for (; i < n16; i += stride) {
+    const uint4 a = __ldcs(p + i);
+    acc ^= a.x ^ a.y ^ a.z ^ a.w;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc ^= __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicXor(out, acc);
+}
+}  // namespace dev
+}  // namespace whff
+
+extern "C" int whff_read_probe(const void* buf, size_t bytes, uint32_t* d_xor, void* stream) {
+  if (!buf || !d_xor || bytes % 16 || reinterpret_cast<uintptr_t>(buf) % 16) {
+    set_error("whff_read_probe: null pointer, or buffer not 16-byte aligned / sized");
+    return WHFF_EINVAL;
+  }
+  int dev = 0, sms = 0;
+  WHFF_CUDA_TRY(cudaGetDevice(&dev));
+  WHFF_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t n16 = (int64_t)(bytes / 16);
+  if (n16 == 0) return WHFF_OK;
+  const int64_t ctas = std::min<int64_t>((int64_t)sms * 8, (n16 + 255) / 256);  // 8 CTAs of 256 threads per SM
+  dev::read_probe_kernel<<<(unsigned)ctas, 256, 0, as_stream(stream)>>>(static_cast<const uint4*>(buf), n16, d_xor);
+  WHFF_CUDA_TRY(cudaGetLastError());
+  return WHFF_OK;
+}
+
 extern "C" const char* whff_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" const char* whff_version(void) { return "whff 0.1 sm_103a"; }

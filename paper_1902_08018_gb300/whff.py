@@ -102,6 +102,7 @@ def library() -> ctypes.CDLL:
         "whff_set_crossover": (c_int, [P, c_int]),
         "whff_get_slice_rows": (c_int, [P, ctypes.POINTER(i64)]),
         "whff_set_slice_rows": (c_int, [P, i64]),
+        "whff_read_probe": (c_int, [P, ctypes.c_size_t, P, P]),
         "whff_batch_create": (c_int, [P, P, c_int, ctypes.POINTER(P)]),
         "whff_batch_step": (c_int, [P, P, P, P, P, P, dbl, P]),
         "whff_batch_destroy": (None, [P]),
@@ -369,6 +370,19 @@ def whff_step_host(h: Handle, x_host: np.ndarray, y_host: np.ndarray, state=None
         sp, _, _ = _vec_args(state, h.M, "state", torch.float64)
     _check(library().whff_step_host(h.ptr, xh.ctypes.data, xh.shape[0], xh.strides[0] // 4, yh.ctypes.data,
                                     yh.strides[0] // 8, sp or None, float(decay), _stream_ptr(stream)))
+
+
+def whff_read_probe(buf, out, stream=None):
+    """XOR of every 32-bit word of a 16-byte-aligned CUDA tensor into out (int32, 1 element, on the GPU):
+    one read of the buffer at full bandwidth, the achievable-read roofline."""
+    import torch
+
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda or not buf.is_contiguous():
+        raise WhffError(-1, "buf must be a contiguous CUDA tensor")
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.int32 or out.numel() < 1:
+        raise WhffError(-1, "out must be a CUDA int32 tensor")
+    _check(library().whff_read_probe(buf.data_ptr(), buf.numel() * buf.element_size(), out.data_ptr(),
+                                     _stream_ptr(stream)))
 
 
 def whff_decompress(h: Handle, out, stream=None):
