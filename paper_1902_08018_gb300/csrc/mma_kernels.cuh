@@ -142,8 +142,13 @@ __device__ __forceinline__ void tmem_load_sum8(uint32_t ta, uint32_t stride, flo
                :
                : "memory");
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
-    v[i] = __uint_as_float(a[i]) + (__uint_as_float(b[i]) + __uint_as_float(c[i]));
+  for (int i = 0; i < 8; i += 2) {  // packed pairs: each half rounds as a + (b + c) would
+    const float2 bc = add_f2(make_float2(__uint_as_float(b[i]), __uint_as_float(b[i + 1])),
+                             make_float2(__uint_as_float(c[i]), __uint_as_float(c[i + 1])));
+    const float2 t = add_f2(make_float2(__uint_as_float(a[i]), __uint_as_float(a[i + 1])), bc);
+    v[i] = t.x;
+    v[i + 1] = t.y;
+  }
 }
 
 
@@ -397,7 +402,11 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
       float v[8];
       tmem_load_sum8(ta + h, NR, v);
 #pragma unroll
-      for (int r = 0; r < 8; ++r) two_sum_acc(hi[h + r], lo[h + r], v[r]);
+      for (int r = 0; r < 8; r += 2) {  // TwoSum on packed pairs of columns (the same bits per half)
+        float2 H = make_float2(hi[h + r], hi[h + r + 1]), Lo = make_float2(lo[h + r], lo[h + r + 1]);
+        two_sum_acc2(H, Lo, make_float2(v[r], v[r + 1]));
+        hi[h + r] = H.x, hi[h + r + 1] = H.y, lo[h + r] = Lo.x, lo[h + r + 1] = Lo.y;
+      }
     }
   };
 

@@ -190,10 +190,12 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
       float v[8];
       tmem_load_sum8(ta + h, NR, v);
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const float ps = __fmul_rn(v[r], s);
-        two_sum_acc(hi[h + r], lo[h + r], ps);
-        lo[h + r] += __fmaf_rn(v[r], s, -ps);
+      for (int r = 0; r < 8; r += 2) {  // packed pairs of columns: each half rounds as the scalar steps
+        const float2 ps = make_float2(__fmul_rn(v[r], s), __fmul_rn(v[r + 1], s));
+        float2 H = make_float2(hi[h + r], hi[h + r + 1]), Lo = make_float2(lo[h + r], lo[h + r + 1]);
+        two_sum_acc2(H, Lo, ps);
+        Lo = add_f2(Lo, fma_f2(make_float2(v[r], v[r + 1]), make_float2(s, s), make_float2(-ps.x, -ps.y)));
+        hi[h + r] = H.x, hi[h + r + 1] = H.y, lo[h + r] = Lo.x, lo[h + r + 1] = Lo.y;
       }
     }
   };

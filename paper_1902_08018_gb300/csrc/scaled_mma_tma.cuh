@@ -261,10 +261,12 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
         float v[8];
         tmem_load_sum8(ta + h, NR, v);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float ps = __fmul_rn(v[q], s);
-          two_sum_acc(hi[h + q], lo[h + q], ps);
-          lo[h + q] += __fmaf_rn(v[q], s, -ps);
+        for (int q = 0; q < 8; q += 2) {  // packed pairs of columns: each half rounds as the scalar steps
+          const float2 ps = make_float2(__fmul_rn(v[q], s), __fmul_rn(v[q + 1], s));
+          float2 H = make_float2(hi[h + q], hi[h + q + 1]), Lo = make_float2(lo[h + q], lo[h + q + 1]);
+          two_sum_acc2(H, Lo, ps);
+          Lo = add_f2(Lo, fma_f2(make_float2(v[q], v[q + 1]), make_float2(s, s), make_float2(-ps.x, -ps.y)));
+          hi[h + q] = H.x, hi[h + q + 1] = H.y, lo[h + q] = Lo.x, lo[h + q + 1] = Lo.y;
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
