@@ -224,25 +224,52 @@ __device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
 __device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
 
-// Four values of one tile row, split exactly into PA BF16 pieces; piece p of
-// the pair (v0, v1) is d[p][0], of (v2, v3) d[p][1].
-template <int PA>
-__device__ __forceinline__ void split_row(const float (&v)[4], uint32_t (&d)[PA][2]) {
+// The 16 coefficients of a block times its scale 2^(E+K-154), as packed pairs
+// in tile-row order: P[a][h] = (V[a][2h], V[a][2h+1]).  The field is OR-ed into
+// the mantissa of 2^(e+23) and one packed subtraction per pair gives the scaled
+// value exactly (wz2_fields_times_scale's values, two per instruction); blocks
+// beyond the trick's exponent range (|a| >= 2^103) decode unscaled and take s
+// by an exact packed multiply.  A zero block decodes to zeros.
+template <int RATE, bool LIFT>
+__device__ __forceinline__ void mma_block_pairs(const uint32_t (&w)[Wz2Layout<RATE>::kWords], float2 (&P)[4][2]) {
+  using Lay = Wz2Layout<RATE>;
+  const uint32_t E = w[0] & 0xFFu, K = (w[0] >> 8) & 31u;
+  const bool trick = E + K <= 258u;
+  const uint32_t creg = trick ? (E ? (E + K - 4u) << 23 : 0u) : 0x4B000000u;
+  const uint32_t mreg = E ? Lay::kMask : 0u;
+  const float bias = E ? __uint_as_float(creg | (1u << (Lay::kW - 1))) : 0.f;
+  uint32_t u[16];
+  wz2_field_bits_impl<RATE>(w, mreg, creg, u, std::make_integer_sequence<int, 16>{});
+  const float2 b2 = make_float2(bias, bias);
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    float a = v[2 * h], b = v[2 * h + 1];
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int p = 0; p < PA; ++p) {
-      d[p][h] = bf16x2_rn(a, b);
-      if (p + 1 < PA) {
-        a -= bf16_lo(d[p][h]);
-        b -= bf16_hi(d[p][h]);
-      }
+    for (int h = 0; h < 2; ++h) {
+      const int m0 = 4 * a + 2 * h, m1 = m0 + 1;
+      const int k0 = LIFT ? seq_field(m0) : m0, k1 = LIFT ? seq_field(m1) : m1;
+      P[a][h] = sub_f2(make_float2(__uint_as_float(u[k0]), __uint_as_float(u[k1])), b2);
     }
+  if (!trick) {
+    const float s = __uint_as_float((E + K - 27u) << 23);
+    const float2 s2 = make_float2(s, s);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) P[a][h] = mul_f2(P[a][h], s2);
   }
 }
 
-
+// Exact split of a pair of values (at most 8 PA significant bits each) into PA
+// BF16 pairs, d[p] = piece p of (v.x, v.y): round to BF16, subtract, repeat --
+// the two subtractions of each step in one packed instruction.
+template <int PA>
+__device__ __forceinline__ void split_pair(float2 v, uint32_t (&d)[PA]) {
+#pragma unroll
+  for (int p = 0; p < PA; ++p) {
+    d[p] = bf16x2_rn(v.x, v.y);
+    if (p + 1 < PA) v = sub_f2(v, make_float2(bf16_lo(d[p]), bf16_hi(d[p])));
+  }
+}
 
 // Persistent grid over the item sequence of one or more passes (members):
 // member k owns items [item_begin, item_begin + tiles S), item = item_begin +
@@ -432,19 +459,18 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int jl = jl0 + 4 * u;
-      float f[16], V[16];
-      wz2_fields_times_scale<RATE>(w[buf][u], f);
-      wz2_unpermute<LIFT>(f, V);
+      float2 P[4][2];
+      mma_block_pairs<RATE, LIFT>(w[buf][u], P);
       const int kstep = jl >> 2, kk = (jl & 3) * 4;
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const float v[4] = {V[4 * a], V[4 * a + 1], V[4 * a + 2], V[4 * a + 3]};
-        uint32_t d[PA][2];
-        split_row<PA>(v, d);
+        uint32_t d0[PA], d1[PA];
+        split_pair<PA>(P[a][0], d0);
+        split_pair<PA>(P[a][1], d1);
         const uint32_t off = tile_off(32 * a + band_l, kk);
 #pragma unroll
         for (int p = 0; p < PA; ++p)
-          *reinterpret_cast<uint2*>(As + (p * kMmaKSteps + kstep) * SM::kATile + off) = make_uint2(d[p][0], d[p][1]);
+          *reinterpret_cast<uint2*>(As + (p * kMmaKSteps + kstep) * SM::kATile + off) = make_uint2(d0[p], d1[p]);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor-core reads
