@@ -473,6 +473,9 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
           *reinterpret_cast<uint2*>(As + (p * kMmaKSteps + kstep) * SM::kATile + off) = make_uint2(d0[p], d1[p]);
       }
     }
+    // this ring slot is free: the words of stage k+2 are on their way from here
+    // on, through the barrier, the MMA issue and the drain
+    if (k + 2 < n) fetch(buf);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes -> tensor-core reads
     if (!__syncthreads_and(ok ? 1 : 0)) return false;
     // group bookkeeping of stage k (the same in every thread)
@@ -513,8 +516,6 @@ __global__ void __launch_bounds__(kMmaThreads, MmaPieces<RATE>::kA == 3 ? 1 : 2)
         *last_commit = k;
       }
     }
-    // this ring slot is free: the words of stage k+2 are loaded while the MMAs run
-    if (k + 2 < n) fetch(buf);
     if (k >= 1) {  // stage k-1 (other buffer): wait for its MMAs; drain its group if it closed one
       const bool done =
           __all_sync(0xFFFFFFFFu, mbar_wait(mma_bar + 8 * (buf ^ 1), (uint32_t)(((k - 1) >> 1) & 1), spin));
