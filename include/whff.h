@@ -158,7 +158,7 @@ int whff_info(const whff_handle* h, int* fmt, int* rate, int64_t* M, int64_t* N,
 /* Launch plan of a resident matrix: *ksplit = column splits per 4-row band
  * (1 for matrices with enough rows to fill the GPU), *launches = kernel
  * launches of one CUDA-core whff_step pass: the fused kernel, the epilogue of
- * shared bands or split-K if any, and for FIXED_LIFT the (2G)^T x transform of
+ * shared bands or split-K if any, and for FIXED_LIFT and FIXED_ACC the (2G)^T x transform of
  * x that the fused kernel reads. */
 int whff_plan(const whff_handle* h, int* ksplit, int* launches);
 

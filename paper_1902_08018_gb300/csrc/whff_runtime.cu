@@ -84,10 +84,11 @@ constexpr int kMaxRhsKernel = 8;  // right-hand sides handled per kernel pass
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// Split-K so that the grid holds enough warps for the GPU: each warp owns one
-// 4-row band; when bands are few (wide matrices), split the columns.
-// WZ2: split the band-major block order into one contiguous range per
-// resident warp (exact balance); bands that straddle ranges get segments.
+// WZ1: split-K so that the grid holds enough warps for the GPU: each warp owns
+// one 4-row band; when bands are few (wide matrices), split the columns.
+// WZ2, WZ3 and the scaled formats: split the band-major unit order into one
+// contiguous range per resident warp (exact balance); bands that straddle
+// ranges get segments.
 // Units of a band that the persistent ranges count: runs of 32 blocks for the
 // fixed-accuracy format, blocks (WZ2) or 16-byte chunks (scaled) otherwise.
 int64_t band_units(const whff_handle* h) { return is_wz3(h->info.fmt) ? ceil_div(h->BN, 32) : h->BN; }
