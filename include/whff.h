@@ -167,7 +167,9 @@ int whff_plan(const whff_handle* h, int* ksplit, int* launches);
  * max_rhs >= 2, passes of crossover..32 columns (default crossover 4, see
  * whff_set_crossover) run on the tensor cores (tcgen05: the stored values
  * split exactly into 1-3 BF16 pieces -- WZ2 by field width, FP16 into two,
- * BF16 and FP8 into one -- and x, transformed for FIXED_LIFT, into three; the
+ * BF16 and FP8 into one -- and x, transformed for FIXED_LIFT, into three;
+ * FP16 in device memory instead keeps its values and takes x, scaled per
+ * column by a power of two, in three FP16 pieces; the
  * piece products above 2^-24 accumulate in FP32 TMEM, drained every 128
  * columns of K into compensated sums, the scaled formats' tile scale applied
  * at the drain); otherwise passes of 8, 4, 2, 1 columns run on the CUDA cores.

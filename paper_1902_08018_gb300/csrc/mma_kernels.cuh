@@ -68,6 +68,11 @@ __device__ __forceinline__ constexpr uint32_t mma_idesc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
+// The same with A and B FP16 (bits 7-9 and 10-12 = 0).
+__device__ __forceinline__ constexpr uint32_t mma_idesc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
 // Byte offset of element (row, k) in a 16-wide K-step tile (no swizzle,
 // K-major): core matrix (row/8, k/8) of 8 rows x 16 bytes, 2 along K.
 __device__ __forceinline__ uint32_t tile_off(int row, int k) {

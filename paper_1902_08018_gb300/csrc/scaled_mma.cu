@@ -9,12 +9,13 @@
 
 namespace whff {
 
-// The TMA-fed BF16 kernel: its shared-memory attribute, set once per width.
-template <int NR>
+// The TMA-fed kernel (BF16, or FP16 with F16): its shared-memory attribute,
+// set once per width and type.
+template <int NR, bool F16>
 static int scaled_tma_attr() {
   static int done = 0;
   if (!done) {
-    auto kern = dev::scaled_mma_tma_kernel<NR>;
+    auto kern = dev::scaled_mma_tma_kernel<NR, F16>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::TmaSmem<NR>::kBytes) !=
             cudaSuccess ||
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
@@ -31,8 +32,9 @@ template <int FMT, int NR>
 static int scaled_mma_one(const ScaledMmaStep& a, cudaStream_t st) {
   using S = dev::ScaledMmaSmem<FMT, NR>;
   auto kern = dev::scaled_mma_kernel<FMT, NR>;
-  const bool tma = FMT == 2 && a.tmap != nullptr;
-  if (tma ? scaled_tma_attr<NR>() != 0
+  constexpr bool kF16 = FMT == 3;
+  const bool tma = (FMT == 2 || FMT == 3) && a.tmap != nullptr;
+  if (tma ? scaled_tma_attr<NR, kF16>() != 0
           : (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes) != cudaSuccess ||
              cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared) != cudaSuccess)) {
@@ -43,9 +45,15 @@ static int scaled_mma_one(const ScaledMmaStep& a, cudaStream_t st) {
   const int tiles = (int)((a.M + 127) / 128);
   const dev::MmaPass pass{a.x, a.y, a.btiles, a.ws, a.ldx, a.ldy, a.N, a.M, 0, 0, 0, nstages, tiles, a.R, a.maxseg};
   const int64_t bthreads = (int64_t)nstages * dev::kMmaStageBlocks * NR;
-  dev::wz2_mma_btiles<false, NR><<<(unsigned)((bthreads + 255) / 256), 256, 0, st>>>(pass, nullptr, 1, bthreads);
+  const bool f16_pieces = tma && kF16;  // FP16 A by TMA: FP16 B pieces of x scaled per column
+  if (f16_pieces) {
+    dev::f16_colexp_kernel<<<(unsigned)NR, 256, 0, st>>>(a.x, a.ldx, a.N, a.R, a.colexp);
+    dev::f16_mma_btiles<NR><<<(unsigned)((bthreads + 255) / 256), 256, 0, st>>>(pass, a.colexp, bthreads);
+  } else {
+    dev::wz2_mma_btiles<false, NR><<<(unsigned)((bthreads + 255) / 256), 256, 0, st>>>(pass, nullptr, 1, bthreads);
+  }
   if (tma) {
-    dev::scaled_mma_tma_kernel<NR><<<(unsigned)a.ctas, dev::kTmaThreads, dev::TmaSmem<NR>::kBytes, st>>>(
+    dev::scaled_mma_tma_kernel<NR, kF16><<<(unsigned)a.ctas, dev::kTmaThreads, dev::TmaSmem<NR>::kBytes, st>>>(
         *static_cast<const CUtensorMap*>(a.tmap), a.row0, a.scales, a.TN, a.btiles, a.ws, nstages, a.R, a.maxseg,
         (int64_t)tiles * nstages, a.L, a.status, a.spin);
   } else {
@@ -55,7 +63,7 @@ static int scaled_mma_one(const ScaledMmaStep& a, cudaStream_t st) {
   }
   const int64_t fin = (int64_t)tiles * a.R * 128;
   dev::scaled_mma_finish<<<(unsigned)((fin + 255) / 256), 256, 0, st>>>(a.ws, a.M, nstages, a.R, a.maxseg, tiles, a.L,
-                                                                       a.y, a.ldy);
+                                                                       a.y, a.ldy, f16_pieces ? a.colexp : nullptr);
   if (a.state)
     dev::wz2_mma_state<<<(unsigned)((a.M + 255) / 256), 256, 0, st>>>(a.y, a.ldy, a.R, a.M, a.state, a.decay);
   return 0;
@@ -102,14 +110,14 @@ static int scaled_mma_occ_one() {
   return std::min(std::min(by_regs, by_smem), by_tmem);
 }
 
-// Resident CTAs per SM of the TMA-fed BF16 kernel, from its registers, shared
+// Resident CTAs per SM of the TMA-fed kernel, from its registers, shared
 // memory and TMEM columns (the occupancy API reported one CTA where two fit).
-template <int NR>
+template <int NR, bool F16>
 static int scaled_tma_occ_one() {
-  auto kern = dev::scaled_mma_tma_kernel<NR>;
+  auto kern = dev::scaled_mma_tma_kernel<NR, F16>;
   cudaFuncAttributes fa;
   int dev = 0, smem_sm = 0, regs_sm = 0, reserved = 0;
-  if (scaled_tma_attr<NR>() || cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+  if (scaled_tma_attr<NR, F16>() || cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
@@ -127,9 +135,11 @@ static int scaled_tma_occ_one() {
 int scaled_mma_occupancy(int fmt, bool tma) {
   switch (fmt) {
     case 2:
-      return tma ? std::min(scaled_tma_occ_one<16>(), scaled_tma_occ_one<32>())
+      return tma ? std::min(scaled_tma_occ_one<16, false>(), scaled_tma_occ_one<32, false>())
                  : std::min(scaled_mma_occ_one<2, 16>(), scaled_mma_occ_one<2, 32>());
-    case 3: return std::min(scaled_mma_occ_one<3, 16>(), scaled_mma_occ_one<3, 32>());
+    case 3:
+      return tma ? std::min(scaled_tma_occ_one<16, true>(), scaled_tma_occ_one<32, true>())
+                 : std::min(scaled_mma_occ_one<3, 16>(), scaled_mma_occ_one<3, 32>());
     case 4: return std::min(scaled_mma_occ_one<4, 16>(), scaled_mma_occ_one<4, 32>());
     default: return 0;
   }
@@ -139,7 +149,7 @@ int scaled_mma_occupancy(int fmt, bool tma) {
 
 namespace whff {
 
-int scaled_tma_map(void* out, const void* payload, int64_t M, int64_t ld) {
+int scaled_tma_map(void* out, const void* payload, int64_t M, int64_t ld, int fmt) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -156,7 +166,8 @@ int scaled_tma_map(void* out, const void* payload, int64_t M, int64_t ld) {
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};  // bytes between rows (a multiple of 16: ld % 16 == 0)
   const cuuint32_t box[2] = {64, 128};                  // 128 bytes x 128 rows: one stage
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  const CUresult r = encode(static_cast<CUtensorMap*>(out),
+                            fmt == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                             const_cast<void*>(payload), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

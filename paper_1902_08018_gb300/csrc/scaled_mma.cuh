@@ -323,8 +323,66 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
 
 // y[r][128 tile + m] = the tile's segment partials of row m, added in order.
 // Thread per (tile, column, row of the tile), the row fastest.
+// Per column r of x (FP16 passes): e_r with max |x_r| * 2^e_r < 2^15, so that
+// the scaled column's FP16 pieces stay below the FP16 maximum (0 for a zero
+// column).  A block per column.
+static __global__ void f16_colexp_kernel(const float* __restrict__ x, int64_t ldx, int64_t N, int R,
+                                         int* __restrict__ colexp) {
+  const int r = (int)blockIdx.x;
+  float m = 0.f;
+  if (r < R)
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) m = fmaxf(m, fabsf(__ldg(x + (int64_t)r * ldx + i)));
+  __shared__ float red[32];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, red[k]);
+    int e = 0;
+    if (m > 0.f) (void)frexpf(m, &e);  // m < 2^e
+    colexp[r] = m > 0.f ? 15 - e : 0;
+  }
+}
+
+// B tiles of an FP16 pass: x_J * 2^e_r in three FP16 pieces (exact: 11 + 11 +
+// 11 significant bits cover FP32's 24; the scale keeps the first below 2^15),
+// in the tile layout of wz2_mma_btiles.  Thread per (stage, J, r).
+template <int NR>
+static __global__ void f16_mma_btiles(MmaPass ps, const int* __restrict__ colexp, int64_t threads) {
+  using S = MmaBTile<NR>;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= threads) return;
+  const int r = (int)(q % NR);
+  const int jl = (int)((q / NR) % kMmaStageBlocks);
+  const int64_t stage = q / ((int64_t)NR * kMmaStageBlocks);
+  const int64_t J = stage * kMmaStageBlocks + jl;
+  __half p[3][4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float v = 0.f;
+    if (r < ps.R && 4 * J + c < ps.N) v = ldexpf(__ldg(ps.x + (int64_t)r * ps.ldx + 4 * J + c), colexp[r]);
+    const __half h0 = __float2half_rn(v);
+    const float r1 = v - __half2float(h0);
+    const __half h1 = __float2half_rn(r1);
+    p[0][c] = h0;
+    p[1][c] = h1;
+    p[2][c] = __float2half_rn(r1 - __half2float(h1));
+  }
+  const int kstep = jl >> 2, kk = (jl & 3) * 4;
+  uint8_t* base = ps.btiles + stage * (int64_t)S::kB;
+#pragma unroll
+  for (int pc = 0; pc < 3; ++pc) {
+    const uint32_t lo = (uint32_t)__half_as_ushort(p[pc][0]) | ((uint32_t)__half_as_ushort(p[pc][1]) << 16);
+    const uint32_t hi = (uint32_t)__half_as_ushort(p[pc][2]) | ((uint32_t)__half_as_ushort(p[pc][3]) << 16);
+    *reinterpret_cast<uint2*>(base + (kstep * 3 + pc) * S::kBTile + tile_off(r, kk)) = make_uint2(lo, hi);
+  }
+}
+
+// colexp (FP16 passes, else null): y of column r is the sum times 2^-e_r (exact).
 static __global__ void scaled_mma_finish(const double* __restrict__ ws, int64_t M, int S, int R, int maxseg,
-                                         int64_t tiles, int64_t L, double* __restrict__ y, int64_t ldy) {
+                                         int64_t tiles, int64_t L, double* __restrict__ y, int64_t ldy,
+                                         const int* __restrict__ colexp) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= tiles * R * 128) return;
   const int m = (int)(q & 127);
@@ -337,7 +395,7 @@ static __global__ void scaled_mma_finish(const double* __restrict__ ws, int64_t 
   const int nseg = (int)((first + S - 1) / L - first / L + 1);
   double acc = 0.0;
   for (int g = 0; g < nseg; ++g) acc += ws[((tile * maxseg + g) * R + r) * 128 + m];
-  y[(int64_t)r * ldy + row] = acc;
+  y[(int64_t)r * ldy + row] = colexp ? ldexp(acc, -colexp[r]) : acc;
 }
 
 }  // namespace dev

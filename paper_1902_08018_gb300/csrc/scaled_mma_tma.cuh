@@ -92,7 +92,10 @@ __device__ __forceinline__ int mbar_wait_or_abort(uint32_t bar, uint32_t parity,
 // Same items, segments and workspace layout as scaled_mma_kernel<BF16, NR>;
 // tmap covers the whole stored matrix (M_total x ld BF16, box 8 x 128), and
 // row0 is the first row of this pass (a row view's offset, a multiple of 128).
-template <int NR>
+// F16: FP16 storage with FP16 B pieces (kind::f16 takes A and B of one type;
+// the B tiles are then the FP16 pieces of x scaled per column, see
+// f16_mma_btiles); otherwise BF16 storage and BF16 pieces.
+template <int NR, bool F16>
 __global__ void __launch_bounds__(kTmaThreads, 2)
     scaled_mma_tma_kernel(const __grid_constant__ CUtensorMap tmap, int64_t row0, const float* __restrict__ scales,
                           int64_t TN, const uint8_t* __restrict__ btiles, double* __restrict__ ws, int S, int R,
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d0),
-            "l"(ad), "l"(bd), "r"(mma_idesc(3 * NR)), "r"(accumulate));
+            "l"(ad), "l"(bd), "r"(F16 ? mma_idesc_f16(3 * NR) : mma_idesc(3 * NR)), "r"(accumulate));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(freed +
                                                                                                       8 * slot)

@@ -56,6 +56,7 @@ struct whff_handle {
   int ws_rhs = 8;               // right-hand sides the workspace is sized for
   double* d_ws_mma = nullptr;   // WZ2 tensor-core passes: tiles x maxseg x 32 x 128 partials
   uint8_t* d_btiles = nullptr;  // WZ2 tensor-core passes: B operand pieces per stage
+  size_t btile_bytes = 0;       // their size; kColexpBytes of FP16 column exponents follow
   float* d_xt = nullptr;        // WZ2 lift: (2G)^T x of a CUDA-core pass, 4 BN floats x 8 columns
   size_t ws_mma_bytes = 0;
   int64_t mma_L = 0;            // (tile, stage) items per CTA of the persistent tensor-core grid
@@ -81,6 +82,8 @@ namespace whff {
 namespace {
 
 constexpr int kMaxRhsKernel = 8;  // right-hand sides handled per kernel pass
+
+constexpr size_t kColexpBytes = 256;  // 32 column exponents of an FP16 tensor-core pass, padded
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -489,7 +492,7 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
     // (tile of 128 rows, stage of 64 columns), equal contiguous ranges per CTA
     const bool lift = info.fmt == WHFF_FMT_FIXED_LIFT;
     // BF16 in device memory: the TMA-fed kernel (its map is encoded below)
-    const bool tma = info.fmt == WHFF_FMT_BF16 && !(flags & WHFF_CREATE_HOST_RESIDENT);
+    const bool tma = (info.fmt == WHFF_FMT_BF16 || info.fmt == WHFF_FMT_FP16) && !(flags & WHFF_CREATE_HOST_RESIDENT);
     const int occ = wz2 ? std::min(mma_occupancy(info.rate, lift, 16), mma_occupancy(info.rate, lift, 32))
                         : scaled_mma_occupancy(info.fmt, tma);
     if (occ < 1) {
@@ -501,9 +504,10 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
     h->ws_mma_cap = mma_ws_need(h, std::min(max_rhs, 32));
     h->ws_mma_bytes = h->ws_mma_cap;
     const size_t btile_bytes = (size_t)ceil_div(info.N, 64) * 3 * 4 * 32 * 16 * 2;  // stages x pieces x ksteps x NR<=32 tile
-    h->ws_mma_bytes += btile_bytes;
-    if (cudaMalloc(&h->d_ws_mma, h->ws_mma_bytes - btile_bytes) != cudaSuccess ||
-        cudaMalloc(&h->d_btiles, btile_bytes) != cudaSuccess) {
+    h->btile_bytes = btile_bytes;
+    h->ws_mma_bytes += btile_bytes + kColexpBytes;  // FP16 passes: per-column exponents of x after the tiles
+    if (cudaMalloc(&h->d_ws_mma, h->ws_mma_bytes - btile_bytes - kColexpBytes) != cudaSuccess ||
+        cudaMalloc(&h->d_btiles, btile_bytes + kColexpBytes) != cudaSuccess) {
       cudaGetLastError();
       set_error("whff_create: cudaMalloc of the tensor-core workspace failed");
       return fail(WHFF_ENOMEM);
@@ -533,10 +537,11 @@ int create_impl(const BlobInfo& info, const uint8_t* src, int max_rhs, unsigned 
     h->d_scales = reinterpret_cast<const float*>(h->d_stream + (uint64_t)info.M * (uint64_t)scaled_ld(info.N) *
                                                                    (uint64_t)elem_bytes(info.fmt));
   }
-  // BF16 tensor-core passes take their A tiles by TMA from device memory
-  // (if the map cannot be encoded the register-fed kernel runs instead, same results)
-  if (info.fmt == WHFF_FMT_BF16 && h->d_ws_mma && !h->h_stream)
-    h->has_tmap = scaled_tma_map(h->tmap, h->d_stream, info.M, scaled_ld(info.N)) == 0;
+  // BF16 and FP16 tensor-core passes take their A tiles by TMA from device
+  // memory (if the map cannot be encoded the register-fed kernel runs instead:
+  // the same results for BF16, the same accuracy bar for FP16)
+  if ((info.fmt == WHFF_FMT_BF16 || info.fmt == WHFF_FMT_FP16) && h->d_ws_mma && !h->h_stream)
+    h->has_tmap = scaled_tma_map(h->tmap, h->d_stream, info.M, scaled_ld(info.N), info.fmt) == 0;
   *out = h;
   return WHFF_OK;
 }
@@ -573,7 +578,8 @@ int launch_mma(const whff_handle* h, const float* x, int R, int64_t ldx, double*
     ScaledMmaStep a{h->info.fmt, h->d_stream, h->d_scales, h->info.M, h->info.N, scaled_ld(h->info.N),
                     ceil_div(h->info.N, kScaleTile), x, ldx, R, h->mma_L, h->mma_ctas, h->mma_maxseg,
                     h->d_ws_mma, h->d_btiles, y, ldy, state, decay, h->d_status, h->wait_polls,
-                    h->has_tmap ? h->tmap : nullptr, h->tma_row0};
+                    h->has_tmap ? h->tmap : nullptr, h->tma_row0,
+                    reinterpret_cast<int*>(h->d_btiles + h->btile_bytes)};
     e = scaled_mma_launch(a, st);
   }
   if (e) {

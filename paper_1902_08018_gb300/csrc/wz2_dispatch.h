@@ -148,14 +148,15 @@ struct ScaledMmaStep {
   double decay;
   int* status;
   uint32_t spin;
-  const void* tmap;  // BF16: CUtensorMap of the whole stored matrix (A tiles by TMA), or null
+  const void* tmap;  // BF16 / FP16: CUtensorMap of the whole stored matrix (A tiles by TMA), or null
   int64_t row0;      // first row of this pass within that matrix (row views)
+  int* colexp;       // FP16 with tmap: 32 ints of scratch for the per-column exponents of x
 };
 int scaled_mma_launch(const ScaledMmaStep& a, cudaStream_t st);
-// Host: encode the TMA map of a BF16 payload (M x ld elements, row-major, box
-// 64 x 128, 128-byte swizzle) into out (a CUtensorMap, 128 bytes, 64-byte
-// aligned); 0 on success.
-int scaled_tma_map(void* out, const void* payload, int64_t M, int64_t ld);
+// Host: encode the TMA map of a BF16 or FP16 (fmt 3) payload (M x ld
+// elements, row-major, box 64 x 128, 128-byte swizzle) into out (a
+// CUtensorMap, 128 bytes, 64-byte aligned); 0 on success.
+int scaled_tma_map(void* out, const void* payload, int64_t M, int64_t ld, int fmt);
 // resident CTAs per SM for R <= 32 (0 on error); tma: the TMA-fed BF16 kernel
 int scaled_mma_occupancy(int fmt, bool tma);
 

@@ -118,3 +118,37 @@ def test_scaled_row_views_and_slices_on_tensor_cores(env, orc, fmt):
     for r in range(R):
         assert _rel(Yv[r], ref[row0:row0 + nrows, r]) <= TOL, r
         assert _rel(Ys[r], ref[:, r]) <= TOL, r
+
+
+@pytest.mark.parametrize("host_resident", [False, True])
+def test_fp16_pass_over_wide_column_ranges(env, orc, host_resident):
+    """FP16 storage on the TMA-fed pass scales each column of x by a power of two before
+    splitting it into FP16 pieces (and the register-fed pass of a host-resident handle
+    does not): columns of very different magnitudes, a column with a wide range inside
+    it and an all-zero column all meet the bar; the zero column gives exact zeros."""
+    W, torch = env
+    M, N = 700, 1300
+    blob = W.whff_compress(_matrix(M, N, 31), 3, 0)
+    Ahat = orc.decode(blob.tobytes())
+    rng = np.random.default_rng(31)
+    X = rng.standard_normal((8, N)).astype(np.float32)
+    X[1] *= 1e-20
+    X[2] *= 1e20
+    X[3] = 0.0
+    X[4, : N // 2] *= 1e-6
+    X[4, N // 2:] *= 1e3
+    X[5] = np.float32(65504.0) * 4  # above the FP16 maximum before scaling
+    X[6, ::2] = 0.0
+    with W.whff_create(blob, max_rhs=8, host_resident=host_resident) as h:
+        assert h.crossover <= 8
+        y = torch.full((8, M), float("nan"), dtype=torch.float64, device="cuda")
+        h.step(torch.from_numpy(X).cuda(), y)
+        torch.cuda.synchronize()
+        assert h.sync_status() == 0
+        Y = y.cpu().numpy()
+    for r in range(8):
+        ref = orc.gemv64(Ahat, X[r].astype(np.float64))
+        if r == 3:
+            assert (Y[r] == 0.0).all()
+        else:
+            assert _rel(Y[r], ref) <= TOL, (r, _rel(Y[r], ref))
