@@ -25,6 +25,7 @@ sum over ranks of bytes streamed / the max-over-ranks time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -231,8 +232,13 @@ def build_workload(order: int, specs, keep_fp64_device: bool, sample_rows: np.nd
     km = matrix_for(order)
     L = W.library()
     blobs = {}
-    accuracy = [spec for spec in specs if spec[0] == 8]  # fixed accuracy: encoded from the whole matrix
-    A_host = np.empty((order, order)) if accuracy else None
+    accuracy = [spec for spec in specs if spec[0] == 8]  # fixed accuracy: its bands appended in row order
+    acc_bufs = {}
+    for spec in accuracy:
+        cap = int(L.whff_accuracy_max_size(order, order))
+        acc_bufs[spec] = np.empty(cap, dtype=np.uint8)  # untouched pages are never backed
+        if L.whff_accuracy_begin(acc_bufs[spec].ctypes.data, cap, order, order, float(spec[1])) != 0:
+            raise RuntimeError(L.whff_last_error().decode())
     for fmt, rate in specs:
         if fmt == 8:
             continue
@@ -246,8 +252,10 @@ def build_workload(order: int, specs, keep_fp64_device: bool, sample_rows: np.nd
     for r0, rows in km.bands(1024):
         if A64 is not None:
             A64[r0:r0 + rows.shape[0]].copy_(torch.from_numpy(rows))
-        if A_host is not None:
-            A_host[r0:r0 + rows.shape[0]] = rows
+        for spec, buf in acc_bufs.items():
+            if L.whff_compress_accuracy_band(buf.ctypes.data, buf.size, rows.ctypes.data, r0, rows.shape[0], order,
+                                             0) != 0:
+                raise RuntimeError(L.whff_last_error().decode())
         sel = (sample_rows >= r0) & (sample_rows < r0 + rows.shape[0])
         for k in np.nonzero(sel)[0]:
             sampled[k] = rows[sample_rows[k] - r0]
@@ -257,9 +265,12 @@ def build_workload(order: int, specs, keep_fp64_device: bool, sample_rows: np.nd
                 raise RuntimeError(L.whff_last_error().decode())
     for b in blobs.values():
         L.whff_blob_seal(b.ctypes.data, b.size)
-    for spec in accuracy:
-        blobs[spec] = W.whff_compress_accuracy(A_host, spec[1])
-    del A_host
+    for spec, buf in acc_bufs.items():
+        used = ctypes.c_size_t()
+        if L.whff_accuracy_seal(buf.ctypes.data, buf.size, ctypes.byref(used)) != 0:
+            raise RuntimeError(L.whff_last_error().decode())
+        blobs[spec] = buf[: used.value].copy()
+    del acc_bufs
     return km, blobs, A64, sampled
 
 

@@ -132,6 +132,22 @@ int whff_compress_band(void* blob, size_t cap, const double* band, int64_t row0,
                        int nthreads);
 int whff_blob_seal(void* blob, size_t cap);
 
+/* The band interface of the fixed-accuracy format (WHFF_FMT_FIXED_ACC), whose
+ * run offsets follow the bands in order: whff_accuracy_begin writes the header,
+ * the tolerance and an empty run index (cap >= 64 + 8 + 8 * ceil(M/4) *
+ * ceil(ceil(N/4)/32) bytes); whff_compress_accuracy_band appends rows [row0,
+ * row0+nrows) given as a band (row-major, lda >= N), row0 the next row not yet
+ * encoded and nrows a multiple of 4 except for the last band (WHFF_EINVAL
+ * otherwise, or when cap cannot hold the band's runs; whff_accuracy_max_size
+ * bounds the whole blob); whff_accuracy_seal checks that every row is in,
+ * writes the stream size and both CRCs and returns the blob length.  Until
+ * sealed the blob is refused by whff_create.  The result equals
+ * whff_compress_accuracy's byte for byte, whatever the band split. */
+int whff_accuracy_begin(void* blob, size_t cap, int64_t M, int64_t N, double tol);
+int whff_compress_accuracy_band(void* blob, size_t cap, const double* band, int64_t row0, int64_t nrows, int64_t lda,
+                                int nthreads);
+int whff_accuracy_seal(void* blob, size_t cap, size_t* len);
+
 /* --------------------------------------------------------------- device side */
 
 /* Make A resident: validate the blob (magic, version, sizes, CRCs), copy its

@@ -25,6 +25,7 @@ from .whff import (  # noqa: F401
     library,
     whff_compress,
     whff_compress_accuracy,
+    whff_compress_accuracy_bands,
     whff_compress_bands,
     whff_create,
     whff_decompress,

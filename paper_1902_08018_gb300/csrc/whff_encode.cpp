@@ -646,13 +646,6 @@ namespace {
 int64_t wz3_runs_per_band(int64_t N) { return ceil_div(ceil_div(N, 4), 32); }
 
 // The 16 FP32 values of block (I, J), edge rows and columns replicated.
-void gather_block(const double* A, int64_t M, int64_t N, int64_t lda, int64_t I, int64_t J, float* vals) {
-  for (int r = 0; r < 4; ++r) {
-    const int64_t gi = std::min(4 * I + r, M - 1);
-    for (int c = 0; c < 4; ++c) vals[4 * r + c] = (float)A[gi * lda + std::min(4 * J + c, N - 1)];
-  }
-}
-
 }  // namespace
 
 extern "C" size_t whff_accuracy_max_size(int64_t M, int64_t N) {
@@ -662,29 +655,80 @@ extern "C" size_t whff_accuracy_max_size(int64_t M, int64_t N) {
          (size_t)(BM * BN) * (size_t)wz3_block_bytes(kWz3Wmax);
 }
 
-extern "C" int whff_compress_accuracy(const double* A, int64_t M, int64_t N, int64_t lda, double tol, void* out,
-                                      size_t out_cap, size_t* out_len, int nthreads) {
-  if (!A || !out || M <= 0 || N <= 0 || lda < N || !(tol >= 0.0) || out_cap < whff_accuracy_max_size(M, N)) {
-    set_error("whff_compress_accuracy: null argument, empty shape, lda < N, tol < 0 or capacity below "
-              "whff_accuracy_max_size");
+namespace {
+// A fixed-accuracy blob under construction keeps two counters in the header's
+// reserved bytes (zero once sealed): the next row a band must start at, and
+// the bytes of block area written so far.
+constexpr int kAccNextRow = 48, kAccArea = 56;
+
+// Block (I, J) of a band holding matrix rows [row0, row0 + rows): rows past M
+// repeat row M-1, columns past N column N-1 (the matrix's edge rule).
+void gather_band_block(const double* band, int64_t row0, int64_t M, int64_t N, int64_t ld, int64_t I, int64_t J,
+                       float* vals) {
+  for (int r = 0; r < 4; ++r) {
+    const int64_t gi = std::min(4 * I + r, M - 1) - row0;
+    for (int c = 0; c < 4; ++c) vals[4 * r + c] = (float)band[gi * ld + std::min(4 * J + c, N - 1)];
+  }
+}
+}  // namespace
+
+extern "C" int whff_accuracy_begin(void* out, size_t out_cap, int64_t M, int64_t N, double tol) {
+  if (!out || M <= 0 || N <= 0 || !(tol >= 0.0)) {
+    set_error("whff_accuracy_begin: null output, empty shape or tol < 0");
     return WHFF_EINVAL;
   }
+  const int64_t BM = ceil_div(M, 4), RB = wz3_runs_per_band(N);
+  const size_t head = (size_t)kHeaderBytes + 8 + 8 * (size_t)(BM * RB);
+  if (out_cap < head) {
+    set_error("whff_accuracy_begin: capacity below header, tolerance and run index");
+    return WHFF_EINVAL;
+  }
+  uint8_t* blob = static_cast<uint8_t*>(out);
+  std::memset(blob, 0, head);
+  write_header(blob, WHFF_FMT_FIXED_ACC, 0, M, N, 0, 0);  // sizes and CRCs are final after the seal
+  uint64_t tol_bits;
+  std::memcpy(&tol_bits, &tol, 8);
+  st64(blob + kHeaderBytes, tol_bits);
+  st64(blob + kAccNextRow, 0);
+  st64(blob + kAccArea, 0);
+  return WHFF_OK;
+}
+
+extern "C" int whff_compress_accuracy_band(void* out, size_t out_cap, const double* band, int64_t row0, int64_t rows,
+                                           int64_t ld, int nthreads) {
+  uint8_t* blob = static_cast<uint8_t*>(out);
+  if (!out || !band || out_cap < (size_t)kHeaderBytes + 8) {
+    set_error("whff_compress_accuracy_band: null argument");
+    return WHFF_EINVAL;
+  }
+  const int64_t M = (int64_t)ld64(blob + 16), N = (int64_t)ld64(blob + 24);
+  const int64_t next = (int64_t)ld64(blob + kAccNextRow);
+  if ((int)ld32(blob + 8) != WHFF_FMT_FIXED_ACC || M <= 0 || N <= 0 || ld < N || row0 != next || rows <= 0 ||
+      row0 + rows > M || (rows % 4 != 0 && row0 + rows != M)) {
+    set_error("whff_compress_accuracy_band: not a blob begun by whff_accuracy_begin, ld < N, or the band does not "
+              "start at the next row / is not a multiple of 4 rows before the last");
+    return WHFF_EINVAL;
+  }
+  double tol;
+  const uint64_t tol_bits = ld64(blob + kHeaderBytes);
+  std::memcpy(&tol, &tol_bits, 8);
   const int64_t BM = ceil_div(M, 4), BN = ceil_div(N, 4), RB = wz3_runs_per_band(N);
-  // pass 1: the width of every run
-  std::vector<uint8_t> width((size_t)(BM * RB));
+  const int64_t I0 = row0 / 4, nI = ceil_div(rows, 4);
+  // pass 1: the width of every run of the band's block rows
+  std::vector<uint8_t> width((size_t)(nI * RB));
   std::atomic<int> err{WHFF_OK};
-  parallel_for(BM, nthreads, [&](int64_t I) {
+  parallel_for(nI, nthreads, [&](int64_t i) {
     float vals[16];
     Wz3Block b;
     for (int64_t r = 0; r < RB; ++r) {
       int W = 0;
       for (int64_t J = 32 * r; J < std::min(BN, 32 * r + 32); ++J) {
-        gather_block(A, M, N, lda, I, J, vals);
+        gather_band_block(band, row0, M, N, ld, I0 + i, J, vals);
         const int e = wz3_block(vals, tol, &b);
         if (e != WHFF_OK) err.store(e);
         W = std::max(W, b.need);
       }
-      width[(size_t)(I * RB + r)] = (uint8_t)W;
+      width[(size_t)(i * RB + r)] = (uint8_t)W;
     }
   });
   if (err.load() != WHFF_OK) {
@@ -692,34 +736,35 @@ extern "C" int whff_compress_accuracy(const double* A, int64_t M, int64_t N, int
                                         : "whff_compress_accuracy: non-finite value");
     return err.load();
   }
-  // offsets of the runs in band-major order
-  std::vector<uint64_t> off((size_t)(BM * RB));
-  uint64_t area = 0;
-  for (int64_t I = 0; I < BM; ++I)
+  // offsets of the runs, after the area written so far
+  std::vector<uint64_t> off((size_t)(nI * RB));
+  uint64_t area = ld64(blob + kAccArea);
+  for (int64_t i = 0; i < nI; ++i)
     for (int64_t r = 0; r < RB; ++r) {
-      off[(size_t)(I * RB + r)] = area;
-      area += (uint64_t)(std::min(BN, 32 * r + 32) - 32 * r) * (uint64_t)wz3_block_bytes(width[(size_t)(I * RB + r)]);
+      off[(size_t)(i * RB + r)] = area;
+      area += (uint64_t)(std::min(BN, 32 * r + 32) - 32 * r) * (uint64_t)wz3_block_bytes(width[(size_t)(i * RB + r)]);
     }
-  uint8_t* blob = static_cast<uint8_t*>(out);
   uint8_t* stream = blob + kHeaderBytes;
   uint8_t* index = stream + 8;
   uint8_t* blocks = index + 8 * (size_t)(BM * RB);
-  uint64_t tol_bits;
-  std::memcpy(&tol_bits, &tol, 8);
-  st64(stream, tol_bits);
-  for (int64_t k = 0; k < BM * RB; ++k) st64(index + 8 * k, off[(size_t)k] | ((uint64_t)width[(size_t)k] << 56));
+  if ((size_t)(blocks - blob) + area > out_cap) {
+    set_error("whff_compress_accuracy_band: capacity exceeded (whff_accuracy_max_size bounds the whole blob)");
+    return WHFF_EINVAL;
+  }
+  for (int64_t k = 0; k < nI * RB; ++k)
+    st64(index + 8 * ((I0 * RB) + k), off[(size_t)k] | ((uint64_t)width[(size_t)k] << 56));
   // pass 2: every block at its run's width
-  parallel_for(BM, nthreads, [&](int64_t I) {
+  parallel_for(nI, nthreads, [&](int64_t i) {
     float vals[16];
     Wz3Block b;
     uint64_t w[8];
     for (int64_t r = 0; r < RB; ++r) {
-      const int W = width[(size_t)(I * RB + r)];
+      const int W = width[(size_t)(i * RB + r)];
       const int nw = wz3_block_bytes(W) / 8;
       const int64_t nb = std::min(BN, 32 * r + 32) - 32 * r;
-      uint8_t* dst = blocks + off[(size_t)(I * RB + r)];
+      uint8_t* dst = blocks + off[(size_t)(i * RB + r)];
       for (int64_t J = 32 * r; J < 32 * r + nb; ++J) {
-        gather_block(A, M, N, lda, I, J, vals);
+        gather_band_block(band, row0, M, N, ld, I0 + i, J, vals);
         wz3_block(vals, tol, &b);
         wz3_put(b, W, w);
         // word-interleaved run: word k of block j at byte 8 (k nb + j)
@@ -727,10 +772,40 @@ extern "C" int whff_compress_accuracy(const double* A, int64_t M, int64_t N, int
       }
     }
   });
-  const uint64_t sbytes = 8 + 8 * (uint64_t)(BM * RB) + area;
-  write_header(blob, WHFF_FMT_FIXED_ACC, 0, M, N, sbytes, crc32(stream, sbytes));
+  st64(blob + kAccNextRow, (uint64_t)(row0 + rows));
+  st64(blob + kAccArea, area);
+  return WHFF_OK;
+}
+
+extern "C" int whff_accuracy_seal(void* out, size_t out_cap, size_t* out_len) {
+  uint8_t* blob = static_cast<uint8_t*>(out);
+  if (!out || out_cap < (size_t)kHeaderBytes + 8 || (int)ld32(blob + 8) != WHFF_FMT_FIXED_ACC) {
+    set_error("whff_accuracy_seal: not a blob begun by whff_accuracy_begin");
+    return WHFF_EINVAL;
+  }
+  const int64_t M = (int64_t)ld64(blob + 16), N = (int64_t)ld64(blob + 24);
+  if (M <= 0 || N <= 0 || (int64_t)ld64(blob + kAccNextRow) != M) {
+    set_error("whff_accuracy_seal: rows still missing (the bands must cover rows 0..M-1 in order)");
+    return WHFF_EINVAL;
+  }
+  const int64_t BM = ceil_div(M, 4), RB = wz3_runs_per_band(N);
+  const uint64_t sbytes = 8 + 8 * (uint64_t)(BM * RB) + ld64(blob + kAccArea);
+  write_header(blob, WHFF_FMT_FIXED_ACC, 0, M, N, sbytes, crc32(blob + kHeaderBytes, sbytes));  // clears 48..63
   if (out_len) *out_len = (size_t)(kHeaderBytes + sbytes);
   return WHFF_OK;
+}
+
+extern "C" int whff_compress_accuracy(const double* A, int64_t M, int64_t N, int64_t lda, double tol, void* out,
+                                      size_t out_cap, size_t* out_len, int nthreads) {
+  if (!A || !out || M <= 0 || N <= 0 || lda < N || !(tol >= 0.0) || out_cap < whff_accuracy_max_size(M, N)) {
+    set_error("whff_compress_accuracy: null argument, empty shape, lda < N, tol < 0 or capacity below "
+              "whff_accuracy_max_size");
+    return WHFF_EINVAL;
+  }
+  int e = whff_accuracy_begin(out, out_cap, M, N, tol);
+  if (!e) e = whff_compress_accuracy_band(out, out_cap, A, 0, M, lda, nthreads);
+  if (!e) e = whff_accuracy_seal(out, out_cap, out_len);
+  return e;
 }
 
 extern "C" int whff_compress(const double* A, int64_t M, int64_t N, int64_t lda, int fmt, int rate, void* out,

@@ -59,6 +59,9 @@ def library() -> ctypes.CDLL:
         "whff_compress": (c_int, [P, i64, i64, i64, c_int, c_int, P, sz, ctypes.POINTER(sz), c_int]),
         "whff_accuracy_max_size": (sz, [i64, i64]),
         "whff_compress_accuracy": (c_int, [P, i64, i64, i64, dbl, P, sz, ctypes.POINTER(sz), c_int]),
+        "whff_accuracy_begin": (c_int, [P, sz, i64, i64, dbl]),
+        "whff_compress_accuracy_band": (c_int, [P, sz, P, i64, i64, i64, c_int]),
+        "whff_accuracy_seal": (c_int, [P, sz, ctypes.POINTER(sz)]),
         "whff_blob_init": (c_int, [P, sz, c_int, c_int, i64, i64]),
         "whff_compress_band": (c_int, [P, sz, P, i64, i64, i64, c_int]),
         "whff_blob_seal": (c_int, [P, sz]),
@@ -161,6 +164,23 @@ def whff_compress_accuracy(A: np.ndarray, tol: float, nthreads: int = 0) -> np.n
     used = ctypes.c_size_t()
     _check(library().whff_compress_accuracy(A.ctypes.data, M, N, N, float(tol), out.ctypes.data, cap,
                                             ctypes.byref(used), nthreads))
+    return out[: used.value].copy()
+
+
+def whff_compress_accuracy_bands(M: int, N: int, bands, tol: float, nthreads: int = 0) -> np.ndarray:
+    """Fixed-accuracy encode of a matrix given as an iterable of (row0, FP64 band), bands in row order."""
+    L = library()
+    cap = int(L.whff_accuracy_max_size(M, N))
+    if cap == 0:
+        raise WhffError(-1, "empty shape")
+    out = np.empty(cap, dtype=np.uint8)
+    _check(L.whff_accuracy_begin(out.ctypes.data, cap, M, N, float(tol)))
+    for row0, band in bands:
+        band = np.ascontiguousarray(band, dtype=np.float64)
+        _check(L.whff_compress_accuracy_band(out.ctypes.data, cap, band.ctypes.data, row0, band.shape[0],
+                                             band.shape[1], nthreads))
+    used = ctypes.c_size_t()
+    _check(L.whff_accuracy_seal(out.ctypes.data, cap, ctypes.byref(used)))
     return out[: used.value].copy()
 
 

@@ -129,3 +129,52 @@ def test_fixed_accuracy_rejections(W):
         W.whff_compress_accuracy(np.ones((4, 4)), -1.0)
     with pytest.raises(W.WhffError):
         W.whff_compress_accuracy(np.full((4, 4), np.nan), 1e-3)
+
+
+@pytest.mark.parametrize("split", [[4], [8, 120], [12, 4, 4, 100, 8], [256]])
+def test_fixed_accuracy_bands_equal_whole_matrix(W, split):
+    """The band interface of the fixed-accuracy format gives the whole-matrix blob byte
+    for byte, for every band split (the last band ragged), and every thread count."""
+    import workloads
+
+    M, N = 259, 1030
+    A = workloads.RectKernelMatrix(M, N, 0.05, 17).dense()
+    want = W.whff_compress_accuracy(A, 1e-5).tobytes()
+    bounds, r = [], 0
+    for k in split:
+        if r >= M:
+            break
+        bounds.append((r, min(M, r + k)))
+        r += k
+    if r < M:
+        bounds.append((r, M))
+    for nt in (1, 0):
+        got = W.whff_compress_accuracy_bands(M, N, ((a, A[a:b]) for a, b in bounds), 1e-5, nthreads=nt)
+        assert got.tobytes() == want, (split, nt)
+
+
+def test_fixed_accuracy_bands_refusals(W):
+    import ctypes
+
+    L = W.library()
+    M, N = 16, 40
+    A = np.ones((M, N))
+    cap = int(L.whff_accuracy_max_size(M, N))
+    out = np.zeros(cap, dtype=np.uint8)
+    assert L.whff_accuracy_begin(out.ctypes.data, cap, M, N, 1e-3) == 0
+    band = np.ascontiguousarray(A[4:8])
+    assert L.whff_compress_accuracy_band(out.ctypes.data, cap, band.ctypes.data, 4, 4, N, 1) != 0  # not the next row
+    band = np.ascontiguousarray(A[0:6])
+    assert L.whff_compress_accuracy_band(out.ctypes.data, cap, band.ctypes.data, 0, 6, N, 1) != 0  # 6 rows mid-matrix
+    band = np.ascontiguousarray(A[0:8])
+    assert L.whff_compress_accuracy_band(out.ctypes.data, cap, band.ctypes.data, 0, 8, N, 1) == 0
+    used = ctypes.c_size_t()
+    assert L.whff_accuracy_seal(out.ctypes.data, cap, ctypes.byref(used)) != 0  # rows 8..15 missing
+    with pytest.raises(W.WhffError):
+        W.whff_create(out, stream=0)  # unsealed: refused before any device work
+    band = np.ascontiguousarray(A[8:16])
+    assert L.whff_compress_accuracy_band(out.ctypes.data, cap, band.ctypes.data, 8, 8, N, 1) == 0
+    assert L.whff_accuracy_seal(out.ctypes.data, cap, ctypes.byref(used)) == 0
+    assert out[: used.value].tobytes() == W.whff_compress_accuracy(A, 1e-3).tobytes()
+    small = np.zeros(70, dtype=np.uint8)
+    assert L.whff_accuracy_begin(small.ctypes.data, small.size, M, N, 1e-3) != 0  # no room for the index
