@@ -41,7 +41,7 @@ int scaled_launch(const ScaledStep& a, cudaStream_t st) {
   if (e) return e;
   if (a.maxseg > 1) {  // shared bands: the chunks of a band are the "blocks" of the segment epilogue
     const int V = scaled_vec(a.fmt);
-    dev::wz2_segment_epilogue<<<(unsigned)((8 * a.M + 255) / 256), 256, 0, st>>>(a.ws, a.M, a.ld / V, a.L, a.maxseg,
+    dev::wz2_segment_epilogue<<<(unsigned)((dev::segment_epilogue_threads(a.M, a.ld / V, a.L) + 255) / 256), 256, 0, st>>>(a.ws, a.M, a.ld / V, a.L, a.maxseg,
                                                                             a.R, a.y, a.ldy, a.state, a.decay);
   }
   return 0;

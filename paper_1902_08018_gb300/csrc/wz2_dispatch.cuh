@@ -55,7 +55,7 @@ static int wz2_launch_lift(const Wz2Step& a, cudaStream_t st) {
     default: return -1;
   }
   if (a.maxseg > 1)
-    dev::wz2_segment_epilogue<<<(unsigned)((8 * a.M + 255) / 256), 256, 0, st>>>(a.ws, a.M, a.BN, a.L, a.maxseg, a.R,
+    dev::wz2_segment_epilogue<<<(unsigned)((dev::segment_epilogue_threads(a.M, a.BN, a.L) + 255) / 256), 256, 0, st>>>(a.ws, a.M, a.BN, a.L, a.maxseg, a.R,
                                                                             a.y, a.ldy, a.state, a.decay);
   return 0;
 }

@@ -585,35 +585,46 @@ __device__ __forceinline__ double seq_sum_strided(const double* __restrict__ p, 
 }
 
 // Sum the segments of bands shared by several warp ranges, then the state
-// update (bands inside one range were finished by the kernel).  Eight lanes per
-// row: lane j adds segments j, j + 8, ... in order, then a fixed xor tree over
-// the eight (the same order every time, so the result is deterministic; with
-// one or two segments it is the plain sum).  A slit of a long matrix has dozens
-// of segments per band: eight lanes keep their loads in flight together.
+// update (bands inside one range were finished by the kernel).  The shared
+// bands are exactly those with a range boundary b = g L strictly inside them
+// (b not a multiple of BN); each is taken by the warp of its first such
+// boundary, so the launch has a warp per boundary (segment_epilogue_threads),
+// not a thread per row.  In that warp, 8 lanes per row of the band: lane j
+// adds segments j, j + 8, ... in order, then a fixed xor tree over the eight
+// (the same order every time, so the result is deterministic; with one or two
+// segments it is the plain sum).  A slit of a long matrix has dozens of
+// segments per band: eight lanes keep their loads in flight together.
+__host__ __device__ inline int64_t segment_epilogue_threads(int64_t M, int64_t BN, int64_t L) {
+  const int64_t total = ((M + 3) / 4) * BN, ranges = (total + L - 1) / L;
+  return ranges > 1 ? 32 * (ranges - 1) : 0;
+}
+
 static __global__ void wz2_segment_epilogue(const double* __restrict__ ws, int64_t M, int64_t BN, int64_t L,
                                             int maxseg, int R, double* __restrict__ y, int64_t ldy,
                                             double* __restrict__ state, double decay) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t row = q >> 3;
-  const int j = (int)(q & 7);
-  const bool valid = row < M;
-  const int64_t I = valid ? row / 4 : 0;
-  const int i = (int)(row % 4);
+  const int64_t g = 1 + (q >> 5);  // the boundary of this warp (warp-uniform)
+  const int i = (int)((q & 31) >> 3), j = (int)(q & 7);
+  const int64_t b = g * L, total = ((M + 3) / 4) * BN;
+  const int64_t I = b / BN;
+  // a boundary inside band I, and the first one there (the previous one is not inside I)
+  const bool mine = b < total && b % BN != 0 && (g - 1) * L <= I * BN;
+  const int64_t row = 4 * I + i;
+  const bool valid = mine && row < M;
   const int64_t g_lo = (I * BN) / L, g_hi = ((I + 1) * BN - 1) / L;
-  const bool shared = valid && g_lo != g_hi;
-  double s = (shared && state) ? state[row] : 0.0;
+  double s = (valid && state) ? state[row] : 0.0;
   for (int r = 0; r < R; ++r) {
     double t = 0.0;
-    if (shared)
+    if (valid)
       for (int64_t seg = j; seg <= g_hi - g_lo; seg += 8) t += ws[((I * maxseg + seg) * R + r) * 4 + i];
 #pragma unroll
     for (int o = 4; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (shared && j == 0) {
+    if (valid && j == 0) {
       y[(int64_t)r * ldy + row] = t;
       s = decay * s + t;
     }
   }
-  if (shared && j == 0 && state) state[row] = s;
+  if (valid && j == 0 && state) state[row] = s;
 }
 
 // ------------------------------------------------------------- batched launch

@@ -18,7 +18,7 @@ int wz3_launch(const Wz3Step& a, cudaStream_t st) {
     dev::wz3_gemv_kernel<8><<<grid, threads, 0, st>>>(index, a.area, a.M, a.BM, (int)a.BN, (int)a.RB, a.xt, ldt, a.L,
                                                       a.maxseg, a.ws, a.y, a.ldy, a.state, a.decay);
   if (a.maxseg > 1)  // units per band: runs
-    dev::wz2_segment_epilogue<<<(unsigned)((8 * a.M + 255) / 256), 256, 0, st>>>(a.ws, a.M, a.RB, a.L, a.maxseg, a.R,
+    dev::wz2_segment_epilogue<<<(unsigned)((dev::segment_epilogue_threads(a.M, a.RB, a.L) + 255) / 256), 256, 0, st>>>(a.ws, a.M, a.RB, a.L, a.maxseg, a.R,
                                                                             a.y, a.ldy, a.state, a.decay);
   return 0;
 }
