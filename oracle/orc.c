@@ -375,7 +375,7 @@ void orc_wz2_decode_block(const uint64_t* words, int rate, int lift, double out[
   }
 }
 
-/* ------------------------------------------- WZ3 (fixed accuracy, planned) */
+/* ---------------------------------------------------- WZ3 (fixed accuracy) */
 #define WZ3_WMAX 31 /* widest field: 13 + 16*31 bits fill one 64-byte block */
 /* The decoded block of WZ2's layout for coefficients v (sequency order with
  * the lift), shift K and exponent emax: the same formulas as
@@ -837,7 +837,7 @@ void orc_state_update(double* s, int64_t M, const double* Y, int R, int64_t ldy,
     for (int64_t i = 0; i < M; i++) s[i] = decay * s[i] + Y[(size_t)r * ldy + i];
 }
 
-/* ------------------------------------------- WZ3 matrix layout (planned) */
+/* ---------------------------------------------------- WZ3 matrix layout */
 /* Stream: [tol: f64] [index: one u64 per run, band-major; bits 0..55 the
  * byte offset of the run within the block area, bits 56..63 its width W]
  * [block area: the runs one after another].  A run is up to 32 consecutive

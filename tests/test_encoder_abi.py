@@ -124,6 +124,19 @@ def test_fixed_accuracy_encoder_byte_identical_to_oracle(W, orc, M, N, tol):
         assert got.tobytes() == want, nt
 
 
+def test_fixed_accuracy_encoder_hand_derived_matrix(W):
+    """The library's WZ3 blob of the hand-derived matrix in tests/golden/wz3_blocks.txt
+    (one lifted step block at K 25 and a constant at K 27 sharing a run of width 4,
+    word-interleaved), whole and band by band."""
+    from test_oracle_wz3 import _golden_wz3, golden_wz3_matrix
+
+    for rec in _golden_wz3()["matrix"]:
+        A, want = golden_wz3_matrix(rec)
+        assert W.whff_compress_accuracy(A, float(rec[1])).tobytes() == want
+        got = W.whff_compress_accuracy_bands(A.shape[0], A.shape[1], [(0, A)], float(rec[1]))
+        assert got.tobytes() == want
+
+
 def test_fixed_accuracy_rejections(W):
     with pytest.raises(W.WhffError):
         W.whff_compress_accuracy(np.ones((4, 4)), -1.0)

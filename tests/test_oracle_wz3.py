@@ -1,9 +1,10 @@
-"""Pins of the oracle's fixed-accuracy reading (WZ3, the planned device format
-for zfp's fixed-accuracy mode): every decoded block within the tolerance of
-its FP32 input, the shift the largest that achieves it, the field width the
+"""Pins of the oracle's fixed-accuracy reading (WZ3, the device format for
+zfp's fixed-accuracy mode, Sec. 4.3): every decoded block within the tolerance
+of its FP32 input, the shift the largest that achieves it, the field width the
 smallest that holds it (the run's width the largest of its blocks), the bit
-layout exactly WZ2's with the width chosen per run, and at WZ2's own error a
-WZ3 block never costs more bits than WZ2's fixed rate."""
+layout exactly WZ2's with the width chosen per run, at WZ2's own error a WZ3
+block never costs more bits than WZ2's fixed rate, and hand-derived blocks, a
+run and a whole matrix (tests/golden/wz3_blocks.txt) reproduced bit for bit."""
 import numpy as np
 import pytest
 
@@ -229,3 +230,81 @@ def test_full_scale_checkerboard_stays_within_31_bit_fields(orc, lift):
     assert len(blob) <= orc.lib().orc_wz3_max_blob_size(8, 8)
     D, _ = orc.wz3_decode(blob)
     assert np.array_equal(D[:4, :4], d)
+
+
+# ------------------------------------------------ hand-derived fixtures
+def _golden_wz3():
+    """Records of tests/golden/wz3_blocks.txt: {kind: [fields, ...]}."""
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "wz3_blocks.txt")
+    out = {"block": [], "run": [], "matrix": []}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = [x.strip() for x in line.split("|")]
+        out[f[0]].append(f[1:])
+    return out
+
+
+def _floats(s):
+    return [float(v) for v in s.split()]
+
+
+def _hex_words(s):
+    return [int(v, 16) for v in s.split()]
+
+
+def _golden_block_input(rec):
+    """The 4x4 FP32 block of a block record (every row the same)."""
+    return np.tile(np.array(_floats(rec[3]), dtype=np.float32), (4, 1))
+
+
+@pytest.mark.parametrize("rec", _golden_wz3()["block"], ids=lambda r: r[0])
+def test_wz3_hand_derived_blocks(orc, rec):
+    name, lift, tol, _, K, W, words, dec = rec
+    lift, tol = bool(int(lift)), float(tol)
+    a = _golden_block_input(rec)
+    emax, k, _, need = orc.wz3_block(a, tol, lift)
+    assert (emax, k, need) == (1, int(K), int(W)), name
+    got, w = orc.wz3_encode_run(a.reshape(1, 4, 4), tol, lift)
+    assert w == int(W)
+    assert [int(x) for x in got] == _hex_words(words), name
+    want = np.tile(np.array(_floats(dec)), (4, 1))
+    assert (orc.wz3_decode_block(got, w, lift) == want).all(), name
+
+
+@pytest.mark.parametrize("rec", _golden_wz3()["run"], ids=lambda r: r[0])
+def test_wz3_hand_derived_run(orc, rec):
+    name, lift, tol, names, W, words = rec
+    blocks = {r[0]: _golden_block_input(r) for r in _golden_wz3()["block"]}
+    a = np.stack([blocks[n] for n in names.split()])
+    got, w = orc.wz3_encode_run(a, float(tol), bool(int(lift)))
+    assert w == int(W)
+    assert [int(x) for x in got] == _hex_words(words), name
+
+
+def golden_wz3_matrix(rec):
+    """(A, expected blob) of a matrix record; the header follows the blob layout
+    (magic, version 1, format 8, rate 0, M, N, stream bytes, CRC-32 of the stream
+    and of the header's first 44 bytes, the rest zero), CRCs from zlib."""
+    import struct
+    import zlib
+
+    name, tol, M, N, row, words = rec
+    M, N = int(M), int(N)
+    A = np.tile(np.array(_floats(row)), (M, 1))
+    stream = b"".join(struct.pack("<Q", w) for w in _hex_words(words))
+    assert struct.unpack("<d", stream[:8])[0] == float(tol)
+    head = b"WZ1\0" + struct.pack("<IIIqqQI", 1, 8, 0, M, N, len(stream), zlib.crc32(stream))
+    head += struct.pack("<I", zlib.crc32(head)) + bytes(16)
+    return A, head + stream
+
+
+@pytest.mark.parametrize("rec", _golden_wz3()["matrix"], ids=lambda r: r[0])
+def test_wz3_hand_derived_matrix(orc, rec):
+    A, want = golden_wz3_matrix(rec)
+    blob = orc.wz3_encode(A, float(rec[1]))
+    assert blob == want
+    dec, tol = orc.wz3_decode(blob)
+    assert tol == float(rec[1]) and (dec == A).all()
