@@ -97,6 +97,10 @@ typedef struct whff_handle whff_handle;
 
 /* ------------------------------------------------------------------ host side */
 
+/* Shapes: every call takes 1 <= M, N <= 2^48 with at most 2^56 4x4 blocks
+ * (ceil(M/4) * ceil(N/4)), so that every derived byte count fits in 63 bits;
+ * a larger shape is WHFF_EINVAL on input and WHFF_EFORMAT in a blob header. */
+
 /* Bytes of the blob (64-byte header + stream) for a format, rate and shape;
  * 0 if the combination is invalid.  WZ1 (fmt 1): 64 + ceil(M/4)*ceil(N/4)*2*rate.
  * Scaled formats: 64 + M*roundup(N,16)*elem_bytes + ceil(M/128)*ceil(N/128)*4

@@ -41,6 +41,16 @@ bool is_blocked(int fmt);        // fixed-size 4x4-block formats (WZ1, WZ2)
 inline bool is_wz3(int fmt) { return fmt == 8; }  // fixed accuracy: 4x4 blocks of variable size, indexed runs
 // row alignment of a row view: a 4-row band (block formats) or a 128-row scale tile
 inline int row_align(int fmt) { return (is_blocked(fmt) || is_wz3(fmt)) ? 4 : kScaleTile; }
+// Shapes the container takes: 1..2^48 rows and columns and at most 2^56 4x4
+// blocks, so that every byte count derived from a shape (a stream, an index,
+// a workspace) fits in 63 bits.  A header outside these bounds is refused
+// before any size is computed from it.
+constexpr int64_t kMaxDim = int64_t(1) << 48;
+constexpr uint64_t kMaxBlocks = uint64_t(1) << 56;
+inline bool shape_ok(int64_t M, int64_t N) {
+  if (M <= 0 || N <= 0 || M > kMaxDim || N > kMaxDim) return false;
+  return (uint64_t)ceil_div(M, 4) <= kMaxBlocks / (uint64_t)ceil_div(N, 4);
+}
 uint64_t stream_size(int fmt, int rate, int64_t M, int64_t N);  // 0 if invalid
 uint32_t crc32_update(uint32_t crc, const uint8_t* p, size_t n);  // crc = 0 to start
 inline uint32_t crc32(const uint8_t* p, size_t n) { return crc32_update(0, p, n); }

@@ -41,7 +41,7 @@ bool wz2_rate_valid(int rate) { return rate >= 8 && rate <= 24 && (rate & 3) == 
 bool is_blocked(int fmt) { return fmt == WHFF_FMT_ZFP || fmt == WHFF_FMT_FIXED_LIFT || fmt == WHFF_FMT_FIXED_BFP; }
 
 uint64_t stream_size(int fmt, int rate, int64_t M, int64_t N) {
-  if (M <= 0 || N <= 0) return 0;
+  if (!shape_ok(M, N)) return 0;
   if (is_blocked(fmt)) {
     if (fmt == WHFF_FMT_ZFP ? !rate_valid(rate) : !wz2_rate_valid(rate)) return 0;
     return (uint64_t)ceil_div(M, 4) * (uint64_t)ceil_div(N, 4) * (uint64_t)(2 * rate);
@@ -127,8 +127,9 @@ int read_header(const uint8_t* blob, size_t len, BlobInfo* info, bool check_stre
   b.stream_bytes = ld64(blob + 32);
   b.crc_stream = ld32(blob + 40);
   b.crc_header = ld32(blob + 44);
+  if (!shape_ok(b.M, b.N)) return WHFF_EFORMAT;
   uint64_t want = stream_size(b.fmt, b.rate, b.M, b.N);
-  if (b.fmt == WHFF_FMT_FIXED_ACC && b.rate == 0 && b.M > 0 && b.N > 0) {  // variable length, within its bounds
+  if (b.fmt == WHFF_FMT_FIXED_ACC && b.rate == 0) {  // variable length, within its bounds
     const int64_t BM = ceil_div(b.M, 4), BN = ceil_div(b.N, 4), RB = ceil_div(BN, 32);
     const uint64_t lo = 8 + 8 * (uint64_t)(BM * RB) + 8 * (uint64_t)(BM * BN);
     const uint64_t hi = 8 + 8 * (uint64_t)(BM * RB) + 64 * (uint64_t)(BM * BN);
@@ -649,7 +650,7 @@ int64_t wz3_runs_per_band(int64_t N) { return ceil_div(ceil_div(N, 4), 32); }
 }  // namespace
 
 extern "C" size_t whff_accuracy_max_size(int64_t M, int64_t N) {
-  if (M <= 0 || N <= 0) return 0;
+  if (!shape_ok(M, N)) return 0;
   const int64_t BM = ceil_div(M, 4), BN = ceil_div(N, 4);
   return (size_t)kHeaderBytes + 8 + 8 * (size_t)(BM * wz3_runs_per_band(N)) +
          (size_t)(BM * BN) * (size_t)wz3_block_bytes(kWz3Wmax);
@@ -673,8 +674,8 @@ void gather_band_block(const double* band, int64_t row0, int64_t M, int64_t N, i
 }  // namespace
 
 extern "C" int whff_accuracy_begin(void* out, size_t out_cap, int64_t M, int64_t N, double tol) {
-  if (!out || M <= 0 || N <= 0 || !(tol >= 0.0)) {
-    set_error("whff_accuracy_begin: null output, empty shape or tol < 0");
+  if (!out || !shape_ok(M, N) || !(tol >= 0.0)) {
+    set_error("whff_accuracy_begin: null output, empty or oversized shape, or tol < 0");
     return WHFF_EINVAL;
   }
   const int64_t BM = ceil_div(M, 4), RB = wz3_runs_per_band(N);
@@ -703,7 +704,7 @@ extern "C" int whff_compress_accuracy_band(void* out, size_t out_cap, const doub
   }
   const int64_t M = (int64_t)ld64(blob + 16), N = (int64_t)ld64(blob + 24);
   const int64_t next = (int64_t)ld64(blob + kAccNextRow);
-  if ((int)ld32(blob + 8) != WHFF_FMT_FIXED_ACC || M <= 0 || N <= 0 || ld < N || row0 != next || rows <= 0 ||
+  if ((int)ld32(blob + 8) != WHFF_FMT_FIXED_ACC || !shape_ok(M, N) || ld < N || row0 != next || rows <= 0 ||
       row0 + rows > M || (rows % 4 != 0 && row0 + rows != M)) {
     set_error("whff_compress_accuracy_band: not a blob begun by whff_accuracy_begin, ld < N, or the band does not "
               "start at the next row / is not a multiple of 4 rows before the last");
@@ -784,7 +785,7 @@ extern "C" int whff_accuracy_seal(void* out, size_t out_cap, size_t* out_len) {
     return WHFF_EINVAL;
   }
   const int64_t M = (int64_t)ld64(blob + 16), N = (int64_t)ld64(blob + 24);
-  if (M <= 0 || N <= 0 || (int64_t)ld64(blob + kAccNextRow) != M) {
+  if (!shape_ok(M, N) || (int64_t)ld64(blob + kAccNextRow) != M) {
     set_error("whff_accuracy_seal: rows still missing (the bands must cover rows 0..M-1 in order)");
     return WHFF_EINVAL;
   }
@@ -797,9 +798,9 @@ extern "C" int whff_accuracy_seal(void* out, size_t out_cap, size_t* out_len) {
 
 extern "C" int whff_compress_accuracy(const double* A, int64_t M, int64_t N, int64_t lda, double tol, void* out,
                                       size_t out_cap, size_t* out_len, int nthreads) {
-  if (!A || !out || M <= 0 || N <= 0 || lda < N || !(tol >= 0.0) || out_cap < whff_accuracy_max_size(M, N)) {
-    set_error("whff_compress_accuracy: null argument, empty shape, lda < N, tol < 0 or capacity below "
-              "whff_accuracy_max_size");
+  if (!A || !out || !shape_ok(M, N) || lda < N || !(tol >= 0.0) || out_cap < whff_accuracy_max_size(M, N)) {
+    set_error("whff_compress_accuracy: null argument, empty or oversized shape, lda < N, tol < 0 or capacity "
+              "below whff_accuracy_max_size");
     return WHFF_EINVAL;
   }
   int e = whff_accuracy_begin(out, out_cap, M, N, tol);

@@ -92,8 +92,8 @@ int launch_rhs(int R, const uint8_t* s, int64_t M, int64_t N, int64_t BM, int64_
 extern "C" int whff_step_noalloc(const void* stream_dev, int rate, int64_t M, int64_t N, const float* x, int R,
                                  int64_t ldx, double* y, int64_t ldy, double* state, double decay, void* stream) {
   using whff::set_error;
-  if (!stream_dev || !x || !y || M <= 0 || N <= 0 || ldx < N || ldy < M) {
-    set_error("whff_step_noalloc: null pointer, empty shape or leading dimension too small");
+  if (!stream_dev || !x || !y || !whff::shape_ok(M, N) || ldx < N || ldy < M) {
+    set_error("whff_step_noalloc: null pointer, empty or oversized shape, or leading dimension too small");
     return WHFF_EINVAL;
   }
   if (rate != 8 && rate != 12 && rate != 16) {

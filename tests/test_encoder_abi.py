@@ -109,6 +109,45 @@ def test_create_rejects_corrupt_blob_without_gpu(W):
     assert e.value.code == -5
 
 
+def _reheader(blob, M, N):
+    """The blob with its header's M and N replaced and the header CRC made valid again."""
+    import struct
+    import zlib
+
+    b = bytearray(np.asarray(blob, dtype=np.uint8).tobytes())
+    b[16:32] = struct.pack("<qq", M, N)
+    b[44:48] = struct.pack("<I", zlib.crc32(bytes(b[:44])))
+    return np.frombuffer(bytes(b), dtype=np.uint8).copy()
+
+
+@pytest.mark.parametrize("M,N", [((1 << 61) + 4, 4), (4, (1 << 61) + 4), ((1 << 48) + 1, 4), (1 << 40, 1 << 40)])
+def test_create_rejects_oversized_shapes_without_gpu(W, M, N):
+    """A header whose shape would wrap the 64-bit size arithmetic is refused before any
+    CUDA call: with M = 2^61 + 4 and N = 4, ceil(M/4) * 32 bytes = 2^64 + 32 wraps to
+    the 32 bytes a 4 x 4 rate-16 stream holds, and the kernels would walk 2^59 blocks."""
+    blob = W.whff_compress(np.ones((4, 4)), W.FMT_FIXED_LIFT, 16)
+    with pytest.raises(W.WhffError) as e:
+        W.whff_create(_reheader(blob, M, N), stream=0)
+    assert e.value.code == -5
+    acc = W.whff_compress_accuracy(np.ones((4, 4)), 0.0)
+    with pytest.raises(W.WhffError) as e:
+        W.whff_create(_reheader(acc, M, N), stream=0)
+    assert e.value.code == -5
+    assert W.compressed_size(W.FMT_FIXED_LIFT, 16, M, N) == 0
+    assert W.compressed_size(W.FMT_BF16, 0, M, N) == 0
+    assert W.library().whff_accuracy_max_size(M, N) == 0
+
+
+def test_largest_accepted_shape_sizes():
+    """The bound keeps the largest accepted shapes' sizes exact (no wrap)."""
+    import paper_1902_08018_gb300 as W
+
+    M, N = 1 << 48, 1 << 14  # 2^46 x 2^12 = 2^58 blocks: over the 2^56 bound
+    assert W.compressed_size(W.FMT_FIXED_LIFT, 16, M, N) == 0
+    M, N = 1 << 48, 1 << 12  # 2^46 x 2^10 = 2^56 blocks: accepted
+    assert W.compressed_size(W.FMT_FIXED_LIFT, 16, M, N) == 64 + (1 << 56) * 32
+
+
 @pytest.mark.parametrize("M,N", [(130, 97), (64, 260), (5, 3), (257, 1030)])
 @pytest.mark.parametrize("tol", [1e-2, 1e-6, 0.0])
 def test_fixed_accuracy_encoder_byte_identical_to_oracle(W, orc, M, N, tol):
