@@ -618,7 +618,7 @@ extern "C" int whff_compress_band(void* blob, size_t cap, const double* band, in
     return WHFF_EFORMAT;
   }
   const int align = is_blocked(b.fmt) ? 4 : kScaleTile;
-  if (!band || row0 < 0 || nrows <= 0 || row0 + nrows > b.M || lda < b.N || row0 % align ||
+  if (!band || row0 < 0 || nrows <= 0 || nrows > b.M - row0 || lda < b.N || row0 % align ||
       (nrows % align && row0 + nrows != b.M)) {
     set_error("whff_compress_band: band must start on a block/tile row and cover whole blocks");
     return WHFF_EINVAL;
@@ -705,7 +705,7 @@ extern "C" int whff_compress_accuracy_band(void* out, size_t out_cap, const doub
   const int64_t M = (int64_t)ld64(blob + 16), N = (int64_t)ld64(blob + 24);
   const int64_t next = (int64_t)ld64(blob + kAccNextRow);
   if ((int)ld32(blob + 8) != WHFF_FMT_FIXED_ACC || !shape_ok(M, N) || ld < N || row0 != next || rows <= 0 ||
-      row0 + rows > M || (rows % 4 != 0 && row0 + rows != M)) {
+      rows > M - row0 || (rows % 4 != 0 && rows != M - row0)) {
     set_error("whff_compress_accuracy_band: not a blob begun by whff_accuracy_begin, ld < N, or the band does not "
               "start at the next row / is not a multiple of 4 rows before the last");
     return WHFF_EINVAL;

@@ -707,7 +707,7 @@ extern "C" int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, dou
 extern "C" int whff_step_rows(whff_handle* h, int64_t row0, int64_t nrows, const float* x, int R, int64_t ldx,
                               double* y, int64_t ldy, double* state, double decay, void* stream) {
   if (!h || !x || !y || R <= 0 || R > h->max_rhs || ldx < h->info.N || row0 < 0 || nrows <= 0 ||
-      row0 + nrows > h->info.M || ldy < nrows) {
+      nrows > h->info.M - row0 || ldy < nrows) {
     set_error("whff_step_rows: null pointer, R out of [1, max_rhs], rows outside the matrix, or ld too small");
     return WHFF_EINVAL;
   }
@@ -880,7 +880,7 @@ extern "C" int whff_graph_create_host(whff_handle* h, const float* x_host, int R
 
 namespace {
 int check_slit(const whff_handle* h, int64_t row0, int64_t nrows, const char* who) {
-  if (row0 < 0 || nrows <= 0 || row0 + nrows > h->info.M || row0 % row_align(h->info.fmt)) {
+  if (row0 < 0 || nrows <= 0 || nrows > h->info.M - row0 || row0 % row_align(h->info.fmt)) {
     set_error(std::string(who) + ": rows outside the matrix, or row0 not a multiple of 4 (block formats) / 128 "
                                  "(scaled formats)");
     return WHFF_EINVAL;
