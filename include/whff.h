@@ -354,7 +354,7 @@ int whff_get_crossover(const whff_handle* h, int* min_rhs);
 int whff_set_crossover(whff_handle* h, int min_rhs);
 
 /* Many resident matrices in one step (uneven sizes, R[i] right-hand sides
- * each): one persistent launch per right-hand-side class (8, 4, 2, 1) whose
+ * each, 1 <= R[i] <= the max_rhs of handle i, else WHFF_EINVAL): one persistent launch per right-hand-side class (8, 4, 2, 1) whose
  * warps split the concatenated block order of all matrices into equal
  * ranges; R[i] is taken in column groups of 8, then one group of 4, 2, 1;
  * a matrix with R[i] at or above its handle's crossover (tensor-core passes

@@ -1359,14 +1359,15 @@ extern "C" int whff_batch_create(whff_handle* const* hs, const int* R, int count
   b->lift = hs[0]->info.fmt == WHFF_FMT_FIXED_LIFT;
   b->scaled_fmt = scaled(hs[0]) ? hs[0]->info.fmt : 0;
   for (int i = 0; i < count; ++i) {
-    const bool ok = hs[i] && R[i] >= 1 &&
+    // R[i] <= max_rhs: a matrix stepped by its own passes uses its handle's workspaces
+    const bool ok = hs[i] && R[i] >= 1 && R[i] <= hs[i]->max_rhs &&
                     (b->scaled_fmt ? hs[i]->info.fmt == b->scaled_fmt
                                    : is_wz2(hs[i]) && hs[i]->info.rate == b->rate &&
                                          (hs[i]->info.fmt == WHFF_FMT_FIXED_LIFT) == b->lift);
     if (!ok) {
       whff_batch_destroy(b);
       set_error("whff_batch_create: all matrices must be resident WZ2 of one format and rate, or of one scaled "
-                "format; R >= 1");
+                "format; 1 <= R[i] <= the handle's max_rhs");
       return WHFF_EINVAL;
     }
   }

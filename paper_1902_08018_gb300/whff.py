@@ -590,7 +590,8 @@ class Server:
 
 
 class Batch:
-    """Many resident WZ2 matrices stepped together (whff_batch_create / whff_batch_step)."""
+    """Many resident matrices (WZ2 of one format and rate, or one scaled format) stepped together
+    (whff_batch_create / whff_batch_step); R[i] at most handle i's max_rhs."""
 
     def __init__(self, handles, R):
         self.handles = list(handles)

@@ -106,7 +106,7 @@ def test_scaled_batch_matches_oracle(env, orc, fmt):
         h.destroy()
 
 
-def test_batch_rejects_mixed_formats(env):
+def test_batch_rejects_mixed_formats_and_wide_requests(env):
     W, torch = env
     h1 = W.whff_create(W.whff_compress(_matrix(64, 64, 1), 5, 12))
     h2 = W.whff_create(W.whff_compress(_matrix(64, 64, 2), 5, 16))
@@ -117,7 +117,10 @@ def test_batch_rejects_mixed_formats(env):
     for pair in ([h3, h4], [h3, h1], [h1, h3]):
         with pytest.raises(W.WhffError):
             W.Batch(pair, [1, 1])
-    for h in (h1, h2, h3, h4):
+    h5 = W.whff_create(W.whff_compress(_matrix(64, 64, 5), 2, 0), max_rhs=4)  # BF16, workspaces for 4
+    with pytest.raises(W.WhffError):
+        W.Batch([h5], [5])  # more columns than the handle's max_rhs
+    for h in (h1, h2, h3, h4, h5):
         h.destroy()
 
 
