@@ -176,6 +176,16 @@ def test_fixed_accuracy_encoder_hand_derived_matrix(W):
         assert got.tobytes() == want
 
 
+def test_scaled_encoder_hand_derived_streams(W):
+    """The library's scaled-format streams of the hand-derived matrices in
+    tests/golden/scaled_blobs.txt (row padding to 16 elements, tile scales after the
+    payload, the FP32 scale's rounding carried into the quotients)."""
+    from test_oracle_gemv_scaled import golden_scaled
+
+    for name, fmt, A, body in golden_scaled():
+        assert W.whff_compress(A, fmt, 0).tobytes()[64:] == body, name
+
+
 def test_fixed_accuracy_rejections(W):
     with pytest.raises(W.WhffError):
         W.whff_compress_accuracy(np.ones((4, 4)), -1.0)

@@ -1,7 +1,8 @@
 """Pins of the oracle's GEMV (Sec. 4.4, dot-product equation and the
 sequential mixed-precision listing), its state update (stand-in for the
 thermal update of Sec. 2.1) and its scaled storage formats, against exact
-rational arithmetic, closed forms and numpy / torch's own conversions."""
+rational arithmetic, closed forms, numpy / torch's own conversions and hand-derived
+streams (tests/golden/scaled_blobs.txt)."""
 import math
 from fractions import Fraction
 
@@ -196,3 +197,54 @@ def test_gemv_mp_follows_the_papers_rounding(orc):
         for v in p:
             s += float(v)
         assert y[i] == np.float32(s)
+
+
+# ----------------------------------------------- hand-derived scaled streams
+def _runs(field, conv):
+    """Values of a fixture field: whitespace-separated, v*k for k copies."""
+    out = []
+    for t in field.split():
+        v, _, k = t.partition("*")
+        out.extend([conv(v)] * (int(k) if k else 1))
+    return out
+
+
+def golden_scaled():
+    """Records of tests/golden/scaled_blobs.txt as (name, fmt, A, expected stream bytes).
+    The stream is assembled here from the layout rule the header documents: M rows of
+    roundup(N, 16) little-endian elements, the padding zero, then the FP32 tile scales."""
+    import os
+    import struct
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "scaled_blobs.txt")
+    recs = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        fmt, name, M, N, rows, scales, qrows = [f.strip() for f in line.split("|")]
+        fmt, M, N = int(fmt), int(M), int(N)
+        A = np.array([_runs(r, float) for r in rows.split(";")])
+        assert A.shape == (M, N), name
+        eb = {2: 2, 3: 2, 4: 1, 7: 4}[fmt]
+        ld = -(-N // 16) * 16
+        packer = {1: "<B", 2: "<H", 4: "<I"}[eb]
+        body = b""
+        for r in qrows.split(";"):
+            q = _runs(r, lambda v: int(v, 16))
+            assert len(q) == N, name
+            body += b"".join(struct.pack(packer, v) for v in q) + bytes((ld - N) * eb)
+        body += b"".join(struct.pack("<I", v) for v in _runs(scales, lambda v: int(v, 16)))
+        recs.append((name, fmt, A, body))
+    return recs
+
+
+@pytest.mark.parametrize("rec", golden_scaled(), ids=lambda r: r[0])
+def test_scaled_hand_derived_streams(orc, rec):
+    import struct
+
+    name, fmt, A, body = rec
+    blob = orc.encode(A, fmt)
+    assert blob[64:] == body, name
+    magic, ver, f, rate, M, N, sbytes = struct.unpack("<4sIIIqqQ", blob[:40])
+    assert (magic, ver, f, rate, M, N, sbytes) == (b"WZ1\0", 1, fmt, 8 * {2: 2, 3: 2, 4: 1, 7: 4}[fmt],
+                                                   A.shape[0], A.shape[1], len(body))
