@@ -12,21 +12,25 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "wz2_blocks.txt")
 
 
 def _golden():
+    """(name, rate, lift, the 16 values, expected leading words): one value fills the
+    block, four are every row of it."""
     rows = []
     for line in open(GOLDEN):
         if line.startswith("#") or not line.strip():
             continue
-        name, rate, lift, val, word = [f.strip() for f in line.split("|")]
-        rows.append((name, int(rate), int(lift), float(val), int(word, 16)))
+        name, rate, lift, val, words = [f.strip() for f in line.split("|")]
+        v = [float(t) for t in val.split()]
+        block = np.full(16, v[0]) if len(v) == 1 else np.tile(np.array(v), 4)
+        rows.append((name, int(rate), int(lift), block, [int(t, 16) for t in words.split()]))
     return rows
 
 
 @pytest.mark.parametrize("row", _golden(), ids=lambda r: r[0])
 def test_wz2_hand_derived_streams(orc, row):
-    name, rate, lift, val, word = row
-    w = orc.wz2_encode_block(np.full(16, val), rate, lift)
-    assert int(w[0]) == word
-    assert (orc.wz2_decode_block(w, rate, lift) == val).all()
+    name, rate, lift, block, words = row
+    w = orc.wz2_encode_block(block, rate, lift)
+    assert [int(x) for x in w[: len(words)]] == words
+    assert (orc.wz2_decode_block(w, rate, lift).reshape(16) == block).all()
 
 
 def _emax(a):
