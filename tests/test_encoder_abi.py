@@ -176,6 +176,23 @@ def test_fixed_accuracy_encoder_hand_derived_matrix(W):
         assert got.tobytes() == want
 
 
+def test_block_encoders_hand_derived_words(W):
+    """The library's WZ1 and WZ2 streams of the hand-derived 4 x 4 blocks in
+    tests/golden/wz1_blocks.txt and wz2_blocks.txt (a one-block matrix's stream is
+    the block's words)."""
+    from test_oracle_wz1 import _golden as wz1_golden
+    from test_oracle_wz2 import _golden as wz2_golden
+
+    for name, rate, block, words, _ in wz1_golden():
+        got = np.frombuffer(W.whff_compress(block.astype(np.float64).reshape(4, 4), W.FMT_ZFP, rate).tobytes()[64:],
+                            dtype=np.uint64)
+        assert [int(x) for x in got[: len(words)]] == words and not got[len(words):].any(), name
+    for name, rate, lift, block, words in wz2_golden():
+        fmt = W.FMT_FIXED_LIFT if lift else W.FMT_FIXED_BFP
+        got = np.frombuffer(W.whff_compress(block.reshape(4, 4), fmt, rate).tobytes()[64:], dtype=np.uint64)
+        assert [int(x) for x in got[: len(words)]] == words, name
+
+
 def test_scaled_encoder_hand_derived_streams(W):
     """The library's scaled-format streams of the hand-derived matrices in
     tests/golden/scaled_blobs.txt (row padding to 16 elements, tile scales after the

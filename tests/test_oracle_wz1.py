@@ -89,24 +89,33 @@ def test_sequency_order(orc):
 
 
 # --------------------------------------------------------------- the coder
+def _block(field):
+    """One value fills the block; four are every row of it."""
+    v = [float(t) for t in field.split()]
+    return np.full(16, v[0], dtype=np.float32) if len(v) == 1 else np.tile(np.array(v, dtype=np.float32), 4)
+
+
 def _golden():
+    """(name, rate, block, leading words, decoded block)."""
     rows = []
     for line in open(GOLDEN):
         if line.startswith("#") or not line.strip():
             continue
-        name, rate, val, word = [f.strip() for f in line.split("|")]
-        rows.append((name, int(rate), float(val), int(word, 16)))
+        f = [t.strip() for t in line.split("|")]
+        name, rate, block, words = f[0], int(f[1]), _block(f[2]), [int(t, 16) for t in f[3].split()]
+        dec = _block(f[4]) if len(f) > 4 else block
+        rows.append((name, rate, block, words, dec))
     return rows
 
 
 @pytest.mark.parametrize("row", _golden(), ids=lambda r: r[0])
 def test_hand_derived_streams(orc, row):
-    name, rate, val, word = row
-    w = orc.encode_block(np.full(16, val, dtype=np.float32), rate)
-    assert int(w[0]) == word
-    assert not w[1:].any()
+    name, rate, block, words, dec = row
+    w = orc.encode_block(block, rate)
+    assert [int(x) for x in w[: len(words)]] == words
+    assert not w[len(words):].any()
     q, emax, nz, vals = orc.decode_block(w, rate)
-    assert (vals == val).all()
+    assert (vals.reshape(16) == dec.astype(np.float64)).all()
 
 
 def _bfp_truncate(a: np.ndarray) -> np.ndarray:
