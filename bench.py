@@ -28,6 +28,7 @@ import argparse
 import ctypes
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -200,6 +201,25 @@ def max_over_ranks(x: float, world: int, device) -> float:
 def whole_job_gbs(bytes_per_step_per_rank: float, ms_per_step: float, world: int) -> float:
     """Replicas: every rank streams its own matrix each step; GB/s of all ranks over the slowest time."""
     return bytes_per_step_per_rank * world / (ms_per_step * 1e-3) / 1e9
+
+
+def psnr_db(nrmse: float) -> float:
+    """PSNR of Table 2: 20 log10(range / (2 RMSE)) = -20 log10(2 NRMSE), NRMSE = RMSE / range."""
+    return float("inf") if nrmse == 0 else -20.0 * math.log10(2.0 * nrmse)
+
+
+def table2_metrics(A: np.ndarray, Ahat: np.ndarray, stored_bytes: int, values: int) -> dict:
+    """The columns of Table 2 for a decoded matrix (or a sample of its rows) against the
+    matrix it encodes: bits per value and Rate = 32 / bits per value (the FP32 matrix's
+    size over the stored size), RMSE, NRMSE = RMSE / (max - min), the largest pointwise
+    error and PSNR."""
+    d = Ahat.astype(np.float64) - A.astype(np.float64)
+    rmse = float(np.sqrt(np.mean(d * d)))
+    span = float(A.max() - A.min())
+    nrmse = rmse / span if span > 0 else 0.0
+    bpv = 8.0 * stored_bytes / values
+    return {"bits_per_value": round(bpv, 3), "rate": round(32.0 / bpv, 2), "rmse": rmse, "nrmse": nrmse,
+            "max_pointwise_error": float(np.abs(d).max()), "psnr_db": round(psnr_db(nrmse), 2)}
 
 
 # ----------------------------------------------------------------- workload
@@ -1135,7 +1155,9 @@ def run_precision(args, rank, world, local_rank):
     """Every storage format of the precision layer on the control-loop matrix, at one
     right-hand side (the heat load of step 0) and at 32 (the heat loads of steps 0..31):
     step time, GB/s of stored bytes, and the relative L2 error of y against FP64 GEMV on
-    the uncompressed matrix (64 sampled rows, the worst of the 32 columns)."""
+    the uncompressed matrix (64 sampled rows, the worst of the 32 columns); and Table 2's
+    columns (bits per value, rate, RMSE, NRMSE, largest pointwise error, PSNR) of the
+    decoded sample rows against the matrix rounded to FP32."""
     import torch
 
     import paper_1902_08018_gb300 as W
@@ -1164,6 +1186,12 @@ def run_precision(args, rank, world, local_rank):
             h = W.whff_create(blobs[spec], max_rhs=32)
             sb = blobs[spec].size - 64
             entry = {"bytes": int(sb)}
+            # Table 2's columns: the decoded sample rows against the matrix rounded to FP32
+            D = torch.empty((order, order), dtype=torch.float64, device=dev)
+            h.decompress(D, stream)
+            Ahat = D[torch.from_numpy(sample_rows).to(dev)].cpu().numpy()
+            del D
+            entry["table2"] = table2_metrics(sampled.astype(np.float32), Ahat, sb, order * order)
             for R, reps in ((1, max(10, args.steps)), (32, max(5, args.steps // 10))):
                 Y = torch.zeros((R, order), dtype=torch.float64, device=dev)
                 for _ in range(3):
