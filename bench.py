@@ -145,9 +145,11 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join("/tmp", f"whff_clocks_{os.getpid()}.csv")
+        self.path = os.path.join("/tmp", f"whff_clocks_{os.getpid()}_{id(self)}.csv")
+        self._summary = None
 
     def __enter__(self):
+        self.fh = None
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -155,6 +157,12 @@ class ClockSampler:
                  "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            if self.fh:
+                self.fh.close()
+                try:
+                    os.remove(self.path)
+                except OSError:
+                    pass
         return self
 
     def __exit__(self, *a):
@@ -167,14 +175,25 @@ class ClockSampler:
             self.fh.close()
 
     def summary(self):
+        """Median SM clock, the largest maximum clock, median power and the throttle
+        reasons seen (read once; the sample file is removed afterwards)."""
+        if self._summary is None:
+            self._summary = self._read()
+        return self._summary
+
+    def _read(self):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
-        with open(self.path) as f:
-            for line in f:
-                parts = [s.strip() for s in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [s.strip() for s in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.remove(self.path)
+        except OSError:
+            pass
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
