@@ -129,8 +129,10 @@ int whff_compress_accuracy(const double* A, int64_t M, int64_t N, int64_t lda, d
 /* Band interface for matrices too large to hold in FP64 at once.
  * whff_blob_init writes the header fields of an empty blob; whff_compress_band
  * encodes rows [row0, row0+nrows) given as a band (row-major, lda) -- row0 and
- * nrows must be multiples of 4 (WZ1) or 128 (scaled formats) except for the
- * last band; whff_blob_seal computes both CRCs once every band is in. */
+ * nrows must be multiples of 4 (block formats: WZ1, WZ2) or 128 (scaled
+ * formats) except for the last band; whff_blob_seal computes both CRCs once
+ * every band is in.  Errors: WHFF_EINVAL (format, shape, capacity, band
+ * bounds), WHFF_ERANGE, WHFF_ENONFINITE. */
 int whff_blob_init(void* blob, size_t cap, int fmt, int rate, int64_t M, int64_t N);
 int whff_compress_band(void* blob, size_t cap, const double* band, int64_t row0, int64_t nrows, int64_t lda,
                        int nthreads);
@@ -231,7 +233,7 @@ int whff_set_slice_rows(whff_handle* h, int64_t rows);
  * whff_step into handle-owned device buffers, copies y (M x R, ldy) back, all
  * asynchronously on the stream (pinned host memory makes the copies truly
  * asynchronous).  state is a DEVICE pointer or NULL.  The caller synchronizes
- * the stream before reading y. */
+ * the stream before reading y.  Errors: as whff_step. */
 int whff_step_host(whff_handle* h, const float* x_host, int R, int64_t ldx, double* y_host, int64_t ldy,
                    double* state, double decay, void* stream);
 
