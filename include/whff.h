@@ -132,7 +132,8 @@ int whff_compress_accuracy(const double* A, int64_t M, int64_t N, int64_t lda, d
  * nrows must be multiples of 4 (block formats: WZ1, WZ2) or 128 (scaled
  * formats) except for the last band; whff_blob_seal computes both CRCs once
  * every band is in.  Errors: WHFF_EINVAL (format, shape, capacity, band
- * bounds), WHFF_ERANGE, WHFF_ENONFINITE. */
+ * bounds), WHFF_EFORMAT (a blob whff_blob_init did not write), WHFF_ERANGE,
+ * WHFF_ENONFINITE. */
 int whff_blob_init(void* blob, size_t cap, int fmt, int rate, int64_t M, int64_t N);
 int whff_compress_band(void* blob, size_t cap, const double* band, int64_t row0, int64_t nrows, int64_t lda,
                        int nthreads);

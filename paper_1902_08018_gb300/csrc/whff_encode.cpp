@@ -619,7 +619,7 @@ extern "C" int whff_compress_band(void* blob, size_t cap, const double* band, in
   }
   const int align = is_blocked(b.fmt) ? 4 : kScaleTile;
   if (!band || row0 < 0 || nrows <= 0 || nrows > b.M - row0 || lda < b.N || row0 % align ||
-      (nrows % align && row0 + nrows != b.M)) {
+      (nrows % align && nrows != b.M - row0)) {
     set_error("whff_compress_band: band must start on a block/tile row and cover whole blocks");
     return WHFF_EINVAL;
   }
