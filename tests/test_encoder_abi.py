@@ -66,6 +66,53 @@ def test_encoder_byte_identical_to_oracle(W, orc, fmt, rate):
         assert (lib == ref).all()
 
 
+def test_encoder_byte_identical_on_a_seeded_sweep_of_shapes(W, orc):
+    """60 small ragged shapes (1..70 rows and columns) in every format and a rate drawn
+    for it, with smooth, wild-range, sparse and integer-valued matrices: the library's
+    blob equals the oracle's byte for byte, for 1 and 3 host threads."""
+    rng = np.random.default_rng(2024)
+    choices = [(1, r) for r in (4, 8, 12, 16, 20, 24, 32, 48, 64)] + [(5, r) for r in (8, 12, 16, 20, 24)] + \
+              [(6, r) for r in (8, 12, 16, 20, 24)] + [(2, 0), (3, 0), (4, 0), (7, 0)]
+    for k in range(60):
+        M, N = (int(v) for v in rng.integers(1, 71, size=2))
+        fmt, rate = choices[int(rng.integers(len(choices)))]
+        kind = k % 4
+        if kind == 0:
+            i, j = np.mgrid[0:M, 0:N]
+            A = np.exp(-((i - M / 2) ** 2 + (j - N / 3) ** 2) / (0.1 * (M * M + N * N) + 1.0))
+        elif kind == 1:
+            A = rng.standard_normal((M, N)) * np.exp(rng.uniform(-40, 40, size=(M, N)))
+        elif kind == 2:
+            A = np.where(rng.random((M, N)) < 0.8, 0.0, rng.standard_normal((M, N)))
+        else:
+            A = rng.integers(-1000, 1000, size=(M, N)).astype(np.float64)
+        ref = np.frombuffer(orc.encode(A, fmt, rate or 16), dtype=np.uint8)
+        for nt in (1, 3):
+            got = W.whff_compress(A, fmt, rate or 16, nthreads=nt)
+            assert got.size == ref.size and (got == ref).all(), (k, M, N, fmt, rate, nt)
+
+
+def test_fixed_accuracy_encoder_byte_identical_on_a_seeded_sweep(W, orc):
+    """30 small ragged shapes (up to 150 columns: several runs per band) at tolerances
+    from 0 to 1, smooth, wild-range and sparse matrices: the library's fixed-accuracy
+    blob equals the oracle's byte for byte."""
+    rng = np.random.default_rng(2025)
+    for k in range(30):
+        M, N = int(rng.integers(1, 40)), int(rng.integers(1, 151))
+        tol = [0.0, 1e-12, 1e-7, 1e-3, 1.0][k % 5]
+        kind = k % 3
+        if kind == 0:
+            i, j = np.mgrid[0:M, 0:N]
+            A = np.cos(0.05 * i) * np.exp(-0.01 * j) + 1e-3 * rng.standard_normal((M, N))
+        elif kind == 1:
+            A = rng.standard_normal((M, N)) * np.exp(rng.uniform(-30, 30, size=(M, N)))
+        else:
+            A = np.where(rng.random((M, N)) < 0.9, 0.0, rng.standard_normal((M, N)))
+        want = orc.wz3_encode(A, tol)
+        got = W.whff_compress_accuracy(A, tol, nthreads=2)
+        assert got.tobytes() == want, (k, M, N, tol)
+
+
 def test_band_encoding_and_thread_count_invariance(W, orc):
     import workloads
 
