@@ -790,7 +790,12 @@ extern "C" int whff_accuracy_seal(void* out, size_t out_cap, size_t* out_len) {
     return WHFF_EINVAL;
   }
   const int64_t BM = ceil_div(M, 4), RB = wz3_runs_per_band(N);
-  const uint64_t sbytes = 8 + 8 * (uint64_t)(BM * RB) + ld64(blob + kAccArea);
+  const uint64_t area = ld64(blob + kAccArea);
+  const uint64_t sbytes = 8 + 8 * (uint64_t)(BM * RB) + area;
+  if (area > (uint64_t)whff_accuracy_max_size(M, N) || sbytes > out_cap - (size_t)kHeaderBytes) {
+    set_error("whff_accuracy_seal: the blob's area counter exceeds its capacity (damaged header)");
+    return WHFF_EINVAL;
+  }
   write_header(blob, WHFF_FMT_FIXED_ACC, 0, M, N, sbytes, crc32(blob + kHeaderBytes, sbytes));  // clears 48..63
   if (out_len) *out_len = (size_t)(kHeaderBytes + sbytes);
   return WHFF_OK;

@@ -304,3 +304,10 @@ def test_fixed_accuracy_bands_refusals(W):
     assert out[: used.value].tobytes() == W.whff_compress_accuracy(A, 1e-3).tobytes()
     small = np.zeros(70, dtype=np.uint8)
     assert L.whff_accuracy_begin(small.ctypes.data, small.size, M, N, 1e-3) != 0  # no room for the index
+    # a damaged area counter of an unsealed blob: the seal refuses it instead of reading past cap
+    assert L.whff_accuracy_begin(out.ctypes.data, cap, M, N, 1e-3) == 0
+    band = np.ascontiguousarray(A)
+    assert L.whff_compress_accuracy_band(out.ctypes.data, cap, band.ctypes.data, 0, M, N, 1) == 0
+    for area in (cap, 1 << 62, (1 << 64) - 8):
+        out[56:64] = np.frombuffer(np.uint64(area).tobytes(), dtype=np.uint8)
+        assert L.whff_accuracy_seal(out.ctypes.data, cap, ctypes.byref(used)) != 0, area
