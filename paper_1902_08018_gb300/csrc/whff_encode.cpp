@@ -740,6 +740,10 @@ extern "C" int whff_compress_accuracy_band(void* out, size_t out_cap, const doub
   // offsets of the runs, after the area written so far
   std::vector<uint64_t> off((size_t)(nI * RB));
   uint64_t area = ld64(blob + kAccArea);
+  if (area > (uint64_t)whff_accuracy_max_size(M, N)) {
+    set_error("whff_compress_accuracy_band: the blob's area counter exceeds its capacity (damaged header)");
+    return WHFF_EINVAL;
+  }
   for (int64_t i = 0; i < nI; ++i)
     for (int64_t r = 0; r < RB; ++r) {
       off[(size_t)(i * RB + r)] = area;

@@ -311,3 +311,9 @@ def test_fixed_accuracy_bands_refusals(W):
     for area in (cap, 1 << 62, (1 << 64) - 8):
         out[56:64] = np.frombuffer(np.uint64(area).tobytes(), dtype=np.uint8)
         assert L.whff_accuracy_seal(out.ctypes.data, cap, ctypes.byref(used)) != 0, area
+    # and a band appended to such a blob is refused before anything is written
+    assert L.whff_accuracy_begin(out.ctypes.data, cap, M, N, 1e-3) == 0
+    out[56:64] = np.frombuffer(np.uint64((1 << 64) - 8).tobytes(), dtype=np.uint8)
+    before = out.copy()
+    assert L.whff_compress_accuracy_band(out.ctypes.data, cap, band.ctypes.data, 0, M, N, 1) != 0
+    assert (out == before).all()
