@@ -161,7 +161,10 @@ int whff_accuracy_seal(void* blob, size_t cap, size_t* len);
  * stream once to device memory on the current device, allocate the split-K
  * workspace for up to max_rhs right-hand sides (0 -> 32) and pick the launch
  * shape.  The handle owns every device allocation it makes; the host blob may
- * be freed afterwards.  Errors: WHFF_EFORMAT, WHFF_ENOMEM, WHFF_ECUDA. */
+ * be freed afterwards.  The calls that launch work on a handle (steps, graphs,
+ * decompress, tune, batches) refuse with WHFF_EINVAL while a device other
+ * than the one current at its creation is current.  Errors: WHFF_EFORMAT,
+ * WHFF_ENOMEM, WHFF_ECUDA. */
 int whff_create(const void* blob, size_t len, int max_rhs, void* stream, whff_handle** h);
 
 /* As whff_create, with flags.  WHFF_CREATE_HOST_RESIDENT keeps the compressed

@@ -87,6 +87,22 @@ constexpr size_t kColexpBytes = 256;  // 32 column exponents of an FP16 tensor-c
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// A handle's kernels run on the device it was created on: a call made while
+// another device is current would launch there against this device's memory.
+int check_device(const whff_handle* h, const char* fn) {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string(fn) + ": no current CUDA device");
+    return WHFF_ECUDA;
+  }
+  if (d != h->device) {
+    set_error(std::string(fn) + ": the current CUDA device is not the one the matrix was made resident on");
+    return WHFF_EINVAL;
+  }
+  return WHFF_OK;
+}
+
 // WZ1: split-K so that the grid holds enough warps for the GPU: each warp owns
 // one 4-row band; when bands are few (wide matrices), split the columns.
 // WZ2, WZ3 and the scaled formats: split the band-major unit order into one
@@ -690,6 +706,7 @@ extern "C" int whff_step(whff_handle* h, const float* x, int R, int64_t ldx, dou
     set_error("whff_step: null pointer, R out of [1, max_rhs], or leading dimension too small");
     return WHFF_EINVAL;
   }
+  if (const int de = check_device(h, "whff_step")) return de;
   const cudaStream_t st = as_stream(stream);
   const int64_t M = h->info.M, slice = h->slice_rows;
   if (slice <= 0 || slice >= M) return step_passes(h, x, R, ldx, y, ldy, state, decay, st);
@@ -715,6 +732,7 @@ extern "C" int whff_step_rows(whff_handle* h, int64_t row0, int64_t nrows, const
     set_error("whff_step_rows: row0 must be a multiple of 4 (block formats) or 128 (scaled formats)");
     return WHFF_EINVAL;
   }
+  if (const int de = check_device(h, "whff_step_rows")) return de;
   return step_view(h, row0, nrows, x, R, ldx, y, ldy, state, decay, as_stream(stream));
 }
 
@@ -742,6 +760,7 @@ extern "C" int whff_step_host(whff_handle* h, const float* x_host, int R, int64_
     set_error("whff_step_host: null pointer, R out of [1, max_rhs], or leading dimension too small");
     return WHFF_EINVAL;
   }
+  if (const int de = check_device(h, "whff_step_host")) return de;
   const cudaStream_t st = as_stream(stream);
   const int64_t N = h->info.N, M = h->info.M;
   WHFF_CUDA_TRY(cudaMemcpy2DAsync(h->d_x, N * sizeof(float), x_host, ldx * sizeof(float), N * sizeof(float), R,
@@ -845,6 +864,7 @@ extern "C" int whff_graph_create_host(whff_handle* h, const float* x_host, int R
     set_error("whff_graph_create_host: invalid argument");
     return WHFF_EINVAL;
   }
+  if (const int de = check_device(h, "whff_graph_create_host")) return de;
   *out = nullptr;
   auto* g = new whff_graph;
   const int64_t N = h->info.N, M = h->info.M;
@@ -920,6 +940,7 @@ extern "C" int whff_graph_create_rows(whff_handle* h, int64_t row0, int64_t nrow
     set_error("whff_graph_create_rows: null argument, R out of [1, max_rhs], or leading dimension too small");
     return WHFF_EINVAL;
   }
+  if (const int de = check_device(h, "whff_graph_create_rows")) return de;
   *out = nullptr;
   int e = check_slit(h, row0, nrows, "whff_graph_create_rows");
   if (e) return e;
@@ -959,6 +980,7 @@ extern "C" int whff_graph_set_rows(whff_graph* g, whff_handle* h, int64_t row0) 
     return WHFF_EINVAL;
   }
   if (!h) h = g->h;
+  if (const int de = check_device(h, "whff_graph_set_rows")) return de;
   if (h != g->h && (h->info.fmt != g->h->info.fmt || h->info.rate != g->h->info.rate || h->info.M != g->h->info.M ||
                     h->info.N != g->h->info.N || h->max_rhs < g->R)) {
     set_error("whff_graph_set_rows: the new handle differs in format, rate, shape or max_rhs");
@@ -1000,6 +1022,7 @@ extern "C" int whff_decompress(whff_handle* h, double* out, int64_t ldo, void* s
     set_error("whff_decompress: null pointer or ldo < N");
     return WHFF_EINVAL;
   }
+  if (const int de = check_device(h, "whff_decompress")) return de;
   const cudaStream_t st = as_stream(stream);
   const auto& b = h->info;
   const int threads = 256;
@@ -1182,6 +1205,7 @@ extern "C" int whff_tune(whff_handle* h, int iters, void* stream, double* best_m
     set_error("whff_tune: WZ2 handles only, iters >= 1");
     return WHFF_EINVAL;
   }
+  if (const int de = check_device(h, "whff_tune")) return de;
   const cudaStream_t st = as_stream(stream);
   WHFF_CUDA_TRY(cudaMemsetAsync(h->d_x, 0, (size_t)h->info.N * 4, st));
   cudaEvent_t e0, e1;
@@ -1360,14 +1384,14 @@ extern "C" int whff_batch_create(whff_handle* const* hs, const int* R, int count
   b->scaled_fmt = scaled(hs[0]) ? hs[0]->info.fmt : 0;
   for (int i = 0; i < count; ++i) {
     // R[i] <= max_rhs: a matrix stepped by its own passes uses its handle's workspaces
-    const bool ok = hs[i] && R[i] >= 1 && R[i] <= hs[i]->max_rhs &&
+    const bool ok = hs[i] && R[i] >= 1 && R[i] <= hs[i]->max_rhs && hs[i]->device == hs[0]->device &&
                     (b->scaled_fmt ? hs[i]->info.fmt == b->scaled_fmt
                                    : is_wz2(hs[i]) && hs[i]->info.rate == b->rate &&
                                          (hs[i]->info.fmt == WHFF_FMT_FIXED_LIFT) == b->lift);
     if (!ok) {
       whff_batch_destroy(b);
       set_error("whff_batch_create: all matrices must be resident WZ2 of one format and rate, or of one scaled "
-                "format; 1 <= R[i] <= the handle's max_rhs");
+                "format on one device; 1 <= R[i] <= the handle's max_rhs");
       return WHFF_EINVAL;
     }
   }
@@ -1578,6 +1602,7 @@ extern "C" int whff_batch_step(whff_batch* b, const float* const* x, const int64
     set_error("whff_batch_step: bad argument");
     return WHFF_EINVAL;
   }
+  if (const int de = check_device(b->hs[0], "whff_batch_step")) return de;
   const cudaStream_t st = as_stream(stream);
   // the pinned tables are reused: wait until the previous step's copies ran
   WHFF_CUDA_TRY(cudaEventSynchronize(b->copied));
