@@ -334,7 +334,13 @@ int encode_block_wz2(const float* vals, int rate, bool lift, uint64_t* out) {
   for (int k = 0; k < 16; ++k) ord[k] = lift ? c[seq[k]] : c[k];
   const int W = wz2_width(rate);
   const int64_t lo = -((int64_t)1 << (W - 1)), hi = ((int64_t)1 << (W - 1)) - 1;
-  int K = 0;
+  // The smallest K that fits is at least bitlen(max |c|) - W: below it the
+  // largest coefficient rounds to a magnitude >= 2^W.  Start the search there.
+  uint64_t mag = 0;
+  for (int k = 0; k < 16; ++k) mag = std::max(mag, (uint64_t)(ord[k] < 0 ? -ord[k] : ord[k]));
+  int blen = 0;
+  while (blen < 64 && (mag >> blen) != 0) ++blen;
+  int K = std::min(std::max(0, blen - W), kWz2Kmax);
   int64_t v[16];
   for (;; ++K) {
     bool fits = true;
