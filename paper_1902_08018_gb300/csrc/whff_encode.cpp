@@ -412,9 +412,32 @@ int wz3_block(const float* vals, double tol, Wz3Block* out) {
     }
     if (fits) break;
   }
+  // A cheap necessary condition first.  The decoded block minus the FP32 input
+  // is D u - t, with u = 2^(emax-30), t the truncation remainder of the block
+  // floating point, D = (2G) (V 2^K - C) (2G)^T.  The column sums of 2G are
+  // (8, 0, 0, 0), so the mean of D over the block is 4 E00, E00 the DC
+  // coefficient's rounding error.  The largest error is at least the absolute
+  // mean, |mean(t) - 4 E00 u|: a shift for which that exceeds tol (with a
+  // margin far above the rounding of this sum) cannot be the answer.
+  double tsum = 0.0, tabs = 0.0;
+  const double grid = std::ldexp(1.0, emax - kWz2Prec);  // the block floating point's step
+  for (int i = 0; i < 16; ++i) {
+    const double a = (double)vals[i];
+    const double t = a - std::trunc(a / grid) * grid;  // exact: a and its truncation share the grid
+    tsum += t;
+    tabs += std::fabs(t);
+  }
+  const double u = std::ldexp(1.0, emax - 30), tmean = tsum / 16.0;
+  const int64_t c00 = ord[0];  // sequency slot 0: the DC coefficient
   int64_t v[16];
   int K = kWz2Kmax;
   for (;; --K) {
+    if (K != Kf) {
+      const int64_t e00 = shift_round_even(c00, K) * ((int64_t)1 << K) - c00;
+      const double m = 4.0 * (double)e00 * u;
+      const double lb = std::fabs(tmean - m) - 1e-12 * (tabs + std::fabs(m));
+      if (lb > tol) continue;
+    }
     for (int k = 0; k < 16; ++k) v[k] = shift_round_even(ord[k], K);
     int64_t T[16];
     for (int k = 0; k < 16; ++k) T[seq[k]] = v[k];
