@@ -113,6 +113,28 @@ def test_fixed_accuracy_encoder_byte_identical_on_a_seeded_sweep(W, orc):
         assert got.tobytes() == want, (k, M, N, tol)
 
 
+def test_fixed_accuracy_encoder_at_tolerances_equal_to_an_achieved_error(W, orc):
+    """Tolerances placed exactly on a shift's decoded error, and one ulp below it,
+    are where a shortcut in the shift search would first differ: the library's
+    one-block blobs equal the oracle's there."""
+    rng = np.random.default_rng(77)
+    for k in range(120):
+        kind = k % 3
+        if kind == 0:
+            a = (1.0 + 0.1 * rng.standard_normal((4, 4))) * 2.0 ** int(rng.integers(-20, 20))
+        elif kind == 1:
+            a = rng.standard_normal((4, 4))
+        else:
+            a = np.exp(-rng.random((4, 4)) * 3.0)
+        a32 = a.astype(np.float32)
+        words, Wr = orc.wz3_encode_run(a32.reshape(1, 4, 4), 10.0 ** float(rng.uniform(-9, -2)))
+        err = float(np.abs(orc.wz3_decode_block(words, Wr) - a32.astype(np.float64)).max())
+        for tol in (err, float(np.nextafter(err, 0.0))):
+            want = orc.wz3_encode(a32.astype(np.float64), tol)
+            got = W.whff_compress_accuracy(a32.astype(np.float64), tol)
+            assert got.tobytes() == want, (k, tol)
+
+
 def test_band_encoding_and_thread_count_invariance(W, orc):
     import workloads
 
