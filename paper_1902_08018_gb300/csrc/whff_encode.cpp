@@ -744,21 +744,46 @@ extern "C" int whff_compress_accuracy_band(void* out, size_t out_cap, const doub
   std::memcpy(&tol, &tol_bits, 8);
   const int64_t BM = ceil_div(M, 4), BN = ceil_div(N, 4), RB = wz3_runs_per_band(N);
   const int64_t I0 = row0 / 4, nI = ceil_div(rows, 4);
-  // pass 1: the width of every run of the band's block rows
+  // One pass over the band's block rows: each row's blocks are coded once, its
+  // runs' widths taken from them and its runs written, word-interleaved, into a
+  // buffer of the row's own; the rows are then placed after the area written so
+  // far, in band-major order.
   std::vector<uint8_t> width((size_t)(nI * RB));
+  std::vector<std::vector<uint8_t>> rowbuf((size_t)nI);
   std::atomic<int> err{WHFF_OK};
   parallel_for(nI, nthreads, [&](int64_t i) {
     float vals[16];
-    Wz3Block b;
+    std::vector<Wz3Block> blk((size_t)BN);
+    for (int64_t J = 0; J < BN; ++J) {
+      gather_band_block(band, row0, M, N, ld, I0 + i, J, vals);
+      const int e = wz3_block(vals, tol, &blk[(size_t)J]);
+      if (e != WHFF_OK) {
+        err.store(e);
+        return;
+      }
+    }
+    size_t bytes = 0;
     for (int64_t r = 0; r < RB; ++r) {
       int W = 0;
-      for (int64_t J = 32 * r; J < std::min(BN, 32 * r + 32); ++J) {
-        gather_band_block(band, row0, M, N, ld, I0 + i, J, vals);
-        const int e = wz3_block(vals, tol, &b);
-        if (e != WHFF_OK) err.store(e);
-        W = std::max(W, b.need);
-      }
+      const int64_t nb = std::min(BN, 32 * r + 32) - 32 * r;
+      for (int64_t J = 32 * r; J < 32 * r + nb; ++J) W = std::max(W, blk[(size_t)J].need);
       width[(size_t)(i * RB + r)] = (uint8_t)W;
+      bytes += (size_t)nb * (size_t)wz3_block_bytes(W);
+    }
+    std::vector<uint8_t>& out_row = rowbuf[(size_t)i];
+    out_row.assign(bytes, 0);
+    uint64_t w[8];
+    size_t at = 0;
+    for (int64_t r = 0; r < RB; ++r) {
+      const int W = width[(size_t)(i * RB + r)];
+      const int nw = wz3_block_bytes(W) / 8;
+      const int64_t nb = std::min(BN, 32 * r + 32) - 32 * r;
+      for (int64_t J = 32 * r; J < 32 * r + nb; ++J) {
+        wz3_put(blk[(size_t)J], W, w);
+        // word-interleaved run: word k of block j at byte 8 (k nb + j)
+        for (int k = 0; k < nw; ++k) st64(out_row.data() + at + 8 * (k * nb + (J - 32 * r)), w[k]);
+      }
+      at += (size_t)nb * (size_t)(8 * nw);
     }
   });
   if (err.load() != WHFF_OK) {
@@ -787,24 +812,9 @@ extern "C" int whff_compress_accuracy_band(void* out, size_t out_cap, const doub
   }
   for (int64_t k = 0; k < nI * RB; ++k)
     st64(index + 8 * ((I0 * RB) + k), off[(size_t)k] | ((uint64_t)width[(size_t)k] << 56));
-  // pass 2: every block at its run's width
   parallel_for(nI, nthreads, [&](int64_t i) {
-    float vals[16];
-    Wz3Block b;
-    uint64_t w[8];
-    for (int64_t r = 0; r < RB; ++r) {
-      const int W = width[(size_t)(i * RB + r)];
-      const int nw = wz3_block_bytes(W) / 8;
-      const int64_t nb = std::min(BN, 32 * r + 32) - 32 * r;
-      uint8_t* dst = blocks + off[(size_t)(i * RB + r)];
-      for (int64_t J = 32 * r; J < 32 * r + nb; ++J) {
-        gather_band_block(band, row0, M, N, ld, I0 + i, J, vals);
-        wz3_block(vals, tol, &b);
-        wz3_put(b, W, w);
-        // word-interleaved run: word k of block j at byte 8 (k nb + j)
-        for (int k = 0; k < nw; ++k) st64(dst + 8 * (k * nb + (J - 32 * r)), w[k]);
-      }
-    }
+    const std::vector<uint8_t>& row = rowbuf[(size_t)i];
+    if (!row.empty()) std::memcpy(blocks + off[(size_t)(i * RB)], row.data(), row.size());
   });
   st64(blob + kAccNextRow, (uint64_t)(row0 + rows));
   st64(blob + kAccArea, area);
