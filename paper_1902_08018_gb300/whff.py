@@ -562,7 +562,15 @@ class Server:
         n = len(model)
         model = np.ascontiguousarray(model, dtype=np.int32)
         arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
-        xs = [np.ascontiguousarray(v, dtype=np.float32) for v in xs]
+        xs = [np.ascontiguousarray(v, dtype=np.float32).reshape(-1) for v in xs]
+        if arr.shape != (n,) or len(xs) != n:
+            raise WhffError(-1, "model, arrival_s and xs need one entry per request")
+        for i in range(n):  # the server copies N floats from each x
+            m = int(model[i])
+            if not 0 <= m < len(self.models):
+                raise WhffError(-1, f"request {i}: unknown model {m}")
+            if xs[i].size < self.models[m].N:
+                raise WhffError(-1, f"request {i}: x has {xs[i].size} entries, model {m} needs {self.models[m].N}")
         xptr = (ctypes.c_void_p * n)(*[v.ctypes.data for v in xs])
         ys = None
         yptr = None

@@ -34,3 +34,4 @@ def test_clock_sampler_without_nvidia_smi_leaves_no_file(monkeypatch):
         pass
     assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
     assert not os.path.exists(c.path)
+

@@ -1,0 +1,24 @@
+"""Host-side argument checks of the Python binding that need no GPU: they run
+before any call into the library."""
+
+
+def test_server_run_checks_requests_before_the_c_call():
+    """The server binding refuses mismatched request arrays, unknown models and short x
+    vectors before the C call, which copies N floats from every x."""
+    import types
+
+    import numpy as np
+    import pytest
+
+    import paper_1902_08018_gb300 as W
+
+    srv = object.__new__(W.Server)  # no device: the checks run before any library call
+    srv._ptr = None
+    srv.models = [types.SimpleNamespace(M=8, N=16)]
+    x = np.zeros(16, dtype=np.float32)
+    with pytest.raises(W.WhffError):
+        srv.run([0, 0], [0.0], [x, x])  # one arrival for two requests
+    with pytest.raises(W.WhffError):
+        srv.run([1], [0.0], [x])  # no model 1
+    with pytest.raises(W.WhffError):
+        srv.run([0], [0.0], [np.zeros(15, dtype=np.float32)])  # 15 < N
