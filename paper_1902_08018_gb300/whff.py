@@ -385,6 +385,8 @@ def whff_step_host(h: Handle, x_host: np.ndarray, y_host: np.ndarray, state=None
     yh = y_host if y_host.ndim == 2 else y_host.reshape(1, -1)
     if xh.dtype != np.float32 or yh.dtype != np.float64 or xh.strides[1] != 4 or yh.strides[1] != 8:
         raise WhffError(-1, "x_host float32 and y_host float64 with contiguous rows expected")
+    if xh.shape[1] < h.N or yh.shape[1] < h.M or yh.shape[0] < xh.shape[0]:
+        raise WhffError(-1, f"x_host needs (R, {h.N}) and y_host (R, {h.M}) with the same R or more rows of y")
     sp = 0
     if state is not None:
         sp, _, _ = _vec_args(state, h.M, "state", torch.float64)
@@ -514,6 +516,8 @@ def whff_graph_create_host(h: Handle, x_host: np.ndarray, y_host: np.ndarray, st
     yh = y_host if y_host.ndim == 2 else y_host.reshape(1, -1)
     if xh.dtype != np.float32 or yh.dtype != np.float64 or xh.strides[1] != 4 or yh.strides[1] != 8:
         raise WhffError(-1, "x_host float32 and y_host float64 with contiguous rows expected")
+    if xh.shape[1] < h.N or yh.shape[1] < h.M or yh.shape[0] < xh.shape[0]:
+        raise WhffError(-1, f"x_host needs (R, {h.N}) and y_host (R, {h.M}) with the same R or more rows of y")
     sp = _vec_args(state, h.M, "state", torch.float64)[0] if state is not None else 0
     g = ctypes.c_void_p()
     _check(library().whff_graph_create_host(h.ptr, xh.ctypes.data, xh.shape[0], xh.strides[0] // 4, yh.ctypes.data,

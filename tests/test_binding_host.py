@@ -22,3 +22,36 @@ def test_server_run_checks_requests_before_the_c_call():
         srv.run([1], [0.0], [x])  # no model 1
     with pytest.raises(W.WhffError):
         srv.run([0], [0.0], [np.zeros(15, dtype=np.float32)])  # 15 < N
+
+
+def test_step_host_checks_shapes_before_the_c_call():
+    """whff_step_host copies R columns of N floats in and R columns of M doubles out:
+    y with fewer rows than x, or rows shorter than N / M, are refused first."""
+    import types
+
+    import numpy as np
+    import pytest
+
+    import paper_1902_08018_gb300 as W
+
+    h = types.SimpleNamespace(M=8, N=16, ptr=None)
+    x = np.zeros((4, 16), dtype=np.float32)
+    with pytest.raises(W.WhffError):
+        W.whff_step_host(h, x, np.zeros((1, 8)))  # one row of y for four columns
+    with pytest.raises(W.WhffError):
+        W.whff_step_host(h, x[:, :15], np.zeros((4, 8)))  # rows shorter than N
+    with pytest.raises(W.WhffError):
+        W.whff_step_host(h, x, np.zeros((4, 7)))  # rows shorter than M
+
+
+def test_host_graph_checks_shapes_before_the_c_call():
+    import types
+
+    import numpy as np
+    import pytest
+
+    import paper_1902_08018_gb300 as W
+
+    h = types.SimpleNamespace(M=8, N=16, ptr=None)
+    with pytest.raises(W.WhffError):
+        W.whff_graph_create_host(h, np.zeros((4, 16), dtype=np.float32), np.zeros((2, 8)))
