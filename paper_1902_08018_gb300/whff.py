@@ -619,6 +619,8 @@ class Batch:
         import torch
 
         n = len(self.handles)
+        if len(xs) != n or len(ys) != n or (states is not None and len(states) != n):
+            raise WhffError(-1, f"one x, y (and state) per matrix: {n} expected")
         xp, lx, yp, ly = [], [], [], []
         for i, h in enumerate(self.handles):
             p, R, ld = _vec_args(xs[i], h.N, "x", torch.float32)
@@ -627,8 +629,17 @@ class Batch:
                 raise WhffError(-1, f"matrix {i}: expected {self.R[i]} right-hand sides")
             xp.append(p), lx.append(ld), yp.append(q), ly.append(ldy)
         sp = None
-        if states is not None:
-            sp = (ctypes.c_void_p * n)(*[(s.data_ptr() if s is not None else None) for s in states])
+        if states is not None:  # each a CUDA float64 vector of M_i entries, or None
+            ptrs = []
+            for i, (h, st) in enumerate(zip(self.handles, states)):
+                if st is None:
+                    ptrs.append(None)
+                    continue
+                p, Rs, _ = _vec_args(st, h.M, f"state {i}", torch.float64)
+                if Rs != 1:
+                    raise WhffError(-1, f"state {i} must be a vector")
+                ptrs.append(p)
+            sp = (ctypes.c_void_p * n)(*ptrs)
         _check(library().whff_batch_step(self._ptr, (ctypes.c_void_p * n)(*xp), (ctypes.c_int64 * n)(*lx),
                                          (ctypes.c_void_p * n)(*yp), (ctypes.c_int64 * n)(*ly), sp, float(decay),
                                          _stream_ptr(stream)))

@@ -55,3 +55,22 @@ def test_host_graph_checks_shapes_before_the_c_call():
     h = types.SimpleNamespace(M=8, N=16, ptr=None)
     with pytest.raises(W.WhffError):
         W.whff_graph_create_host(h, np.zeros((4, 16), dtype=np.float32), np.zeros((2, 8)))
+
+
+def test_batch_step_checks_its_lists_before_the_c_call():
+    """Batch.step refuses lists whose lengths differ from the batch's before any library
+    call (the per-tensor checks need CUDA tensors and run on the GPU)."""
+    import types
+
+    import pytest
+
+    import paper_1902_08018_gb300 as W
+
+    b = object.__new__(W.Batch)
+    b._ptr = None
+    b.handles = [types.SimpleNamespace(M=8, N=16), types.SimpleNamespace(M=4, N=4)]
+    b.R = [1, 1]
+    with pytest.raises(W.WhffError):
+        b.step([None], [None, None])
+    with pytest.raises(W.WhffError):
+        b.step([None, None], [None, None], states=[None])
