@@ -238,7 +238,8 @@ def table2_metrics(A: np.ndarray, Ahat: np.ndarray, stored_bytes: int, values: i
     nrmse = rmse / span if span > 0 else 0.0
     bpv = 8.0 * stored_bytes / values
     return {"bits_per_value": round(bpv, 3), "rate": round(32.0 / bpv, 2), "rmse": rmse, "nrmse": nrmse,
-            "max_pointwise_error": float(np.abs(d).max()), "psnr_db": round(psnr_db(nrmse), 2)}
+            "max_pointwise_error": float(np.abs(d).max()),
+            "psnr_db": round(psnr_db(nrmse), 2) if nrmse > 0 else None}  # None: lossless (strict JSON has no inf)
 
 
 # ----------------------------------------------------------------- workload

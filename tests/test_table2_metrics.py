@@ -63,4 +63,5 @@ def test_table2_metrics_closed_forms():
     m = bench.table2_metrics(A, B, stored_bytes=A.size * 2, values=A.size)
     assert m["rmse"] == pytest.approx(0.5 / math.sqrt(A.size), rel=1e-12)
     assert m["max_pointwise_error"] == 0.5 and m["bits_per_value"] == 16.0 and m["rate"] == 2.0
-    assert bench.table2_metrics(A, A, 1, 1)["psnr_db"] == float("inf")
+    assert bench.table2_metrics(A, A, 1, 1)["psnr_db"] is None  # lossless: no finite PSNR
+    assert bench.psnr_db(0.0) == float("inf")
